@@ -1,0 +1,420 @@
+"""Pins for the FP64 CPU oracle: checks against what the paper and the
+mathematics fix, never against the oracle's own formulas.
+
+Each test names the mistake it would catch.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1411_7018_gb300 import problems as P
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(x) for x in line.split()])
+    return np.array(rows)
+
+
+# --------------------------------------------------------------------------
+# Point solve: the local cubic of Section 2 and its root rule
+# --------------------------------------------------------------------------
+
+def _printed_cubic(a, b, c, r, s, t, h, f):
+    """Coefficients (highest first) of P3(v) exactly as printed in Eq. (MA3Dcubic)."""
+    return [-8.0,
+            4.0 * (a + b + c),
+            2.0 * (r * r + s * s + t * t - a * b - a * c - b * c),
+            a * b * c - a * t * t - b * s * s - c * r * r + 2.0 * r * s * t - h ** 6 * f]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_point_update_is_smallest_real_root_of_printed_cubic(seed):
+    """Catches a dropped term, wrong sign or wrong 1/4 factor in the cubic, a
+    wrong shift v = v0 + h^2 z/2, and picking a root other than the smallest.
+    Reference: numpy's companion-matrix roots of the printed monomial P3."""
+    rng = np.random.default_rng(seed)
+    checked = 0
+    for _ in range(400):
+        a, b, c = rng.uniform(0.5, 3.0, 3)
+        r, s, t = rng.uniform(-0.6, 0.6, 3)
+        h = 1.0
+        f = rng.uniform(-0.5, 2.0) if seed % 2 else rng.uniform(0.01, 2.0)
+        coeffs = _printed_cubic(a, b, c, r, s, t, h, f)
+        roots = np.roots(coeffs)
+        real = np.sort(roots[np.abs(roots.imag) < 1e-9].real)
+        if real.size == 0:
+            continue
+        # skip near-multiple smallest roots, where numpy's roots lose accuracy
+        if real.size > 1 and real[1] - real[0] < 1e-3:
+            continue
+        v0 = rng.uniform(-1.0, 1.0)
+        v = O.point_update([a, b, c, r, s, t], v0, h, f)
+        assert abs(v - real[0]) <= 1e-9 * max(1.0, abs(real[0])), (coeffs, real, v)
+        checked += 1
+    assert checked > 200
+
+
+def test_point_update_on_fine_step_vs_extended_precision():
+    """At a small step h the printed monomial form cancels; compare with the
+    smallest real root computed by numpy's roots on the cubic in the shifted
+    variable w = v - v0 (exact algebra, coefficients formed in longdouble)."""
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        h = 1.0 / 64
+        v0 = rng.uniform(0.5, 2.0)
+        Hm = np.eye(3) + 0.2 * rng.uniform(-1, 1, (3, 3))
+        Hm = (Hm + Hm.T) / 2
+        a, b, c = 2 * v0 + h * h * Hm[0, 0], 2 * v0 + h * h * Hm[1, 1], 2 * v0 + h * h * Hm[2, 2]
+        r, s, t = h * h * Hm[0, 1], h * h * Hm[0, 2], h * h * Hm[1, 2]
+        f = rng.uniform(0.2, 2.0)
+        # det(Hm - z I) - f, z = 2 (v - v0) / h^2: characteristic polynomial of Hm
+        cp = np.poly(Hm)             # z^3 - T z^2 + M z - D
+        coeffs = [-cp[0], -cp[1], -cp[2], -cp[3] - f]
+        z = np.roots(coeffs)
+        zr = np.sort(z[np.abs(z.imag) < 1e-9].real)
+        v_ref = v0 + 0.5 * h * h * zr[0]
+        v = O.point_update([a, b, c, r, s, t], v0, h, f)
+        assert abs(v - v_ref) <= 1e-13 * abs(v_ref)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_smallest_root_theorem_2_2_bracket(seed):
+    """Theorem 2.2: for rhs > 0 the selected root lies in [l1 - rhs^(1/3), l1)
+    and det(H - zI) = rhs; eigenvalues agree with LAPACK."""
+    rng = np.random.default_rng(100 + seed)
+    for _ in range(300):
+        A = rng.normal(size=(3, 3))
+        H = A + A.T + rng.uniform(-2, 2) * np.eye(3)
+        rhs = float(np.exp(rng.uniform(-4, 3)))
+        lam = np.linalg.eigvalsh(H)
+        np.testing.assert_allclose(O.sym3_eigenvalues(H), lam, rtol=0, atol=1e-12 * np.abs(lam).max())
+        z = O.smallest_root(H, rhs)
+        assert lam[0] - rhs ** (1 / 3) - 1e-12 <= z < lam[0]
+        assert abs(np.linalg.det(H - z * np.eye(3)) - rhs) <= 1e-10 * max(rhs, np.abs(lam).max() ** 3)
+
+
+def test_single_unknown_grid_closed_form():
+    """3^3 grid (one unknown, Section 3's coarsest grid): one sweep gives the
+    smallest real root of the printed cubic for the boundary data."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        g = rng.uniform(0, 1, (3, 3, 3))
+        g[1, 1, 1] = 0.0
+        f = np.full((3, 3, 3), rng.uniform(0.1, 3))
+        h = 0.5
+        u = g.copy()
+        O.gs_sweep(u, f, h)
+        a = g[1, 1, 2] + g[1, 1, 0]
+        b = g[1, 2, 1] + g[1, 0, 1]
+        c = g[2, 1, 1] + g[0, 1, 1]
+        r = 0.25 * (g[1, 2, 2] + g[1, 0, 0] - g[1, 2, 0] - g[1, 0, 2])
+        s = 0.25 * (g[2, 1, 2] + g[0, 1, 0] - g[2, 1, 0] - g[0, 1, 2])
+        t = 0.25 * (g[2, 2, 1] + g[0, 0, 1] - g[0, 2, 1] - g[2, 0, 1])
+        roots = np.roots(_printed_cubic(a, b, c, r, s, t, h, f[1, 1, 1]))
+        real = np.sort(roots[np.abs(roots.imag) < 1e-9].real)
+        assert abs(u[1, 1, 1] - real[0]) <= 1e-9
+
+
+# --------------------------------------------------------------------------
+# Discrete operator: Eqs. (2.1)-(2.6) and the determinant of Section 1
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [9, 17])
+def test_discrete_hessian_exact_on_cubic_polynomials(n):
+    """Centred second differences are exact for cubic polynomials, so the
+    discrete Hessian must equal the analytic one.  Catches a wrong weight,
+    sign, neighbour or 1/4 factor in any of the six stencils."""
+    rng = np.random.default_rng(n)
+    x, y, z = P.grid_coords(n)
+    cf = rng.normal(size=20)
+    mons = [(i, j, k) for i in range(4) for j in range(4) for k in range(4) if i + j + k <= 3]
+    u = sum(c * x ** i * y ** j * z ** k for c, (i, j, k) in zip(cf, mons))
+
+    def d2(p, q):
+        out = 0.0
+        for c, (i, j, k) in zip(cf, mons):
+            e = [i, j, k]
+            coef = c
+            for v in (p, q):
+                coef = coef * e[v]
+                e[v] -= 1
+            if coef == 0 or min(e) < 0:
+                continue
+            out = out + coef * x ** e[0] * y ** e[1] * z ** e[2]
+        return out + 0.0 * x
+
+    H = O.discrete_hessian(np.ascontiguousarray(u), 1.0 / (n - 1))
+    exact = [d2(0, 0), d2(1, 1), d2(2, 2), d2(0, 1), d2(0, 2), d2(1, 2)]
+    for m in range(6):
+        np.testing.assert_allclose(H[m][1:-1, 1:-1, 1:-1], exact[m][1:-1, 1:-1, 1:-1], rtol=0, atol=1e-9)
+
+
+def test_discrete_ma_is_det_of_discrete_hessian():
+    """Section 1's explicit determinant (including the 2 uxy uyz uxz term)
+    against LAPACK's determinant of the (pinned) discrete Hessian."""
+    pr = P.make("cosine", 9, seed=5)
+    rng = np.random.default_rng(0)
+    u = pr.u + 1e-3 * rng.normal(size=pr.u.shape)
+    h = pr.h
+    Hs = O.discrete_hessian(u, h)
+    d = O.discrete_ma(u, h)
+    for (k, j, i) in [(1, 1, 1), (3, 4, 5), (7, 7, 7), (2, 6, 3)]:
+        M = np.array([[Hs[0, k, j, i], Hs[3, k, j, i], Hs[4, k, j, i]],
+                      [Hs[3, k, j, i], Hs[1, k, j, i], Hs[5, k, j, i]],
+                      [Hs[4, k, j, i], Hs[5, k, j, i], Hs[2, k, j, i]]])
+        assert abs(np.linalg.det(M) - d[k, j, i]) <= 1e-12 * abs(d[k, j, i])
+
+
+@pytest.mark.parametrize("n", [9, 17, 33])
+def test_quadratic_is_exact_and_a_fixed_point(n):
+    """u = |x|^2/2, f = 1: every grid value is a dyadic rational and the
+    centred scheme is exact, so the residual is exactly zero and a sweep
+    (Theorem 2.1) leaves u unchanged."""
+    pr = P.make("quadratic", n)
+    r = O.residual(pr.u, pr.f, pr.h)
+    assert np.all(r == 0.0)
+    u = pr.u.copy()
+    O.gs_sweep(u, pr.f, pr.h)
+    assert np.max(np.abs(u - pr.u)) <= 2 * np.spacing(pr.u.max())
+
+
+def test_norm_definitions():
+    n = 17
+    h = 1.0 / 16
+    v = np.zeros((n, n, n))
+    v[1:-1, 1:-1, 1:-1] = 3.0
+    v[0] = 100.0     # shell values are ignored
+    assert O.norm(v, h, O.NORM_MAX) == 3.0
+    np.testing.assert_allclose(O.norm(v, h, O.NORM_L2), 3.0 * np.sqrt(h ** 3 * 15 ** 3), rtol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Grid transfers (Section 3)
+# --------------------------------------------------------------------------
+
+def test_restriction_of_linear_functions():
+    """Both weightings sum to one and are symmetric, so they reproduce linear
+    functions on the coarse interior; injection picks the even points."""
+    n = 17
+    x, y, z = P.grid_coords(n)
+    v = np.ascontiguousarray(0.3 + 1.7 * x - 0.4 * y + 2.2 * z)
+    xc, yc, zc = P.grid_coords(9)
+    vc = 0.3 + 1.7 * xc - 0.4 * yc + 2.2 * zc
+    for kind in (O.HALF_WEIGHTING, O.FULL_WEIGHTING):
+        rc = O.restrict_residual(v, kind)
+        np.testing.assert_allclose(rc[1:-1, 1:-1, 1:-1], vc[1:-1, 1:-1, 1:-1], atol=1e-14)
+        assert np.all(rc[0] == 0) and np.all(rc[:, :, -1] == 0)
+        uc = O.restrict_solution(v, kind)
+        np.testing.assert_allclose(uc, vc, atol=1e-14)
+    np.testing.assert_array_equal(O.inject(v), v[::2, ::2, ::2])
+
+
+def test_half_weighting_stencil_weights():
+    """The printed half-weighting stencil: 6/12 at the centre, 1/12 on faces,
+    nothing on edges or corners."""
+    n = 9
+    for (dk, dj, di), w in [((0, 0, 0), 6 / 12), ((0, 0, 1), 1 / 12), ((1, 0, 0), 1 / 12),
+                            ((0, 1, 1), 0.0), ((1, 1, 1), 0.0)]:
+        v = np.zeros((n, n, n))
+        v[4 + dk, 4 + dj, 4 + di] = 1.0
+        assert O.restrict_residual(v, O.HALF_WEIGHTING)[2, 2, 2] == w
+
+
+def test_trilinear_prolongation_exact_and_full_weighting_is_its_adjoint():
+    """Trilinear interpolation reproduces trilinear functions; full weighting
+    equals (1/8) times the transpose of the prolongation (matrix check)."""
+    nc, nf = 5, 9
+    xc, yc, zc = P.grid_coords(nc)
+    xf, yf, zf = P.grid_coords(nf)
+    tri = lambda x, y, z: 1 + 2 * x - y + 0.5 * z + 3 * x * y - 2 * y * z + x * z + 4 * x * y * z
+    dc = np.zeros((nc, nc, nc))
+    dc[1:-1, 1:-1, 1:-1] = tri(xc, yc, zc)[1:-1, 1:-1, 1:-1]
+    uf = np.zeros((nf, nf, nf))
+    O.prolong_add(dc, np.zeros_like(dc), uf)
+    # exact wherever every coarse point used is interior (the shell holds 0)
+    np.testing.assert_allclose(uf[2:-2, 2:-2, 2:-2], tri(xf, yf, zf)[2:-2, 2:-2, 2:-2], atol=1e-13)
+    ic = [(k, j, i) for k in range(1, nc - 1) for j in range(1, nc - 1) for i in range(1, nc - 1)]
+    ifn = [(k, j, i) for k in range(1, nf - 1) for j in range(1, nf - 1) for i in range(1, nf - 1)]
+    Pm = np.zeros((len(ifn), len(ic)))
+    for col, p in enumerate(ic):
+        e = np.zeros((nc, nc, nc)); e[p] = 1.0
+        out = np.zeros((nf, nf, nf))
+        O.prolong_add(e, np.zeros_like(e), out)
+        Pm[:, col] = [out[q] for q in ifn]
+    Rm = np.zeros((len(ic), len(ifn)))
+    for col, q in enumerate(ifn):
+        e = np.zeros((nf, nf, nf)); e[q] = 1.0
+        rc = O.restrict_residual(e, O.FULL_WEIGHTING)
+        Rm[:, col] = [rc[p] for p in ic]
+    np.testing.assert_allclose(Rm, Pm.T / 8.0, atol=1e-15)
+
+
+def test_interpolate_and_coarse_rhs():
+    nc, nf = 5, 9
+    xc, yc, zc = P.grid_coords(nc)
+    xf, yf, zf = P.grid_coords(nf)
+    lin = lambda x, y, z: 2 - x + 3 * y + z
+    uf = np.zeros((nf, nf, nf))
+    O.interpolate(np.ascontiguousarray(lin(xc, yc, zc)), uf)
+    np.testing.assert_allclose(uf[1:-1, 1:-1, 1:-1], lin(xf, yf, zf)[1:-1, 1:-1, 1:-1], atol=1e-14)
+    # tau right-hand side on |x|^2/2 (exact scheme): S_H(w) = 1 everywhere
+    w = np.ascontiguousarray(P.make("quadratic", nc).u)
+    rc = np.zeros_like(w); rc[1:-1, 1:-1, 1:-1] = 0.25
+    b = O.coarse_rhs(w, rc, 0.25)
+    np.testing.assert_array_equal(b[1:-1, 1:-1, 1:-1], 1.25)
+
+
+# --------------------------------------------------------------------------
+# Smoother ordering
+# --------------------------------------------------------------------------
+
+def test_colour_points_are_independent():
+    """Within one colour the update order must not matter (no stencil
+    neighbour shares the colour): forward and reversed visits agree bitwise."""
+    pr = P.make("exp", 17)
+    rng = np.random.default_rng(1)
+    u0 = pr.u + 1e-2 * rng.normal(size=pr.u.shape) * (pr.initial() == 0)
+    u0 = np.ascontiguousarray(u0)
+    a, b = u0.copy(), u0.copy()
+    O.gs_sweep(a, pr.f, pr.h, O.COLOUR8)
+    O.gs_sweep(b, pr.f, pr.h, O.COLOUR8_REVERSED)
+    np.testing.assert_array_equal(a, b)
+    c = u0.copy()
+    O.gs_sweep(c, pr.f, pr.h, O.LEXICOGRAPHIC)
+    assert np.max(np.abs(c - a)) > 0
+
+
+# --------------------------------------------------------------------------
+# The discrete solution: brute force, theorems, printed errors
+# --------------------------------------------------------------------------
+
+def _newton_brute_force(pr, tol=1e-13):
+    """Global Newton on F(u) = det(D^2_h u) - f over all interior unknowns with
+    a dense finite-difference Jacobian, started at the exact solution."""
+    n, h = pr.n, pr.h
+    u = np.ascontiguousarray(pr.u.copy())
+    idx = [(k, j, i) for k in range(1, n - 1) for j in range(1, n - 1) for i in range(1, n - 1)]
+
+    def F(v):
+        d = O.discrete_ma(np.ascontiguousarray(v), h)
+        return np.array([d[p] - pr.f[p] for p in idx])
+
+    for _ in range(30):
+        F0 = F(u)
+        if np.max(np.abs(F0)) <= tol * np.max(np.abs(pr.f)):
+            break
+        J = np.zeros((len(idx), len(idx)))
+        eps = 1e-7
+        for col, p in enumerate(idx):
+            up, um = u.copy(), u.copy()
+            up[p] += eps; um[p] -= eps
+            J[:, col] = (F(up) - F(um)) / (2 * eps)
+        du = np.linalg.solve(J, -F0)
+        for col, p in enumerate(idx):
+            u[p] += du[col]
+    return u
+
+
+@pytest.mark.parametrize("name,n,coarsest", [("exp", 5, 3), ("exp", 9, 5), ("cosine", 9, 3)])
+def test_multigrid_solution_equals_brute_force_newton(name, n, coarsest):
+    """The FMG + V-cycle solution is the discrete solution of Eq. (MA_discrete)
+    that an independent dense Newton solve finds."""
+    pr = P.make(name, n, seed=2)
+    u_ref = _newton_brute_force(pr)
+    u = pr.initial()
+    info = O.solve(u, pr.f, pr.h, tol=1e-13, max_cycles=60, params=O.Params(coarsest_n=coarsest))
+    assert info.res_hist[-1] <= 1e-12
+    assert np.max(np.abs(u - u_ref)) <= 1e-11 * np.max(np.abs(u_ref))
+
+
+@pytest.mark.parametrize("name", ["exp", "cosine", "sine"])
+def test_converged_solution_is_convex_and_a_fixed_point(name):
+    """Theorem 2.2: the discrete Hessian of the fixed point is positive
+    definite at every interior point; Theorem 2.1: it is a fixed point of
+    the smallest-root sweep (one more sweep moves it only by round-off)."""
+    pr = P.make(name, 17, seed=4)
+    u = pr.initial()
+    O.solve(u, pr.f, pr.h, tol=1e-12, max_cycles=60)
+    Hs = O.discrete_hessian(u, pr.h)
+    M = np.stack([np.stack([Hs[0], Hs[3], Hs[4]]), np.stack([Hs[3], Hs[1], Hs[5]]),
+                  np.stack([Hs[4], Hs[5], Hs[2]])])[:, :, 1:-1, 1:-1, 1:-1]
+    lam = np.linalg.eigvalsh(np.moveaxis(M, (0, 1), (-2, -1)))
+    assert lam.min() > 0
+    v = u.copy()
+    O.gs_sweep(v, pr.f, pr.h)
+    assert np.max(np.abs(v - u)) <= 1e-12 * np.max(np.abs(u))
+
+
+def test_example4_errors_match_table3():
+    """Table 3 (Example 4): the max-norm error of the converged discrete
+    solution.  The Gauss-Seidel column (run to convergence) must match within
+    10 %; the FMG column within a factor 1.4; the observed order is 2."""
+    g = _load_golden("table3_example4.txt")
+    errs = {}
+    for N, fmg_err, gs_err in g:
+        N = int(N)
+        if N > 64:
+            continue
+        pr = P.make("exp", N + 1)
+        u = pr.initial()
+        O.solve(u, pr.f, pr.h, tol=1e-11, max_cycles=60)
+        e = np.max(np.abs(u - pr.u))
+        errs[N] = e
+        assert fmg_err / 1.4 <= e <= fmg_err * 1.4, (N, e, fmg_err)
+        if not np.isnan(gs_err):
+            assert abs(e - gs_err) <= 0.10 * gs_err, (N, e, gs_err)
+    for N in (16, 32, 64):
+        order = np.log2(errs[N // 2] / errs[N])
+        assert 1.9 <= order <= 2.1
+
+
+def test_example5_errors_match_table5():
+    """Table 5 (Example 5 on (0, pi)^3, non-unit domain)."""
+    g = _load_golden("table5_example5.txt")
+    for N, fmg_err, gs_err in g:
+        N = int(N)
+        if N > 32:
+            continue
+        pr = P.make("sine", N + 1)
+        u = pr.initial()
+        O.solve(u, pr.f, pr.h, tol=1e-11, max_cycles=60)
+        e = np.max(np.abs(u - pr.u))
+        assert fmg_err / 1.4 <= e <= fmg_err * 1.4, (N, e, fmg_err)
+        if not np.isnan(gs_err):
+            assert abs(e - gs_err) <= 0.15 * gs_err, (N, e, gs_err)
+
+
+def test_vcycle_convergence_is_mesh_independent():
+    """Section 4: mesh-independent V-cycle convergence.  Cycles from the FMG
+    start to a 1e-9 relative residual differ by at most 3 across N = 16..64
+    and every grid converges at least 3x per cycle on average."""
+    cycles = []
+    for n in (17, 33, 65):
+        pr = P.make("cosine", n, seed=1)
+        u = pr.initial()
+        info = O.solve(u, pr.f, pr.h, tol=1e-9, max_cycles=40)
+        cycles.append(info.cycles)
+        rate = (info.res_hist[-1] / info.res_hist[0]) ** (1.0 / info.cycles)
+        assert rate < 1 / 3
+    assert max(cycles) - min(cycles) <= 3
+
+
+def test_half_weighting_option_converges_on_small_grid():
+    """The paper's half-weighting residual restriction with injection for the
+    approximation (Section 3): converges on the two-grid 9^3 problem."""
+    pr = P.make("exp", 9)
+    u = pr.initial()
+    info = O.solve(u, pr.f, pr.h, tol=1e-10, max_cycles=40,
+                   params=O.Params(restrict_kind=O.HALF_WEIGHTING, approx_restrict=O.APPROX_INJECTION))
+    assert info.res_hist[-1] <= 1e-10
