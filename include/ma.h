@@ -1,0 +1,230 @@
+/*
+ * ma.h -- C ABI of libma, a GB300 (sm_103a) FAS multigrid solver for the 3D
+ * elliptic Monge-Ampere equation
+ *
+ *     det(D^2 u) = f > 0 in the cube,   u = g on its boundary,   u convex
+ *
+ * (Liu, Froese, Oberman, Xiao, "A multigrid scheme for 3D Monge-Ampere
+ * equations", Section 1, Eqs. (MA3D) and (DBC)).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Grids (Section 2): n = N + 1 points per side including the boundary
+ *    shell, h = len / N, point (i, j, k) at x0 + (i h, j h, k h).  A grid
+ *    array holds n^3 doubles in [k][j][i] order (i fastest), shell included.
+ *    Hierarchy calls require n = 2^L (coarsest_n - 1) + 1.
+ *  - Pointers named *_dev are device pointers (cudaMalloc'd or torch CUDA
+ *    tensors) on the current device; *_host are host pointers.  The library
+ *    never frees or keeps caller pointers beyond the call unless stated.
+ *  - Every call is asynchronous on the given stream unless it says it blocks.
+ *    A hierarchy is bound to the stream it was created with and is not
+ *    thread-safe.
+ *  - Every call returns ma_status; on failure ma_last_error_string() gives a
+ *    one-line reason (thread-local).  No C++ exception crosses the ABI.
+ *    MA_ERR_INVALID_ARG: a null pointer, a bad size or option, or a
+ *    workspace smaller than the footprint.  MA_ERR_CUDA: a CUDA runtime error
+ *    (the message names it).  MA_ERR_NOT_CONVERGED / MA_ERR_NONFINITE: see
+ *    ma_solve.
+ *  - The library allocates no device memory: every device buffer a hierarchy
+ *    uses lives in the caller's workspace.  It allocates a few bytes of pinned
+ *    host memory per hierarchy for norm read-back.
+ */
+#ifndef MA_H
+#define MA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MA_OK = 0,
+    MA_ERR_INVALID_ARG = 1,
+    MA_ERR_OOM = 2,
+    MA_ERR_CUDA = 3,
+    MA_ERR_NOT_CONVERGED = 4,
+    MA_ERR_NONFINITE = 5
+} ma_status;
+
+/* Residual restriction I_h^H (Section 3): the printed 7-point half
+ * weighting, or 27-point full weighting (weights 8/4/2/1 over 64). */
+enum { MA_HALF_WEIGHTING = 0, MA_FULL_WEIGHTING = 1 };
+/* Approximation restriction (Algorithm 1 step 4): straight injection
+ * (Section 3), or the residual's own weighting applied to u.  The coarse
+ * iterate u_H starts equal to w_H in both cases. */
+enum { MA_APPROX_INJECTION = 0, MA_APPROX_WEIGHTED = 1 };
+/* Arithmetic: everything in FP64, or FP32 correction cycles under an FP64
+ * fine-grid residual and update (defect correction). */
+enum { MA_FP64 = 0, MA_MIXED = 1 };
+/* Norms over the fine interior: max, or discrete L2 sqrt(h^3 sum v^2)
+ * (stopping rule of Section 4). */
+enum { MA_NORM_MAX = 0, MA_NORM_L2 = 1 };
+/* Initial iterate for ma_solve: one FMG pass (Algorithm 2), the Dirichlet
+ * data with a zero interior, or the current iterate. */
+enum { MA_INIT_FMG = 0, MA_INIT_ZERO = 1, MA_INIT_KEEP = 2 };
+
+/* A cudaStream_t (NULL = the legacy default stream). */
+typedef void *ma_stream_t;
+
+typedef struct ma_hierarchy ma_hierarchy;
+
+/* Problem and cycle description (Sections 2-4). */
+typedef struct {
+    int n;               /* points per side incl. boundary; n = 2^L (coarsest_n-1) + 1 */
+    double x0[3];        /* cube origin (informational; f and g are given on the grid) */
+    double len;          /* cube edge; h = len / (n - 1)                               */
+    int nu1, nu2;        /* pre/post smoothing sweeps (Section 4 uses 2, 2)            */
+    int coarsest_n;      /* 3 (Section 4, h0 = 1/2) or 5                               */
+    int restrict_kind;   /* MA_HALF_WEIGHTING | MA_FULL_WEIGHTING                      */
+    int approx_restrict; /* MA_APPROX_INJECTION | MA_APPROX_WEIGHTED                   */
+    int precision;       /* MA_FP64 | MA_MIXED                                         */
+    int coarse_sweeps;   /* > 0: that many sweeps on the coarsest grid (Section 4 uses
+                            1); 0: sweep until max|du| <= 1e-14 max|u| (cap 100)        */
+} ma_hier_desc;
+
+/* Stopping rule for ma_solve.  Converged when ||f - det(D^2_h u)|| <= tol *
+ * (relative ? ||f|| : 1), norm over the fine interior, evaluated in FP64. */
+typedef struct {
+    double tol;
+    int norm;            /* MA_NORM_MAX | MA_NORM_L2                        */
+    int relative;        /* 1: relative to ||f|| on the interior; 0: absolute */
+    int max_cycles;      /* V-cycles (outer iterations in MA_MIXED) at most    */
+    int init;            /* MA_INIT_FMG | MA_INIT_ZERO | MA_INIT_KEEP          */
+} ma_solve_opts;
+
+typedef struct {
+    int cycles;                       /* V-cycles run after the initial iterate        */
+    double res0;                      /* residual norm of the initial iterate           */
+    double res;                       /* final residual norm (same scaling as tol)      */
+    int status;                       /* the ma_status ma_solve returned                */
+    int floor_reached;                /* 1 if stopped because the residual stagnated at
+                                         the round-off floor above tol                  */
+    long long nonconvex_root_events;  /* point solves whose right-hand side was <= 0     */
+} ma_solve_result;
+
+/* ---- hierarchy (the method as a whole) ---------------------------------- */
+
+/* Bytes of device workspace a hierarchy with this description needs
+ * (all level grids and reduction scratch).  Host only; no CUDA call. */
+ma_status ma_hierarchy_footprint(const ma_hier_desc *desc, size_t *bytes);
+
+/* Build a hierarchy inside the caller's device workspace (>= footprint
+ * bytes, 256-byte aligned).  The caller keeps ownership of the workspace and
+ * must keep it alive until ma_destroy_hierarchy.  Fields are not initialised:
+ * call ma_set_rhs_bc next. */
+ma_status ma_create_hierarchy(const ma_hier_desc *desc, void *dev_workspace, size_t bytes,
+                              ma_stream_t stream, ma_hierarchy **out);
+
+/* Copy the data of Eqs. (MA3D)/(DBC) in: f_dev is read on the interior
+ * (must be finite and > 0 there), g_dev on the boundary shell; the interior of
+ * g_dev is taken as the initial iterate (used by MA_INIT_KEEP).  Both are n^3
+ * doubles; they are copied, so the caller may free them after the stream
+ * reaches this point.  Checks f > 0 on the device and blocks for that check. */
+ma_status ma_set_rhs_bc(ma_hierarchy *h, const double *f_dev, const double *g_dev);
+
+/* ncycles FAS V-cycles (Algorithm 1) on the finest level.  Asynchronous. */
+ma_status ma_vcycle(ma_hierarchy *h, int ncycles);
+
+/* Solve to tolerance: the chosen initial iterate, then V-cycles until the
+ * stopping rule holds (MA_OK), max_cycles is reached, or the residual
+ * stagnates above tol (three cycles in a row each reducing it by less than
+ * 20 %: the round-off floor; result->floor_reached = 1).  Both of the latter
+ * return MA_ERR_NOT_CONVERGED; a NaN/Inf residual returns MA_ERR_NONFINITE.
+ * Blocks on the stream (one small read-back per cycle); result is filled in
+ * every case. */
+ma_status ma_solve(ma_hierarchy *h, const ma_solve_opts *opts, ma_solve_result *result);
+
+/* Norm of the fine-level FP64 residual f - det(D^2_h u) of the current
+ * iterate (Algorithm 1 step 3; Section 4 norms).  Blocks on the stream. */
+ma_status ma_residual_norm(ma_hierarchy *h, int norm, double *out);
+
+/* Copy the current fine-level iterate (n^3 doubles, shell included) to u_dev.
+ * Asynchronous. */
+ma_status ma_get_solution(ma_hierarchy *h, double *u_dev);
+
+/* Replace the current fine-level iterate (shell included) from u_dev
+ * (checkpoint/restart).  Asynchronous. */
+ma_status ma_set_solution(ma_hierarchy *h, const double *u_dev);
+
+/* Grid size, level count and workspace bytes of a hierarchy. */
+ma_status ma_hierarchy_info(const ma_hierarchy *h, int *n, int *levels, size_t *bytes);
+
+/* Release the host-side state; the caller frees the workspace afterwards.
+ * Synchronises the hierarchy's stream first. */
+ma_status ma_destroy_hierarchy(ma_hierarchy *h);
+
+/* Thread-local text of the last failure ("" if none). */
+const char *ma_last_error_string(void);
+
+/* Diagnostics: the number of kernel launches this library has issued in this
+ * process so far (all devices, all hierarchies).  Host only. */
+ma_status ma_kernel_launch_count(unsigned long long *out);
+
+/* ---- single steps on raw device grids (each row of the V-cycle) ----------
+ * These run exactly the kernels a hierarchy runs, on caller arrays of one
+ * level (n^3 doubles, [k][j][i]).  n must be odd and >= 3.  All are
+ * asynchronous on the given stream. */
+
+/* nsweeps nonlinear Gauss-Seidel sweeps (Section 2, Eq. realroots) in place
+ * on u_dev with right-hand side rhs_dev (f on the finest level, b_H on coarse
+ * ones): eight colours c = (i&1)|(j&1)<<1|(k&1)<<2 in ascending order; each
+ * point takes the smallest real root of its local cubic.  The shell is not
+ * written.  If events_dev is not NULL, the count of point solves whose
+ * right-hand side was <= 0 is added to *events_dev (one unsigned 64-bit
+ * integer on the device). */
+ma_status ma_smooth(double *u_dev, const double *rhs_dev, int n, double h, int nsweeps,
+                    unsigned long long *events_dev, ma_stream_t stream);
+
+/* r = rhs - det(D^2_h u) on the interior and 0 on the shell (Algorithm 1
+ * step 3, the operator of Eq. MA_discrete). */
+ma_status ma_residual(const double *u_dev, const double *rhs_dev, double *r_dev, int n, double h,
+                      ma_stream_t stream);
+
+/* Residual restriction r_H = I_h^H r_h (Section 3) from a fine grid of nf
+ * points per side to the coarse grid of (nf+1)/2: kind MA_HALF_WEIGHTING or
+ * MA_FULL_WEIGHTING on the coarse interior, 0 on the coarse shell. */
+ma_status ma_restrict_residual(const double *rf_dev, int nf, double *rc_dev, int kind,
+                               ma_stream_t stream);
+
+/* Approximation restriction (Algorithm 1 step 4): with approx =
+ * MA_APPROX_INJECTION, uc = uf(2I, 2J, 2K) everywhere; with
+ * MA_APPROX_WEIGHTED, the kind weighting on the coarse interior and injection
+ * on the shell. */
+ma_status ma_restrict_solution(const double *uf_dev, int nf, double *uc_dev, int approx, int kind,
+                               ma_stream_t stream);
+
+/* tau-corrected coarse right-hand side b_H = det(D^2_H w_H) + r_H on the
+ * coarse interior, 0 on the shell (Algorithm 1 step 5). */
+ma_status ma_coarse_rhs(const double *wc_dev, const double *rc_dev, double *bc_dev, int nc, double H,
+                        ma_stream_t stream);
+
+/* u_h += I_H^h (u_H - w_H) on the fine interior, trilinear interpolation
+ * (Algorithm 1 steps 7-8); nf = 2 nc - 1. */
+ma_status ma_prolong_add(const double *uc_dev, const double *wc_dev, int nc, double *uf_dev,
+                         ma_stream_t stream);
+
+/* Fine interior := trilinear interpolation of the coarse solution (Algorithm
+ * 2 step 4 with trilinear in place of cubic interpolation); shell untouched. */
+ma_status ma_interpolate(const double *uc_dev, int nc, double *uf_dev, ma_stream_t stream);
+
+/* Approximate solve on a coarsest grid (Algorithm 1 step 1), one thread
+ * block: sweeps > 0 runs that many sweeps, 0 sweeps until
+ * max|du| <= 1e-14 max|u| (at most 100).  n <= 17. */
+ma_status ma_coarsest_solve(double *u_dev, const double *rhs_dev, int n, double h, int sweeps,
+                            unsigned long long *events_dev, ma_stream_t stream);
+
+/* Bytes of device scratch ma_norm needs for a grid of n points per side. */
+ma_status ma_norm_scratch_bytes(int n, size_t *bytes);
+
+/* Max norm and discrete L2 norm sqrt(h^3 sum v^2) of v over the interior
+ * (Section 4), written to out_host[0] and out_host[1].  scratch_dev holds at
+ * least ma_norm_scratch_bytes(n) bytes.  Blocks on the stream. */
+ma_status ma_norm(const double *v_dev, int n, double h, void *scratch_dev, size_t scratch_bytes,
+                  double *out_host, ma_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MA_H */

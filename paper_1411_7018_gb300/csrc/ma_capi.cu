@@ -1,0 +1,477 @@
+// ma_capi.cu -- the C ABI of include/ma.h: hierarchy layout inside the
+// caller's workspace, the FAS V-cycle and FMG drivers (Algorithms 1 and 2 of
+// Liu, Froese, Oberman, Xiao), the stopping rule of Section 4, and the
+// single-step entry points.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "ma.h"
+#include "ma_hier.h"
+#include "ma_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+ma_status fail(ma_status st, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define MA_CK(call)                                                                           \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(MA_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool valid_step_grid(int n) { return n >= 3 && (n % 2) == 1 && n <= 4097; }
+
+// Level sizes n_0 = n > n_1 > ... > n_{L-1} = coarsest_n with n_{l+1} = (n_l+1)/2.
+int level_count(int n, int coarsest)
+{
+    int L = 1, m = n;
+    while (m > coarsest) {
+        if ((m - 1) % 2 != 0) return -1;
+        m = (m + 1) / 2;
+        ++L;
+        if (L > ma::kMaxLevels) return -1;
+    }
+    return m == coarsest ? L : -1;
+}
+
+ma_status check_desc(const ma_hier_desc* d)
+{
+    if (!d) return fail(MA_ERR_INVALID_ARG, "null descriptor");
+    if (!(d->coarsest_n == 3 || d->coarsest_n == 5 || d->coarsest_n == 9 || d->coarsest_n == 17))
+        return fail(MA_ERR_INVALID_ARG, "coarsest_n must be 3, 5, 9 or 17 (got %d)", d->coarsest_n);
+    if (d->n < d->coarsest_n || level_count(d->n, d->coarsest_n) < 1)
+        return fail(MA_ERR_INVALID_ARG, "n = %d is not 2^L (coarsest_n - 1) + 1 for coarsest_n = %d", d->n,
+                    d->coarsest_n);
+    if (d->n > 4097) return fail(MA_ERR_INVALID_ARG, "n = %d exceeds 4097", d->n);
+    if (!(d->len > 0.0) || !std::isfinite(d->len)) return fail(MA_ERR_INVALID_ARG, "len must be finite and > 0");
+    if (d->nu1 < 0 || d->nu2 < 0 || d->nu1 > 64 || d->nu2 > 64 || d->nu1 + d->nu2 == 0)
+        return fail(MA_ERR_INVALID_ARG, "nu1, nu2 must be in [0, 64] and not both 0");
+    if (d->restrict_kind != MA_HALF_WEIGHTING && d->restrict_kind != MA_FULL_WEIGHTING)
+        return fail(MA_ERR_INVALID_ARG, "bad restrict_kind %d", d->restrict_kind);
+    if (d->approx_restrict != MA_APPROX_INJECTION && d->approx_restrict != MA_APPROX_WEIGHTED)
+        return fail(MA_ERR_INVALID_ARG, "bad approx_restrict %d", d->approx_restrict);
+    if (d->precision != MA_FP64 && d->precision != MA_MIXED)
+        return fail(MA_ERR_INVALID_ARG, "bad precision %d", d->precision);
+    if (d->coarse_sweeps < 0 || d->coarse_sweeps > 1000)
+        return fail(MA_ERR_INVALID_ARG, "coarse_sweeps must be in [0, 1000]");
+    return MA_OK;
+}
+
+// Carves the workspace (or, with base == nullptr, only measures it).
+size_t layout(ma_hierarchy* H, const ma_hier_desc* d, char* base)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off = align_up(off + bytes);
+        return p;
+    };
+    const int L = level_count(d->n, d->coarsest_n);
+    int m = d->n;
+    double h = d->len / (d->n - 1);
+    for (int l = 0; l < L; ++l) {
+        const size_t pts = (size_t)m * m * m;
+        ma::Level& lv = H->lev[l];
+        lv.n = m;
+        lv.h = h;
+        lv.u = (double*)take(pts * sizeof(double));
+        lv.rhs = (double*)take(pts * sizeof(double));
+        lv.r = (double*)take(pts * sizeof(double));
+        lv.w = (double*)take(pts * sizeof(double));
+        m = (m + 1) / 2;
+        h *= 2.0;
+    }
+    H->L = L;
+    H->npartials = ma::residual_partial_count(d->n);
+    H->partials = (double*)take(2 * sizeof(double) * (size_t)H->npartials);
+    H->out2 = (double*)take(4 * sizeof(double));
+    H->events = (unsigned long long*)take(sizeof(unsigned long long));
+    H->flag = (int*)take(sizeof(int));
+    return off;
+}
+
+// Algorithm 1 from level l0 down to the coarsest grid and back.
+cudaError_t vcycle_from(ma_hierarchy* H, int l0)
+{
+    cudaStream_t s = H->s;
+    const ma_hier_desc& d = H->d;
+    cudaError_t e;
+    for (int l = l0; l < H->L - 1; ++l) {
+        ma::Level& F = H->lev[l];
+        ma::Level& C = H->lev[l + 1];
+        if ((e = ma::launch_smooth(F.u, F.rhs, F.n, F.h, d.nu1, H->events, s)) != cudaSuccess) return e;   // (2)
+        if ((e = ma::launch_residual(F.u, F.rhs, F.r, F.n, F.h, nullptr, s)) != cudaSuccess) return e;     // (3)
+        if ((e = ma::launch_restrict_level(F.u, F.r, F.n, C.w, C.u, C.r, d.restrict_kind, d.approx_restrict, s)) !=
+            cudaSuccess)
+            return e;                                                                                        // (3)-(4)
+        if ((e = ma::launch_coarse_rhs(C.w, C.r, C.rhs, C.n, C.h, s)) != cudaSuccess) return e;             // (5)
+    }
+    ma::Level& B = H->lev[H->L - 1];
+    if ((e = ma::launch_coarsest(B.u, B.rhs, B.n, B.h, d.coarse_sweeps, H->events, s)) != cudaSuccess) return e;  // (1)
+    for (int l = H->L - 2; l >= l0; --l) {
+        ma::Level& F = H->lev[l];
+        ma::Level& C = H->lev[l + 1];
+        if ((e = ma::launch_prolong_add(C.u, C.w, C.n, F.u, s)) != cudaSuccess) return e;                  // (7)-(8)
+        if ((e = ma::launch_smooth(F.u, F.rhs, F.n, F.h, d.nu2, H->events, s)) != cudaSuccess) return e;  // (9)
+    }
+    return cudaSuccess;
+}
+
+// Algorithm 2: inject f (and the Dirichlet data) down, solve the coarsest
+// problem from a zero interior, then interpolate up with one V-cycle per level.
+cudaError_t fmg(ma_hierarchy* H)
+{
+    cudaStream_t s = H->s;
+    cudaError_t e;
+    for (int l = 0; l < H->L - 1; ++l) {
+        ma::Level& F = H->lev[l];
+        ma::Level& C = H->lev[l + 1];
+        if ((e = ma::launch_inject(F.rhs, F.n, C.rhs, s)) != cudaSuccess) return e;
+        if ((e = ma::launch_inject(F.u, F.n, C.u, s)) != cudaSuccess) return e;
+    }
+    ma::Level& B = H->lev[H->L - 1];
+    if ((e = ma::launch_zero_interior(B.u, B.n, s)) != cudaSuccess) return e;
+    if ((e = ma::launch_coarsest(B.u, B.rhs, B.n, B.h, H->d.coarse_sweeps, H->events, s)) != cudaSuccess) return e;
+    for (int l = H->L - 2; l >= 0; --l) {
+        if ((e = ma::launch_interpolate(H->lev[l + 1].u, H->lev[l + 1].n, H->lev[l].u, s)) != cudaSuccess) return e;
+        if ((e = vcycle_from(H, l)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Fine-level residual norms (max, L2) into host[0..1]; blocks on the stream.
+ma_status fine_residual_norms(ma_hierarchy* H, double* mx, double* l2)
+{
+    ma::Level& F = H->lev[0];
+    MA_CK(ma::launch_residual(F.u, F.rhs, F.r, F.n, F.h, H->partials, H->s));
+    MA_CK(ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s));
+    MA_CK(cudaMemcpyAsync(H->host, H->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, H->s));
+    MA_CK(cudaStreamSynchronize(H->s));
+    *mx = H->host[0];
+    *l2 = H->host[1];
+    return MA_OK;
+}
+
+ma_status rhs_norms(ma_hierarchy* H, double* mx, double* l2)
+{
+    ma::Level& F = H->lev[0];
+    MA_CK(ma::launch_norm_partials(F.rhs, F.n, H->partials, H->s));
+    MA_CK(ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s));
+    MA_CK(cudaMemcpyAsync(H->host, H->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, H->s));
+    MA_CK(cudaStreamSynchronize(H->s));
+    *mx = H->host[0];
+    *l2 = H->host[1];
+    return MA_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* ma_last_error_string(void) { return g_err; }
+
+ma_status ma_kernel_launch_count(unsigned long long* out)
+{
+    if (!out) return fail(MA_ERR_INVALID_ARG, "null out");
+    *out = ma::launch_count();
+    return MA_OK;
+}
+
+ma_status ma_hierarchy_footprint(const ma_hier_desc* desc, size_t* bytes)
+{
+    ma_status st = check_desc(desc);
+    if (st != MA_OK) return st;
+    if (!bytes) return fail(MA_ERR_INVALID_ARG, "null bytes");
+    ma_hierarchy tmp;
+    tmp.d = *desc;
+    *bytes = layout(&tmp, desc, nullptr);
+    return MA_OK;
+}
+
+ma_status ma_create_hierarchy(const ma_hier_desc* desc, void* dev_workspace, size_t bytes, ma_stream_t stream,
+                              ma_hierarchy** out)
+{
+    ma_status st = check_desc(desc);
+    if (st != MA_OK) return st;
+    if (!out) return fail(MA_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    if (!dev_workspace) return fail(MA_ERR_INVALID_ARG, "null workspace");
+    if (((uintptr_t)dev_workspace) % kAlign != 0) return fail(MA_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+    ma_hierarchy* H = new (std::nothrow) ma_hierarchy();
+    if (!H) return fail(MA_ERR_OOM, "host allocation failed");
+    H->d = *desc;
+    const size_t need = layout(H, desc, (char*)dev_workspace);
+    if (bytes < need) {
+        delete H;
+        return fail(MA_ERR_INVALID_ARG, "workspace of %zu bytes < footprint %zu", bytes, need);
+    }
+    H->ws = (char*)dev_workspace;
+    H->bytes = need;
+    H->s = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&H->device);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&H->host, 4 * sizeof(double) + sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(H->events, 0, sizeof(unsigned long long), H->s);
+    if (e != cudaSuccess) {
+        if (H->host) cudaFreeHost(H->host);
+        delete H;
+        return fail(MA_ERR_CUDA, "create: %s", cudaGetErrorString(e));
+    }
+    *out = H;
+    return MA_OK;
+}
+
+ma_status ma_destroy_hierarchy(ma_hierarchy* H)
+{
+    if (!H) return MA_OK;
+    DeviceGuard g(H->device);
+    cudaError_t e = cudaStreamSynchronize(H->s);
+    if (H->host) cudaFreeHost(H->host);
+    delete H;
+    if (e != cudaSuccess) return fail(MA_ERR_CUDA, "destroy: %s", cudaGetErrorString(e));
+    return MA_OK;
+}
+
+ma_status ma_hierarchy_info(const ma_hierarchy* H, int* n, int* levels, size_t* bytes)
+{
+    if (!H) return fail(MA_ERR_INVALID_ARG, "null hierarchy");
+    if (n) *n = H->d.n;
+    if (levels) *levels = H->L;
+    if (bytes) *bytes = H->bytes;
+    return MA_OK;
+}
+
+ma_status ma_set_rhs_bc(ma_hierarchy* H, const double* f_dev, const double* g_dev)
+{
+    if (!H || !f_dev || !g_dev) return fail(MA_ERR_INVALID_ARG, "null argument");
+    DeviceGuard g(H->device);
+    ma::Level& F = H->lev[0];
+    MA_CK(cudaMemsetAsync(H->flag, 0, sizeof(int), H->s));
+    MA_CK(ma::launch_copy_rhs_bc(f_dev, g_dev, F.rhs, F.u, F.n, H->flag, H->s));
+    int bad = 0;
+    MA_CK(cudaMemcpyAsync(&H->host[2], H->flag, sizeof(int), cudaMemcpyDeviceToHost, H->s));
+    MA_CK(cudaStreamSynchronize(H->s));
+    std::memcpy(&bad, &H->host[2], sizeof(int));
+    if (bad) return fail(MA_ERR_INVALID_ARG, "%d grid values invalid (f must be finite and > 0 inside, g finite)", bad);
+    return MA_OK;
+}
+
+ma_status ma_vcycle(ma_hierarchy* H, int ncycles)
+{
+    if (!H || ncycles < 0) return fail(MA_ERR_INVALID_ARG, "bad arguments");
+    DeviceGuard g(H->device);
+    for (int c = 0; c < ncycles; ++c) MA_CK(vcycle_from(H, 0));
+    return MA_OK;
+}
+
+ma_status ma_residual_norm(ma_hierarchy* H, int norm, double* out)
+{
+    if (!H || !out || (norm != MA_NORM_MAX && norm != MA_NORM_L2)) return fail(MA_ERR_INVALID_ARG, "bad arguments");
+    DeviceGuard g(H->device);
+    double mx, l2;
+    ma_status st = fine_residual_norms(H, &mx, &l2);
+    if (st != MA_OK) return st;
+    *out = norm == MA_NORM_MAX ? mx : l2;
+    return MA_OK;
+}
+
+ma_status ma_get_solution(ma_hierarchy* H, double* u_dev)
+{
+    if (!H || !u_dev) return fail(MA_ERR_INVALID_ARG, "null argument");
+    DeviceGuard g(H->device);
+    const size_t pts = (size_t)H->d.n * H->d.n * H->d.n;
+    MA_CK(cudaMemcpyAsync(u_dev, H->lev[0].u, pts * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
+    return MA_OK;
+}
+
+ma_status ma_set_solution(ma_hierarchy* H, const double* u_dev)
+{
+    if (!H || !u_dev) return fail(MA_ERR_INVALID_ARG, "null argument");
+    DeviceGuard g(H->device);
+    const size_t pts = (size_t)H->d.n * H->d.n * H->d.n;
+    MA_CK(cudaMemcpyAsync(H->lev[0].u, u_dev, pts * sizeof(double), cudaMemcpyDeviceToDevice, H->s));
+    return MA_OK;
+}
+
+ma_status ma_solve(ma_hierarchy* H, const ma_solve_opts* opts, ma_solve_result* res)
+{
+    if (!H || !opts || !res) return fail(MA_ERR_INVALID_ARG, "null argument");
+    if (!(opts->tol >= 0.0) || opts->max_cycles < 0 || (opts->norm != MA_NORM_MAX && opts->norm != MA_NORM_L2) ||
+        opts->init < MA_INIT_FMG || opts->init > MA_INIT_KEEP)
+        return fail(MA_ERR_INVALID_ARG, "bad solve options");
+    DeviceGuard g(H->device);
+    std::memset(res, 0, sizeof *res);
+    MA_CK(cudaMemsetAsync(H->events, 0, sizeof(unsigned long long), H->s));
+    double scale = 1.0;
+    if (opts->relative) {
+        double fm, f2;
+        ma_status st = rhs_norms(H, &fm, &f2);
+        if (st != MA_OK) return st;
+        scale = opts->norm == MA_NORM_MAX ? fm : f2;
+        if (!(scale > 0.0)) scale = 1.0;
+    }
+    if (opts->init == MA_INIT_FMG) MA_CK(fmg(H));
+    else if (opts->init == MA_INIT_ZERO) MA_CK(ma::launch_zero_interior(H->lev[0].u, H->lev[0].n, H->s));
+    double mx, l2;
+    ma_status st = fine_residual_norms(H, &mx, &l2);
+    if (st != MA_OK) return st;
+    double rel = (opts->norm == MA_NORM_MAX ? mx : l2) / scale;
+    res->res0 = rel;
+    int stagnant = 0;
+    ma_status out = MA_OK;
+    while (true) {
+        if (!std::isfinite(rel)) { out = MA_ERR_NONFINITE; break; }
+        if (rel <= opts->tol) break;
+        if (res->cycles >= opts->max_cycles) { out = MA_ERR_NOT_CONVERGED; break; }
+        MA_CK(vcycle_from(H, 0));
+        res->cycles += 1;
+        st = fine_residual_norms(H, &mx, &l2);
+        if (st != MA_OK) return st;
+        const double nrel = (opts->norm == MA_NORM_MAX ? mx : l2) / scale;
+        // three cycles in a row that barely reduce the residual: round-off floor
+        stagnant = (nrel > 0.8 * rel) ? stagnant + 1 : 0;
+        rel = nrel;
+        if (stagnant >= 3 && rel > opts->tol) {
+            res->floor_reached = 1;
+            out = MA_ERR_NOT_CONVERGED;
+            break;
+        }
+    }
+    res->res = rel;
+    unsigned long long ev = 0;
+    MA_CK(cudaMemcpyAsync(H->host + 3, H->events, sizeof ev, cudaMemcpyDeviceToHost, H->s));
+    MA_CK(cudaStreamSynchronize(H->s));
+    std::memcpy(&ev, H->host + 3, sizeof ev);
+    res->nonconvex_root_events = (long long)ev;
+    res->status = out;
+    if (out == MA_ERR_NONFINITE) return fail(out, "residual became non-finite after %d cycles", res->cycles);
+    if (out == MA_ERR_NOT_CONVERGED)
+        return fail(out, "not converged: residual %.3e > tol %.3e after %d cycles%s", rel, opts->tol, res->cycles,
+                    res->floor_reached ? " (round-off floor)" : "");
+    return MA_OK;
+}
+
+// ---- single steps ----------------------------------------------------------
+
+ma_status ma_smooth(double* u, const double* rhs, int n, double h, int nsweeps, unsigned long long* events,
+                    ma_stream_t stream)
+{
+    if (!u || !rhs || !valid_step_grid(n) || !(h > 0.0) || nsweeps < 0)
+        return fail(MA_ERR_INVALID_ARG, "ma_smooth: bad arguments");
+    MA_CK(ma::launch_smooth(u, rhs, n, h, nsweeps, events, (cudaStream_t)stream));
+    return MA_OK;
+}
+
+ma_status ma_residual(const double* u, const double* rhs, double* r, int n, double h, ma_stream_t stream)
+{
+    if (!u || !rhs || !r || !valid_step_grid(n) || !(h > 0.0)) return fail(MA_ERR_INVALID_ARG, "ma_residual: bad arguments");
+    MA_CK(ma::launch_residual(u, rhs, r, n, h, nullptr, (cudaStream_t)stream));
+    return MA_OK;
+}
+
+ma_status ma_restrict_residual(const double* rf, int nf, double* rc, int kind, ma_stream_t stream)
+{
+    if (!rf || !rc || !valid_step_grid(nf) || nf < 5 || (kind != MA_HALF_WEIGHTING && kind != MA_FULL_WEIGHTING))
+        return fail(MA_ERR_INVALID_ARG, "ma_restrict_residual: bad arguments");
+    MA_CK(ma::launch_restrict_residual(rf, nf, rc, kind, (cudaStream_t)stream));
+    return MA_OK;
+}
+
+ma_status ma_restrict_solution(const double* uf, int nf, double* uc, int approx, int kind, ma_stream_t stream)
+{
+    if (!uf || !uc || !valid_step_grid(nf) || nf < 5 || (kind != MA_HALF_WEIGHTING && kind != MA_FULL_WEIGHTING) ||
+        (approx != MA_APPROX_INJECTION && approx != MA_APPROX_WEIGHTED))
+        return fail(MA_ERR_INVALID_ARG, "ma_restrict_solution: bad arguments");
+    MA_CK(ma::launch_restrict_solution(uf, nf, uc, approx, kind, (cudaStream_t)stream));
+    return MA_OK;
+}
+
+ma_status ma_coarse_rhs(const double* wc, const double* rc, double* bc, int nc, double Hs, ma_stream_t stream)
+{
+    if (!wc || !rc || !bc || !valid_step_grid(nc) || !(Hs > 0.0))
+        return fail(MA_ERR_INVALID_ARG, "ma_coarse_rhs: bad arguments");
+    MA_CK(ma::launch_coarse_rhs(wc, rc, bc, nc, Hs, (cudaStream_t)stream));
+    return MA_OK;
+}
+
+ma_status ma_prolong_add(const double* uc, const double* wc, int nc, double* uf, ma_stream_t stream)
+{
+    if (!uc || !wc || !uf || !valid_step_grid(nc)) return fail(MA_ERR_INVALID_ARG, "ma_prolong_add: bad arguments");
+    MA_CK(ma::launch_prolong_add(uc, wc, nc, uf, (cudaStream_t)stream));
+    return MA_OK;
+}
+
+ma_status ma_interpolate(const double* uc, int nc, double* uf, ma_stream_t stream)
+{
+    if (!uc || !uf || !valid_step_grid(nc)) return fail(MA_ERR_INVALID_ARG, "ma_interpolate: bad arguments");
+    MA_CK(ma::launch_interpolate(uc, nc, uf, (cudaStream_t)stream));
+    return MA_OK;
+}
+
+ma_status ma_coarsest_solve(double* u, const double* rhs, int n, double h, int sweeps, unsigned long long* events,
+                            ma_stream_t stream)
+{
+    if (!u || !rhs || !valid_step_grid(n) || n > 17 || !(h > 0.0) || sweeps < 0 || sweeps > 1000)
+        return fail(MA_ERR_INVALID_ARG, "ma_coarsest_solve: bad arguments (n <= 17)");
+    MA_CK(ma::launch_coarsest(u, rhs, n, h, sweeps, events, (cudaStream_t)stream));
+    return MA_OK;
+}
+
+ma_status ma_norm_scratch_bytes(int n, size_t* bytes)
+{
+    if (!valid_step_grid(n) || !bytes) return fail(MA_ERR_INVALID_ARG, "ma_norm_scratch_bytes: bad arguments");
+    *bytes = (2 * (size_t)ma::norm_partial_count(n) + 2) * sizeof(double);
+    return MA_OK;
+}
+
+ma_status ma_norm(const double* v, int n, double h, void* scratch, size_t scratch_bytes, double* out_host,
+                  ma_stream_t stream)
+{
+    size_t need = 0;
+    if (!v || !scratch || !out_host || !(h > 0.0) || ma_norm_scratch_bytes(n, &need) != MA_OK)
+        return fail(MA_ERR_INVALID_ARG, "ma_norm: bad arguments");
+    if (scratch_bytes < need) return fail(MA_ERR_INVALID_ARG, "ma_norm: scratch %zu < %zu bytes", scratch_bytes, need);
+    cudaStream_t s = (cudaStream_t)stream;
+    double* partials = (double*)scratch;
+    const int count = ma::norm_partial_count(n);
+    double* out2 = partials + 2 * (size_t)count;
+    MA_CK(ma::launch_norm_partials(v, n, partials, s));
+    MA_CK(ma::launch_norm_final(partials, count, h, out2, s));
+    MA_CK(cudaMemcpyAsync(out_host, out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MA_CK(cudaStreamSynchronize(s));
+    return MA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,40 @@
+// ma_hier.h -- host-side state of a hierarchy (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "ma.h"
+
+namespace ma {
+
+constexpr int kMaxLevels = 16;
+
+// One grid of the hierarchy: n points per side, step h; all fields are
+// n^3 doubles in the caller's workspace.
+struct Level {
+    int n = 0;
+    double h = 0.0;
+    double* u = nullptr;     // iterate (w_h / u_H of Algorithm 1); shell = Dirichlet data
+    double* rhs = nullptr;   // f on the finest level, b_H on coarse levels
+    double* r = nullptr;     // residual; on coarse levels the restricted r_H
+    double* w = nullptr;     // coarse levels: the restricted approximation w_H
+};
+
+}  // namespace ma
+
+struct ma_hierarchy {
+    ma_hier_desc d{};
+    int L = 0;
+    ma::Level lev[ma::kMaxLevels];
+    cudaStream_t s = nullptr;
+    int device = 0;
+    char* ws = nullptr;
+    size_t bytes = 0;
+    double* partials = nullptr;          // norm partials (2 per block)
+    int npartials = 0;
+    double* out2 = nullptr;              // device: reduced norms
+    unsigned long long* events = nullptr;  // device: nonconvex root events
+    int* flag = nullptr;                 // device: input validation count
+    double* host = nullptr;              // pinned host read-back (4 doubles + 1 counter)
+};

@@ -1,0 +1,38 @@
+// ma_internal.h -- launchers shared by the C-ABI layer (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace ma {
+
+// Kernel launches issued by this library in this process (all devices).
+void count_launches(unsigned long long k);
+unsigned long long launch_count();
+
+// FP64 kernels (ma_kernels_f64.cu).  All grids are n^3 doubles, [k][j][i].
+cudaError_t launch_smooth(double* u, const double* rhs, int n, double h, int nsweeps,
+                          unsigned long long* events, cudaStream_t s);
+cudaError_t launch_residual(const double* u, const double* rhs, double* r, int n, double h,
+                            double* partials, cudaStream_t s);
+int residual_partial_count(int n);
+cudaError_t launch_norm_partials(const double* v, int n, double* partials, cudaStream_t s);
+int norm_partial_count(int n);
+cudaError_t launch_norm_final(const double* partials, int count, double h, double* out2, cudaStream_t s);
+cudaError_t launch_restrict_residual(const double* rf, int nf, double* rc, int kind, cudaStream_t s);
+cudaError_t launch_restrict_solution(const double* uf, int nf, double* uc, int approx, int kind,
+                                     cudaStream_t s);
+cudaError_t launch_restrict_level(const double* uf, const double* rf, int nf, double* wc, double* uc, double* rc,
+                                  int kind, int approx, cudaStream_t s);
+cudaError_t launch_coarse_rhs(const double* wc, const double* rc, double* bc, int nc, double H,
+                              cudaStream_t s);
+cudaError_t launch_prolong_add(const double* uc, const double* wc, int nc, double* uf, cudaStream_t s);
+cudaError_t launch_interpolate(const double* uc, int nc, double* uf, cudaStream_t s);
+cudaError_t launch_inject(const double* vf, int nf, double* vc, cudaStream_t s);
+cudaError_t launch_zero_interior(double* u, int n, cudaStream_t s);
+cudaError_t launch_coarsest(double* u, const double* rhs, int n, double h, int sweeps,
+                            unsigned long long* events, cudaStream_t s);
+cudaError_t launch_copy_rhs_bc(const double* f, const double* g, double* rhs, double* u, int n,
+                               int* bad, cudaStream_t s);
+
+}  // namespace ma

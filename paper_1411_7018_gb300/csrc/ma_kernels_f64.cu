@@ -1,0 +1,513 @@
+// ma_kernels_f64.cu -- FP64 kernels of the FAS V-cycle (Algorithm 1 of Liu,
+// Froese, Oberman, Xiao) on one level grid of n^3 doubles, [k][j][i] order,
+// boundary shell included.
+//
+//   smoother        Section 2: 8-colour nonlinear Gauss-Seidel, smallest root
+//   residual        Algorithm 1 step 3 (r = rhs - det D^2_h u), norm partials
+//   restriction     Section 3: half/full weighting, injection (steps 3-4)
+//   coarse rhs      Algorithm 1 step 5 (tau correction)
+//   prolongation    Section 3 trilinear, Algorithm 1 steps 7-8
+//   coarsest solve  Algorithm 1 step 1, one thread block
+//
+// FP64 throughput is the bound of these kernels on GB300 (FP64 issues at
+// about 1/70 of the FP32 rate), so the point solve keeps its FP64 work to the
+// stencil, one determinant and one Newton correction (ma_point.cuh).
+#include <atomic>
+
+#include "ma_internal.h"
+#include "ma_point.cuh"
+
+namespace ma {
+
+namespace {
+
+constexpr int BX = 32, BY = 4;
+
+__device__ __forceinline__ long long lin(int i, int j, int k, int n)
+{
+    return ((long long)k * n + j) * n + i;
+}
+
+// ---------------------------------------------------------------------------
+// Smoother: one colour phase.  Colour c = (i&1) | (j&1)<<1 | (k&1)<<2; the
+// interior points of parity p along an axis start at 1 (p = 1) or 2 (p = 0).
+// Every stencil neighbour differs from the centre in at least one index
+// parity, so the points of one colour are independent and one launch may
+// update them all in parallel.
+// ---------------------------------------------------------------------------
+template <int PI, int PJ, int PK>
+__global__ void __launch_bounds__(BX * BY) k_smooth_colour(double* u, const double* __restrict__ rhs, int n,
+                                                            double h6, unsigned long long* events)
+{
+    const int i = (PI ? 1 : 2) + 2 * (int)(blockIdx.x * BX + threadIdx.x);
+    const int j = (PJ ? 1 : 2) + 2 * (int)(blockIdx.y * BY + threadIdx.y);
+    const int k = (PK ? 1 : 2) + 2 * (int)blockIdx.z;
+    if (i > n - 2 || j > n - 2 || k > n - 2) return;
+    const long long sy = n, sz = (long long)n * n;
+    const long long p = lin(i, j, k, n);
+    const double v0 = u[p];
+    const HessS H = gather_hess(u, p, sy, sz, v0);
+    bool nonconvex = false;
+    const double z = smallest_root(H, h6 * rhs[p], &nonconvex);
+    u[p] = fma(0.5, z, v0);
+    if (nonconvex && events) atomicAdd(events, 1ull);
+}
+
+// Interior indices of one parity along an axis of n points (n odd).
+__host__ __device__ __forceinline__ int colour_count(int n, int parity) { return parity ? (n - 1) / 2 : (n - 3) / 2; }
+
+template <int C>
+cudaError_t launch_colour(double* u, const double* rhs, int n, double h6, unsigned long long* ev, cudaStream_t s)
+{
+    constexpr int PI = C & 1, PJ = (C >> 1) & 1, PK = (C >> 2) & 1;
+    const int ni = colour_count(n, PI), nj = colour_count(n, PJ), nk = colour_count(n, PK);
+    if (ni <= 0 || nj <= 0 || nk <= 0) return cudaSuccess;
+    dim3 grid((ni + BX - 1) / BX, (nj + BY - 1) / BY, nk);
+    count_launches(1);
+    k_smooth_colour<PI, PJ, PK><<<grid, dim3(BX, BY), 0, s>>>(u, rhs, n, h6, ev);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Block reduction of (max |x|, sum x^2) in a fixed order (deterministic).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_reduce_store(double mx, double ss, double* partials, int slot)
+{
+    __shared__ double smx[BX * BY / 32], sss[BX * BY / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        ss += __shfl_down_sync(0xffffffffu, ss, o);
+    }
+    const int t = threadIdx.y * BX + threadIdx.x;
+    if ((t & 31) == 0) { smx[t >> 5] = mx; sss[t >> 5] = ss; }
+    __syncthreads();
+    if (t == 0) {
+        double m = smx[0], q = sss[0];
+        for (int w = 1; w < BX * BY / 32; ++w) { m = fmax(m, smx[w]); q += sss[w]; }
+        partials[2 * slot] = m;
+        partials[2 * slot + 1] = q;
+    }
+}
+
+constexpr int KZ = 16;   // z-blocks of the reduction grids; each loops over k
+
+dim3 reduce_grid(int n) { return dim3((n + BX - 1) / BX, (n + BY - 1) / BY, n < KZ ? n : KZ); }
+
+// r = rhs - det(D^2_h u) on the interior, 0 on the shell; optional
+// (max |r|, sum r^2) partials over the interior, one pair per block.
+__global__ void __launch_bounds__(BX * BY) k_residual(const double* __restrict__ u, const double* __restrict__ rhs,
+                                                      double* __restrict__ r, int n, double inv_h6,
+                                                      double* partials)
+{
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const long long sy = n, sz = (long long)n * n;
+    double mx = 0.0, ss = 0.0;
+    for (int k = blockIdx.z; k < n; k += gridDim.z) {
+        if (i < n && j < n) {
+            const long long p = lin(i, j, k, n);
+            double val = 0.0;
+            if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
+                const HessS H = gather_hess(u, p, sy, sz, u[p]);
+                val = fma(-det0(H), inv_h6, rhs[p]);
+                mx = fmax(mx, fabs(val));
+                ss = fma(val, val, ss);
+            }
+            r[p] = val;
+        }
+    }
+    if (partials) block_reduce_store(mx, ss, partials, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(BX * BY) k_norm_partials(const double* __restrict__ v, int n, double* partials)
+{
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    double mx = 0.0, ss = 0.0;
+    for (int k = blockIdx.z; k < n; k += gridDim.z) {
+        if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
+            const double x = v[lin(i, j, k, n)];
+            mx = fmax(mx, fabs(x));
+            ss = fma(x, x, ss);
+        }
+    }
+    block_reduce_store(mx, ss, partials, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+}
+
+// One block folds the partials in a fixed order: out2 = (max, sqrt(h^3 sum)).
+__global__ void __launch_bounds__(256) k_norm_final(const double* __restrict__ partials, int count, double h3,
+                                                    double* out2)
+{
+    __shared__ double smx[256], sss[256];
+    double mx = 0.0, ss = 0.0;
+    for (int q = threadIdx.x; q < count; q += 256) {
+        mx = fmax(mx, partials[2 * q]);
+        ss += partials[2 * q + 1];
+    }
+    smx[threadIdx.x] = mx;
+    sss[threadIdx.x] = ss;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            smx[threadIdx.x] = fmax(smx[threadIdx.x], smx[threadIdx.x + w]);
+            sss[threadIdx.x] += sss[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out2[0] = smx[0];
+        out2[1] = sqrt(h3 * sss[0]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Grid transfers.  Coarse point (I, J, K) sits on fine point (2I, 2J, 2K).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double weighted_restrict(const double* __restrict__ v, long long p, long long sy,
+                                                    long long sz, int kind)
+{
+    if (kind == 0) {   // half weighting: (6 centre + 6 faces) / 12
+        const double faces = (v[p + 1] + v[p - 1]) + (v[p + sy] + v[p - sy]) + (v[p + sz] + v[p - sz]);
+        return fma(6.0, v[p], faces) * (1.0 / 12.0);
+    }
+    // full weighting: separable (1 2 1)/4 along each axis
+    double acc = 0.0;
+    #pragma unroll
+    for (int dk = -1; dk <= 1; ++dk) {
+        double plane = 0.0;
+        #pragma unroll
+        for (int dj = -1; dj <= 1; ++dj) {
+            const long long q = p + dk * sz + dj * sy;
+            const double row = v[q - 1] + 2.0 * v[q] + v[q + 1];
+            plane += (dj == 0 ? 2.0 : 1.0) * row;
+        }
+        acc += (dk == 0 ? 2.0 : 1.0) * plane;
+    }
+    return acc * (1.0 / 64.0);
+}
+
+// Coarse-grid outputs, any may be null: rc = I r (0 on the shell);
+// wc = approximation restriction of uf; uc = copy of wc (coarse iterate).
+__global__ void __launch_bounds__(BX * BY) k_restrict(const double* __restrict__ uf, const double* __restrict__ rf,
+                                                      int nf, double* __restrict__ wc, double* __restrict__ uc,
+                                                      double* __restrict__ rc, int nc, int kind, int approx)
+{
+    const int I = blockIdx.x * BX + threadIdx.x;
+    const int J = blockIdx.y * BY + threadIdx.y;
+    const int K = blockIdx.z;
+    if (I >= nc || J >= nc) return;
+    const long long pc = lin(I, J, K, nc);
+    const long long pf = lin(2 * I, 2 * J, 2 * K, nf);
+    const long long sy = nf, sz = (long long)nf * nf;
+    const bool interior = I > 0 && J > 0 && K > 0 && I < nc - 1 && J < nc - 1 && K < nc - 1;
+    if (rc) rc[pc] = interior ? weighted_restrict(rf, pf, sy, sz, kind) : 0.0;
+    if (uf) {
+        const double w = (interior && approx == 1) ? weighted_restrict(uf, pf, sy, sz, kind) : uf[pf];
+        if (wc) wc[pc] = w;
+        if (uc) uc[pc] = w;
+    }
+}
+
+// b_H = det(D^2_H w_H) + r_H on the interior, 0 on the shell.
+__global__ void __launch_bounds__(BX * BY) k_coarse_rhs(const double* __restrict__ wc, const double* __restrict__ rc,
+                                                        double* __restrict__ bc, int nc, double inv_H6)
+{
+    const int I = blockIdx.x * BX + threadIdx.x;
+    const int J = blockIdx.y * BY + threadIdx.y;
+    const int K = blockIdx.z;
+    if (I >= nc || J >= nc) return;
+    const long long p = lin(I, J, K, nc);
+    double b = 0.0;
+    if (I > 0 && J > 0 && K > 0 && I < nc - 1 && J < nc - 1 && K < nc - 1) {
+        const HessS H = gather_hess(wc, p, nc, (long long)nc * nc, wc[p]);
+        b = fma(det0(H), inv_H6, rc[p]);
+    }
+    bc[p] = b;
+}
+
+// Trilinear interpolation at fine interior points: along each axis an even
+// index sits on a coarse point, an odd one halfway between two.
+// add != 0: uf += I(uc - wc) (correction); add == 0: uf = I(uc).
+__global__ void __launch_bounds__(BX * BY) k_prolong(const double* __restrict__ uc, const double* __restrict__ wc,
+                                                     int nc, double* __restrict__ uf, int nf, int add)
+{
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i < 1 || j < 1 || k < 1 || i > nf - 2 || j > nf - 2 || k > nf - 2) return;
+    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+    const int oi = i & 1, oj = j & 1, ok = k & 1;
+    double s = 0.0;
+    for (int dk = 0; dk <= ok; ++dk)
+        for (int dj = 0; dj <= oj; ++dj)
+            for (int di = 0; di <= oi; ++di) {
+                const long long q = lin(I0 + di, J0 + dj, K0 + dk, nc);
+                s += add ? (uc[q] - wc[q]) : uc[q];
+            }
+    const double w = 1.0 / (double)(1 << (oi + oj + ok));
+    const long long p = lin(i, j, k, nf);
+    uf[p] = add ? fma(s, w, uf[p]) : s * w;
+}
+
+__global__ void k_inject(const double* __restrict__ vf, int nf, double* __restrict__ vc, int nc)
+{
+    const int I = blockIdx.x * BX + threadIdx.x;
+    const int J = blockIdx.y * BY + threadIdx.y;
+    const int K = blockIdx.z;
+    if (I >= nc || J >= nc) return;
+    vc[lin(I, J, K, nc)] = vf[lin(2 * I, 2 * J, 2 * K, nf)];
+}
+
+__global__ void k_zero_interior(double* u, int n)
+{
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i < 1 || j < 1 || k < 1 || i > n - 2 || j > n - 2 || k > n - 2) return;
+    u[lin(i, j, k, n)] = 0.0;
+}
+
+// rhs := f, u := g (whole grids); counts interior points with f not finite
+// or f <= 0 and shell points with g not finite.
+__global__ void k_copy_rhs_bc(const double* __restrict__ f, const double* __restrict__ g, double* __restrict__ rhs,
+                              double* __restrict__ u, int n, int* bad)
+{
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= n || j >= n) return;
+    const long long p = lin(i, j, k, n);
+    const double fv = f[p], gv = g[p];
+    rhs[p] = fv;
+    u[p] = gv;
+    const bool interior = i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1;
+    const bool ok = interior ? (isfinite(fv) && fv > 0.0 && isfinite(gv)) : isfinite(gv);
+    if (!ok) atomicAdd(bad, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest grid: one thread block sweeps the whole grid in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int COARSE_THREADS = 256;
+
+__device__ __forceinline__ HessS gather_hess_plain(const double* u, int p, int sy, int sz, double v0)
+{
+    const double* q = u + p;
+    const double a = q[1] + q[-1];
+    const double b = q[sy] + q[-sy];
+    const double c = q[sz] + q[-sz];
+    const double r4 = (q[sy + 1] + q[-sy - 1]) - (q[sy - 1] + q[-sy + 1]);
+    const double s4 = (q[sz + 1] + q[-sz - 1]) - (q[sz - 1] + q[-sz + 1]);
+    const double t4 = (q[sz + sy] + q[-sz - sy]) - (q[sy - sz] + q[-sy + sz]);
+    HessS H;
+    H.A = fma(-2.0, v0, a);
+    H.B = fma(-2.0, v0, b);
+    H.C = fma(-2.0, v0, c);
+    H.R = 0.25 * r4;
+    H.S = 0.25 * s4;
+    H.T = 0.25 * t4;
+    return H;
+}
+
+__global__ void __launch_bounds__(COARSE_THREADS) k_coarsest(double* u, const double* __restrict__ rhs, int n,
+                                                             double h6, int sweeps, unsigned long long* events)
+{
+    extern __shared__ double sm[];
+    const int m = n * n * n;
+    double* su = sm;
+    double* sr = sm + m;
+    __shared__ double red[COARSE_THREADS / 32][2];
+    __shared__ int stop;
+    for (int q = threadIdx.x; q < m; q += COARSE_THREADS) { su[q] = u[q]; sr[q] = rhs[q]; }
+    __syncthreads();
+    const int max_sweeps = sweeps > 0 ? sweeps : 100;
+    unsigned long long ev = 0;
+    for (int s = 0; s < max_sweeps; ++s) {
+        double du = 0.0, um = 0.0;
+        for (int c = 0; c < 8; ++c) {
+            const int pi = c & 1, pj = (c >> 1) & 1, pk = (c >> 2) & 1;
+            const int ni = colour_count(n, pi), nj = colour_count(n, pj), nk = colour_count(n, pk);
+            const int cnt = (ni > 0 && nj > 0 && nk > 0) ? ni * nj * nk : 0;
+            for (int t = threadIdx.x; t < cnt; t += COARSE_THREADS) {
+                const int i = (pi ? 1 : 2) + 2 * (t % ni);
+                const int j = (pj ? 1 : 2) + 2 * ((t / ni) % nj);
+                const int k = (pk ? 1 : 2) + 2 * (t / (ni * nj));
+                const int p = (k * n + j) * n + i;
+                const double v0 = su[p];
+                const HessS H = gather_hess_plain(su, p, n, n * n, v0);
+                bool nonconvex = false;
+                const double z = smallest_root(H, h6 * sr[p], &nonconvex);
+                const double v = fma(0.5, z, v0);
+                su[p] = v;
+                du = fmax(du, fabs(v - v0));
+                um = fmax(um, fabs(v));
+                ev += nonconvex ? 1ull : 0ull;
+            }
+            __syncthreads();
+        }
+        if (sweeps > 0) continue;
+        // converged when max |du| <= 1e-14 max |u| over this sweep's updates
+        for (int o = 16; o > 0; o >>= 1) {
+            du = fmax(du, __shfl_down_sync(0xffffffffu, du, o));
+            um = fmax(um, __shfl_down_sync(0xffffffffu, um, o));
+        }
+        if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5][0] = du; red[threadIdx.x >> 5][1] = um; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < COARSE_THREADS / 32; ++w) { a = fmax(a, red[w][0]); b = fmax(b, red[w][1]); }
+            stop = (a <= 1e-14 * b) ? 1 : 0;
+        }
+        __syncthreads();
+        if (stop) break;
+    }
+    for (int q = threadIdx.x; q < m; q += COARSE_THREADS) u[q] = su[q];
+    if (events && ev) atomicAdd(events, ev);
+}
+
+}  // namespace
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static inline double pow6(double h) { const double h2 = h * h; return h2 * h2 * h2; }
+
+cudaError_t launch_smooth(double* u, const double* rhs, int n, double h, int nsweeps,
+                          unsigned long long* events, cudaStream_t s)
+{
+    const double h6 = pow6(h);
+    for (int sw = 0; sw < nsweeps; ++sw) {
+        cudaError_t e;
+        if ((e = launch_colour<0>(u, rhs, n, h6, events, s)) != cudaSuccess) return e;
+        if ((e = launch_colour<1>(u, rhs, n, h6, events, s)) != cudaSuccess) return e;
+        if ((e = launch_colour<2>(u, rhs, n, h6, events, s)) != cudaSuccess) return e;
+        if ((e = launch_colour<3>(u, rhs, n, h6, events, s)) != cudaSuccess) return e;
+        if ((e = launch_colour<4>(u, rhs, n, h6, events, s)) != cudaSuccess) return e;
+        if ((e = launch_colour<5>(u, rhs, n, h6, events, s)) != cudaSuccess) return e;
+        if ((e = launch_colour<6>(u, rhs, n, h6, events, s)) != cudaSuccess) return e;
+        if ((e = launch_colour<7>(u, rhs, n, h6, events, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int residual_partial_count(int n)
+{
+    const dim3 g = reduce_grid(n);
+    return (int)(g.x * g.y * g.z);
+}
+
+int norm_partial_count(int n) { return residual_partial_count(n); }
+
+cudaError_t launch_residual(const double* u, const double* rhs, double* r, int n, double h,
+                            double* partials, cudaStream_t s)
+{
+    count_launches(1);
+    k_residual<<<reduce_grid(n), dim3(BX, BY), 0, s>>>(u, rhs, r, n, 1.0 / pow6(h), partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm_partials(const double* v, int n, double* partials, cudaStream_t s)
+{
+    count_launches(1);
+    k_norm_partials<<<reduce_grid(n), dim3(BX, BY), 0, s>>>(v, n, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm_final(const double* partials, int count, double h, double* out2, cudaStream_t s)
+{
+    count_launches(1);
+    k_norm_final<<<1, 256, 0, s>>>(partials, count, h * h * h, out2);
+    return cudaGetLastError();
+}
+
+static dim3 grid_of(int n) { return dim3((n + BX - 1) / BX, (n + BY - 1) / BY, n); }
+
+cudaError_t launch_restrict_residual(const double* rf, int nf, double* rc, int kind, cudaStream_t s)
+{
+    const int nc = (nf + 1) / 2;
+    count_launches(1);
+    k_restrict<<<grid_of(nc), dim3(BX, BY), 0, s>>>(nullptr, rf, nf, nullptr, nullptr, rc, nc, kind, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_solution(const double* uf, int nf, double* uc, int approx, int kind, cudaStream_t s)
+{
+    const int nc = (nf + 1) / 2;
+    count_launches(1);
+    k_restrict<<<grid_of(nc), dim3(BX, BY), 0, s>>>(uf, nullptr, nf, nullptr, uc, nullptr, nc, kind, approx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_level(const double* uf, const double* rf, int nf, double* wc, double* uc, double* rc,
+                                  int kind, int approx, cudaStream_t s)
+{
+    const int nc = (nf + 1) / 2;
+    count_launches(1);
+    k_restrict<<<grid_of(nc), dim3(BX, BY), 0, s>>>(uf, rf, nf, wc, uc, rc, nc, kind, approx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_rhs(const double* wc, const double* rc, double* bc, int nc, double H, cudaStream_t s)
+{
+    count_launches(1);
+    k_coarse_rhs<<<grid_of(nc), dim3(BX, BY), 0, s>>>(wc, rc, bc, nc, 1.0 / pow6(H));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(const double* uc, const double* wc, int nc, double* uf, cudaStream_t s)
+{
+    const int nf = 2 * nc - 1;
+    count_launches(1);
+    k_prolong<<<grid_of(nf), dim3(BX, BY), 0, s>>>(uc, wc, nc, uf, nf, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interpolate(const double* uc, int nc, double* uf, cudaStream_t s)
+{
+    const int nf = 2 * nc - 1;
+    count_launches(1);
+    k_prolong<<<grid_of(nf), dim3(BX, BY), 0, s>>>(uc, nullptr, nc, uf, nf, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject(const double* vf, int nf, double* vc, cudaStream_t s)
+{
+    const int nc = (nf + 1) / 2;
+    count_launches(1);
+    k_inject<<<grid_of(nc), dim3(BX, BY), 0, s>>>(vf, nf, vc, nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_interior(double* u, int n, cudaStream_t s)
+{
+    count_launches(1);
+    k_zero_interior<<<grid_of(n), dim3(BX, BY), 0, s>>>(u, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_rhs_bc(const double* f, const double* g, double* rhs, double* u, int n, int* bad,
+                               cudaStream_t s)
+{
+    count_launches(1);
+    k_copy_rhs_bc<<<grid_of(n), dim3(BX, BY), 0, s>>>(f, g, rhs, u, n, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarsest(double* u, const double* rhs, int n, double h, int sweeps,
+                            unsigned long long* events, cudaStream_t s)
+{
+    const size_t smem = 2 * sizeof(double) * (size_t)n * n * n;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_coarsest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    count_launches(1);
+    k_coarsest<<<1, COARSE_THREADS, smem, s>>>(u, rhs, n, pow6(h), sweeps, events);
+    return cudaGetLastError();
+}
+
+}  // namespace ma

@@ -1,0 +1,224 @@
+// ma_point.cuh -- per-point arithmetic of the nonlinear Gauss-Seidel smoother
+// (Section 2 of Liu, Froese, Oberman, Xiao): the 19-point stencil gather, the
+// discrete Hessian, and the smallest-real-root selection of Eq. (realroots).
+//
+// Working units.  Everything is kept "h^2-scaled": Hs = h^2 D^2(u^h; v0),
+// the discrete Hessian at the current centre value v0 times h^2, whose
+// entries are exactly a - 2 v0, b - 2 v0, c - 2 v0, r, s, t with a..t the
+// neighbour combinations defined after Eq. (MA3Dcubic).  With the centre
+// moved to v = v0 + zeta / 2 the local equation P3(v) = 0 is
+//     g(zeta) = det(Hs - zeta I) - h^6 rhs = 0,
+// the same cubic as Eq. (MA3Dcubic) in the shifted variable (exact algebra;
+// it avoids the cancellation of the monomial coefficients noted in the
+// round-off remark of Example 4).  Theorem 2.2: for rhs > 0, g is decreasing
+// and convex left of the smallest eigenvalue l1 of Hs, g(l1) < 0, and the
+// smallest real root is the unique root below l1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace ma {
+
+struct HessS {   // h^2-scaled symmetric Hessian: diagonal A, B, C; off-diagonal R (xy), S (xz), T (yz)
+    double A, B, C, R, S, T;
+};
+
+struct HessSf {
+    float A, B, C, R, S, T;
+};
+
+// 19-point gather at linear index p with strides sy (one j step) and sz
+// (one k step); v0 is the current centre value.  Neighbour loads go through
+// the read-only path: no launch writes a point and reads it as a neighbour.
+__device__ __forceinline__ HessS gather_hess(const double* __restrict__ u, long long p, long long sy,
+                                             long long sz, double v0)
+{
+    const double* q = u + p;
+    const double a = __ldg(q + 1) + __ldg(q - 1);
+    const double b = __ldg(q + sy) + __ldg(q - sy);
+    const double c = __ldg(q + sz) + __ldg(q - sz);
+    const double r4 = (__ldg(q + sy + 1) + __ldg(q - sy - 1)) - (__ldg(q + sy - 1) + __ldg(q - sy + 1));
+    const double s4 = (__ldg(q + sz + 1) + __ldg(q - sz - 1)) - (__ldg(q + sz - 1) + __ldg(q - sz + 1));
+    const double t4 = (__ldg(q + sz + sy) + __ldg(q - sz - sy)) - (__ldg(q + sy - sz) + __ldg(q - sy + sz));
+    HessS H;
+    H.A = fma(-2.0, v0, a);
+    H.B = fma(-2.0, v0, b);
+    H.C = fma(-2.0, v0, c);
+    H.R = 0.25 * r4;
+    H.S = 0.25 * s4;
+    H.T = 0.25 * t4;
+    return H;
+}
+
+// det(Hs - z I) by cofactor expansion along the first row.
+__device__ __forceinline__ double det_shift(const HessS& H, double z)
+{
+    const double a = H.A - z, b = H.B - z, c = H.C - z;
+    const double c1 = fma(b, c, -H.T * H.T);
+    const double c2 = fma(H.R, c, -H.S * H.T);
+    const double c3 = fma(H.R, H.T, -b * H.S);
+    return fma(a, c1, fma(-H.R, c2, H.S * c3));
+}
+
+__device__ __forceinline__ double det0(const HessS& H)
+{
+    const double c1 = fma(H.B, H.C, -H.T * H.T);
+    const double c2 = fma(H.R, H.C, -H.S * H.T);
+    const double c3 = fma(H.R, H.T, -H.B * H.S);
+    return fma(H.A, c1, fma(-H.R, c2, H.S * c3));
+}
+
+// Sum of the principal 2x2 minors of (Hs - z I); g'(z) = -minors_shift(z).
+__device__ __forceinline__ double minors_shift(const HessS& H, double z)
+{
+    const double a = H.A - z, b = H.B - z, c = H.C - z;
+    return fma(a, b, -H.R * H.R) + fma(a, c, -H.S * H.S) + fma(b, c, -H.T * H.T);
+}
+
+__device__ __forceinline__ float det_shift_f(const HessSf& H, float z)
+{
+    const float a = H.A - z, b = H.B - z, c = H.C - z;
+    const float c1 = fmaf(b, c, -H.T * H.T);
+    const float c2 = fmaf(H.R, c, -H.S * H.T);
+    const float c3 = fmaf(H.R, H.T, -b * H.S);
+    return fmaf(a, c1, fmaf(-H.R, c2, H.S * c3));
+}
+
+__device__ __forceinline__ float minors_shift_f(const HessSf& H, float z)
+{
+    const float a = H.A - z, b = H.B - z, c = H.C - z;
+    return fmaf(a, b, -H.R * H.R) + fmaf(a, c, -H.S * H.S) + fmaf(b, c, -H.T * H.T);
+}
+
+// Lower bound of the smallest eigenvalue (Gershgorin discs).
+template <typename M, typename F>
+__device__ __forceinline__ F gershgorin_low(const M& H)
+{
+    const F g0 = H.A - fabs(H.R) - fabs(H.S);
+    const F g1 = H.B - fabs(H.R) - fabs(H.T);
+    const F g2 = H.C - fabs(H.S) - fabs(H.T);
+    return fmin(g0, fmin(g1, g2));
+}
+
+// Sylvester's criterion: Hs positive definite.
+template <typename M, typename F>
+__device__ __forceinline__ bool is_pd(const M& H, F det)
+{
+    return H.A > F(0) && H.A * H.B - H.R * H.R > F(0) && det > F(0);
+}
+
+// FP64 monotone Newton from a point left of the root (g >= 0 there): for
+// rhs > 0 the iterates increase to the unique root below l1 (convexity).
+// Used when the FP32 first pass is not trustworthy (degenerate or far from
+// convex); each step costs an FP64 division.
+__device__ __noinline__ double root_f64_monotone(const HessS H, double rhs6)
+{
+    double z = gershgorin_low<HessS, double>(H) - cbrt(rhs6);
+    for (int it = 0; it < 200; ++it) {
+        const double g = det_shift(H, z) - rhs6;
+        const double m = minors_shift(H, z);
+        if (!(g > 0.0) || !(m > 0.0)) break;
+        const double zn = z + g / m;
+        if (!(zn > z)) break;
+        z = zn;
+    }
+    return z;
+}
+
+// rhs <= 0: no root lies below l1; Eq. (realroots) taken literally -- the
+// smallest real root of det(Hs - z I) = rhs6, i.e. of
+// z^3 - T z^2 + M z - (D - rhs6) with T, M, D the trace, minor sum and
+// determinant of Hs.  Trigonometric form when there are three real roots,
+// Cardano's formula when there is one, then two FP64 Newton polishes.
+__device__ __noinline__ double root_f64_all_real_min(const HessS H, double rhs6)
+{
+    const double T = H.A + H.B + H.C;
+    const double M = minors_shift(H, 0.0);
+    const double D = det0(H);
+    const double a2 = -T, a1 = M, a0 = rhs6 - D;   // z^3 + a2 z^2 + a1 z + a0
+    const double p = a1 - a2 * a2 / 3.0;
+    const double q = 2.0 * a2 * a2 * a2 / 27.0 - a2 * a1 / 3.0 + a0;
+    const double disc = 0.25 * q * q + p * p * p / 27.0;
+    double roots[3];
+    int nr;
+    if (p < 0.0 && disc <= 0.0) {
+        const double m = 2.0 * sqrt(-p / 3.0);
+        double arg = 1.5 * q / p * sqrt(-3.0 / p);
+        arg = fmin(1.0, fmax(-1.0, arg));
+        const double phi = acos(arg) / 3.0;
+        const double tp = 2.0943951023931954923;   // 2 pi / 3
+        roots[0] = m * cos(phi) - a2 / 3.0;
+        roots[1] = m * cos(phi - tp) - a2 / 3.0;
+        roots[2] = m * cos(phi - 2.0 * tp) - a2 / 3.0;
+        nr = 3;
+    } else {
+        const double sq = sqrt(fmax(disc, 0.0));
+        roots[0] = cbrt(-0.5 * q + sq) + cbrt(-0.5 * q - sq) - a2 / 3.0;
+        nr = 1;
+    }
+    double best = INFINITY;
+    for (int k = 0; k < nr; ++k) {
+        double z = roots[k];
+        for (int it = 0; it < 2; ++it) {
+            const double g = det_shift(H, z) - rhs6;
+            const double m = minors_shift(H, z);
+            if (m == 0.0) break;
+            const double zn = z + g / m;
+            if (!isfinite(zn)) break;
+            z = zn;
+        }
+        best = fmin(best, z);
+    }
+    return best;
+}
+
+// Smallest real root zeta of det(Hs - zeta I) = rhs6 (rhs6 = h^6 rhs).
+//
+// Fast path (rhs6 > 0): Newton in FP32 on the FP32-rounded cubic -- from
+// zeta = 0 when Hs is positive definite (0 < l1, so Newton converges to the
+// root below l1 with at most one step overshooting to its left), else from
+// the Gershgorin bound minus rhs^(1/3) (left of the root) -- then one Newton
+// correction whose residual g(zeta) is evaluated in FP64 with the FP32
+// derivative.  That correction contracts the FP32 error by the derivative's
+// relative error (~1e-7), leaving the root at FP64 accuracy; the fixed point
+// of the sweep is therefore the FP64 discrete solution.  Degenerate cases
+// (tiny derivative, no convergence, non-finite) take the FP64 path.
+// *nonconvex is set when rhs6 <= 0.
+__device__ __forceinline__ double smallest_root(const HessS& H, double rhs6, bool* nonconvex)
+{
+    if (!(rhs6 > 0.0)) {
+        *nonconvex = true;
+        return root_f64_all_real_min(H, rhs6);
+    }
+    HessSf F;
+    F.A = (float)H.A; F.B = (float)H.B; F.C = (float)H.C;
+    F.R = (float)H.R; F.S = (float)H.S; F.T = (float)H.T;
+    const float r6 = (float)rhs6;
+    const float scale = fabsf(F.A) + fabsf(F.B) + fabsf(F.C) + fabsf(F.R) + fabsf(F.S) + fabsf(F.T);
+    const float d0 = det_shift_f(F, 0.0f);
+    float z = is_pd<HessSf, float>(F, d0) ? 0.0f : gershgorin_low<HessSf, float>(F) - cbrtf(r6);
+    bool conv = false;
+    float m = 0.0f;
+    for (int it = 0; it < 60; ++it) {
+        const float g = det_shift_f(F, z) - r6;
+        m = minors_shift_f(F, z);
+        const float dz = g / m;
+        z += dz;
+        if (!isfinite(z)) break;
+        // FP32 resolves the root to ~1e-7 of the entries' size; stop there.
+        if (fabsf(dz) <= 2e-6f * scale) { conv = true; break; }
+    }
+    m = minors_shift_f(F, z);
+    // m = -g'(root); a small m (near-degenerate Hessian at the root) makes
+    // the FP32 root and derivative too inaccurate for one FP64 correction.
+    if (!conv || !(m > 0.05f * scale * scale) || !(r6 > 0.0f)) {
+        return root_f64_monotone(H, rhs6);
+    }
+    double zd = (double)z;
+    const double g64 = det_shift(H, zd) - rhs6;
+    zd = fma(g64, (double)(1.0f / m), zd);
+    return zd;
+}
+
+}  // namespace ma

@@ -1,0 +1,306 @@
+"""Python binding of libma (include/ma.h): ctypes argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own; a non-zero ma_status raises MAError carrying
+ma_last_error_string().  Device buffers are torch CUDA tensors (float64,
+contiguous) or raw device addresses; streams are torch.cuda.Stream objects or
+None for the current stream.  There is no CPU fallback: if libma.so cannot be
+built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+from . import build as _build
+
+MA_OK, MA_ERR_INVALID_ARG, MA_ERR_OOM, MA_ERR_CUDA, MA_ERR_NOT_CONVERGED, MA_ERR_NONFINITE = range(6)
+MA_HALF_WEIGHTING, MA_FULL_WEIGHTING = 0, 1
+MA_APPROX_INJECTION, MA_APPROX_WEIGHTED = 0, 1
+MA_FP64, MA_MIXED = 0, 1
+MA_NORM_MAX, MA_NORM_L2 = 0, 1
+MA_INIT_FMG, MA_INIT_ZERO, MA_INIT_KEEP = 0, 1, 2
+
+STATUS_NAMES = {0: "MA_OK", 1: "MA_ERR_INVALID_ARG", 2: "MA_ERR_OOM", 3: "MA_ERR_CUDA",
+                4: "MA_ERR_NOT_CONVERGED", 5: "MA_ERR_NONFINITE"}
+
+
+class MAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ma_hier_desc(C.Structure):
+    _fields_ = [("n", C.c_int), ("x0", C.c_double * 3), ("len", C.c_double), ("nu1", C.c_int),
+                ("nu2", C.c_int), ("coarsest_n", C.c_int), ("restrict_kind", C.c_int),
+                ("approx_restrict", C.c_int), ("precision", C.c_int), ("coarse_sweeps", C.c_int)]
+
+
+class ma_solve_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("norm", C.c_int), ("relative", C.c_int), ("max_cycles", C.c_int),
+                ("init", C.c_int)]
+
+
+class ma_solve_result(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("res0", C.c_double), ("res", C.c_double), ("status", C.c_int),
+                ("floor_reached", C.c_int), ("nonconvex_root_events", C.c_longlong)]
+
+
+_vp = C.c_void_p
+_SIGS = {
+    "ma_hierarchy_footprint": [C.POINTER(ma_hier_desc), C.POINTER(C.c_size_t)],
+    "ma_create_hierarchy": [C.POINTER(ma_hier_desc), _vp, C.c_size_t, _vp, C.POINTER(_vp)],
+    "ma_set_rhs_bc": [_vp, _vp, _vp],
+    "ma_vcycle": [_vp, C.c_int],
+    "ma_solve": [_vp, C.POINTER(ma_solve_opts), C.POINTER(ma_solve_result)],
+    "ma_residual_norm": [_vp, C.c_int, C.POINTER(C.c_double)],
+    "ma_get_solution": [_vp, _vp],
+    "ma_set_solution": [_vp, _vp],
+    "ma_hierarchy_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)],
+    "ma_destroy_hierarchy": [_vp],
+    "ma_smooth": [_vp, _vp, C.c_int, C.c_double, C.c_int, _vp, _vp],
+    "ma_residual": [_vp, _vp, _vp, C.c_int, C.c_double, _vp],
+    "ma_restrict_residual": [_vp, C.c_int, _vp, C.c_int, _vp],
+    "ma_restrict_solution": [_vp, C.c_int, _vp, C.c_int, C.c_int, _vp],
+    "ma_coarse_rhs": [_vp, _vp, _vp, C.c_int, C.c_double, _vp],
+    "ma_prolong_add": [_vp, _vp, C.c_int, _vp, _vp],
+    "ma_interpolate": [_vp, C.c_int, _vp, _vp],
+    "ma_coarsest_solve": [_vp, _vp, C.c_int, C.c_double, C.c_int, _vp, _vp],
+    "ma_norm_scratch_bytes": [C.c_int, C.POINTER(C.c_size_t)],
+    "ma_norm": [_vp, C.c_int, C.c_double, _vp, C.c_size_t, C.POINTER(C.c_double), _vp],
+    "ma_kernel_launch_count": [C.POINTER(C.c_ulonglong)],
+}
+# Declared in include/ma.h; the test suite checks that the library exports them.
+EXPORTED = sorted(list(_SIGS) + ["ma_last_error_string"])
+
+_lib = None
+
+
+def load():
+    """Build (if stale) and load libma.so; raises if that is impossible."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(str(path))
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.ma_last_error_string.argtypes = []
+        L.ma_last_error_string.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st: int) -> int:
+    if st != MA_OK:
+        msg = load().ma_last_error_string().decode(errors="replace")
+        raise MAError(st, msg)
+    return st
+
+
+def _ptr(x) -> int | None:
+    """Device address of a torch tensor (or an int address, or None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return x.data_ptr()
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ---- hierarchy ------------------------------------------------------------
+
+def ma_hierarchy_footprint(desc: ma_hier_desc) -> int:
+    b = C.c_size_t(0)
+    _check(load().ma_hierarchy_footprint(C.byref(desc), C.byref(b)))
+    return b.value
+
+
+def ma_create_hierarchy(desc: ma_hier_desc, workspace, nbytes: int, stream=None) -> int:
+    h = _vp()
+    _check(load().ma_create_hierarchy(C.byref(desc), _ptr(workspace), nbytes, _stream(stream), C.byref(h)))
+    return h.value
+
+
+def ma_set_rhs_bc(hier: int, f, g) -> None:
+    _check(load().ma_set_rhs_bc(hier, _ptr(f), _ptr(g)))
+
+
+def ma_vcycle(hier: int, ncycles: int = 1) -> None:
+    _check(load().ma_vcycle(hier, ncycles))
+
+
+def ma_solve(hier: int, opts: ma_solve_opts, raise_on_error: bool = True) -> ma_solve_result:
+    res = ma_solve_result()
+    st = load().ma_solve(hier, C.byref(opts), C.byref(res))
+    if raise_on_error:
+        _check(st)
+    return res
+
+
+def ma_residual_norm(hier: int, norm: int = MA_NORM_MAX) -> float:
+    out = C.c_double(0.0)
+    _check(load().ma_residual_norm(hier, norm, C.byref(out)))
+    return out.value
+
+
+def ma_get_solution(hier: int, u) -> None:
+    _check(load().ma_get_solution(hier, _ptr(u)))
+
+
+def ma_set_solution(hier: int, u) -> None:
+    _check(load().ma_set_solution(hier, _ptr(u)))
+
+
+def ma_hierarchy_info(hier: int):
+    n, L, b = C.c_int(0), C.c_int(0), C.c_size_t(0)
+    _check(load().ma_hierarchy_info(hier, C.byref(n), C.byref(L), C.byref(b)))
+    return n.value, L.value, b.value
+
+
+def ma_destroy_hierarchy(hier: int) -> None:
+    _check(load().ma_destroy_hierarchy(hier))
+
+
+def ma_kernel_launch_count() -> int:
+    out = C.c_ulonglong(0)
+    _check(load().ma_kernel_launch_count(C.byref(out)))
+    return out.value
+
+
+def ma_last_error_string() -> str:
+    return load().ma_last_error_string().decode(errors="replace")
+
+
+# ---- single steps ---------------------------------------------------------
+
+def ma_smooth(u, rhs, n: int, h: float, nsweeps: int = 1, events=None, stream=None) -> None:
+    _check(load().ma_smooth(_ptr(u), _ptr(rhs), n, h, nsweeps, _ptr(events), _stream(stream)))
+
+
+def ma_residual(u, rhs, r, n: int, h: float, stream=None) -> None:
+    _check(load().ma_residual(_ptr(u), _ptr(rhs), _ptr(r), n, h, _stream(stream)))
+
+
+def ma_restrict_residual(rf, nf: int, rc, kind: int, stream=None) -> None:
+    _check(load().ma_restrict_residual(_ptr(rf), nf, _ptr(rc), kind, _stream(stream)))
+
+
+def ma_restrict_solution(uf, nf: int, uc, approx: int, kind: int, stream=None) -> None:
+    _check(load().ma_restrict_solution(_ptr(uf), nf, _ptr(uc), approx, kind, _stream(stream)))
+
+
+def ma_coarse_rhs(wc, rc, bc, nc: int, H: float, stream=None) -> None:
+    _check(load().ma_coarse_rhs(_ptr(wc), _ptr(rc), _ptr(bc), nc, H, _stream(stream)))
+
+
+def ma_prolong_add(uc, wc, nc: int, uf, stream=None) -> None:
+    _check(load().ma_prolong_add(_ptr(uc), _ptr(wc), nc, _ptr(uf), _stream(stream)))
+
+
+def ma_interpolate(uc, nc: int, uf, stream=None) -> None:
+    _check(load().ma_interpolate(_ptr(uc), nc, _ptr(uf), _stream(stream)))
+
+
+def ma_coarsest_solve(u, rhs, n: int, h: float, sweeps: int = 0, events=None, stream=None) -> None:
+    _check(load().ma_coarsest_solve(_ptr(u), _ptr(rhs), n, h, sweeps, _ptr(events), _stream(stream)))
+
+
+def ma_norm_scratch_bytes(n: int) -> int:
+    b = C.c_size_t(0)
+    _check(load().ma_norm_scratch_bytes(n, C.byref(b)))
+    return b.value
+
+
+def ma_norm(v, n: int, h: float, scratch, scratch_bytes: int, stream=None):
+    out = (C.c_double * 2)()
+    _check(load().ma_norm(_ptr(v), n, h, _ptr(scratch), scratch_bytes, out, _stream(stream)))
+    return out[0], out[1]
+
+
+# ---- convenience: a hierarchy whose workspace is a torch tensor --------------
+
+@dataclass
+class SolveResult:
+    cycles: int
+    res0: float
+    res: float
+    status: int
+    floor_reached: bool
+    nonconvex_root_events: int
+
+
+def make_desc(n: int, length: float = 1.0, x0=(0.0, 0.0, 0.0), nu1: int = 2, nu2: int = 2,
+              coarsest_n: int = 5, restrict_kind: int = MA_FULL_WEIGHTING,
+              approx_restrict: int = MA_APPROX_WEIGHTED, precision: int = MA_FP64,
+              coarse_sweeps: int = 0) -> ma_hier_desc:
+    d = ma_hier_desc()
+    d.n = n
+    d.x0[0], d.x0[1], d.x0[2] = x0
+    d.len = length
+    d.nu1, d.nu2 = nu1, nu2
+    d.coarsest_n = coarsest_n
+    d.restrict_kind = restrict_kind
+    d.approx_restrict = approx_restrict
+    d.precision = precision
+    d.coarse_sweeps = coarse_sweeps
+    return d
+
+
+class Hierarchy:
+    """Owns a torch uint8 workspace tensor and the hierarchy built in it."""
+
+    def __init__(self, desc: ma_hier_desc, stream=None, device=None):
+        import torch
+        self.desc = desc
+        self.nbytes = ma_hierarchy_footprint(desc)
+        self.workspace = torch.empty(self.nbytes + 256, dtype=torch.uint8,
+                                     device=device or torch.device("cuda"))
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self.stream = stream
+        self.handle = ma_create_hierarchy(desc, aligned, self.nbytes, stream)
+
+    def set_rhs_bc(self, f, g):
+        ma_set_rhs_bc(self.handle, f, g)
+
+    def vcycle(self, ncycles: int = 1):
+        ma_vcycle(self.handle, ncycles)
+
+    def solve(self, tol: float = 1e-10, norm: int = MA_NORM_MAX, relative: bool = True,
+              max_cycles: int = 50, init: int = MA_INIT_FMG, raise_on_error: bool = True) -> SolveResult:
+        o = ma_solve_opts(tol, norm, 1 if relative else 0, max_cycles, init)
+        r = ma_solve(self.handle, o, raise_on_error)
+        return SolveResult(r.cycles, r.res0, r.res, r.status, bool(r.floor_reached), r.nonconvex_root_events)
+
+    def residual_norm(self, norm: int = MA_NORM_MAX) -> float:
+        return ma_residual_norm(self.handle, norm)
+
+    def get_solution(self, u):
+        ma_get_solution(self.handle, u)
+
+    def set_solution(self, u):
+        ma_set_solution(self.handle, u)
+
+    def close(self):
+        if self.handle:
+            ma_destroy_hierarchy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

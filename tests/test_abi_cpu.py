@@ -1,0 +1,66 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point include/*.h declares; host-only calls behave (no compute)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import shutil
+
+import pytest
+
+from paper_1411_7018_gb300 import libma as M
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                                reason="nvcc not available")
+
+
+def declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(inc, fn)).read()
+            names.update(re.findall(r"^\s*(?:ma_status|const char \*)\s*(ma_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = M.load()
+    names = declared_symbols()
+    assert len(names) >= 20
+    for name in sorted(names):
+        assert hasattr(lib, name), name
+    assert set(M.EXPORTED) >= names
+
+
+def test_footprint_is_host_only_and_counts_levels():
+    d = M.make_desc(33)
+    nb = M.ma_hierarchy_footprint(d)
+    # four n^3 double fields per level (33, 17, 9, 5) plus reduction scratch
+    fields = 4 * 8 * sum(m ** 3 for m in (33, 17, 9, 5))
+    assert fields <= nb <= fields + 256 * 64 + 2 * 8 * 16 * 9 * 2 * 33
+    d2 = M.make_desc(257)
+    assert M.ma_hierarchy_footprint(d2) > 4 * 8 * 257 ** 3
+
+
+@pytest.mark.parametrize("kw", [dict(n=32), dict(n=33, coarsest_n=4), dict(n=33, nu1=0, nu2=0),
+                                dict(n=33, restrict_kind=7), dict(n=33, precision=3), dict(n=33, length=0.0),
+                                dict(n=35)])
+def test_bad_descriptors_rejected(kw):
+    length = kw.pop("length", 1.0)
+    d = M.make_desc(length=length, **kw)
+    with pytest.raises(M.MAError) as ei:
+        M.ma_hierarchy_footprint(d)
+    assert ei.value.status == M.MA_ERR_INVALID_ARG
+    assert M.ma_last_error_string()
+
+
+def test_step_calls_reject_bad_arguments_before_any_launch():
+    lib = M.load()
+    assert lib.ma_smooth(None, None, 33, 0.1, 1, None, None) == M.MA_ERR_INVALID_ARG
+    assert lib.ma_residual(C.c_void_p(256), C.c_void_p(256), C.c_void_p(256), 32, 0.1, None) == M.MA_ERR_INVALID_ARG
+    assert lib.ma_coarsest_solve(C.c_void_p(256), C.c_void_p(256), 33, 0.1, 0, None, None) == M.MA_ERR_INVALID_ARG
+    assert M.ma_norm_scratch_bytes(33) > 0
