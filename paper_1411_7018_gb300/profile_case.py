@@ -1,0 +1,56 @@
+"""Run one piece of the solver on a benchmark-shaped grid, for profiler captures.
+
+    python -m paper_1411_7018_gb300.profile_case --case smooth --n 257 --reps 2
+
+Cases: ``smooth`` (FP64 smoother sweeps, 8 colour launches each), ``residual``
+(the FP64 residual kernel), ``vcycle`` (whole FP64 V-cycles of a resident
+hierarchy), ``solve`` (one FMG + V-cycle solve to 1e-10).  The grid holds
+Example 4 (u = exp(|x|^2/2)) with a small seeded perturbation; fields of a
+257^3 grid are 136 MB each, larger than L2.  Prints nothing but a one-line
+summary; it measures nothing itself.
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+import torch
+
+from . import libma as M
+from . import problems
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", choices=["smooth", "residual", "vcycle", "solve"], default="smooth")
+    ap.add_argument("--n", type=int, default=257)
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--problem", default="exp")
+    a = ap.parse_args()
+    pr = problems.make(a.problem, a.n)
+    rng = np.random.default_rng(0)
+    u0 = pr.u.copy()
+    u0[1:-1, 1:-1, 1:-1] += 1e-6 * rng.standard_normal((a.n - 2,) * 3)
+    u = torch.from_numpy(u0).cuda()
+    f = torch.from_numpy(pr.f).cuda()
+    if a.case == "smooth":
+        for _ in range(a.reps):
+            M.ma_smooth(u, f, a.n, pr.h, 1)
+    elif a.case == "residual":
+        r = torch.empty_like(u)
+        for _ in range(a.reps):
+            M.ma_residual(u, f, r, a.n, pr.h)
+    else:
+        H = M.Hierarchy(M.make_desc(a.n, length=pr.length))
+        H.set_rhs_bc(f, u)
+        if a.case == "vcycle":
+            H.vcycle(a.reps)
+        else:
+            H.solve(tol=1e-10)
+        H.close()
+    torch.cuda.synchronize()
+    print(f"profile_case {a.case} n={a.n} reps={a.reps} done")
+
+
+if __name__ == "__main__":
+    main()
