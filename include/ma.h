@@ -223,6 +223,34 @@ ma_status ma_norm_scratch_bytes(int n, size_t *bytes);
 ma_status ma_norm(const double *v_dev, int n, double h, void *scratch_dev, size_t scratch_bytes,
                   double *out_host, ma_stream_t stream);
 
+/* ---- norms without any scratch from the caller ------------------------------
+ * No counterpart in the paper: an allocation-free variant of ma_norm for
+ * callers that cannot allocate device memory where they need a norm (their
+ * device memory is all owned and reserved by another allocator, or the
+ * implicit device synchronisation of cudaMalloc/cudaFree is not acceptable
+ * in their loop) and have no spare buffer to lend as scratch. */
+
+/* Largest grid (points per side) ma_norm_static serves. */
+#define MA_NORM_STATIC_MAX_N 513
+
+/* Same result as ma_norm (max norm and discrete L2 norm of v over the
+ * interior, into out_host[0] and out_host[1]; blocks on the stream), with the
+ * reduction scratch taken from a fixed array of about 550 KB inside this
+ * library's device memory instead of from the caller.  Every GPU that loads
+ * the library holds that array until the process exits.  The library
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *  - n must be odd, 3 <= n <= MA_NORM_STATIC_MAX_N; larger grids return
+ *    MA_ERR_INVALID_ARG with a message naming the limit.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current) and caches it; make
+ *    that first call before any stream capture.
+ *  - All calls on a device share the one array and it keeps the last call's
+ *    contents (each call overwrites every entry it reads, so nothing needs
+ *    clearing).  Calls whose kernels overlap on the GPU -- on different
+ *    streams, or from different host threads -- race on it and may return
+ *    wrong norms; serialise them. */
+ma_status ma_norm_static(const double *v_dev, int n, double h, double *out_host, ma_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

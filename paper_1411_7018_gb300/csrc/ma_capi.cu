@@ -199,6 +199,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+void ma::set_last_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
 extern "C" {
 
 const char* ma_last_error_string(void) { return g_err; }

@@ -10,6 +10,9 @@ namespace ma {
 void count_launches(unsigned long long k);
 unsigned long long launch_count();
 
+// Sets the thread-local text ma_last_error_string() returns.
+void set_last_error(const char* msg);
+
 // FP64 kernels (ma_kernels_f64.cu).  All grids are n^3 doubles, [k][j][i].
 cudaError_t launch_smooth(double* u, const double* rhs, int n, double h, int nsweeps,
                           unsigned long long* events, cudaStream_t s);

@@ -70,6 +70,7 @@ _SIGS = {
     "ma_norm_scratch_bytes": [C.c_int, C.POINTER(C.c_size_t)],
     "ma_norm": [_vp, C.c_int, C.c_double, _vp, C.c_size_t, C.POINTER(C.c_double), _vp],
     "ma_kernel_launch_count": [C.POINTER(C.c_ulonglong)],
+    "ma_norm_static": [_vp, C.c_int, C.c_double, C.POINTER(C.c_double), _vp],
 }
 # Declared in include/ma.h; the test suite checks that the library exports them.
 EXPORTED = sorted(list(_SIGS) + ["ma_last_error_string"])
@@ -227,6 +228,19 @@ def ma_norm_scratch_bytes(n: int) -> int:
 def ma_norm(v, n: int, h: float, scratch, scratch_bytes: int, stream=None):
     out = (C.c_double * 2)()
     _check(load().ma_norm(_ptr(v), n, h, _ptr(scratch), scratch_bytes, out, _stream(stream)))
+    return out[0], out[1]
+
+
+MA_NORM_STATIC_MAX_N = 513
+
+
+def ma_norm_static(v, n: int, h: float, stream=None):
+    """ma_norm without caller scratch: for callers that cannot allocate device
+    memory (all of it owned by another allocator, or no implicit cudaMalloc
+    synchronisation allowed).  n <= MA_NORM_STATIC_MAX_N; calls that overlap
+    on the GPU race on the library's one fixed scratch array."""
+    out = (C.c_double * 2)()
+    _check(load().ma_norm_static(_ptr(v), n, h, out, _stream(stream)))
     return out[0], out[1]
 
 
