@@ -214,6 +214,27 @@ ma_status ma_interpolate(const double *uc_dev, int nc, double *uf_dev, ma_stream
 ma_status ma_coarsest_solve(double *u_dev, const double *rhs_dev, int n, double h, int sweeps,
                             unsigned long long *events_dev, ma_stream_t stream);
 
+/* ---- single steps of the mixed-precision correction cycle -----------------
+ * The correction problem for a fixed FP64 iterate u is
+ *     N(e) = det(D^2_h (u + e)) - det(D^2_h u) = rhs,
+ * i.e. det(D^2_h(u + e)) = f when rhs = f - det(D^2_h u); FP32 cycles solve it
+ * for e and the FP64 driver updates u += e (defect correction; the FP64 work
+ * is the fine residual and the update, motivated by the round-off remark of
+ * Example 4).  N is evaluated as tr(cof(B) K) + tr(B cof(K)) + det(K) with
+ * B = D^2_h u and K = D^2_h e, so its round-off scales with e.  u is passed as
+ * an FP32 split u = u_hi + u_lo (u_hi = (float)u, u_lo = (float)(u - u_hi));
+ * e, rhs and res are n^3 floats, [k][j][i]; e is 0 on the shell. */
+
+/* nsweeps 8-colour sweeps on e: at each point the new e is the one whose
+ * u + e takes the smallest real root of the local cubic (Section 2, Eq.
+ * realroots) for right-hand side det(D^2_h u) + rhs. */
+ma_status ma_smooth_correction(float *e_dev, const float *u_hi_dev, const float *u_lo_dev, const float *rhs_dev,
+                               int n, double h, int nsweeps, unsigned long long *events_dev, ma_stream_t stream);
+
+/* res = rhs - N(e) on the interior, 0 on the shell. */
+ma_status ma_residual_correction(const float *e_dev, const float *u_hi_dev, const float *u_lo_dev,
+                                 const float *rhs_dev, float *res_dev, int n, double h, ma_stream_t stream);
+
 /* Bytes of device scratch ma_norm needs for a grid of n points per side. */
 ma_status ma_norm_scratch_bytes(int n, size_t *bytes);
 

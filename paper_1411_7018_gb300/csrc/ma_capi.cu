@@ -98,6 +98,14 @@ size_t layout(ma_hierarchy* H, const ma_hier_desc* d, char* base)
         lv.rhs = (double*)take(pts * sizeof(double));
         lv.r = (double*)take(pts * sizeof(double));
         lv.w = (double*)take(pts * sizeof(double));
+        if (d->precision == MA_MIXED) {
+            lv.e = (float*)take(pts * sizeof(float));
+            lv.hi = (float*)take(pts * sizeof(float));
+            lv.lo = (float*)take(pts * sizeof(float));
+            lv.rhs32 = (float*)take(pts * sizeof(float));
+            lv.res32 = (float*)take(pts * sizeof(float));
+            lv.w32 = (float*)take(pts * sizeof(float));
+        }
         m = (m + 1) / 2;
         h *= 2.0;
     }
@@ -139,7 +147,9 @@ cudaError_t vcycle_from(ma_hierarchy* H, int l0)
 
 // Algorithm 2: inject f (and the Dirichlet data) down, solve the coarsest
 // problem from a zero interior, then interpolate up with one V-cycle per level.
-cudaError_t fmg(ma_hierarchy* H)
+// With finest_vcycle false the finest level only receives the interpolated
+// iterate (the mixed-precision solve continues from there).
+cudaError_t fmg(ma_hierarchy* H, bool finest_vcycle = true)
 {
     cudaStream_t s = H->s;
     cudaError_t e;
@@ -154,22 +164,102 @@ cudaError_t fmg(ma_hierarchy* H)
     if ((e = ma::launch_coarsest(B.u, B.rhs, B.n, B.h, H->d.coarse_sweeps, H->events, s)) != cudaSuccess) return e;
     for (int l = H->L - 2; l >= 0; --l) {
         if ((e = ma::launch_interpolate(H->lev[l + 1].u, H->lev[l + 1].n, H->lev[l].u, s)) != cudaSuccess) return e;
+        if (l == 0 && !finest_vcycle) break;
         if ((e = vcycle_from(H, l)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-// Fine-level residual norms (max, L2) into host[0..1]; blocks on the stream.
-ma_status fine_residual_norms(ma_hierarchy* H, double* mx, double* l2)
+// ---- mixed precision: FP32 FAS cycle on the correction e --------------------
+
+// Base u = hi + lo on the finest level from the FP64 iterate (after u += e
+// when apply), e = 0; coarse bases by injection.
+cudaError_t refresh_base(ma_hierarchy* H, int apply)
+{
+    cudaStream_t s = H->s;
+    cudaError_t e;
+    ma::Level& F = H->lev[0];
+    if ((e = ma::launch_split_update(F.u, F.e, F.hi, F.lo, F.n, apply, s)) != cudaSuccess) return e;
+    for (int l = 0; l < H->L - 1; ++l) {
+        ma::Level& A = H->lev[l];
+        ma::Level& C = H->lev[l + 1];
+        if ((e = ma::launch_inject_f32(A.hi, A.n, C.hi, s)) != cudaSuccess) return e;
+        if ((e = ma::launch_inject_f32(A.lo, A.n, C.lo, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// One FAS V-cycle (Algorithm 1 structure) for N(e) = rhs32 on every level,
+// starting from the current e on the finest level.
+cudaError_t corr_vcycle(ma_hierarchy* H)
+{
+    cudaStream_t s = H->s;
+    const ma_hier_desc& d = H->d;
+    cudaError_t e;
+    for (int l = 0; l < H->L - 1; ++l) {
+        ma::Level& F = H->lev[l];
+        ma::Level& C = H->lev[l + 1];
+        if ((e = ma::launch_smooth_corr(F.e, F.hi, F.lo, F.rhs32, F.n, F.h, d.nu1, H->events, s)) != cudaSuccess)
+            return e;
+        if ((e = ma::launch_residual_corr(F.e, F.hi, F.lo, F.rhs32, F.res32, F.n, F.h, s)) != cudaSuccess) return e;
+        if ((e = ma::launch_restrict_level_f32(F.e, F.res32, F.n, C.w32, C.e, C.res32, d.restrict_kind,
+                                               d.approx_restrict, s)) != cudaSuccess)
+            return e;
+        if ((e = ma::launch_coarse_rhs_corr(C.w32, C.hi, C.lo, C.res32, C.rhs32, C.n, C.h, s)) != cudaSuccess)
+            return e;
+    }
+    ma::Level& B = H->lev[H->L - 1];
+    if ((e = ma::launch_coarsest_corr(B.e, B.hi, B.lo, B.rhs32, B.n, B.h, d.coarse_sweeps, H->events, s)) !=
+        cudaSuccess)
+        return e;
+    for (int l = H->L - 2; l >= 0; --l) {
+        ma::Level& F = H->lev[l];
+        ma::Level& C = H->lev[l + 1];
+        if ((e = ma::launch_prolong_add_f32(C.e, C.w32, C.n, F.e, s)) != cudaSuccess) return e;
+        if ((e = ma::launch_smooth_corr(F.e, F.hi, F.lo, F.rhs32, F.n, F.h, d.nu2, H->events, s)) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+// FP64 fine residual into rhs32 (the correction problem's right-hand side)
+// with norm partials; the caller reads the norms.
+cudaError_t mixed_residual(ma_hierarchy* H)
 {
     ma::Level& F = H->lev[0];
-    MA_CK(ma::launch_residual(F.u, F.rhs, F.r, F.n, F.h, H->partials, H->s));
-    MA_CK(ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s));
+    cudaError_t e = ma::launch_residual64_to32(F.u, F.rhs, F.rhs32, F.n, F.h, H->partials, H->s);
+    if (e != cudaSuccess) return e;
+    return ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s);
+}
+
+// One outer (defect-correction) iteration: FP64 residual, FP32 correction
+// V-cycle, FP64 update.  Leaves the base refreshed for the next iteration.
+cudaError_t mixed_iteration(ma_hierarchy* H)
+{
+    cudaError_t e;
+    if ((e = refresh_base(H, 0)) != cudaSuccess) return e;
+    if ((e = mixed_residual(H)) != cudaSuccess) return e;
+    if ((e = corr_vcycle(H)) != cudaSuccess) return e;
+    return refresh_base(H, 1);
+}
+
+// Reads the reduced norms (max, L2) in out2 back to the host; blocks.
+ma_status read_norms(ma_hierarchy* H, double* mx, double* l2)
+{
     MA_CK(cudaMemcpyAsync(H->host, H->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, H->s));
     MA_CK(cudaStreamSynchronize(H->s));
     *mx = H->host[0];
     *l2 = H->host[1];
     return MA_OK;
+}
+
+// Fine-level FP64 residual norms (max, L2); blocks on the stream.
+ma_status fine_residual_norms(ma_hierarchy* H, double* mx, double* l2)
+{
+    ma::Level& F = H->lev[0];
+    MA_CK(ma::launch_residual(F.u, F.rhs, F.r, F.n, F.h, H->partials, H->s));
+    MA_CK(ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s));
+    return read_norms(H, mx, l2);
 }
 
 ma_status rhs_norms(ma_hierarchy* H, double* mx, double* l2)
@@ -294,7 +384,10 @@ ma_status ma_vcycle(ma_hierarchy* H, int ncycles)
 {
     if (!H || ncycles < 0) return fail(MA_ERR_INVALID_ARG, "bad arguments");
     DeviceGuard g(H->device);
-    for (int c = 0; c < ncycles; ++c) MA_CK(vcycle_from(H, 0));
+    for (int c = 0; c < ncycles; ++c) {
+        if (H->d.precision == MA_MIXED) MA_CK(mixed_iteration(H));
+        else MA_CK(vcycle_from(H, 0));
+    }
     return MA_OK;
 }
 
@@ -344,10 +437,20 @@ ma_status ma_solve(ma_hierarchy* H, const ma_solve_opts* opts, ma_solve_result* 
         scale = opts->norm == MA_NORM_MAX ? fm : f2;
         if (!(scale > 0.0)) scale = 1.0;
     }
-    if (opts->init == MA_INIT_FMG) MA_CK(fmg(H));
+    const bool mixed = H->d.precision == MA_MIXED;
+    // In mixed precision the FMG pass stops at the interpolated finest iterate
+    // and the FP32-corrected outer iterations take over from there.
+    if (opts->init == MA_INIT_FMG) MA_CK(fmg(H, !mixed));
     else if (opts->init == MA_INIT_ZERO) MA_CK(ma::launch_zero_interior(H->lev[0].u, H->lev[0].n, H->s));
     double mx, l2;
-    ma_status st = fine_residual_norms(H, &mx, &l2);
+    ma_status st;
+    if (mixed) {
+        MA_CK(refresh_base(H, 0));
+        MA_CK(mixed_residual(H));
+        st = read_norms(H, &mx, &l2);
+    } else {
+        st = fine_residual_norms(H, &mx, &l2);
+    }
     if (st != MA_OK) return st;
     double rel = (opts->norm == MA_NORM_MAX ? mx : l2) / scale;
     res->res0 = rel;
@@ -357,9 +460,16 @@ ma_status ma_solve(ma_hierarchy* H, const ma_solve_opts* opts, ma_solve_result* 
         if (!std::isfinite(rel)) { out = MA_ERR_NONFINITE; break; }
         if (rel <= opts->tol) break;
         if (res->cycles >= opts->max_cycles) { out = MA_ERR_NOT_CONVERGED; break; }
-        MA_CK(vcycle_from(H, 0));
+        if (mixed) {
+            MA_CK(corr_vcycle(H));
+            MA_CK(refresh_base(H, 1));
+            MA_CK(mixed_residual(H));
+            st = read_norms(H, &mx, &l2);
+        } else {
+            MA_CK(vcycle_from(H, 0));
+            st = fine_residual_norms(H, &mx, &l2);
+        }
         res->cycles += 1;
-        st = fine_residual_norms(H, &mx, &l2);
         if (st != MA_OK) return st;
         const double nrel = (opts->norm == MA_NORM_MAX ? mx : l2) / scale;
         // three cycles in a row that barely reduce the residual: round-off floor
@@ -448,6 +558,24 @@ ma_status ma_coarsest_solve(double* u, const double* rhs, int n, double h, int s
     if (!u || !rhs || !valid_step_grid(n) || n > 17 || !(h > 0.0) || sweeps < 0 || sweeps > 1000)
         return fail(MA_ERR_INVALID_ARG, "ma_coarsest_solve: bad arguments (n <= 17)");
     MA_CK(ma::launch_coarsest(u, rhs, n, h, sweeps, events, (cudaStream_t)stream));
+    return MA_OK;
+}
+
+ma_status ma_smooth_correction(float* e, const float* hi, const float* lo, const float* rhs, int n, double h,
+                               int nsweeps, unsigned long long* events, ma_stream_t stream)
+{
+    if (!e || !hi || !lo || !rhs || !valid_step_grid(n) || !(h > 0.0) || nsweeps < 0)
+        return fail(MA_ERR_INVALID_ARG, "ma_smooth_correction: bad arguments");
+    MA_CK(ma::launch_smooth_corr(e, hi, lo, rhs, n, h, nsweeps, events, (cudaStream_t)stream));
+    return MA_OK;
+}
+
+ma_status ma_residual_correction(const float* e, const float* hi, const float* lo, const float* rhs, float* res,
+                                 int n, double h, ma_stream_t stream)
+{
+    if (!e || !hi || !lo || !rhs || !res || !valid_step_grid(n) || !(h > 0.0))
+        return fail(MA_ERR_INVALID_ARG, "ma_residual_correction: bad arguments");
+    MA_CK(ma::launch_residual_corr(e, hi, lo, rhs, res, n, h, (cudaStream_t)stream));
     return MA_OK;
 }
 

@@ -19,6 +19,13 @@ struct Level {
     double* rhs = nullptr;   // f on the finest level, b_H on coarse levels
     double* r = nullptr;     // residual; on coarse levels the restricted r_H
     double* w = nullptr;     // coarse levels: the restricted approximation w_H
+    // mixed precision (FP32 correction cycle); null in FP64 mode
+    float* e = nullptr;      // correction
+    float* hi = nullptr;     // base u = hi + lo (FP32 split)
+    float* lo = nullptr;
+    float* rhs32 = nullptr;  // correction-problem right-hand side (fine: the FP64 residual)
+    float* res32 = nullptr;  // correction residual; on coarse levels the restricted one
+    float* w32 = nullptr;    // coarse levels: the restricted correction
 };
 
 }  // namespace ma

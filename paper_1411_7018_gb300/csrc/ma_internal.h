@@ -38,4 +38,22 @@ cudaError_t launch_coarsest(double* u, const double* rhs, int n, double h, int s
 cudaError_t launch_copy_rhs_bc(const double* f, const double* g, double* rhs, double* u, int n,
                                int* bad, cudaStream_t s);
 
+// Mixed-precision kernels (ma_kernels_mixed.cu): FP32 correction cycle fields
+// are n^3 floats; the base u is split as hi + lo.
+cudaError_t launch_smooth_corr(float* e, const float* hi, const float* lo, const float* rhs, int n, double h,
+                               int nsweeps, unsigned long long* events, cudaStream_t s);
+cudaError_t launch_residual_corr(const float* e, const float* hi, const float* lo, const float* rhs, float* res,
+                                 int n, double h, cudaStream_t s);
+cudaError_t launch_coarse_rhs_corr(const float* w, const float* hi, const float* lo, const float* resc, float* rhs,
+                                   int nc, double H, cudaStream_t s);
+cudaError_t launch_restrict_level_f32(const float* ef, const float* rf, int nf, float* wc, float* ec, float* rc,
+                                      int kind, int approx, cudaStream_t s);
+cudaError_t launch_prolong_add_f32(const float* ec, const float* wc, int nc, float* ef, cudaStream_t s);
+cudaError_t launch_inject_f32(const float* vf, int nf, float* vc, cudaStream_t s);
+cudaError_t launch_coarsest_corr(float* e, const float* hi, const float* lo, const float* rhs, int n, double h,
+                                 int sweeps, unsigned long long* events, cudaStream_t s);
+cudaError_t launch_split_update(double* u, float* e, float* hi, float* lo, int n, int apply, cudaStream_t s);
+cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r, int n, double h, double* partials,
+                                   cudaStream_t s);
+
 }  // namespace ma

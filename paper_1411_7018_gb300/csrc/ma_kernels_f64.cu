@@ -16,6 +16,7 @@
 
 #include "ma_internal.h"
 #include "ma_point.cuh"
+#include "ma_transfer.cuh"
 
 namespace ma {
 
@@ -160,54 +161,6 @@ __global__ void __launch_bounds__(256) k_norm_final(const double* __restrict__ p
     }
 }
 
-// ---------------------------------------------------------------------------
-// Grid transfers.  Coarse point (I, J, K) sits on fine point (2I, 2J, 2K).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double weighted_restrict(const double* __restrict__ v, long long p, long long sy,
-                                                    long long sz, int kind)
-{
-    if (kind == 0) {   // half weighting: (6 centre + 6 faces) / 12
-        const double faces = (v[p + 1] + v[p - 1]) + (v[p + sy] + v[p - sy]) + (v[p + sz] + v[p - sz]);
-        return fma(6.0, v[p], faces) * (1.0 / 12.0);
-    }
-    // full weighting: separable (1 2 1)/4 along each axis
-    double acc = 0.0;
-    #pragma unroll
-    for (int dk = -1; dk <= 1; ++dk) {
-        double plane = 0.0;
-        #pragma unroll
-        for (int dj = -1; dj <= 1; ++dj) {
-            const long long q = p + dk * sz + dj * sy;
-            const double row = v[q - 1] + 2.0 * v[q] + v[q + 1];
-            plane += (dj == 0 ? 2.0 : 1.0) * row;
-        }
-        acc += (dk == 0 ? 2.0 : 1.0) * plane;
-    }
-    return acc * (1.0 / 64.0);
-}
-
-// Coarse-grid outputs, any may be null: rc = I r (0 on the shell);
-// wc = approximation restriction of uf; uc = copy of wc (coarse iterate).
-__global__ void __launch_bounds__(BX * BY) k_restrict(const double* __restrict__ uf, const double* __restrict__ rf,
-                                                      int nf, double* __restrict__ wc, double* __restrict__ uc,
-                                                      double* __restrict__ rc, int nc, int kind, int approx)
-{
-    const int I = blockIdx.x * BX + threadIdx.x;
-    const int J = blockIdx.y * BY + threadIdx.y;
-    const int K = blockIdx.z;
-    if (I >= nc || J >= nc) return;
-    const long long pc = lin(I, J, K, nc);
-    const long long pf = lin(2 * I, 2 * J, 2 * K, nf);
-    const long long sy = nf, sz = (long long)nf * nf;
-    const bool interior = I > 0 && J > 0 && K > 0 && I < nc - 1 && J < nc - 1 && K < nc - 1;
-    if (rc) rc[pc] = interior ? weighted_restrict(rf, pf, sy, sz, kind) : 0.0;
-    if (uf) {
-        const double w = (interior && approx == 1) ? weighted_restrict(uf, pf, sy, sz, kind) : uf[pf];
-        if (wc) wc[pc] = w;
-        if (uc) uc[pc] = w;
-    }
-}
-
 // b_H = det(D^2_H w_H) + r_H on the interior, 0 on the shell.
 __global__ void __launch_bounds__(BX * BY) k_coarse_rhs(const double* __restrict__ wc, const double* __restrict__ rc,
                                                         double* __restrict__ bc, int nc, double inv_H6)
@@ -223,48 +176,6 @@ __global__ void __launch_bounds__(BX * BY) k_coarse_rhs(const double* __restrict
         b = fma(det0(H), inv_H6, rc[p]);
     }
     bc[p] = b;
-}
-
-// Trilinear interpolation at fine interior points: along each axis an even
-// index sits on a coarse point, an odd one halfway between two.
-// add != 0: uf += I(uc - wc) (correction); add == 0: uf = I(uc).
-__global__ void __launch_bounds__(BX * BY) k_prolong(const double* __restrict__ uc, const double* __restrict__ wc,
-                                                     int nc, double* __restrict__ uf, int nf, int add)
-{
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i < 1 || j < 1 || k < 1 || i > nf - 2 || j > nf - 2 || k > nf - 2) return;
-    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
-    const int oi = i & 1, oj = j & 1, ok = k & 1;
-    double s = 0.0;
-    for (int dk = 0; dk <= ok; ++dk)
-        for (int dj = 0; dj <= oj; ++dj)
-            for (int di = 0; di <= oi; ++di) {
-                const long long q = lin(I0 + di, J0 + dj, K0 + dk, nc);
-                s += add ? (uc[q] - wc[q]) : uc[q];
-            }
-    const double w = 1.0 / (double)(1 << (oi + oj + ok));
-    const long long p = lin(i, j, k, nf);
-    uf[p] = add ? fma(s, w, uf[p]) : s * w;
-}
-
-__global__ void k_inject(const double* __restrict__ vf, int nf, double* __restrict__ vc, int nc)
-{
-    const int I = blockIdx.x * BX + threadIdx.x;
-    const int J = blockIdx.y * BY + threadIdx.y;
-    const int K = blockIdx.z;
-    if (I >= nc || J >= nc) return;
-    vc[lin(I, J, K, nc)] = vf[lin(2 * I, 2 * J, 2 * K, nf)];
-}
-
-__global__ void k_zero_interior(double* u, int n)
-{
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i < 1 || j < 1 || k < 1 || i > n - 2 || j > n - 2 || k > n - 2) return;
-    u[lin(i, j, k, n)] = 0.0;
 }
 
 // rhs := f, u := g (whole grids); counts interior points with f not finite
@@ -424,13 +335,13 @@ cudaError_t launch_norm_final(const double* partials, int count, double h, doubl
     return cudaGetLastError();
 }
 
-static dim3 grid_of(int n) { return dim3((n + BX - 1) / BX, (n + BY - 1) / BY, n); }
+using xfer::grid_of;
 
 cudaError_t launch_restrict_residual(const double* rf, int nf, double* rc, int kind, cudaStream_t s)
 {
     const int nc = (nf + 1) / 2;
     count_launches(1);
-    k_restrict<<<grid_of(nc), dim3(BX, BY), 0, s>>>(nullptr, rf, nf, nullptr, nullptr, rc, nc, kind, 0);
+    xfer::k_restrict<double><<<grid_of(nc), dim3(BX, BY), 0, s>>>(nullptr, rf, nf, nullptr, nullptr, rc, nc, kind, 0);
     return cudaGetLastError();
 }
 
@@ -438,7 +349,7 @@ cudaError_t launch_restrict_solution(const double* uf, int nf, double* uc, int a
 {
     const int nc = (nf + 1) / 2;
     count_launches(1);
-    k_restrict<<<grid_of(nc), dim3(BX, BY), 0, s>>>(uf, nullptr, nf, nullptr, uc, nullptr, nc, kind, approx);
+    xfer::k_restrict<double><<<grid_of(nc), dim3(BX, BY), 0, s>>>(uf, nullptr, nf, nullptr, uc, nullptr, nc, kind, approx);
     return cudaGetLastError();
 }
 
@@ -447,7 +358,7 @@ cudaError_t launch_restrict_level(const double* uf, const double* rf, int nf, do
 {
     const int nc = (nf + 1) / 2;
     count_launches(1);
-    k_restrict<<<grid_of(nc), dim3(BX, BY), 0, s>>>(uf, rf, nf, wc, uc, rc, nc, kind, approx);
+    xfer::k_restrict<double><<<grid_of(nc), dim3(BX, BY), 0, s>>>(uf, rf, nf, wc, uc, rc, nc, kind, approx);
     return cudaGetLastError();
 }
 
@@ -462,7 +373,7 @@ cudaError_t launch_prolong_add(const double* uc, const double* wc, int nc, doubl
 {
     const int nf = 2 * nc - 1;
     count_launches(1);
-    k_prolong<<<grid_of(nf), dim3(BX, BY), 0, s>>>(uc, wc, nc, uf, nf, 1);
+    xfer::k_prolong<double><<<grid_of(nf), dim3(BX, BY), 0, s>>>(uc, wc, nc, uf, nf, 1);
     return cudaGetLastError();
 }
 
@@ -470,7 +381,7 @@ cudaError_t launch_interpolate(const double* uc, int nc, double* uf, cudaStream_
 {
     const int nf = 2 * nc - 1;
     count_launches(1);
-    k_prolong<<<grid_of(nf), dim3(BX, BY), 0, s>>>(uc, nullptr, nc, uf, nf, 0);
+    xfer::k_prolong<double><<<grid_of(nf), dim3(BX, BY), 0, s>>>(uc, nullptr, nc, uf, nf, 0);
     return cudaGetLastError();
 }
 
@@ -478,14 +389,14 @@ cudaError_t launch_inject(const double* vf, int nf, double* vc, cudaStream_t s)
 {
     const int nc = (nf + 1) / 2;
     count_launches(1);
-    k_inject<<<grid_of(nc), dim3(BX, BY), 0, s>>>(vf, nf, vc, nc);
+    xfer::k_inject<double><<<grid_of(nc), dim3(BX, BY), 0, s>>>(vf, nf, vc, nc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_zero_interior(double* u, int n, cudaStream_t s)
 {
     count_launches(1);
-    k_zero_interior<<<grid_of(n), dim3(BX, BY), 0, s>>>(u, n);
+    xfer::k_zero_interior<double><<<grid_of(n), dim3(BX, BY), 0, s>>>(u, n);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,454 @@
+// ma_kernels_mixed.cu -- kernels of the mixed-precision solve: FP32 FAS
+// V-cycles on a correction e under an FP64 fine-grid residual and update
+// (defect correction).  The paper computes in FP64 throughout and notes that
+// round-off limits its finest grid (round-off remark of Example 4, Section 4);
+// here FP64 is kept exactly where that round-off bites -- the fine residual
+// f - det(D^2_h u) and the update u += e -- and everything that only has to
+// produce a correction runs in FP32.
+//
+// Correction operator.  With u fixed, the correction problem is
+//     N(e) = det(B + K(e)) - det(B) = r,    B = D^2_h u,  K(e) = D^2_h e,
+// which is exactly det(D^2_h (u + e)) = f when r = f - det(D^2_h u).  For 3x3
+// matrices det(B + K) - det(B) = tr(cof(B) K) + tr(B cof(K)) + det(K), so N(e)
+// is evaluated without subtracting two O(f) numbers: its FP32 round-off scales
+// with the correction, not with f.  B comes from an FP32 hi/lo split of u
+// (u = hi + lo to ~2^-48 relative) with differences to the centre taken first,
+// which keeps ~1e-5 relative accuracy where FP32 u alone would give percent
+// errors at 513^3.  The point update solves N = r for the centre value with
+// the same smallest-root rule as the FP64 smoother (Section 2, Eq. realroots):
+// det(G - z I) = det(B) + r with G = B + K, the root below the smallest
+// eigenvalue of G; FP32 Newton from z = 0 when G is positive definite, else
+// the FP64 routines of ma_point.cuh on the same data.
+#include <atomic>
+
+#include "ma_internal.h"
+#include "ma_point.cuh"
+#include "ma_transfer.cuh"
+
+namespace ma {
+
+namespace {
+
+using xfer::BX;
+using xfer::BY;
+using xfer::grid_of;
+using xfer::lin;
+
+struct S3f {
+    float xx, yy, zz, xy, xz, yz;
+};
+
+// B = D^2_h u from the hi/lo split, differences to the centre first.
+__device__ __forceinline__ S3f base_hess(const float* __restrict__ hi, const float* __restrict__ lo, long long p,
+                                         long long sy, long long sz, float inv_h2)
+{
+    const float vh = hi[p], vl = lo[p];
+    auto d = [&](long long o) -> float { return (__ldg(hi + p + o) - vh) + (__ldg(lo + p + o) - vl); };
+    S3f B;
+    const float q = 0.25f * inv_h2;
+    B.xx = (d(1) + d(-1)) * inv_h2;
+    B.yy = (d(sy) + d(-sy)) * inv_h2;
+    B.zz = (d(sz) + d(-sz)) * inv_h2;
+    B.xy = ((d(sy + 1) + d(-sy - 1)) - (d(sy - 1) + d(-sy + 1))) * q;
+    B.xz = ((d(sz + 1) + d(-sz - 1)) - (d(sz - 1) + d(-sz + 1))) * q;
+    B.yz = ((d(sz + sy) + d(-sz - sy)) - (d(sy - sz) + d(-sy + sz))) * q;
+    return B;
+}
+
+// K = D^2_h e at the current centre value e0.
+__device__ __forceinline__ S3f corr_hess(const float* __restrict__ e, long long p, long long sy, long long sz,
+                                         float e0, float inv_h2)
+{
+    auto d = [&](long long o) -> float { return __ldg(e + p + o) - e0; };
+    S3f K;
+    const float q = 0.25f * inv_h2;
+    K.xx = (d(1) + d(-1)) * inv_h2;
+    K.yy = (d(sy) + d(-sy)) * inv_h2;
+    K.zz = (d(sz) + d(-sz)) * inv_h2;
+    K.xy = ((d(sy + 1) + d(-sy - 1)) - (d(sy - 1) + d(-sy + 1))) * q;
+    K.xz = ((d(sz + 1) + d(-sz - 1)) - (d(sz - 1) + d(-sz + 1))) * q;
+    K.yz = ((d(sz + sy) + d(-sz - sy)) - (d(sy - sz) + d(-sy + sz))) * q;
+    return K;
+}
+
+__device__ __forceinline__ float det3(const S3f& A)
+{
+    return A.xx * (A.yy * A.zz - A.yz * A.yz) - A.xy * (A.xy * A.zz - A.xz * A.yz) +
+           A.xz * (A.xy * A.yz - A.yy * A.xz);
+}
+
+// tr(cof(A) X) for symmetric A, X.
+__device__ __forceinline__ float cof_dot(const S3f& A, const S3f& X)
+{
+    const float cxx = A.yy * A.zz - A.yz * A.yz;
+    const float cyy = A.xx * A.zz - A.xz * A.xz;
+    const float czz = A.xx * A.yy - A.xy * A.xy;
+    const float cxy = A.xz * A.yz - A.xy * A.zz;
+    const float cxz = A.xy * A.yz - A.xz * A.yy;
+    const float cyz = A.xy * A.xz - A.xx * A.yz;
+    return cxx * X.xx + cyy * X.yy + czz * X.zz + 2.0f * (cxy * X.xy + cxz * X.xz + cyz * X.yz);
+}
+
+// N = det(B + K) - det(B) by the 3x3 expansion.
+__device__ __forceinline__ float delta_det(const S3f& B, const S3f& K)
+{
+    return cof_dot(B, K) + cof_dot(K, B) + det3(K);
+}
+
+// Smallest-root update of the correction problem at one point; returns z with
+// e_new = e0 + h^2 z / 2.
+__device__ __forceinline__ float corr_root(const S3f& B, const S3f& K, float r, bool* nonconvex)
+{
+    S3f G;
+    G.xx = B.xx + K.xx; G.yy = B.yy + K.yy; G.zz = B.zz + K.zz;
+    G.xy = B.xy + K.xy; G.xz = B.xz + K.xz; G.yz = B.yz + K.yz;
+    const float c = delta_det(B, K) - r;   // F(0)
+    const float T = G.xx + G.yy + G.zz;
+    const float M = (G.xx * G.yy - G.xy * G.xy) + (G.xx * G.zz - G.xz * G.xz) + (G.yy * G.zz - G.yz * G.yz);
+    const float dG = det3(G);
+    const bool pd = G.xx > 0.0f && G.xx * G.yy - G.xy * G.xy > 0.0f && dG > 0.0f;
+    const float scale = fabsf(G.xx) + fabsf(G.yy) + fabsf(G.zz) + fabsf(G.xy) + fabsf(G.xz) + fabsf(G.yz);
+    if (pd && M > 0.05f * scale * scale) {
+        // F(z) = c - z M + z^2 T - z^3 = det(G - zI) - det(B) - r
+        float z = 0.0f;
+        for (int it = 0; it < 30; ++it) {
+            const float F = c - z * (M - z * (T - z));
+            const float Mz = M - z * (2.0f * T - 3.0f * z);
+            const float dz = F / Mz;
+            z += dz;
+            if (!isfinite(z)) break;
+            if (fabsf(dz) <= 1e-6f * fabsf(z) + 1e-12f * scale) return z;
+        }
+    }
+    // FP64 on the same data: the target is det(G - zI) = det(B) + r.
+    HessS H;
+    H.A = G.xx; H.B = G.yy; H.C = G.zz; H.R = G.xy; H.S = G.xz; H.T = G.yz;
+    const double tot = (double)det3(B) + (double)r;
+    if (tot > 0.0) return (float)root_f64_monotone(H, tot);
+    *nonconvex = true;
+    return (float)root_f64_all_real_min(H, tot);
+}
+
+template <int PI, int PJ, int PK>
+__global__ void __launch_bounds__(BX * BY) k_smooth_corr(float* e, const float* __restrict__ hi,
+                                                          const float* __restrict__ lo, const float* __restrict__ rhs,
+                                                          int n, float inv_h2, float h2half,
+                                                          unsigned long long* events)
+{
+    const int i = (PI ? 1 : 2) + 2 * (int)(blockIdx.x * BX + threadIdx.x);
+    const int j = (PJ ? 1 : 2) + 2 * (int)(blockIdx.y * BY + threadIdx.y);
+    const int k = (PK ? 1 : 2) + 2 * (int)blockIdx.z;
+    if (i > n - 2 || j > n - 2 || k > n - 2) return;
+    const long long sy = n, sz = (long long)n * n;
+    const long long p = lin(i, j, k, n);
+    const float e0 = e[p];
+    const S3f B = base_hess(hi, lo, p, sy, sz, inv_h2);
+    const S3f K = corr_hess(e, p, sy, sz, e0, inv_h2);
+    bool nonconvex = false;
+    const float z = corr_root(B, K, rhs[p], &nonconvex);
+    e[p] = fmaf(h2half, z, e0);
+    if (nonconvex && events) atomicAdd(events, 1ull);
+}
+
+__host__ __device__ __forceinline__ int colour_count(int n, int parity) { return parity ? (n - 1) / 2 : (n - 3) / 2; }
+
+template <int C>
+cudaError_t launch_colour_corr(float* e, const float* hi, const float* lo, const float* rhs, int n, float inv_h2,
+                               float h2half, unsigned long long* ev, cudaStream_t s)
+{
+    constexpr int PI = C & 1, PJ = (C >> 1) & 1, PK = (C >> 2) & 1;
+    const int ni = colour_count(n, PI), nj = colour_count(n, PJ), nk = colour_count(n, PK);
+    if (ni <= 0 || nj <= 0 || nk <= 0) return cudaSuccess;
+    dim3 grid((ni + BX - 1) / BX, (nj + BY - 1) / BY, nk);
+    count_launches(1);
+    k_smooth_corr<PI, PJ, PK><<<grid, dim3(BX, BY), 0, s>>>(e, hi, lo, rhs, n, inv_h2, h2half, ev);
+    return cudaGetLastError();
+}
+
+// res = rhs - N(e) on the interior, 0 on the shell.
+__global__ void __launch_bounds__(BX * BY) k_residual_corr(const float* __restrict__ e, const float* __restrict__ hi,
+                                                           const float* __restrict__ lo,
+                                                           const float* __restrict__ rhs, float* __restrict__ res,
+                                                           int n, float inv_h2)
+{
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= n || j >= n) return;
+    const long long p = lin(i, j, k, n);
+    float v = 0.0f;
+    if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
+        const long long sy = n, sz = (long long)n * n;
+        const S3f B = base_hess(hi, lo, p, sy, sz, inv_h2);
+        const S3f K = corr_hess(e, p, sy, sz, e[p], inv_h2);
+        v = rhs[p] - delta_det(B, K);
+    }
+    res[p] = v;
+}
+
+// rhs_H = N_H(w_H) + res_H on the coarse interior, 0 on the shell.
+__global__ void __launch_bounds__(BX * BY) k_coarse_rhs_corr(const float* __restrict__ w, const float* __restrict__ hi,
+                                                             const float* __restrict__ lo,
+                                                             const float* __restrict__ resc, float* __restrict__ rhs,
+                                                             int n, float inv_h2)
+{
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= n || j >= n) return;
+    const long long p = lin(i, j, k, n);
+    float v = 0.0f;
+    if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
+        const long long sy = n, sz = (long long)n * n;
+        const S3f B = base_hess(hi, lo, p, sy, sz, inv_h2);
+        const S3f K = corr_hess(w, p, sy, sz, w[p], inv_h2);
+        v = delta_det(B, K) + resc[p];
+    }
+    rhs[p] = v;
+}
+
+// Coarsest correction grid: one block, shared memory, FP32 sweeps until
+// max|de| <= 1e-6 max|e| (or a fixed count).
+constexpr int CT = 256;
+
+__device__ __forceinline__ S3f base_hess_sm(const float* hi, const float* lo, int p, int sy, int sz, float inv_h2)
+{
+    const float vh = hi[p], vl = lo[p];
+    auto d = [&](int o) -> float { return (hi[p + o] - vh) + (lo[p + o] - vl); };
+    S3f B;
+    const float q = 0.25f * inv_h2;
+    B.xx = (d(1) + d(-1)) * inv_h2;
+    B.yy = (d(sy) + d(-sy)) * inv_h2;
+    B.zz = (d(sz) + d(-sz)) * inv_h2;
+    B.xy = ((d(sy + 1) + d(-sy - 1)) - (d(sy - 1) + d(-sy + 1))) * q;
+    B.xz = ((d(sz + 1) + d(-sz - 1)) - (d(sz - 1) + d(-sz + 1))) * q;
+    B.yz = ((d(sz + sy) + d(-sz - sy)) - (d(sy - sz) + d(-sy + sz))) * q;
+    return B;
+}
+
+__device__ __forceinline__ S3f corr_hess_sm(const float* e, int p, int sy, int sz, float e0, float inv_h2)
+{
+    auto d = [&](int o) -> float { return e[p + o] - e0; };
+    S3f K;
+    const float q = 0.25f * inv_h2;
+    K.xx = (d(1) + d(-1)) * inv_h2;
+    K.yy = (d(sy) + d(-sy)) * inv_h2;
+    K.zz = (d(sz) + d(-sz)) * inv_h2;
+    K.xy = ((d(sy + 1) + d(-sy - 1)) - (d(sy - 1) + d(-sy + 1))) * q;
+    K.xz = ((d(sz + 1) + d(-sz - 1)) - (d(sz - 1) + d(-sz + 1))) * q;
+    K.yz = ((d(sz + sy) + d(-sz - sy)) - (d(sy - sz) + d(-sy + sz))) * q;
+    return K;
+}
+
+__global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __restrict__ hi,
+                                                      const float* __restrict__ lo, const float* __restrict__ rhs,
+                                                      int n, float inv_h2, float h2half, int sweeps,
+                                                      unsigned long long* events)
+{
+    extern __shared__ float smf[];
+    const int m = n * n * n;
+    float* se = smf;
+    float* sh = smf + m;
+    float* sl = smf + 2 * m;
+    float* sr = smf + 3 * m;
+    __shared__ float red[CT / 32][2];
+    __shared__ int stop;
+    for (int q = threadIdx.x; q < m; q += CT) { se[q] = e[q]; sh[q] = hi[q]; sl[q] = lo[q]; sr[q] = rhs[q]; }
+    __syncthreads();
+    const int max_sweeps = sweeps > 0 ? sweeps : 60;
+    unsigned long long ev = 0;
+    for (int s = 0; s < max_sweeps; ++s) {
+        float du = 0.0f, um = 0.0f;
+        for (int c = 0; c < 8; ++c) {
+            const int pi = c & 1, pj = (c >> 1) & 1, pk = (c >> 2) & 1;
+            const int ni = colour_count(n, pi), nj = colour_count(n, pj), nk = colour_count(n, pk);
+            const int cnt = (ni > 0 && nj > 0 && nk > 0) ? ni * nj * nk : 0;
+            for (int t = threadIdx.x; t < cnt; t += CT) {
+                const int i = (pi ? 1 : 2) + 2 * (t % ni);
+                const int j = (pj ? 1 : 2) + 2 * ((t / ni) % nj);
+                const int k = (pk ? 1 : 2) + 2 * (t / (ni * nj));
+                const int p = (k * n + j) * n + i;
+                const float e0 = se[p];
+                const S3f B = base_hess_sm(sh, sl, p, n, n * n, inv_h2);
+                const S3f K = corr_hess_sm(se, p, n, n * n, e0, inv_h2);
+                bool nonconvex = false;
+                const float z = corr_root(B, K, sr[p], &nonconvex);
+                const float v = fmaf(h2half, z, e0);
+                se[p] = v;
+                du = fmaxf(du, fabsf(v - e0));
+                um = fmaxf(um, fabsf(v));
+                ev += nonconvex ? 1ull : 0ull;
+            }
+            __syncthreads();
+        }
+        if (sweeps > 0) continue;
+        for (int o = 16; o > 0; o >>= 1) {
+            du = fmaxf(du, __shfl_down_sync(0xffffffffu, du, o));
+            um = fmaxf(um, __shfl_down_sync(0xffffffffu, um, o));
+        }
+        if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5][0] = du; red[threadIdx.x >> 5][1] = um; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float a = 0.0f, b = 0.0f;
+            for (int w = 0; w < CT / 32; ++w) { a = fmaxf(a, red[w][0]); b = fmaxf(b, red[w][1]); }
+            stop = (a <= 1e-6f * b) ? 1 : 0;
+        }
+        __syncthreads();
+        if (stop) break;
+    }
+    for (int q = threadIdx.x; q < m; q += CT) e[q] = se[q];
+    if (events && ev) atomicAdd(events, ev);
+}
+
+// u += e (optional), then u = hi + lo (FP32 split) and e = 0, over the whole grid.
+__global__ void k_split_update(double* __restrict__ u, float* __restrict__ e, float* __restrict__ hi,
+                               float* __restrict__ lo, long long m, int apply)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    double v = u[p];
+    if (apply) {
+        v += (double)e[p];
+        u[p] = v;
+    }
+    const float h = (float)v;
+    hi[p] = h;
+    lo[p] = (float)(v - (double)h);
+    e[p] = 0.0f;
+}
+
+// FP64 fine residual r = rhs - det(D^2_h u), written as FP32, with the
+// (max, sum of squares) norm partials of the FP64 values.
+__global__ void __launch_bounds__(BX * BY) k_residual64_to32(const double* __restrict__ u,
+                                                             const double* __restrict__ rhs, float* __restrict__ r,
+                                                             int n, double inv_h6, double* partials)
+{
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const long long sy = n, sz = (long long)n * n;
+    double mx = 0.0, ss = 0.0;
+    for (int k = blockIdx.z; k < n; k += gridDim.z) {
+        if (i < n && j < n) {
+            const long long p = lin(i, j, k, n);
+            double val = 0.0;
+            if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
+                const HessS H = gather_hess(u, p, sy, sz, u[p]);
+                val = fma(-det0(H), inv_h6, rhs[p]);
+                mx = fmax(mx, fabs(val));
+                ss = fma(val, val, ss);
+            }
+            r[p] = (float)val;
+        }
+    }
+    __shared__ double smx[BX * BY / 32], sss[BX * BY / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        ss += __shfl_down_sync(0xffffffffu, ss, o);
+    }
+    const int t = threadIdx.y * BX + threadIdx.x;
+    if ((t & 31) == 0) { smx[t >> 5] = mx; sss[t >> 5] = ss; }
+    __syncthreads();
+    if (t == 0) {
+        double a = smx[0], b = sss[0];
+        for (int w = 1; w < BX * BY / 32; ++w) { a = fmax(a, smx[w]); b += sss[w]; }
+        const int slot = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        partials[2 * slot] = a;
+        partials[2 * slot + 1] = b;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_smooth_corr(float* e, const float* hi, const float* lo, const float* rhs, int n, double h,
+                               int nsweeps, unsigned long long* events, cudaStream_t s)
+{
+    const float inv_h2 = (float)(1.0 / (h * h));
+    const float h2half = (float)(0.5 * h * h);
+    for (int sw = 0; sw < nsweeps; ++sw) {
+        cudaError_t e_;
+        if ((e_ = launch_colour_corr<0>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<1>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<2>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<3>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<4>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<5>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<6>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<7>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_residual_corr(const float* e, const float* hi, const float* lo, const float* rhs, float* res,
+                                 int n, double h, cudaStream_t s)
+{
+    count_launches(1);
+    k_residual_corr<<<grid_of(n), dim3(BX, BY), 0, s>>>(e, hi, lo, rhs, res, n, (float)(1.0 / (h * h)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_rhs_corr(const float* w, const float* hi, const float* lo, const float* resc, float* rhs,
+                                   int nc, double H, cudaStream_t s)
+{
+    count_launches(1);
+    k_coarse_rhs_corr<<<grid_of(nc), dim3(BX, BY), 0, s>>>(w, hi, lo, resc, rhs, nc, (float)(1.0 / (H * H)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_level_f32(const float* ef, const float* rf, int nf, float* wc, float* ec, float* rc,
+                                      int kind, int approx, cudaStream_t s)
+{
+    const int nc = (nf + 1) / 2;
+    count_launches(1);
+    xfer::k_restrict<float><<<grid_of(nc), dim3(BX, BY), 0, s>>>(ef, rf, nf, wc, ec, rc, nc, kind, approx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add_f32(const float* ec, const float* wc, int nc, float* ef, cudaStream_t s)
+{
+    const int nf = 2 * nc - 1;
+    count_launches(1);
+    xfer::k_prolong<float><<<grid_of(nf), dim3(BX, BY), 0, s>>>(ec, wc, nc, ef, nf, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject_f32(const float* vf, int nf, float* vc, cudaStream_t s)
+{
+    const int nc = (nf + 1) / 2;
+    count_launches(1);
+    xfer::k_inject<float><<<grid_of(nc), dim3(BX, BY), 0, s>>>(vf, nf, vc, nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarsest_corr(float* e, const float* hi, const float* lo, const float* rhs, int n, double h,
+                                 int sweeps, unsigned long long* events, cudaStream_t s)
+{
+    const size_t smem = 4 * sizeof(float) * (size_t)n * n * n;
+    if (smem > 48 * 1024) {
+        cudaError_t e_ = cudaFuncSetAttribute(k_coarsest_corr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e_ != cudaSuccess) return e_;
+    }
+    count_launches(1);
+    k_coarsest_corr<<<1, CT, smem, s>>>(e, hi, lo, rhs, n, (float)(1.0 / (h * h)), (float)(0.5 * h * h), sweeps,
+                                        events);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_update(double* u, float* e, float* hi, float* lo, int n, int apply, cudaStream_t s)
+{
+    const long long m = (long long)n * n * n;
+    count_launches(1);
+    k_split_update<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(u, e, hi, lo, m, apply);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r, int n, double h, double* partials,
+                                   cudaStream_t s)
+{
+    const double h2 = h * h;
+    count_launches(1);
+    const dim3 g((n + BX - 1) / BX, (n + BY - 1) / BY, n < 16 ? n : 16);
+    k_residual64_to32<<<g, dim3(BX, BY), 0, s>>>(u, rhs, r, n, 1.0 / (h2 * h2 * h2), partials);
+    return cudaGetLastError();
+}
+
+}  // namespace ma

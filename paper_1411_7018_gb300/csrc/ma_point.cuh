@@ -112,7 +112,7 @@ __device__ __forceinline__ bool is_pd(const M& H, F det)
 // rhs > 0 the iterates increase to the unique root below l1 (convexity).
 // Used when the FP32 first pass is not trustworthy (degenerate or far from
 // convex); each step costs an FP64 division.
-__device__ __noinline__ double root_f64_monotone(const HessS H, double rhs6)
+static __device__ __noinline__ double root_f64_monotone(const HessS H, double rhs6)
 {
     double z = gershgorin_low<HessS, double>(H) - cbrt(rhs6);
     for (int it = 0; it < 200; ++it) {
@@ -131,7 +131,7 @@ __device__ __noinline__ double root_f64_monotone(const HessS H, double rhs6)
 // z^3 - T z^2 + M z - (D - rhs6) with T, M, D the trace, minor sum and
 // determinant of Hs.  Trigonometric form when there are three real roots,
 // Cardano's formula when there is one, then two FP64 Newton polishes.
-__device__ __noinline__ double root_f64_all_real_min(const HessS H, double rhs6)
+static __device__ __noinline__ double root_f64_all_real_min(const HessS H, double rhs6)
 {
     const double T = H.A + H.B + H.C;
     const double M = minors_shift(H, 0.0);

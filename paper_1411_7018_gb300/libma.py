@@ -70,6 +70,8 @@ _SIGS = {
     "ma_norm_scratch_bytes": [C.c_int, C.POINTER(C.c_size_t)],
     "ma_norm": [_vp, C.c_int, C.c_double, _vp, C.c_size_t, C.POINTER(C.c_double), _vp],
     "ma_kernel_launch_count": [C.POINTER(C.c_ulonglong)],
+    "ma_smooth_correction": [_vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp, _vp],
+    "ma_residual_correction": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp],
     "ma_norm_static": [_vp, C.c_int, C.c_double, C.POINTER(C.c_double), _vp],
 }
 # Declared in include/ma.h; the test suite checks that the library exports them.
@@ -217,6 +219,16 @@ def ma_interpolate(uc, nc: int, uf, stream=None) -> None:
 
 def ma_coarsest_solve(u, rhs, n: int, h: float, sweeps: int = 0, events=None, stream=None) -> None:
     _check(load().ma_coarsest_solve(_ptr(u), _ptr(rhs), n, h, sweeps, _ptr(events), _stream(stream)))
+
+
+def ma_smooth_correction(e, u_hi, u_lo, rhs, n: int, h: float, nsweeps: int = 1, events=None, stream=None) -> None:
+    _check(load().ma_smooth_correction(_ptr(e), _ptr(u_hi), _ptr(u_lo), _ptr(rhs), n, h, nsweeps, _ptr(events),
+                                       _stream(stream)))
+
+
+def ma_residual_correction(e, u_hi, u_lo, rhs, res, n: int, h: float, stream=None) -> None:
+    _check(load().ma_residual_correction(_ptr(e), _ptr(u_hi), _ptr(u_lo), _ptr(rhs), _ptr(res), n, h,
+                                         _stream(stream)))
 
 
 def ma_norm_scratch_bytes(n: int) -> int:

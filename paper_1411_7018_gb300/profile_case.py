@@ -3,8 +3,10 @@
     python -m paper_1411_7018_gb300.profile_case --case smooth --n 257 --reps 2
 
 Cases: ``smooth`` (FP64 smoother sweeps, 8 colour launches each), ``residual``
-(the FP64 residual kernel), ``vcycle`` (whole FP64 V-cycles of a resident
-hierarchy), ``solve`` (one FMG + V-cycle solve to 1e-10).  The grid holds
+(the FP64 residual kernel), ``smooth_corr`` (FP32 correction-smoother sweeps
+of the mixed path on a small smooth correction), ``vcycle`` (whole V-cycles of
+a resident hierarchy), ``solve`` (one FMG + V-cycle solve to 1e-10);
+``--precision mixed`` runs the hierarchy cases in mixed precision.  The grid holds
 Example 4 (u = exp(|x|^2/2)) with a small seeded perturbation; fields of a
 257^3 grid are 136 MB each, larger than L2.  Prints nothing but a one-line
 summary; it measures nothing itself.
@@ -22,7 +24,8 @@ from . import problems
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["smooth", "residual", "vcycle", "solve"], default="smooth")
+    ap.add_argument("--case", choices=["smooth", "residual", "smooth_corr", "vcycle", "solve"], default="smooth")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--problem", default="exp")
@@ -40,13 +43,22 @@ def main():
         r = torch.empty_like(u)
         for _ in range(a.reps):
             M.ma_residual(u, f, r, a.n, pr.h)
+    elif a.case == "smooth_corr":
+        hi = u.float()
+        lo = (u - hi.double()).float()
+        e = torch.zeros_like(hi)
+        rhs = (1e-6 * f).float()
+        rhs[0], rhs[-1] = 0, 0
+        for _ in range(a.reps):
+            M.ma_smooth_correction(e, hi, lo, rhs, a.n, pr.h, 1)
     else:
-        H = M.Hierarchy(M.make_desc(a.n, length=pr.length))
+        prec = M.MA_MIXED if a.precision == "mixed" else M.MA_FP64
+        H = M.Hierarchy(M.make_desc(a.n, length=pr.length, precision=prec))
         H.set_rhs_bc(f, u)
         if a.case == "vcycle":
             H.vcycle(a.reps)
         else:
-            H.solve(tol=1e-10)
+            H.solve(tol=1e-10, raise_on_error=False)
         H.close()
     torch.cuda.synchronize()
     print(f"profile_case {a.case} n={a.n} reps={a.reps} done")

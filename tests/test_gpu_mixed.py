@@ -1,0 +1,131 @@
+"""GPU parity of the mixed-precision path (FP32 correction cycles under an FP64
+residual and update) against the FP64 CPU oracle.
+
+The correction operator N(e) = det(D^2_h(u + e)) - det(D^2_h u) has a plain
+definition, so its oracle is two FP64 oracle evaluations of the discrete
+Monge-Ampere operator; a correction sweep is one oracle Gauss-Seidel sweep on
+w = u + e with right-hand side det(D^2_h u) + rhs.  FP32 bounds: the
+correction kernels carry ~1e-5 relative error in the base Hessian (hi/lo
+split) and FP32 rounding of e, so they are compared relative to the size of
+the quantity they compute.  Whole solves meet the same FP64 tolerance as the
+FP64 path and are compared with the oracle at the FP64 bound (1e-10 relative).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_1411_7018_gb300 import libma as M
+from paper_1411_7018_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    M.load()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def split(u):
+    hi = u.astype(np.float32)
+    lo = (u - hi.astype(np.float64)).astype(np.float32)
+    return hi, lo
+
+
+def smooth_correction_field(n, amp, seed):
+    x, y, z = P.grid_coords(n)
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.5, 1.5, 3)
+    e = amp * np.sin(np.pi * x) * np.sin(np.pi * y) * np.sin(np.pi * z) * (1 + a[0] * x + a[1] * y * z)
+    e += 0.1 * amp * rng.standard_normal(e.shape)
+    e[0], e[-1], e[:, 0], e[:, -1], e[:, :, 0], e[:, :, -1] = 0, 0, 0, 0, 0, 0
+    return e.astype(np.float32)
+
+
+@pytest.mark.parametrize("name,n,amp", [("exp", 33, 1e-4), ("cosine", 65, 1e-5), ("exp", 129, 1e-6)])
+def test_correction_residual_matches_oracle_definition(name, n, amp):
+    pr = P.make(name, n, seed=3)
+    u = pr.u
+    e = smooth_correction_field(n, amp, n)
+    rng = np.random.default_rng(1)
+    rhs = (1e-3 * rng.standard_normal(u.shape)).astype(np.float32)
+    N_ref = O.discrete_ma(np.ascontiguousarray(u + e.astype(np.float64)), pr.h) - O.discrete_ma(u, pr.h)
+    ref = rhs.astype(np.float64) - N_ref
+    ref[0], ref[-1], ref[:, 0], ref[:, -1], ref[:, :, 0], ref[:, :, -1] = 0, 0, 0, 0, 0, 0
+    hi, lo = split(u)
+    res = torch.empty(u.shape, dtype=torch.float32, device="cuda")
+    M.ma_residual_correction(dev(e), dev(hi), dev(lo), dev(rhs), res, n, pr.h)
+    got = host(res).astype(np.float64)
+    inner = (slice(1, -1),) * 3
+    scale = np.max(np.abs(N_ref[inner])) + np.max(np.abs(rhs))
+    assert np.max(np.abs(got - ref)) <= 2e-4 * scale
+
+
+@pytest.mark.parametrize("name,n,amp", [("exp", 33, 1e-4), ("cosine", 65, 1e-5)])
+def test_correction_sweep_matches_oracle_sweep(name, n, amp):
+    pr = P.make(name, n, seed=4)
+    u = pr.u
+    e = smooth_correction_field(n, amp, n + 1)
+    rng = np.random.default_rng(2)
+    rhs = (1e-2 * rng.standard_normal(u.shape) * np.max(pr.f)).astype(np.float32)
+    rhs[0], rhs[-1] = 0, 0
+    w = np.ascontiguousarray(u + e.astype(np.float64))
+    ftot = O.discrete_ma(u, pr.h) + rhs.astype(np.float64)
+    O.gs_sweep(w, ftot, pr.h)
+    e_ref = w - u
+    hi, lo = split(u)
+    ed = dev(e)
+    M.ma_smooth_correction(ed, dev(hi), dev(lo), dev(rhs), n, pr.h, 1)
+    got = host(ed).astype(np.float64)
+    change = np.max(np.abs(e_ref - e.astype(np.float64)))
+    assert change > 0
+    assert np.max(np.abs(got - e_ref)) <= 1e-3 * change + 1e-6 * np.max(np.abs(e_ref))
+
+
+@pytest.mark.parametrize("name,n", [("exp", 33), ("cosine", 65), ("exp", 129), ("quadratic", 65), ("sine", 65)])
+def test_mixed_solve_matches_fp64_oracle(name, n):
+    pr = P.make(name, n, seed=5)
+    H = M.Hierarchy(M.make_desc(n, length=pr.length, precision=M.MA_MIXED))
+    H.set_rhs_bc(dev(pr.f), dev(pr.initial()))
+    res = H.solve(tol=1e-10, max_cycles=40)
+    u = torch.empty_like(dev(pr.f))
+    H.get_solution(u)
+    got = host(u)
+    H.close()
+    ref = pr.initial()
+    O.solve(ref, pr.f, pr.h, tol=1e-10, params=O.Params())
+    assert res.res <= 1e-10
+    assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
+    e_gpu, e_ref = np.max(np.abs(got - pr.u)), np.max(np.abs(ref - pr.u))
+    assert abs(e_gpu - e_ref) <= 1e-3 * e_ref + 1e-12 * np.max(np.abs(ref))
+
+
+def test_mixed_and_fp64_agree_at_257():
+    pr = P.make("exp", 257)
+    outs = {}
+    for prec in (M.MA_FP64, M.MA_MIXED):
+        H = M.Hierarchy(M.make_desc(257, precision=prec))
+        H.set_rhs_bc(dev(pr.f), dev(pr.initial()))
+        r = H.solve(tol=1e-10, max_cycles=40)
+        assert r.res <= 1e-10
+        u = torch.empty_like(dev(pr.f))
+        H.get_solution(u)
+        outs[prec] = host(u)
+        H.close()
+    assert np.max(np.abs(outs[M.MA_FP64] - outs[M.MA_MIXED])) <= 1e-10 * np.max(np.abs(pr.u))
+    r = O.residual(outs[M.MA_MIXED], pr.f, pr.h)
+    assert np.max(np.abs(r)) <= 1.5e-10 * np.max(np.abs(pr.f[1:-1, 1:-1, 1:-1]))
