@@ -81,6 +81,8 @@ typedef struct {
     int precision;       /* MA_FP64 | MA_MIXED                                         */
     int coarse_sweeps;   /* > 0: that many sweeps on the coarsest grid (Section 4 uses
                             1); 0: sweep until max|du| <= 1e-14 max|u| (cap 100)        */
+    int inner_cycles;    /* MA_MIXED: FP32 correction V-cycles per FP64 residual and
+                            update (0: the default, 3); ignored in MA_FP64              */
 } ma_hier_desc;
 
 /* Stopping rule for ma_solve.  Converged when ||f - det(D^2_h u)|| <= tol *
@@ -227,9 +229,12 @@ ma_status ma_coarsest_solve(double *u_dev, const double *rhs_dev, int n, double 
 
 /* nsweeps 8-colour sweeps on e: at each point the new e is the one whose
  * u + e takes the smallest real root of the local cubic (Section 2, Eq.
- * realroots) for right-hand side det(D^2_h u) + rhs. */
-ma_status ma_smooth_correction(float *e_dev, const float *u_hi_dev, const float *u_lo_dev, const float *rhs_dev,
-                               int n, double h, int nsweeps, unsigned long long *events_dev, ma_stream_t stream);
+ * realroots) for right-hand side det(D^2_h u) + rhs.  B = D^2_h u is first
+ * computed once into b_scratch_dev (6 (n-2)^3 floats, overwritten; colour-
+ * major layout) and read from there by every sweep. */
+ma_status ma_smooth_correction(float *e_dev, float *b_scratch_dev, const float *u_hi_dev, const float *u_lo_dev,
+                               const float *rhs_dev, int n, double h, int nsweeps, unsigned long long *events_dev,
+                               ma_stream_t stream);
 
 /* res = rhs - N(e) on the interior, 0 on the shell. */
 ma_status ma_residual_correction(const float *e_dev, const float *u_hi_dev, const float *u_lo_dev,

@@ -74,6 +74,8 @@ ma_status check_desc(const ma_hier_desc* d)
         return fail(MA_ERR_INVALID_ARG, "bad precision %d", d->precision);
     if (d->coarse_sweeps < 0 || d->coarse_sweeps > 1000)
         return fail(MA_ERR_INVALID_ARG, "coarse_sweeps must be in [0, 1000]");
+    if (d->inner_cycles < 0 || d->inner_cycles > 16)
+        return fail(MA_ERR_INVALID_ARG, "inner_cycles must be in [0, 16]");
     return MA_OK;
 }
 
@@ -100,6 +102,7 @@ size_t layout(ma_hierarchy* H, const ma_hier_desc* d, char* base)
         lv.w = (double*)take(pts * sizeof(double));
         if (d->precision == MA_MIXED) {
             lv.e = (float*)take(pts * sizeof(float));
+            lv.bstore = (float*)take(ma::base_store_floats(m) * sizeof(float));
             lv.hi = (float*)take(pts * sizeof(float));
             lv.lo = (float*)take(pts * sizeof(float));
             lv.rhs32 = (float*)take(pts * sizeof(float));
@@ -186,6 +189,10 @@ cudaError_t refresh_base(ma_hierarchy* H, int apply)
         if ((e = ma::launch_inject_f32(A.hi, A.n, C.hi, s)) != cudaSuccess) return e;
         if ((e = ma::launch_inject_f32(A.lo, A.n, C.lo, s)) != cudaSuccess) return e;
     }
+    for (int l = 0; l < H->L; ++l) {
+        ma::Level& A = H->lev[l];
+        if ((e = ma::launch_base_colour(A.hi, A.lo, A.bstore, A.n, A.h, s)) != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 
@@ -199,7 +206,7 @@ cudaError_t corr_vcycle(ma_hierarchy* H)
     for (int l = 0; l < H->L - 1; ++l) {
         ma::Level& F = H->lev[l];
         ma::Level& C = H->lev[l + 1];
-        if ((e = ma::launch_smooth_corr(F.e, F.hi, F.lo, F.rhs32, F.n, F.h, d.nu1, H->events, s)) != cudaSuccess)
+        if ((e = ma::launch_smooth_corr(F.e, F.bstore, F.rhs32, F.n, F.h, d.nu1, H->events, s)) != cudaSuccess)
             return e;
         if ((e = ma::launch_residual_corr(F.e, F.hi, F.lo, F.rhs32, F.res32, F.n, F.h, s)) != cudaSuccess) return e;
         if ((e = ma::launch_restrict_level_f32(F.e, F.res32, F.n, C.w32, C.e, C.res32, d.restrict_kind,
@@ -216,7 +223,7 @@ cudaError_t corr_vcycle(ma_hierarchy* H)
         ma::Level& F = H->lev[l];
         ma::Level& C = H->lev[l + 1];
         if ((e = ma::launch_prolong_add_f32(C.e, C.w32, C.n, F.e, s)) != cudaSuccess) return e;
-        if ((e = ma::launch_smooth_corr(F.e, F.hi, F.lo, F.rhs32, F.n, F.h, d.nu2, H->events, s)) != cudaSuccess)
+        if ((e = ma::launch_smooth_corr(F.e, F.bstore, F.rhs32, F.n, F.h, d.nu2, H->events, s)) != cudaSuccess)
             return e;
     }
     return cudaSuccess;
@@ -232,6 +239,51 @@ cudaError_t mixed_residual(ma_hierarchy* H)
     return ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s);
 }
 
+// Runs body() as a CUDA graph captured once on the hierarchy's private
+// stream and replayed on its own stream: one graph launch instead of the
+// ~10^2 - 10^3 kernel launches of a cycle or an FMG pass.
+template <typename F>
+cudaError_t run_graph(ma_hierarchy* H, ma::GraphSlot& gs, F body)
+{
+    if (!gs.exec) {
+        const unsigned long long before = ma::launch_count();
+        cudaError_t e = cudaStreamBeginCapture(H->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        cudaStream_t user = H->s;
+        H->s = H->cap;
+        const cudaError_t eb = body();
+        H->s = user;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(H->cap, &g);
+        const unsigned long long captured = ma::launch_count() - before;
+        ma::uncount_launches(captured);   // captured, not run
+        if (eb != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return eb != cudaSuccess ? eb : e;
+        }
+        e = cudaGraphInstantiate(&gs.exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            gs.exec = nullptr;
+            return e;
+        }
+        gs.graph = g;
+        gs.launches = captured;
+    }
+    ma::count_launches(gs.launches);
+    return cudaGraphLaunch(gs.exec, H->s);
+}
+
+void destroy_graphs(ma_hierarchy* H)
+{
+    ma::GraphSlot* slots[4] = {&H->g_init[0], &H->g_init[1], &H->g_init[2], &H->g_cycle};
+    for (ma::GraphSlot* gs : slots) {
+        if (gs->exec) cudaGraphExecDestroy(gs->exec);
+        if (gs->graph) cudaGraphDestroy(gs->graph);
+        *gs = ma::GraphSlot();
+    }
+}
+
 // One outer (defect-correction) iteration: FP64 residual, FP32 correction
 // V-cycle, FP64 update.  Leaves the base refreshed for the next iteration.
 cudaError_t mixed_iteration(ma_hierarchy* H)
@@ -239,7 +291,9 @@ cudaError_t mixed_iteration(ma_hierarchy* H)
     cudaError_t e;
     if ((e = refresh_base(H, 0)) != cudaSuccess) return e;
     if ((e = mixed_residual(H)) != cudaSuccess) return e;
-    if ((e = corr_vcycle(H)) != cudaSuccess) return e;
+    const int inner = H->d.inner_cycles > 0 ? H->d.inner_cycles : 3;
+    for (int c = 0; c < inner; ++c)
+        if ((e = corr_vcycle(H)) != cudaSuccess) return e;
     return refresh_base(H, 1);
 }
 
@@ -334,10 +388,17 @@ ma_status ma_create_hierarchy(const ma_hier_desc* desc, void* dev_workspace, siz
     H->bytes = need;
     H->s = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&H->device);
+    if (e == cudaSuccess) e = ma::prepare_coarsest_kernels();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&H->host, 4 * sizeof(double) + sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(H->events, 0, sizeof(unsigned long long), H->s);
+    for (int l = 0; l < H->L && e == cudaSuccess; ++l) {   // corrections start at zero (shell stays zero)
+        const size_t pts = (size_t)H->lev[l].n * H->lev[l].n * H->lev[l].n;
+        if (H->lev[l].e) e = cudaMemsetAsync(H->lev[l].e, 0, pts * sizeof(float), H->s);
+    }
     if (e != cudaSuccess) {
         if (H->host) cudaFreeHost(H->host);
+        if (H->cap) cudaStreamDestroy(H->cap);
         delete H;
         return fail(MA_ERR_CUDA, "create: %s", cudaGetErrorString(e));
     }
@@ -350,6 +411,8 @@ ma_status ma_destroy_hierarchy(ma_hierarchy* H)
     if (!H) return MA_OK;
     DeviceGuard g(H->device);
     cudaError_t e = cudaStreamSynchronize(H->s);
+    destroy_graphs(H);
+    if (H->cap) cudaStreamDestroy(H->cap);
     if (H->host) cudaFreeHost(H->host);
     delete H;
     if (e != cudaSuccess) return fail(MA_ERR_CUDA, "destroy: %s", cudaGetErrorString(e));
@@ -438,19 +501,25 @@ ma_status ma_solve(ma_hierarchy* H, const ma_solve_opts* opts, ma_solve_result* 
         if (!(scale > 0.0)) scale = 1.0;
     }
     const bool mixed = H->d.precision == MA_MIXED;
-    // In mixed precision the FMG pass stops at the interpolated finest iterate
+    // Initial iterate and its residual norm, then one graph per cycle.  In
+    // mixed precision the FMG pass stops at the interpolated finest iterate
     // and the FP32-corrected outer iterations take over from there.
-    if (opts->init == MA_INIT_FMG) MA_CK(fmg(H, !mixed));
-    else if (opts->init == MA_INIT_ZERO) MA_CK(ma::launch_zero_interior(H->lev[0].u, H->lev[0].n, H->s));
+    const int init = opts->init;
+    MA_CK(run_graph(H, H->g_init[init], [&]() -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        if (init == MA_INIT_FMG) e = fmg(H, !mixed);
+        else if (init == MA_INIT_ZERO) e = ma::launch_zero_interior(H->lev[0].u, H->lev[0].n, H->s);
+        if (e != cudaSuccess) return e;
+        if (mixed) {
+            if ((e = refresh_base(H, 0)) != cudaSuccess) return e;
+            return mixed_residual(H);
+        }
+        ma::Level& F = H->lev[0];
+        if ((e = ma::launch_residual(F.u, F.rhs, F.r, F.n, F.h, H->partials, H->s)) != cudaSuccess) return e;
+        return ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s);
+    }));
     double mx, l2;
-    ma_status st;
-    if (mixed) {
-        MA_CK(refresh_base(H, 0));
-        MA_CK(mixed_residual(H));
-        st = read_norms(H, &mx, &l2);
-    } else {
-        st = fine_residual_norms(H, &mx, &l2);
-    }
+    ma_status st = read_norms(H, &mx, &l2);
     if (st != MA_OK) return st;
     double rel = (opts->norm == MA_NORM_MAX ? mx : l2) / scale;
     res->res0 = rel;
@@ -460,15 +529,21 @@ ma_status ma_solve(ma_hierarchy* H, const ma_solve_opts* opts, ma_solve_result* 
         if (!std::isfinite(rel)) { out = MA_ERR_NONFINITE; break; }
         if (rel <= opts->tol) break;
         if (res->cycles >= opts->max_cycles) { out = MA_ERR_NOT_CONVERGED; break; }
-        if (mixed) {
-            MA_CK(corr_vcycle(H));
-            MA_CK(refresh_base(H, 1));
-            MA_CK(mixed_residual(H));
-            st = read_norms(H, &mx, &l2);
-        } else {
-            MA_CK(vcycle_from(H, 0));
-            st = fine_residual_norms(H, &mx, &l2);
-        }
+        MA_CK(run_graph(H, H->g_cycle, [&]() -> cudaError_t {
+            cudaError_t e;
+            if (mixed) {
+                const int inner = H->d.inner_cycles > 0 ? H->d.inner_cycles : 3;
+                for (int c = 0; c < inner; ++c)
+                    if ((e = corr_vcycle(H)) != cudaSuccess) return e;
+                if ((e = refresh_base(H, 1)) != cudaSuccess) return e;
+                return mixed_residual(H);
+            }
+            if ((e = vcycle_from(H, 0)) != cudaSuccess) return e;
+            ma::Level& F = H->lev[0];
+            if ((e = ma::launch_residual(F.u, F.rhs, F.r, F.n, F.h, H->partials, H->s)) != cudaSuccess) return e;
+            return ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s);
+        }));
+        st = read_norms(H, &mx, &l2);
         res->cycles += 1;
         if (st != MA_OK) return st;
         const double nrel = (opts->norm == MA_NORM_MAX ? mx : l2) / scale;
@@ -557,16 +632,19 @@ ma_status ma_coarsest_solve(double* u, const double* rhs, int n, double h, int s
 {
     if (!u || !rhs || !valid_step_grid(n) || n > 17 || !(h > 0.0) || sweeps < 0 || sweeps > 1000)
         return fail(MA_ERR_INVALID_ARG, "ma_coarsest_solve: bad arguments (n <= 17)");
+    MA_CK(ma::prepare_coarsest_kernels());
     MA_CK(ma::launch_coarsest(u, rhs, n, h, sweeps, events, (cudaStream_t)stream));
     return MA_OK;
 }
 
-ma_status ma_smooth_correction(float* e, const float* hi, const float* lo, const float* rhs, int n, double h,
-                               int nsweeps, unsigned long long* events, ma_stream_t stream)
+ma_status ma_smooth_correction(float* e, float* b_scratch, const float* hi, const float* lo, const float* rhs, int n,
+                               double h, int nsweeps, unsigned long long* events, ma_stream_t stream)
 {
-    if (!e || !hi || !lo || !rhs || !valid_step_grid(n) || !(h > 0.0) || nsweeps < 0)
+    if (!e || !b_scratch || !hi || !lo || !rhs || !valid_step_grid(n) || !(h > 0.0) || nsweeps < 0)
         return fail(MA_ERR_INVALID_ARG, "ma_smooth_correction: bad arguments");
-    MA_CK(ma::launch_smooth_corr(e, hi, lo, rhs, n, h, nsweeps, events, (cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    MA_CK(ma::launch_base_colour(hi, lo, b_scratch, n, h, s));
+    MA_CK(ma::launch_smooth_corr(e, b_scratch, rhs, n, h, nsweeps, events, s));
     return MA_OK;
 }
 

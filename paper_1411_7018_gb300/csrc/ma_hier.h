@@ -21,6 +21,7 @@ struct Level {
     double* w = nullptr;     // coarse levels: the restricted approximation w_H
     // mixed precision (FP32 correction cycle); null in FP64 mode
     float* e = nullptr;      // correction
+    float* bstore = nullptr; // B = D^2_h u per colour (6 floats per interior point), refreshed per outer iteration
     float* hi = nullptr;     // base u = hi + lo (FP32 split)
     float* lo = nullptr;
     float* rhs32 = nullptr;  // correction-problem right-hand side (fine: the FP64 residual)
@@ -28,6 +29,15 @@ struct Level {
     float* w32 = nullptr;    // coarse levels: the restricted correction
 };
 
+}  // namespace ma
+
+namespace ma {
+// A captured sequence of launches, replayed as one CUDA graph.
+struct GraphSlot {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;   // kernels in the graph
+};
 }  // namespace ma
 
 struct ma_hierarchy {
@@ -44,4 +54,7 @@ struct ma_hierarchy {
     unsigned long long* events = nullptr;  // device: nonconvex root events
     int* flag = nullptr;                 // device: input validation count
     double* host = nullptr;              // pinned host read-back (4 doubles + 1 counter)
+    cudaStream_t cap = nullptr;          // private stream the graphs are captured on
+    ma::GraphSlot g_init[3];             // per ma_solve init kind: init + first residual norm
+    ma::GraphSlot g_cycle;               // one cycle + residual norm
 };

@@ -8,6 +8,10 @@ namespace ma {
 
 // Kernel launches issued by this library in this process (all devices).
 void count_launches(unsigned long long k);
+void uncount_launches(unsigned long long k);
+// Sets the coarsest-grid kernels' shared-memory limits for grids up to n = 17
+// (call outside stream capture).
+cudaError_t prepare_coarsest_kernels();
 unsigned long long launch_count();
 
 // Sets the thread-local text ma_last_error_string() returns.
@@ -40,8 +44,12 @@ cudaError_t launch_copy_rhs_bc(const double* f, const double* g, double* rhs, do
 
 // Mixed-precision kernels (ma_kernels_mixed.cu): FP32 correction cycle fields
 // are n^3 floats; the base u is split as hi + lo.
-cudaError_t launch_smooth_corr(float* e, const float* hi, const float* lo, const float* rhs, int n, double h,
-                               int nsweeps, unsigned long long* events, cudaStream_t s);
+// Per-level store of B = D^2_h u (from the hi/lo split) in colour-major SoA
+// layout: base_store_floats(n) floats, filled by launch_base_colour.
+size_t base_store_floats(int n);
+cudaError_t launch_base_colour(const float* hi, const float* lo, float* bstore, int n, double h, cudaStream_t s);
+cudaError_t launch_smooth_corr(float* e, const float* bstore, const float* rhs, int n, double h, int nsweeps,
+                               unsigned long long* events, cudaStream_t s);
 cudaError_t launch_residual_corr(const float* e, const float* hi, const float* lo, const float* rhs, float* res,
                                  int n, double h, cudaStream_t s);
 cudaError_t launch_coarse_rhs_corr(const float* w, const float* hi, const float* lo, const float* resc, float* rhs,

@@ -49,8 +49,8 @@ __global__ void __launch_bounds__(BX * BY) k_smooth_colour(double* u, const doub
     const double v0 = u[p];
     const HessS H = gather_hess(u, p, sy, sz, v0);
     bool nonconvex = false;
-    const double z = smallest_root(H, h6 * rhs[p], &nonconvex);
-    u[p] = fma(0.5, z, v0);
+    const double z = smallest_root(H, h6 * rhs[p], &nonconvex);   // h6 = 64 h^6: the 4 Hs scaling
+    u[p] = fma(0.125, z, v0);
     if (nonconvex && events) atomicAdd(events, 1ull);
 }
 
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(BX * BY) k_residual(const double* __restrict__
             double val = 0.0;
             if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
                 const HessS H = gather_hess(u, p, sy, sz, u[p]);
-                val = fma(-det0(H), inv_h6, rhs[p]);
+                val = fma(-det0(H), inv_h6, rhs[p]);   // inv_h6 = 1 / (64 h^6)
                 mx = fmax(mx, fabs(val));
                 ss = fma(val, val, ss);
             }
@@ -211,12 +211,13 @@ __device__ __forceinline__ HessS gather_hess_plain(const double* u, int p, int s
     const double s4 = (q[sz + 1] + q[-sz - 1]) - (q[sz - 1] + q[-sz + 1]);
     const double t4 = (q[sz + sy] + q[-sz - sy]) - (q[sy - sz] + q[-sy + sz]);
     HessS H;
-    H.A = fma(-2.0, v0, a);
-    H.B = fma(-2.0, v0, b);
-    H.C = fma(-2.0, v0, c);
-    H.R = 0.25 * r4;
-    H.S = 0.25 * s4;
-    H.T = 0.25 * t4;
+    const double m8v = -8.0 * v0;
+    H.A = fma(4.0, a, m8v);
+    H.B = fma(4.0, b, m8v);
+    H.C = fma(4.0, c, m8v);
+    H.R = r4;
+    H.S = s4;
+    H.T = t4;
     return H;
 }
 
@@ -247,8 +248,8 @@ __global__ void __launch_bounds__(COARSE_THREADS) k_coarsest(double* u, const do
                 const double v0 = su[p];
                 const HessS H = gather_hess_plain(su, p, n, n * n, v0);
                 bool nonconvex = false;
-                const double z = smallest_root(H, h6 * sr[p], &nonconvex);
-                const double v = fma(0.5, z, v0);
+                const double z = smallest_root_precise(H, h6 * sr[p], &nonconvex);
+                const double v = fma(0.125, z, v0);
                 su[p] = v;
                 du = fmax(du, fabs(v - v0));
                 um = fmax(um, fabs(v));
@@ -280,12 +281,14 @@ __global__ void __launch_bounds__(COARSE_THREADS) k_coarsest(double* u, const do
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void uncount_launches(unsigned long long k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-static inline double pow6(double h) { const double h2 = h * h; return h2 * h2 * h2; }
+// 64 h^6: determinants of the 4 Hs matrices the gathers return are 64 h^6 det(D^2 u).
+static inline double pow6(double h) { const double h2 = h * h; return 64.0 * h2 * h2 * h2; }
 
 cudaError_t launch_smooth(double* u, const double* rhs, int n, double h, int nsweeps,
                           unsigned long long* events, cudaStream_t s)
@@ -412,13 +415,15 @@ cudaError_t launch_coarsest(double* u, const double* rhs, int n, double h, int s
                             unsigned long long* events, cudaStream_t s)
 {
     const size_t smem = 2 * sizeof(double) * (size_t)n * n * n;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_coarsest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
     count_launches(1);
     k_coarsest<<<1, COARSE_THREADS, smem, s>>>(u, rhs, n, pow6(h), sweeps, events);
     return cudaGetLastError();
+}
+
+cudaError_t prepare_coarsest_f64()
+{
+    return cudaFuncSetAttribute(k_coarsest, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * sizeof(double) * 17 * 17 * 17));
 }
 
 }  // namespace ma

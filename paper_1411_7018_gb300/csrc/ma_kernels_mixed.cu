@@ -38,37 +38,42 @@ struct S3f {
     float xx, yy, zz, xy, xz, yz;
 };
 
-// B = D^2_h u from the hi/lo split, differences to the centre first.
+// Scaled Hessian (divided by h^2) from a difference functor d(di, dj, dk) =
+// value at the offset minus the centre value; every user builds B and K
+// through this one routine, in the same order of operations.
+template <typename D>
+__device__ __forceinline__ S3f hess_from_diff(D d, float inv_h2)
+{
+    S3f B;
+    const float q = 0.25f * inv_h2;
+    B.xx = (d(1, 0, 0) + d(-1, 0, 0)) * inv_h2;
+    B.yy = (d(0, 1, 0) + d(0, -1, 0)) * inv_h2;
+    B.zz = (d(0, 0, 1) + d(0, 0, -1)) * inv_h2;
+    B.xy = ((d(1, 1, 0) + d(-1, -1, 0)) - (d(-1, 1, 0) + d(1, -1, 0))) * q;
+    B.xz = ((d(1, 0, 1) + d(-1, 0, -1)) - (d(-1, 0, 1) + d(1, 0, -1))) * q;
+    B.yz = ((d(0, 1, 1) + d(0, -1, -1)) - (d(0, 1, -1) + d(0, -1, 1))) * q;
+    return B;
+}
+
+// B = D^2_h u from the hi/lo split of u in global memory.
 __device__ __forceinline__ S3f base_hess(const float* __restrict__ hi, const float* __restrict__ lo, long long p,
                                          long long sy, long long sz, float inv_h2)
 {
     const float vh = hi[p], vl = lo[p];
-    auto d = [&](long long o) -> float { return (__ldg(hi + p + o) - vh) + (__ldg(lo + p + o) - vl); };
-    S3f B;
-    const float q = 0.25f * inv_h2;
-    B.xx = (d(1) + d(-1)) * inv_h2;
-    B.yy = (d(sy) + d(-sy)) * inv_h2;
-    B.zz = (d(sz) + d(-sz)) * inv_h2;
-    B.xy = ((d(sy + 1) + d(-sy - 1)) - (d(sy - 1) + d(-sy + 1))) * q;
-    B.xz = ((d(sz + 1) + d(-sz - 1)) - (d(sz - 1) + d(-sz + 1))) * q;
-    B.yz = ((d(sz + sy) + d(-sz - sy)) - (d(sy - sz) + d(-sy + sz))) * q;
-    return B;
+    return hess_from_diff(
+        [&](int di, int dj, int dk) -> float {
+            const long long o = p + di + dj * sy + dk * sz;
+            return (__ldg(hi + o) - vh) + (__ldg(lo + o) - vl);
+        },
+        inv_h2);
 }
 
-// K = D^2_h e at the current centre value e0.
+// K = D^2_h e at the current centre value e0, e in global memory.
 __device__ __forceinline__ S3f corr_hess(const float* __restrict__ e, long long p, long long sy, long long sz,
                                          float e0, float inv_h2)
 {
-    auto d = [&](long long o) -> float { return __ldg(e + p + o) - e0; };
-    S3f K;
-    const float q = 0.25f * inv_h2;
-    K.xx = (d(1) + d(-1)) * inv_h2;
-    K.yy = (d(sy) + d(-sy)) * inv_h2;
-    K.zz = (d(sz) + d(-sz)) * inv_h2;
-    K.xy = ((d(sy + 1) + d(-sy - 1)) - (d(sy - 1) + d(-sy + 1))) * q;
-    K.xz = ((d(sz + 1) + d(-sz - 1)) - (d(sz - 1) + d(-sz + 1))) * q;
-    K.yz = ((d(sz + sy) + d(-sz - sy)) - (d(sy - sz) + d(-sy + sz))) * q;
-    return K;
+    return hess_from_diff(
+        [&](int di, int dj, int dk) -> float { return __ldg(e + p + di + dj * sy + dk * sz) - e0; }, inv_h2);
 }
 
 __device__ __forceinline__ float det3(const S3f& A)
@@ -129,20 +134,72 @@ __device__ __forceinline__ float corr_root(const S3f& B, const S3f& K, float r, 
     return (float)root_f64_all_real_min(H, tot);
 }
 
-template <int PI, int PJ, int PK>
-__global__ void __launch_bounds__(BX * BY) k_smooth_corr(float* e, const float* __restrict__ hi,
-                                                          const float* __restrict__ lo, const float* __restrict__ rhs,
-                                                          int n, float inv_h2, float h2half,
-                                                          unsigned long long* events)
+__host__ __device__ __forceinline__ int colour_count(int n, int parity) { return parity ? (n - 1) / 2 : (n - 3) / 2; }
+
+// ---------------------------------------------------------------------------
+// Correction smoother, one colour per launch.  B = D^2_h u does not change
+// during an outer iteration, so it is computed once per level and stored per
+// colour (k_base_colour): colour c's interior points form a dense
+// ni x nj x nk box, and its six B components are six dense arrays of that box
+// (SoA), so a warp's loads of B are contiguous.  e and rhs stay in the
+// natural [k][j][i] layout (e is read through its 19-point stencil).
+// ---------------------------------------------------------------------------
+
+// Offset of colour c's block inside the per-level B store (6 floats per point).
+__host__ __device__ __forceinline__ long long colour_offset(int n, int c)
 {
-    const int i = (PI ? 1 : 2) + 2 * (int)(blockIdx.x * BX + threadIdx.x);
-    const int j = (PJ ? 1 : 2) + 2 * (int)(blockIdx.y * BY + threadIdx.y);
-    const int k = (PK ? 1 : 2) + 2 * (int)blockIdx.z;
-    if (i > n - 2 || j > n - 2 || k > n - 2) return;
+    long long off = 0;
+    for (int q = 0; q < c; ++q)
+        off += 6LL * colour_count(n, q & 1) * colour_count(n, (q >> 1) & 1) * colour_count(n, (q >> 2) & 1);
+    return off;
+}
+
+__global__ void __launch_bounds__(BX * BY) k_base_colour(const float* __restrict__ hi, const float* __restrict__ lo,
+                                                         float* __restrict__ bstore, int n, float inv_h2)
+{
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i < 1 || j < 1 || k < 1 || i > n - 2 || j > n - 2 || k > n - 2) return;
+    const long long sy = n, sz = (long long)n * n;
+    const S3f B = base_hess(hi, lo, lin(i, j, k, n), sy, sz, inv_h2);
+    const int pi = i & 1, pj = j & 1, pk = k & 1;
+    const int c = pi | (pj << 1) | (pk << 2);
+    const int ni = colour_count(n, pi), nj = colour_count(n, pj), nk = colour_count(n, pk);
+    const long long cnt = (long long)ni * nj * nk;
+    const int ii = (i - (pi ? 1 : 2)) >> 1, jj = (j - (pj ? 1 : 2)) >> 1, kk = (k - (pk ? 1 : 2)) >> 1;
+    float* b = bstore + colour_offset(n, c) + ((long long)kk * nj + jj) * ni + ii;
+    b[0] = B.xx;
+    b[cnt] = B.yy;
+    b[2 * cnt] = B.zz;
+    b[3 * cnt] = B.xy;
+    b[4 * cnt] = B.xz;
+    b[5 * cnt] = B.yz;
+}
+
+template <int PI, int PJ, int PK>
+__global__ void __launch_bounds__(BX * BY) k_smooth_corr(float* e, const float* __restrict__ bc,
+                                                          const float* __restrict__ rhs, int n, float inv_h2,
+                                                          float h2half, unsigned long long* events)
+{
+    const int ii = blockIdx.x * BX + threadIdx.x;
+    const int jj = blockIdx.y * BY + threadIdx.y;
+    const int kk = blockIdx.z;
+    const int ni = colour_count(n, PI), nj = colour_count(n, PJ);
+    if (ii >= ni || jj >= nj) return;
+    const int i = (PI ? 1 : 2) + 2 * ii, j = (PJ ? 1 : 2) + 2 * jj, k = (PK ? 1 : 2) + 2 * kk;
+    const long long cnt = (long long)ni * nj * colour_count(n, PK);
+    const float* b = bc + ((long long)kk * nj + jj) * ni + ii;
+    S3f B;
+    B.xx = __ldg(b);
+    B.yy = __ldg(b + cnt);
+    B.zz = __ldg(b + 2 * cnt);
+    B.xy = __ldg(b + 3 * cnt);
+    B.xz = __ldg(b + 4 * cnt);
+    B.yz = __ldg(b + 5 * cnt);
     const long long sy = n, sz = (long long)n * n;
     const long long p = lin(i, j, k, n);
     const float e0 = e[p];
-    const S3f B = base_hess(hi, lo, p, sy, sz, inv_h2);
     const S3f K = corr_hess(e, p, sy, sz, e0, inv_h2);
     bool nonconvex = false;
     const float z = corr_root(B, K, rhs[p], &nonconvex);
@@ -150,18 +207,17 @@ __global__ void __launch_bounds__(BX * BY) k_smooth_corr(float* e, const float* 
     if (nonconvex && events) atomicAdd(events, 1ull);
 }
 
-__host__ __device__ __forceinline__ int colour_count(int n, int parity) { return parity ? (n - 1) / 2 : (n - 3) / 2; }
-
 template <int C>
-cudaError_t launch_colour_corr(float* e, const float* hi, const float* lo, const float* rhs, int n, float inv_h2,
-                               float h2half, unsigned long long* ev, cudaStream_t s)
+cudaError_t launch_colour_corr(float* e, const float* bstore, const float* rhs, int n, float inv_h2, float h2half,
+                               unsigned long long* ev, cudaStream_t s)
 {
     constexpr int PI = C & 1, PJ = (C >> 1) & 1, PK = (C >> 2) & 1;
     const int ni = colour_count(n, PI), nj = colour_count(n, PJ), nk = colour_count(n, PK);
     if (ni <= 0 || nj <= 0 || nk <= 0) return cudaSuccess;
     dim3 grid((ni + BX - 1) / BX, (nj + BY - 1) / BY, nk);
     count_launches(1);
-    k_smooth_corr<PI, PJ, PK><<<grid, dim3(BX, BY), 0, s>>>(e, hi, lo, rhs, n, inv_h2, h2half, ev);
+    k_smooth_corr<PI, PJ, PK><<<grid, dim3(BX, BY), 0, s>>>(e, bstore + colour_offset(n, C), rhs, n, inv_h2, h2half,
+                                                             ev);
     return cudaGetLastError();
 }
 
@@ -208,36 +264,25 @@ __global__ void __launch_bounds__(BX * BY) k_coarse_rhs_corr(const float* __rest
 }
 
 // Coarsest correction grid: one block, shared memory, FP32 sweeps until
-// max|de| <= 1e-6 max|e| (or a fixed count).
+// max|de| <= 2e-6 max|e| (FP32 resolution of the correction; at most 40
+// sweeps), or a fixed count.
 constexpr int CT = 256;
 
 __device__ __forceinline__ S3f base_hess_sm(const float* hi, const float* lo, int p, int sy, int sz, float inv_h2)
 {
     const float vh = hi[p], vl = lo[p];
-    auto d = [&](int o) -> float { return (hi[p + o] - vh) + (lo[p + o] - vl); };
-    S3f B;
-    const float q = 0.25f * inv_h2;
-    B.xx = (d(1) + d(-1)) * inv_h2;
-    B.yy = (d(sy) + d(-sy)) * inv_h2;
-    B.zz = (d(sz) + d(-sz)) * inv_h2;
-    B.xy = ((d(sy + 1) + d(-sy - 1)) - (d(sy - 1) + d(-sy + 1))) * q;
-    B.xz = ((d(sz + 1) + d(-sz - 1)) - (d(sz - 1) + d(-sz + 1))) * q;
-    B.yz = ((d(sz + sy) + d(-sz - sy)) - (d(sy - sz) + d(-sy + sz))) * q;
-    return B;
+    return hess_from_diff(
+        [&](int di, int dj, int dk) -> float {
+            const int o = p + di + dj * sy + dk * sz;
+            return (hi[o] - vh) + (lo[o] - vl);
+        },
+        inv_h2);
 }
 
 __device__ __forceinline__ S3f corr_hess_sm(const float* e, int p, int sy, int sz, float e0, float inv_h2)
 {
-    auto d = [&](int o) -> float { return e[p + o] - e0; };
-    S3f K;
-    const float q = 0.25f * inv_h2;
-    K.xx = (d(1) + d(-1)) * inv_h2;
-    K.yy = (d(sy) + d(-sy)) * inv_h2;
-    K.zz = (d(sz) + d(-sz)) * inv_h2;
-    K.xy = ((d(sy + 1) + d(-sy - 1)) - (d(sy - 1) + d(-sy + 1))) * q;
-    K.xz = ((d(sz + 1) + d(-sz - 1)) - (d(sz - 1) + d(-sz + 1))) * q;
-    K.yz = ((d(sz + sy) + d(-sz - sy)) - (d(sy - sz) + d(-sy + sz))) * q;
-    return K;
+    return hess_from_diff([&](int di, int dj, int dk) -> float { return e[p + di + dj * sy + dk * sz] - e0; },
+                          inv_h2);
 }
 
 __global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __restrict__ hi,
@@ -255,7 +300,7 @@ __global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __r
     __shared__ int stop;
     for (int q = threadIdx.x; q < m; q += CT) { se[q] = e[q]; sh[q] = hi[q]; sl[q] = lo[q]; sr[q] = rhs[q]; }
     __syncthreads();
-    const int max_sweeps = sweeps > 0 ? sweeps : 60;
+    const int max_sweeps = sweeps > 0 ? sweeps : 40;
     unsigned long long ev = 0;
     for (int s = 0; s < max_sweeps; ++s) {
         float du = 0.0f, um = 0.0f;
@@ -291,7 +336,7 @@ __global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __r
         if (threadIdx.x == 0) {
             float a = 0.0f, b = 0.0f;
             for (int w = 0; w < CT / 32; ++w) { a = fmaxf(a, red[w][0]); b = fmaxf(b, red[w][1]); }
-            stop = (a <= 1e-6f * b) ? 1 : 0;
+            stop = (a <= 2e-6f * b) ? 1 : 0;
         }
         __syncthreads();
         if (stop) break;
@@ -308,12 +353,14 @@ __global__ void k_split_update(double* __restrict__ u, float* __restrict__ e, fl
     if (p >= m) return;
     double v = u[p];
     if (apply) {
-        v += (double)e[p];
+        v += f2d(e[p]);
         u[p] = v;
     }
-    const float h = (float)v;
+    // hi = v truncated to FP32; v - hi is exact in FP64 and below one FP32
+    // ulp of hi, so lo = its FP32 truncation keeps v = hi + lo to ~2^-47.
+    const float h = d2f_trunc(v);
     hi[p] = h;
-    lo[p] = (float)(v - (double)h);
+    lo[p] = d2f_trunc(v - f2d(h));
     e[p] = 0.0f;
 }
 
@@ -333,7 +380,7 @@ __global__ void __launch_bounds__(BX * BY) k_residual64_to32(const double* __res
             double val = 0.0;
             if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
                 const HessS H = gather_hess(u, p, sy, sz, u[p]);
-                val = fma(-det0(H), inv_h6, rhs[p]);
+                val = fma(-det0(H), inv_h6, rhs[p]);   // inv_h6 = 1 / (64 h^6)
                 mx = fmax(mx, fabs(val));
                 ss = fma(val, val, ss);
             }
@@ -359,21 +406,33 @@ __global__ void __launch_bounds__(BX * BY) k_residual64_to32(const double* __res
 
 }  // namespace
 
-cudaError_t launch_smooth_corr(float* e, const float* hi, const float* lo, const float* rhs, int n, double h,
-                               int nsweeps, unsigned long long* events, cudaStream_t s)
+size_t base_store_floats(int n)
+{
+    return n >= 3 ? 6 * (size_t)(n - 2) * (n - 2) * (n - 2) : 0;
+}
+
+cudaError_t launch_base_colour(const float* hi, const float* lo, float* bstore, int n, double h, cudaStream_t s)
+{
+    count_launches(1);
+    k_base_colour<<<grid_of(n), dim3(BX, BY), 0, s>>>(hi, lo, bstore, n, (float)(1.0 / (h * h)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_smooth_corr(float* e, const float* bstore, const float* rhs, int n, double h, int nsweeps,
+                               unsigned long long* events, cudaStream_t s)
 {
     const float inv_h2 = (float)(1.0 / (h * h));
     const float h2half = (float)(0.5 * h * h);
     for (int sw = 0; sw < nsweeps; ++sw) {
         cudaError_t e_;
-        if ((e_ = launch_colour_corr<0>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<1>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<2>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<3>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<4>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<5>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<6>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<7>(e, hi, lo, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<0>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<1>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<2>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<3>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<4>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<5>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<6>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<7>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
     }
     return cudaSuccess;
 }
@@ -423,14 +482,20 @@ cudaError_t launch_coarsest_corr(float* e, const float* hi, const float* lo, con
                                  int sweeps, unsigned long long* events, cudaStream_t s)
 {
     const size_t smem = 4 * sizeof(float) * (size_t)n * n * n;
-    if (smem > 48 * 1024) {
-        cudaError_t e_ = cudaFuncSetAttribute(k_coarsest_corr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e_ != cudaSuccess) return e_;
-    }
     count_launches(1);
     k_coarsest_corr<<<1, CT, smem, s>>>(e, hi, lo, rhs, n, (float)(1.0 / (h * h)), (float)(0.5 * h * h), sweeps,
                                         events);
     return cudaGetLastError();
+}
+
+cudaError_t prepare_coarsest_f64();
+
+cudaError_t prepare_coarsest_kernels()
+{
+    cudaError_t e = prepare_coarsest_f64();
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_coarsest_corr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(4 * sizeof(float) * 17 * 17 * 17));
 }
 
 cudaError_t launch_split_update(double* u, float* e, float* hi, float* lo, int n, int apply, cudaStream_t s)
@@ -447,7 +512,7 @@ cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r,
     const double h2 = h * h;
     count_launches(1);
     const dim3 g((n + BX - 1) / BX, (n + BY - 1) / BY, n < 16 ? n : 16);
-    k_residual64_to32<<<g, dim3(BX, BY), 0, s>>>(u, rhs, r, n, 1.0 / (h2 * h2 * h2), partials);
+    k_residual64_to32<<<g, dim3(BX, BY), 0, s>>>(u, rhs, r, n, 1.0 / (64.0 * h2 * h2 * h2), partials);
     return cudaGetLastError();
 }
 

@@ -2,7 +2,8 @@
 // (Section 2 of Liu, Froese, Oberman, Xiao): the 19-point stencil gather, the
 // discrete Hessian, and the smallest-real-root selection of Eq. (realroots).
 //
-// Working units.  Everything is kept "h^2-scaled": Hs = h^2 D^2(u^h; v0),
+// Working units.  Everything is kept "h^2-scaled": Hs = h^2 D^2(u^h; v0)
+// (the gathers return 4 Hs, with the right-hand side scaled to match),
 // the discrete Hessian at the current centre value v0 times h^2, whose
 // entries are exactly a - 2 v0, b - 2 v0, c - 2 v0, r, s, t with a..t the
 // neighbour combinations defined after Eq. (MA3Dcubic).  With the centre
@@ -20,6 +21,37 @@
 
 namespace ma {
 
+// FP64 <-> FP32 moves done with integer operations on the bit patterns, so
+// they do not occupy GB300's narrow FP64 pipe (which also executes the
+// conversion instructions).  d2f_trunc truncates (the result is only an FP32
+// starting value, never stored as a solution); values below FP32's normal
+// range become signed zero, above it infinity.  f2d is exact for normal
+// floats and zero.
+__device__ __forceinline__ float d2f_trunc(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const unsigned sign = (unsigned)hi & 0x80000000u;
+    const int ex = ((hi >> 20) & 0x7ff) - 1023 + 127;
+    const unsigned mant = (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29);
+    unsigned r = sign;
+    if (ex >= 255) r |= 0x7f800000u;
+    else if (ex > 0) r |= ((unsigned)ex << 23) | mant;
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u;
+    const int ex = (b >> 23) & 0xff;
+    if (ex == 0) return __hiloint2double((int)sign, 0);
+    const unsigned mant = b & 0x7fffffu;
+    const unsigned hi = ex == 255 ? (sign | 0x7ff00000u | (mant >> 3))
+                                  : (sign | ((unsigned)(ex - 127 + 1023) << 20) | (mant >> 3));
+    return __hiloint2double((int)hi, (int)(mant << 29));
+}
+
 struct HessS {   // h^2-scaled symmetric Hessian: diagonal A, B, C; off-diagonal R (xy), S (xz), T (yz)
     double A, B, C, R, S, T;
 };
@@ -29,8 +61,11 @@ struct HessSf {
 };
 
 // 19-point gather at linear index p with strides sy (one j step) and sz
-// (one k step); v0 is the current centre value.  Neighbour loads go through
-// the read-only path: no launch writes a point and reads it as a neighbour.
+// (one k step); v0 is the current centre value.  Returns 4 Hs (the
+// h^2-scaled discrete Hessian times 4): 4(a - 2 v0), ..., 4r = the bare cross
+// sums, so no 1/4 scalings are spent; callers use det(4 Hs) = 64 det(Hs) and
+// v = v0 + zeta4 / 8.  Neighbour loads go through the read-only path: no
+// launch writes a point and reads it as a neighbour.
 __device__ __forceinline__ HessS gather_hess(const double* __restrict__ u, long long p, long long sy,
                                              long long sz, double v0)
 {
@@ -42,12 +77,13 @@ __device__ __forceinline__ HessS gather_hess(const double* __restrict__ u, long 
     const double s4 = (__ldg(q + sz + 1) + __ldg(q - sz - 1)) - (__ldg(q + sz - 1) + __ldg(q - sz + 1));
     const double t4 = (__ldg(q + sz + sy) + __ldg(q - sz - sy)) - (__ldg(q + sy - sz) + __ldg(q - sy + sz));
     HessS H;
-    H.A = fma(-2.0, v0, a);
-    H.B = fma(-2.0, v0, b);
-    H.C = fma(-2.0, v0, c);
-    H.R = 0.25 * r4;
-    H.S = 0.25 * s4;
-    H.T = 0.25 * t4;
+    const double m8v = -8.0 * v0;
+    H.A = fma(4.0, a, m8v);
+    H.B = fma(4.0, b, m8v);
+    H.C = fma(4.0, c, m8v);
+    H.R = r4;
+    H.S = s4;
+    H.T = t4;
     return H;
 }
 
@@ -192,9 +228,9 @@ __device__ __forceinline__ double smallest_root(const HessS& H, double rhs6, boo
         return root_f64_all_real_min(H, rhs6);
     }
     HessSf F;
-    F.A = (float)H.A; F.B = (float)H.B; F.C = (float)H.C;
-    F.R = (float)H.R; F.S = (float)H.S; F.T = (float)H.T;
-    const float r6 = (float)rhs6;
+    F.A = d2f_trunc(H.A); F.B = d2f_trunc(H.B); F.C = d2f_trunc(H.C);
+    F.R = d2f_trunc(H.R); F.S = d2f_trunc(H.S); F.T = d2f_trunc(H.T);
+    const float r6 = d2f_trunc(rhs6);
     const float scale = fabsf(F.A) + fabsf(F.B) + fabsf(F.C) + fabsf(F.R) + fabsf(F.S) + fabsf(F.T);
     const float d0 = det_shift_f(F, 0.0f);
     float z = is_pd<HessSf, float>(F, d0) ? 0.0f : gershgorin_low<HessSf, float>(F) - cbrtf(r6);
@@ -215,10 +251,26 @@ __device__ __forceinline__ double smallest_root(const HessS& H, double rhs6, boo
     if (!conv || !(m > 0.05f * scale * scale) || !(r6 > 0.0f)) {
         return root_f64_monotone(H, rhs6);
     }
-    double zd = (double)z;
+    double zd = f2d(z);
     const double g64 = det_shift(H, zd) - rhs6;
-    zd = fma(g64, (double)(1.0f / m), zd);
+    zd = fma(g64, f2d(1.0f / m), zd);
     return zd;
+}
+
+// The same root, then one more Newton step with the FP64 derivative: a few
+// ulps of the root instead of ~1e-14 of the entries' size.  For the coarsest
+// grid, which is swept to a 1e-14 relative change.
+__device__ __forceinline__ double smallest_root_precise(const HessS& H, double rhs6, bool* nonconvex)
+{
+    double z = smallest_root(H, rhs6, nonconvex);
+    if (*nonconvex) return z;
+    const double g = det_shift(H, z) - rhs6;
+    const double m = minors_shift(H, z);
+    if (m > 0.0) {
+        const double zn = z + g / m;
+        if (isfinite(zn)) z = zn;
+    }
+    return z;
 }
 
 }  // namespace ma

@@ -34,7 +34,8 @@ class MAError(RuntimeError):
 class ma_hier_desc(C.Structure):
     _fields_ = [("n", C.c_int), ("x0", C.c_double * 3), ("len", C.c_double), ("nu1", C.c_int),
                 ("nu2", C.c_int), ("coarsest_n", C.c_int), ("restrict_kind", C.c_int),
-                ("approx_restrict", C.c_int), ("precision", C.c_int), ("coarse_sweeps", C.c_int)]
+                ("approx_restrict", C.c_int), ("precision", C.c_int), ("coarse_sweeps", C.c_int),
+                ("inner_cycles", C.c_int)]
 
 
 class ma_solve_opts(C.Structure):
@@ -70,7 +71,7 @@ _SIGS = {
     "ma_norm_scratch_bytes": [C.c_int, C.POINTER(C.c_size_t)],
     "ma_norm": [_vp, C.c_int, C.c_double, _vp, C.c_size_t, C.POINTER(C.c_double), _vp],
     "ma_kernel_launch_count": [C.POINTER(C.c_ulonglong)],
-    "ma_smooth_correction": [_vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp, _vp],
+    "ma_smooth_correction": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp, _vp],
     "ma_residual_correction": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp],
     "ma_norm_static": [_vp, C.c_int, C.c_double, C.POINTER(C.c_double), _vp],
 }
@@ -221,9 +222,10 @@ def ma_coarsest_solve(u, rhs, n: int, h: float, sweeps: int = 0, events=None, st
     _check(load().ma_coarsest_solve(_ptr(u), _ptr(rhs), n, h, sweeps, _ptr(events), _stream(stream)))
 
 
-def ma_smooth_correction(e, u_hi, u_lo, rhs, n: int, h: float, nsweeps: int = 1, events=None, stream=None) -> None:
-    _check(load().ma_smooth_correction(_ptr(e), _ptr(u_hi), _ptr(u_lo), _ptr(rhs), n, h, nsweeps, _ptr(events),
-                                       _stream(stream)))
+def ma_smooth_correction(e, b_scratch, u_hi, u_lo, rhs, n: int, h: float, nsweeps: int = 1, events=None,
+                         stream=None) -> None:
+    _check(load().ma_smooth_correction(_ptr(e), _ptr(b_scratch), _ptr(u_hi), _ptr(u_lo), _ptr(rhs), n, h, nsweeps,
+                                       _ptr(events), _stream(stream)))
 
 
 def ma_residual_correction(e, u_hi, u_lo, rhs, res, n: int, h: float, stream=None) -> None:
@@ -271,7 +273,7 @@ class SolveResult:
 def make_desc(n: int, length: float = 1.0, x0=(0.0, 0.0, 0.0), nu1: int = 2, nu2: int = 2,
               coarsest_n: int = 5, restrict_kind: int = MA_FULL_WEIGHTING,
               approx_restrict: int = MA_APPROX_WEIGHTED, precision: int = MA_FP64,
-              coarse_sweeps: int = 0) -> ma_hier_desc:
+              coarse_sweeps: int = 0, inner_cycles: int = 0) -> ma_hier_desc:
     d = ma_hier_desc()
     d.n = n
     d.x0[0], d.x0[1], d.x0[2] = x0
@@ -282,6 +284,7 @@ def make_desc(n: int, length: float = 1.0, x0=(0.0, 0.0, 0.0), nu1: int = 2, nu2
     d.approx_restrict = approx_restrict
     d.precision = precision
     d.coarse_sweeps = coarse_sweeps
+    d.inner_cycles = inner_cycles
     return d
 
 
