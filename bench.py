@@ -5,13 +5,15 @@ Gauss-Seidel) on one GB300 per rank.
 
 Default workload: Example 4 of the paper (u = exp(|x|^2/2) on [0,1]^3) on a
 257^3 grid (16,581,375 unknowns), stopping at a relative max-norm residual of
-1e-10, FP64.  A step is one complete solve: copy f and g into the resident
-hierarchy, FMG, V-cycles to tolerance.  Inputs are resident in HBM when the
+1e-10 evaluated in FP64.  A step is one complete solve: copy f and g into the
+resident hierarchy, FMG, cycles to tolerance.  value = the mixed-precision
+solve (FP32 correction cycles under an FP64 residual and update); the plain
+FP64 solve of the same workload is reported beside it ("fp64").  Inputs are resident in HBM when the
 timed region starts; the hierarchy's working set (4 x 136 MB of level-0
 fields) exceeds the 129 MB L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--n 257] [--problem exp] [--tol 1e-10] [--precision fp64]
+                  [--n 257] [--problem exp] [--tol 1e-10]
 
 --impl reference times the FP64 CPU oracle (oracle/) on the host cores.  Under
 torchrun (N > 1) each rank solves its own copy of the workload (replicas, no
@@ -31,11 +33,17 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# FP64 operations of one smoother point update (gather 15 adds + 3 scalings,
-# shifted determinant 12, h^6 rhs 1, subtraction 1, FP64 Newton correction 1,
-# centre update 1); the FP32 first pass is not counted.
-SMOOTH_FP64_OPS_PER_POINT = 34
-FP64_PEAK_GOPS = 625.0   # nominal 1.25 TFLOP/s FP64 = 625 G FP64 pipe ops/s (one FMA = 2 flops)
+# FP64 operations of one FP64-smoother point update: gather 15 adds + 1 (-8 v0),
+# 4x-scaled diagonal 3, shifted determinant 12, h^6 rhs 1, subtraction 1,
+# FP64 Newton correction 1, centre update 1; the FP32 first pass and the
+# integer FP64<->FP32 moves are not counted.
+SMOOTH_FP64_OPS_PER_POINT = 35
+FP64_PEAK_GOPS = 629.0   # 2 FP64 ops/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s, FMA = 2 flops)
+# Algorithmic HBM bytes of one FP32 correction-smoother point update: base
+# Hessian 6 x 4 B, rhs 4 B, e read 4 B and written 4 B (each e value read
+# once per sweep for the stencils, counted at its own update).
+CORR_SMOOTH_BYTES_PER_POINT = 36
+HBM_PEAK_GBS = 6663.9    # MEASURED_PEAKS.json hbm_gbs (copy bandwidth)
 
 
 def parse():
@@ -47,7 +55,7 @@ def parse():
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--problem", default="exp")
     ap.add_argument("--tol", type=float, default=1e-10)
-    ap.add_argument("--precision", choices=["fp64"], default="fp64")
+
     return ap.parse_args()
 
 
@@ -179,56 +187,92 @@ def main():
     pr = problems.make(args.problem, args.n)
     f_dev = torch.from_numpy(pr.f).to(dev)
     g_dev = torch.from_numpy(pr.initial()).to(dev)
-    desc = M.make_desc(pr.n, length=pr.length, precision=M.MA_FP64)
-    H = M.Hierarchy(desc, device=dev)
+    hier = {"mixed": M.Hierarchy(M.make_desc(pr.n, length=pr.length, precision=M.MA_MIXED), device=dev),
+            "fp64": M.Hierarchy(M.make_desc(pr.n, length=pr.length, precision=M.MA_FP64), device=dev)}
 
-    def step():
+    def step(H):
         H.set_rhs_bc(f_dev, g_dev)
         r = H.solve(tol=args.tol, max_cycles=60)
         return r
 
-    for _ in range(args.warmup):
-        res = step()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    def timed(H, steps):
+        """CUDA-event time per solve on the solve stream (max over ranks)."""
+        for _ in range(args.warmup):
+            step(H)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        l0 = M.ma_kernel_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cyc = []
+        for _ in range(steps):
+            r = step(H)
+            cyc.append(r.cycles)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = M.ma_kernel_launch_count() - l0
+        ms = e0.elapsed_time(e1) / steps
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dist.barrier()
+        return float(t.item()), statistics.mean(cyc), r, launches
+
     sampler = ClockSampler(local)
     sampler.start()
-    l0 = M.ma_kernel_launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    cycles = []
-    for _ in range(args.steps):
-        res = step()
-        cycles.append(res.cycles)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    launches = M.ma_kernel_launch_count() - l0
+    ms_mixed, cyc_mixed, res_mixed, launches = timed(hier["mixed"], args.steps)
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    ms_max = float(t.item())
-    value = world * pr.unknowns / (ms_max / 1e3)
+    ms_fp64, cyc_fp64, res_fp64, _ = timed(hier["fp64"], max(1, args.steps // 2))
+    value = world * pr.unknowns / (ms_mixed / 1e3)
+    sols = {}
+    for k, H in hier.items():
+        u = torch.empty_like(f_dev)
+        H.get_solution(u)
+        sols[k] = u.cpu().numpy()
+    torch.cuda.synchronize()
+    err = {k: float(np.max(np.abs(v - pr.u))) for k, v in sols.items()}
+    diff = float(np.max(np.abs(sols["mixed"] - sols["fp64"])) / np.max(np.abs(pr.u)))
 
-    # smoother kernel duration (same kernel, grid and stream as inside the solve)
-    u_tmp = torch.empty_like(f_dev)
-    H.get_solution(u_tmp)
+    # live kernel timings on the solve stream, same grid: the FP32 correction
+    # smoother (one colour phase) and the FP64 smoother
+    n, h = pr.n, pr.h
+    u64 = torch.from_numpy(sols["mixed"]).to(dev)
+    hi = u64.float()
+    lo = (u64 - hi.double()).float()
+    e = torch.zeros_like(hi)
+    rhs = (1e-8 * f_dev).float()
+    rhs[0], rhs[-1] = 0, 0
+    _keep, scr, nb = M.correction_scratch(n, device=dev)
+    M.ma_smooth_correction(e, hi, lo, rhs, n, h, 1, scr, nb)
     sweeps = 4
-    M.ma_smooth(u_tmp, f_dev, pr.n, pr.h, 1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    M.ma_smooth(u_tmp, f_dev, pr.n, pr.h, sweeps)
+    M.ma_smooth_correction(e, hi, lo, rhs, n, h, sweeps, scr, nb)
     e1.record(stream)
     torch.cuda.synchronize()
-    launch_ms = e0.elapsed_time(e1) / (8 * sweeps)
-    pts_per_launch = (pr.n - 2) ** 3 / 8.0
-    achieved = SMOOTH_FP64_OPS_PER_POINT * pts_per_launch / (launch_ms / 1e3) / 1e9
+    # the call also runs the base-Hessian and layout kernels; time them alone and subtract
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    M.ma_smooth_correction(e, hi, lo, rhs, n, h, 0, scr, nb)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    corr_launch_ms = (e0.elapsed_time(e1) - b0.elapsed_time(b1)) / (8 * sweeps)
+    pts_launch = (n - 2) ** 3 / 8.0
+    corr_gbs = CORR_SMOOTH_BYTES_PER_POINT * pts_launch / (corr_launch_ms / 1e3) / 1e9
+    u_tmp = u64.clone()
+    M.ma_smooth(u_tmp, f_dev, n, h, 1)
+    e0.record(stream)
+    M.ma_smooth(u_tmp, f_dev, n, h, sweeps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    f64_launch_ms = e0.elapsed_time(e1) / (8 * sweeps)
+    f64_gops = SMOOTH_FP64_OPS_PER_POINT * pts_launch / (f64_launch_ms / 1e3) / 1e9
+    del u_tmp, hi, lo, e, rhs, _keep
 
-    # end to end through the C ABI with host buffers (pinned)
+    # end to end through the C ABI with host buffers (pinned), mixed precision
+    H = hier["mixed"]
     f_host = torch.from_numpy(pr.f).pin_memory()
     g_host = torch.from_numpy(pr.initial()).pin_memory()
     u_host = torch.empty_like(f_host).pin_memory()
@@ -245,26 +289,38 @@ def main():
         u_host.copy_(ud, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    err = float(np.max(np.abs(u_host.numpy() - pr.u)))
 
     cpu = oracle_sample(pr, args.tol) if (rank == 0 and world == 1) else None
-    H.close()
+    for H in hier.values():
+        H.close()
     if rank == 0:
         line = {
             "metric": "unknowns solved to tolerance per second",
             "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.problem} {args.n}^3 FMG-FAS V(2,2) 8-colour GS, tol {args.tol:g} "
-                                   "relative max-norm", "n": args.n, "tol": args.tol,
-                       "precision": args.precision, "restrict": "full weighting",
-                       "parallelism": f"replicas x{world}", "l2": "working set larger than L2"},
-            "cycles_per_solve": statistics.mean(cycles), "residual": res.res,
-            "error_vs_exact": err,
-            "roofline": {"bound": "alu", "kernel": "k_smooth_colour (FP64 smoother colour phase)",
-                         "achieved": achieved, "peak": FP64_PEAK_GOPS, "unit": "GFP64op/s",
-                         "frac": achieved / FP64_PEAK_GOPS, "traffic": None,
-                         "launch_ms": launch_ms, "ops_per_point": SMOOTH_FP64_OPS_PER_POINT},
+            "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"Example 4 exp(|x|^2/2) {args.n}^3, FMG + FAS V(2,2), 8-colour nonlinear GS, "
+                                   f"tol {args.tol:g} relative max-norm residual (FP64)",
+                       "n": args.n, "tol": args.tol,
+                       "precision": "mixed: FP32 correction V-cycles x3 per FP64 fine residual and update",
+                       "restrict": "full weighting", "parallelism": f"replicas x{world}",
+                       "l2": "working set larger than L2 (no flush needed)"},
+            "cycles_per_solve": cyc_mixed, "residual": res_mixed.res,
+            "fp64": {"value": world * pr.unknowns / (ms_fp64 / 1e3), "unit": "unknowns/s",
+                     "ms_per_step": ms_fp64, "cycles_per_solve": cyc_fp64, "residual": res_fp64.res},
+            "mixed_vs_fp64": ms_fp64 / ms_mixed,
+            "accuracy": {"max_err_vs_exact_mixed": err["mixed"], "max_err_vs_exact_fp64": err["fp64"],
+                         "max_rel_diff_mixed_vs_fp64": diff},
+            "roofline": {"bound": "hbm", "kernel": "k_smooth_corr (FP32 correction smoother, one colour phase)",
+                         "achieved": corr_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                         "frac": corr_gbs / HBM_PEAK_GBS, "traffic": None,
+                         "launch_ms": corr_launch_ms, "bytes_per_point": CORR_SMOOTH_BYTES_PER_POINT,
+                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+            "roofline_fp64_smoother": {"bound": "alu", "kernel": "k_smooth_colour (FP64 smoother, one colour phase)",
+                                       "achieved": f64_gops, "peak": FP64_PEAK_GOPS, "unit": "GFP64op/s",
+                                       "frac": f64_gops / FP64_PEAK_GOPS, "launch_ms": f64_launch_ms,
+                                       "ops_per_point": SMOOTH_FP64_OPS_PER_POINT,
+                                       "peak_source": "nominal 2 FP64 ops/clk/SM x 152 SMs x 2.07 GHz"},
             "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")} if cpu else None,
             "e2e": {"value": world * pr.unknowns / e2e_s, "unit": "unknowns/s",
                     "h2d_bytes_per_step": 2 * 8 * pr.n ** 3, "d2h_bytes_per_step": 8 * pr.n ** 3},

@@ -75,7 +75,8 @@ typedef struct {
     double x0[3];        /* cube origin (informational; f and g are given on the grid) */
     double len;          /* cube edge; h = len / (n - 1)                               */
     int nu1, nu2;        /* pre/post smoothing sweeps (Section 4 uses 2, 2)            */
-    int coarsest_n;      /* 3 (Section 4, h0 = 1/2) or 5                               */
+    int coarsest_n;      /* 3 (Section 4, h0 = 1/2: one unknown, so one sweep solves it
+                            exactly) or 5, 9, 17                                       */
     int restrict_kind;   /* MA_HALF_WEIGHTING | MA_FULL_WEIGHTING                      */
     int approx_restrict; /* MA_APPROX_INJECTION | MA_APPROX_WEIGHTED                   */
     int precision;       /* MA_FP64 | MA_MIXED                                         */
@@ -227,18 +228,25 @@ ma_status ma_coarsest_solve(double *u_dev, const double *rhs_dev, int n, double 
  * an FP32 split u = u_hi + u_lo (u_hi = (float)u, u_lo = (float)(u - u_hi));
  * e, rhs and res are n^3 floats, [k][j][i]; e is 0 on the shell. */
 
+/* Bytes of device scratch the two calls below need: the base Hessian
+ * B = D^2_h u (FP32, six per interior point, colour-major order) and the
+ * right-hand side in colour-major order. */
+ma_status ma_correction_scratch_bytes(int n, size_t *bytes);
+
 /* nsweeps 8-colour sweeps on e: at each point the new e is the one whose
  * u + e takes the smallest real root of the local cubic (Section 2, Eq.
- * realroots) for right-hand side det(D^2_h u) + rhs.  B = D^2_h u is first
- * computed once into b_scratch_dev (6 (n-2)^3 floats, overwritten; colour-
- * major layout) and read from there by every sweep. */
-ma_status ma_smooth_correction(float *e_dev, float *b_scratch_dev, const float *u_hi_dev, const float *u_lo_dev,
-                               const float *rhs_dev, int n, double h, int nsweeps, unsigned long long *events_dev,
-                               ma_stream_t stream);
+ * realroots) for right-hand side det(D^2_h u) + rhs, with D^2_h u taken from
+ * the FP32 store.  scratch_dev: >= ma_correction_scratch_bytes(n) bytes,
+ * 256-byte aligned, overwritten. */
+ma_status ma_smooth_correction(float *e_dev, const float *u_hi_dev, const float *u_lo_dev, const float *rhs_dev, int n,
+                               double h, int nsweeps, void *scratch_dev, size_t scratch_bytes,
+                               unsigned long long *events_dev, ma_stream_t stream);
 
-/* res = rhs - N(e) on the interior, 0 on the shell. */
+/* res = rhs - N(e) on the interior, 0 on the shell (same B store; same
+ * scratch rules as ma_smooth_correction). */
 ma_status ma_residual_correction(const float *e_dev, const float *u_hi_dev, const float *u_lo_dev,
-                                 const float *rhs_dev, float *res_dev, int n, double h, ma_stream_t stream);
+                                 const float *rhs_dev, float *res_dev, int n, double h, void *scratch_dev,
+                                 size_t scratch_bytes, ma_stream_t stream);
 
 /* Bytes of device scratch ma_norm needs for a grid of n points per side. */
 ma_status ma_norm_scratch_bytes(int n, size_t *bytes);

@@ -36,7 +36,7 @@ class Params:
     approximation restriction (injection or the residual's weighting)."""
     nu1: int = 2
     nu2: int = 2
-    coarsest_n: int = 5
+    coarsest_n: int = 3
     restrict_kind: int = FULL_WEIGHTING
     coarse_sweeps: int = 0
     ordering: int = COLOUR8

@@ -102,10 +102,10 @@ size_t layout(ma_hierarchy* H, const ma_hier_desc* d, char* base)
         lv.w = (double*)take(pts * sizeof(double));
         if (d->precision == MA_MIXED) {
             lv.e = (float*)take(pts * sizeof(float));
-            lv.bstore = (float*)take(ma::base_store_floats(m) * sizeof(float));
+            lv.bstore = (void*)take(ma::base_store_bytes(m));
             lv.hi = (float*)take(pts * sizeof(float));
             lv.lo = (float*)take(pts * sizeof(float));
-            lv.rhs32 = (float*)take(pts * sizeof(float));
+            lv.rhs32 = (float*)take(ma::cm_points(m) * sizeof(float));
             lv.res32 = (float*)take(pts * sizeof(float));
             lv.w32 = (float*)take(pts * sizeof(float));
         }
@@ -208,15 +208,15 @@ cudaError_t corr_vcycle(ma_hierarchy* H)
         ma::Level& C = H->lev[l + 1];
         if ((e = ma::launch_smooth_corr(F.e, F.bstore, F.rhs32, F.n, F.h, d.nu1, H->events, s)) != cudaSuccess)
             return e;
-        if ((e = ma::launch_residual_corr(F.e, F.hi, F.lo, F.rhs32, F.res32, F.n, F.h, s)) != cudaSuccess) return e;
+        if ((e = ma::launch_residual_corr(F.e, F.bstore, F.rhs32, F.res32, F.n, F.h, s)) != cudaSuccess) return e;
         if ((e = ma::launch_restrict_level_f32(F.e, F.res32, F.n, C.w32, C.e, C.res32, d.restrict_kind,
                                                d.approx_restrict, s)) != cudaSuccess)
             return e;
-        if ((e = ma::launch_coarse_rhs_corr(C.w32, C.hi, C.lo, C.res32, C.rhs32, C.n, C.h, s)) != cudaSuccess)
+        if ((e = ma::launch_coarse_rhs_corr(C.w32, C.bstore, C.res32, C.rhs32, C.n, C.h, s)) != cudaSuccess)
             return e;
     }
     ma::Level& B = H->lev[H->L - 1];
-    if ((e = ma::launch_coarsest_corr(B.e, B.hi, B.lo, B.rhs32, B.n, B.h, d.coarse_sweeps, H->events, s)) !=
+    if ((e = ma::launch_coarsest_corr(B.e, B.bstore, B.rhs32, B.n, B.h, d.coarse_sweeps, H->events, s)) !=
         cudaSuccess)
         return e;
     for (int l = H->L - 2; l >= 0; --l) {
@@ -637,23 +637,55 @@ ma_status ma_coarsest_solve(double* u, const double* rhs, int n, double h, int s
     return MA_OK;
 }
 
-ma_status ma_smooth_correction(float* e, float* b_scratch, const float* hi, const float* lo, const float* rhs, int n,
-                               double h, int nsweeps, unsigned long long* events, ma_stream_t stream)
+// Scratch of the correction step calls: the BF16 base-Hessian store, then the
+// colour-major right-hand side (256-byte aligned).
+static size_t corr_scratch_split(int n) { return align_up(ma::base_store_bytes(n)); }
+
+ma_status ma_correction_scratch_bytes(int n, size_t* bytes)
 {
-    if (!e || !b_scratch || !hi || !lo || !rhs || !valid_step_grid(n) || !(h > 0.0) || nsweeps < 0)
+    if (!valid_step_grid(n) || !bytes) return fail(MA_ERR_INVALID_ARG, "ma_correction_scratch_bytes: bad arguments");
+    *bytes = corr_scratch_split(n) + ma::cm_points(n) * sizeof(float);
+    return MA_OK;
+}
+
+static ma_status corr_setup(const float* hi, const float* lo, const float* rhs, int n, double h, void* scratch,
+                            size_t scratch_bytes, cudaStream_t s, float** rhs_cm)
+{
+    size_t need = 0;
+    ma_status st = ma_correction_scratch_bytes(n, &need);
+    if (st != MA_OK) return st;
+    if (scratch_bytes < need) return fail(MA_ERR_INVALID_ARG, "correction scratch %zu < %zu bytes", scratch_bytes, need);
+    if (((uintptr_t)scratch) % kAlign != 0) return fail(MA_ERR_INVALID_ARG, "scratch not 256-byte aligned");
+    *rhs_cm = (float*)((char*)scratch + corr_scratch_split(n));
+    MA_CK(ma::launch_base_colour(hi, lo, scratch, n, h, s));
+    MA_CK(ma::launch_to_cm(rhs, *rhs_cm, n, s));
+    return MA_OK;
+}
+
+ma_status ma_smooth_correction(float* e, const float* hi, const float* lo, const float* rhs, int n, double h,
+                               int nsweeps, void* scratch, size_t scratch_bytes, unsigned long long* events,
+                               ma_stream_t stream)
+{
+    if (!e || !scratch || !hi || !lo || !rhs || !valid_step_grid(n) || !(h > 0.0) || nsweeps < 0)
         return fail(MA_ERR_INVALID_ARG, "ma_smooth_correction: bad arguments");
     cudaStream_t s = (cudaStream_t)stream;
-    MA_CK(ma::launch_base_colour(hi, lo, b_scratch, n, h, s));
-    MA_CK(ma::launch_smooth_corr(e, b_scratch, rhs, n, h, nsweeps, events, s));
+    float* rhs_cm = nullptr;
+    ma_status st = corr_setup(hi, lo, rhs, n, h, scratch, scratch_bytes, s, &rhs_cm);
+    if (st != MA_OK) return st;
+    MA_CK(ma::launch_smooth_corr(e, scratch, rhs_cm, n, h, nsweeps, events, s));
     return MA_OK;
 }
 
 ma_status ma_residual_correction(const float* e, const float* hi, const float* lo, const float* rhs, float* res,
-                                 int n, double h, ma_stream_t stream)
+                                 int n, double h, void* scratch, size_t scratch_bytes, ma_stream_t stream)
 {
-    if (!e || !hi || !lo || !rhs || !res || !valid_step_grid(n) || !(h > 0.0))
+    if (!e || !hi || !lo || !rhs || !res || !scratch || !valid_step_grid(n) || !(h > 0.0))
         return fail(MA_ERR_INVALID_ARG, "ma_residual_correction: bad arguments");
-    MA_CK(ma::launch_residual_corr(e, hi, lo, rhs, res, n, h, (cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    float* rhs_cm = nullptr;
+    ma_status st = corr_setup(hi, lo, rhs, n, h, scratch, scratch_bytes, s, &rhs_cm);
+    if (st != MA_OK) return st;
+    MA_CK(ma::launch_residual_corr(e, scratch, rhs_cm, res, n, h, s));
     return MA_OK;
 }
 

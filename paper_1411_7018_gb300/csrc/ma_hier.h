@@ -21,10 +21,10 @@ struct Level {
     double* w = nullptr;     // coarse levels: the restricted approximation w_H
     // mixed precision (FP32 correction cycle); null in FP64 mode
     float* e = nullptr;      // correction
-    float* bstore = nullptr; // B = D^2_h u per colour (6 floats per interior point), refreshed per outer iteration
+    void* bstore = nullptr;  // B = D^2_h u, colour-major BF16 (6 per interior point), refreshed per outer iteration
     float* hi = nullptr;     // base u = hi + lo (FP32 split)
     float* lo = nullptr;
-    float* rhs32 = nullptr;  // correction-problem right-hand side (fine: the FP64 residual)
+    float* rhs32 = nullptr;  // correction-problem right-hand side, colour-major (fine: the FP64 residual)
     float* res32 = nullptr;  // correction residual; on coarse levels the restricted one
     float* w32 = nullptr;    // coarse levels: the restricted correction
 };

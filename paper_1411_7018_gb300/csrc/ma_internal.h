@@ -42,26 +42,28 @@ cudaError_t launch_coarsest(double* u, const double* rhs, int n, double h, int s
 cudaError_t launch_copy_rhs_bc(const double* f, const double* g, double* rhs, double* u, int n,
                                int* bad, cudaStream_t s);
 
-// Mixed-precision kernels (ma_kernels_mixed.cu): FP32 correction cycle fields
-// are n^3 floats; the base u is split as hi + lo.
-// Per-level store of B = D^2_h u (from the hi/lo split) in colour-major SoA
-// layout: base_store_floats(n) floats, filled by launch_base_colour.
-size_t base_store_floats(int n);
-cudaError_t launch_base_colour(const float* hi, const float* lo, float* bstore, int n, double h, cudaStream_t s);
-cudaError_t launch_smooth_corr(float* e, const float* bstore, const float* rhs, int n, double h, int nsweeps,
+// Mixed-precision kernels (ma_kernels_mixed.cu).  e, res, w are n^3 floats
+// in the natural layout; hi + lo is the FP32 split of the FP64 iterate; the
+// base Hessian store (BF16, base_store_bytes) and the correction right-hand
+// side (cm_points floats) are in colour-major order.
+size_t base_store_bytes(int n);
+size_t cm_points(int n);
+cudaError_t launch_base_colour(const float* hi, const float* lo, void* bstore, int n, double h, cudaStream_t s);
+cudaError_t launch_to_cm(const float* nat, float* cm, int n, cudaStream_t s);
+cudaError_t launch_smooth_corr(float* e, const void* bstore, const float* rhs_cm, int n, double h, int nsweeps,
                                unsigned long long* events, cudaStream_t s);
-cudaError_t launch_residual_corr(const float* e, const float* hi, const float* lo, const float* rhs, float* res,
-                                 int n, double h, cudaStream_t s);
-cudaError_t launch_coarse_rhs_corr(const float* w, const float* hi, const float* lo, const float* resc, float* rhs,
-                                   int nc, double H, cudaStream_t s);
+cudaError_t launch_residual_corr(const float* e, const void* bstore, const float* rhs_cm, float* res, int n,
+                                 double h, cudaStream_t s);
+cudaError_t launch_coarse_rhs_corr(const float* w, const void* bstore, const float* resc, float* rhs_cm, int nc,
+                                   double H, cudaStream_t s);
 cudaError_t launch_restrict_level_f32(const float* ef, const float* rf, int nf, float* wc, float* ec, float* rc,
                                       int kind, int approx, cudaStream_t s);
 cudaError_t launch_prolong_add_f32(const float* ec, const float* wc, int nc, float* ef, cudaStream_t s);
 cudaError_t launch_inject_f32(const float* vf, int nf, float* vc, cudaStream_t s);
-cudaError_t launch_coarsest_corr(float* e, const float* hi, const float* lo, const float* rhs, int n, double h,
-                                 int sweeps, unsigned long long* events, cudaStream_t s);
+cudaError_t launch_coarsest_corr(float* e, const void* bstore, const float* rhs_cm, int n, double h, int sweeps,
+                                 unsigned long long* events, cudaStream_t s);
 cudaError_t launch_split_update(double* u, float* e, float* hi, float* lo, int n, int apply, cudaStream_t s);
-cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r, int n, double h, double* partials,
-                                   cudaStream_t s);
+cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r_cm, int n, double h,
+                                   double* partials, cudaStream_t s);
 
 }  // namespace ma

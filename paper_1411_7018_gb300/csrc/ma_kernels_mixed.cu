@@ -119,7 +119,7 @@ __device__ __forceinline__ float corr_root(const S3f& B, const S3f& K, float r, 
         for (int it = 0; it < 30; ++it) {
             const float F = c - z * (M - z * (T - z));
             const float Mz = M - z * (2.0f * T - 3.0f * z);
-            const float dz = F / Mz;
+            const float dz = __fdividef(F, Mz);
             z += dz;
             if (!isfinite(z)) break;
             if (fabsf(dz) <= 1e-6f * fabsf(z) + 1e-12f * scale) return z;
@@ -137,23 +137,58 @@ __device__ __forceinline__ float corr_root(const S3f& B, const S3f& K, float r, 
 __host__ __device__ __forceinline__ int colour_count(int n, int parity) { return parity ? (n - 1) / 2 : (n - 3) / 2; }
 
 // ---------------------------------------------------------------------------
-// Correction smoother, one colour per launch.  B = D^2_h u does not change
-// during an outer iteration, so it is computed once per level and stored per
-// colour (k_base_colour): colour c's interior points form a dense
-// ni x nj x nk box, and its six B components are six dense arrays of that box
-// (SoA), so a warp's loads of B are contiguous.  e and rhs stay in the
-// natural [k][j][i] layout (e is read through its 19-point stencil).
+// Colour-major stores.  Colour c = (i&1)|(j&1)<<1|(k&1)<<2; its interior
+// points form a dense ni x nj x nk box (ni = interior indices of parity i&1
+// along an axis), and the boxes of colours 0..7 follow each other.  A warp of
+// one colour phase then reads contiguous memory.  Two per-level arrays use
+// this layout: the base Hessian B = D^2_h u (six FP32 components per point,
+// component-major inside each colour box, refreshed once per outer
+// iteration) and the correction right-hand side rhs.  (A BF16 B halves the
+// bytes a sweep streams, but its 2^-9 error cost an extra FP64 outer
+// iteration per solve, more than the sweeps saved.)
 // ---------------------------------------------------------------------------
 
-// Offset of colour c's block inside the per-level B store (6 floats per point).
-__host__ __device__ __forceinline__ long long colour_offset(int n, int c)
+// Points of colours 0..c-1.
+__host__ __device__ __forceinline__ long long cm_offset(int n, int c)
 {
     long long off = 0;
     for (int q = 0; q < c; ++q)
-        off += 6LL * colour_count(n, q & 1) * colour_count(n, (q >> 1) & 1) * colour_count(n, (q >> 2) & 1);
+        off += (long long)colour_count(n, q & 1) * colour_count(n, (q >> 1) & 1) * colour_count(n, (q >> 2) & 1);
     return off;
 }
 
+struct CmPos {
+    long long off;   // points of lower colours
+    long long cnt;   // points of this colour
+    long long idx;   // position inside this colour's box
+};
+
+// Colour-major position of interior point (i, j, k).
+__device__ __forceinline__ CmPos cm_pos(int i, int j, int k, int n)
+{
+    const int pi = i & 1, pj = j & 1, pk = k & 1;
+    const int ni = colour_count(n, pi), nj = colour_count(n, pj), nk = colour_count(n, pk);
+    const int ii = (i - (pi ? 1 : 2)) >> 1, jj = (j - (pj ? 1 : 2)) >> 1, kk = (k - (pk ? 1 : 2)) >> 1;
+    CmPos r;
+    r.off = cm_offset(n, pi | (pj << 1) | (pk << 2));
+    r.cnt = (long long)ni * nj * nk;
+    r.idx = ((long long)kk * nj + jj) * ni + ii;
+    return r;
+}
+
+__device__ __forceinline__ S3f load_b(const float* __restrict__ b, long long cnt)
+{
+    S3f B;
+    B.xx = __ldg(b);
+    B.yy = __ldg(b + cnt);
+    B.zz = __ldg(b + 2 * cnt);
+    B.xy = __ldg(b + 3 * cnt);
+    B.xz = __ldg(b + 4 * cnt);
+    B.yz = __ldg(b + 5 * cnt);
+    return B;
+}
+
+// B from the hi/lo split, stored at the point's colour-major slot.
 __global__ void __launch_bounds__(BX * BY) k_base_colour(const float* __restrict__ hi, const float* __restrict__ lo,
                                                          float* __restrict__ bstore, int n, float inv_h2)
 {
@@ -163,23 +198,32 @@ __global__ void __launch_bounds__(BX * BY) k_base_colour(const float* __restrict
     if (i < 1 || j < 1 || k < 1 || i > n - 2 || j > n - 2 || k > n - 2) return;
     const long long sy = n, sz = (long long)n * n;
     const S3f B = base_hess(hi, lo, lin(i, j, k, n), sy, sz, inv_h2);
-    const int pi = i & 1, pj = j & 1, pk = k & 1;
-    const int c = pi | (pj << 1) | (pk << 2);
-    const int ni = colour_count(n, pi), nj = colour_count(n, pj), nk = colour_count(n, pk);
-    const long long cnt = (long long)ni * nj * nk;
-    const int ii = (i - (pi ? 1 : 2)) >> 1, jj = (j - (pj ? 1 : 2)) >> 1, kk = (k - (pk ? 1 : 2)) >> 1;
-    float* b = bstore + colour_offset(n, c) + ((long long)kk * nj + jj) * ni + ii;
+    const CmPos c = cm_pos(i, j, k, n);
+    float* b = bstore + 6 * c.off + c.idx;
     b[0] = B.xx;
-    b[cnt] = B.yy;
-    b[2 * cnt] = B.zz;
-    b[3 * cnt] = B.xy;
-    b[4 * cnt] = B.xz;
-    b[5 * cnt] = B.yz;
+    b[c.cnt] = B.yy;
+    b[2 * c.cnt] = B.zz;
+    b[3 * c.cnt] = B.xy;
+    b[4 * c.cnt] = B.xz;
+    b[5 * c.cnt] = B.yz;
 }
 
+// Natural-layout interior values -> colour-major order.
+__global__ void __launch_bounds__(BX * BY) k_to_cm(const float* __restrict__ nat, float* __restrict__ cm, int n)
+{
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i < 1 || j < 1 || k < 1 || i > n - 2 || j > n - 2 || k > n - 2) return;
+    const CmPos c = cm_pos(i, j, k, n);
+    cm[c.off + c.idx] = nat[lin(i, j, k, n)];
+}
+
+// Correction smoother, one colour per launch: bc / rc point at this colour's
+// B and rhs boxes; e is in the natural layout (19-point stencil).
 template <int PI, int PJ, int PK>
 __global__ void __launch_bounds__(BX * BY) k_smooth_corr(float* e, const float* __restrict__ bc,
-                                                          const float* __restrict__ rhs, int n, float inv_h2,
+                                                          const float* __restrict__ rc, int n, float inv_h2,
                                                           float h2half, unsigned long long* events)
 {
     const int ii = blockIdx.x * BX + threadIdx.x;
@@ -189,43 +233,38 @@ __global__ void __launch_bounds__(BX * BY) k_smooth_corr(float* e, const float* 
     if (ii >= ni || jj >= nj) return;
     const int i = (PI ? 1 : 2) + 2 * ii, j = (PJ ? 1 : 2) + 2 * jj, k = (PK ? 1 : 2) + 2 * kk;
     const long long cnt = (long long)ni * nj * colour_count(n, PK);
-    const float* b = bc + ((long long)kk * nj + jj) * ni + ii;
-    S3f B;
-    B.xx = __ldg(b);
-    B.yy = __ldg(b + cnt);
-    B.zz = __ldg(b + 2 * cnt);
-    B.xy = __ldg(b + 3 * cnt);
-    B.xz = __ldg(b + 4 * cnt);
-    B.yz = __ldg(b + 5 * cnt);
+    const long long idx = ((long long)kk * nj + jj) * ni + ii;
+    const S3f B = load_b(bc + idx, cnt);
     const long long sy = n, sz = (long long)n * n;
     const long long p = lin(i, j, k, n);
     const float e0 = e[p];
     const S3f K = corr_hess(e, p, sy, sz, e0, inv_h2);
     bool nonconvex = false;
-    const float z = corr_root(B, K, rhs[p], &nonconvex);
+    const float z = corr_root(B, K, __ldg(rc + idx), &nonconvex);
     e[p] = fmaf(h2half, z, e0);
     if (nonconvex && events) atomicAdd(events, 1ull);
 }
 
 template <int C>
-cudaError_t launch_colour_corr(float* e, const float* bstore, const float* rhs, int n, float inv_h2, float h2half,
-                               unsigned long long* ev, cudaStream_t s)
+cudaError_t launch_colour_corr(float* e, const float* bstore, const float* rhs_cm, int n, float inv_h2,
+                               float h2half, unsigned long long* ev, cudaStream_t s)
 {
     constexpr int PI = C & 1, PJ = (C >> 1) & 1, PK = (C >> 2) & 1;
     const int ni = colour_count(n, PI), nj = colour_count(n, PJ), nk = colour_count(n, PK);
     if (ni <= 0 || nj <= 0 || nk <= 0) return cudaSuccess;
     dim3 grid((ni + BX - 1) / BX, (nj + BY - 1) / BY, nk);
+    const long long off = cm_offset(n, C);
     count_launches(1);
-    k_smooth_corr<PI, PJ, PK><<<grid, dim3(BX, BY), 0, s>>>(e, bstore + colour_offset(n, C), rhs, n, inv_h2, h2half,
+    k_smooth_corr<PI, PJ, PK><<<grid, dim3(BX, BY), 0, s>>>(e, bstore + 6 * off, rhs_cm + off, n, inv_h2, h2half,
                                                              ev);
     return cudaGetLastError();
 }
 
-// res = rhs - N(e) on the interior, 0 on the shell.
-__global__ void __launch_bounds__(BX * BY) k_residual_corr(const float* __restrict__ e, const float* __restrict__ hi,
-                                                           const float* __restrict__ lo,
-                                                           const float* __restrict__ rhs, float* __restrict__ res,
-                                                           int n, float inv_h2)
+// res = rhs - N(e) on the interior (natural layout), 0 on the shell.
+__global__ void __launch_bounds__(BX * BY) k_residual_corr(const float* __restrict__ e,
+                                                           const float* __restrict__ bstore,
+                                                           const float* __restrict__ rhs_cm,
+                                                           float* __restrict__ res, int n, float inv_h2)
 {
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
@@ -235,32 +274,30 @@ __global__ void __launch_bounds__(BX * BY) k_residual_corr(const float* __restri
     float v = 0.0f;
     if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
         const long long sy = n, sz = (long long)n * n;
-        const S3f B = base_hess(hi, lo, p, sy, sz, inv_h2);
+        const CmPos c = cm_pos(i, j, k, n);
+        const S3f B = load_b(bstore + 6 * c.off + c.idx, c.cnt);
         const S3f K = corr_hess(e, p, sy, sz, e[p], inv_h2);
-        v = rhs[p] - delta_det(B, K);
+        v = rhs_cm[c.off + c.idx] - delta_det(B, K);
     }
     res[p] = v;
 }
 
-// rhs_H = N_H(w_H) + res_H on the coarse interior, 0 on the shell.
-__global__ void __launch_bounds__(BX * BY) k_coarse_rhs_corr(const float* __restrict__ w, const float* __restrict__ hi,
-                                                             const float* __restrict__ lo,
-                                                             const float* __restrict__ resc, float* __restrict__ rhs,
-                                                             int n, float inv_h2)
+// rhs_H = N_H(w_H) + res_H on the coarse interior, written colour-major.
+__global__ void __launch_bounds__(BX * BY) k_coarse_rhs_corr(const float* __restrict__ w,
+                                                             const float* __restrict__ bstore,
+                                                             const float* __restrict__ resc,
+                                                             float* __restrict__ rhs_cm, int n, float inv_h2)
 {
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
     const int k = blockIdx.z;
-    if (i >= n || j >= n) return;
+    if (i < 1 || j < 1 || k < 1 || i > n - 2 || j > n - 2 || k > n - 2) return;
     const long long p = lin(i, j, k, n);
-    float v = 0.0f;
-    if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
-        const long long sy = n, sz = (long long)n * n;
-        const S3f B = base_hess(hi, lo, p, sy, sz, inv_h2);
-        const S3f K = corr_hess(w, p, sy, sz, w[p], inv_h2);
-        v = delta_det(B, K) + resc[p];
-    }
-    rhs[p] = v;
+    const long long sy = n, sz = (long long)n * n;
+    const CmPos c = cm_pos(i, j, k, n);
+    const S3f B = load_b(bstore + 6 * c.off + c.idx, c.cnt);
+    const S3f K = corr_hess(w, p, sy, sz, w[p], inv_h2);
+    rhs_cm[c.off + c.idx] = delta_det(B, K) + resc[p];
 }
 
 // Coarsest correction grid: one block, shared memory, FP32 sweeps until
@@ -268,42 +305,35 @@ __global__ void __launch_bounds__(BX * BY) k_coarse_rhs_corr(const float* __rest
 // sweeps), or a fixed count.
 constexpr int CT = 256;
 
-__device__ __forceinline__ S3f base_hess_sm(const float* hi, const float* lo, int p, int sy, int sz, float inv_h2)
-{
-    const float vh = hi[p], vl = lo[p];
-    return hess_from_diff(
-        [&](int di, int dj, int dk) -> float {
-            const int o = p + di + dj * sy + dk * sz;
-            return (hi[o] - vh) + (lo[o] - vl);
-        },
-        inv_h2);
-}
-
 __device__ __forceinline__ S3f corr_hess_sm(const float* e, int p, int sy, int sz, float e0, float inv_h2)
 {
     return hess_from_diff([&](int di, int dj, int dk) -> float { return e[p + di + dj * sy + dk * sz] - e0; },
                           inv_h2);
 }
 
-__global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __restrict__ hi,
-                                                      const float* __restrict__ lo, const float* __restrict__ rhs,
-                                                      int n, float inv_h2, float h2half, int sweeps,
-                                                      unsigned long long* events)
+// smem: e (n^3, natural), B (6 floats per interior point, colour-major),
+// rhs (colour-major).
+__global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __restrict__ bstore,
+                                                      const float* __restrict__ rhs_cm, int n, float inv_h2,
+                                                      float h2half, int sweeps, unsigned long long* events)
 {
     extern __shared__ float smf[];
     const int m = n * n * n;
+    const int mi = (n - 2) * (n - 2) * (n - 2);
     float* se = smf;
-    float* sh = smf + m;
-    float* sl = smf + 2 * m;
-    float* sr = smf + 3 * m;
+    float* sb = smf + m;
+    float* sr = smf + m + 6 * mi;
     __shared__ float red[CT / 32][2];
     __shared__ int stop;
-    for (int q = threadIdx.x; q < m; q += CT) { se[q] = e[q]; sh[q] = hi[q]; sl[q] = lo[q]; sr[q] = rhs[q]; }
+    for (int q = threadIdx.x; q < m; q += CT) se[q] = e[q];
+    for (int q = threadIdx.x; q < 6 * mi; q += CT) sb[q] = bstore[q];
+    for (int q = threadIdx.x; q < mi; q += CT) sr[q] = rhs_cm[q];
     __syncthreads();
     const int max_sweeps = sweeps > 0 ? sweeps : 40;
     unsigned long long ev = 0;
     for (int s = 0; s < max_sweeps; ++s) {
         float du = 0.0f, um = 0.0f;
+        long long off = 0;
         for (int c = 0; c < 8; ++c) {
             const int pi = c & 1, pj = (c >> 1) & 1, pk = (c >> 2) & 1;
             const int ni = colour_count(n, pi), nj = colour_count(n, pj), nk = colour_count(n, pk);
@@ -314,16 +344,19 @@ __global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __r
                 const int k = (pk ? 1 : 2) + 2 * (t / (ni * nj));
                 const int p = (k * n + j) * n + i;
                 const float e0 = se[p];
-                const S3f B = base_hess_sm(sh, sl, p, n, n * n, inv_h2);
+                const float* b = sb + 6 * off + t;
+                S3f B;
+                B.xx = b[0]; B.yy = b[cnt]; B.zz = b[2 * cnt]; B.xy = b[3 * cnt]; B.xz = b[4 * cnt]; B.yz = b[5 * cnt];
                 const S3f K = corr_hess_sm(se, p, n, n * n, e0, inv_h2);
                 bool nonconvex = false;
-                const float z = corr_root(B, K, sr[p], &nonconvex);
+                const float z = corr_root(B, K, sr[off + t], &nonconvex);
                 const float v = fmaf(h2half, z, e0);
                 se[p] = v;
                 du = fmaxf(du, fabsf(v - e0));
                 um = fmaxf(um, fabsf(v));
                 ev += nonconvex ? 1ull : 0ull;
             }
+            off += cnt;
             __syncthreads();
         }
         if (sweeps > 0) continue;
@@ -364,10 +397,11 @@ __global__ void k_split_update(double* __restrict__ u, float* __restrict__ e, fl
     e[p] = 0.0f;
 }
 
-// FP64 fine residual r = rhs - det(D^2_h u), written as FP32, with the
-// (max, sum of squares) norm partials of the FP64 values.
+// FP64 fine residual r = rhs - det(D^2_h u), written as FP32 in colour-major
+// order (the correction problem's right-hand side), with the (max, sum of
+// squares) norm partials of the FP64 values.
 __global__ void __launch_bounds__(BX * BY) k_residual64_to32(const double* __restrict__ u,
-                                                             const double* __restrict__ rhs, float* __restrict__ r,
+                                                             const double* __restrict__ rhs, float* __restrict__ r_cm,
                                                              int n, double inv_h6, double* partials)
 {
     const int i = blockIdx.x * BX + threadIdx.x;
@@ -383,8 +417,9 @@ __global__ void __launch_bounds__(BX * BY) k_residual64_to32(const double* __res
                 val = fma(-det0(H), inv_h6, rhs[p]);   // inv_h6 = 1 / (64 h^6)
                 mx = fmax(mx, fabs(val));
                 ss = fma(val, val, ss);
+                const CmPos c = cm_pos(i, j, k, n);
+                r_cm[c.off + c.idx] = d2f_trunc(val);
             }
-            r[p] = (float)val;
         }
     }
     __shared__ double smx[BX * BY / 32], sss[BX * BY / 32];
@@ -406,50 +441,62 @@ __global__ void __launch_bounds__(BX * BY) k_residual64_to32(const double* __res
 
 }  // namespace
 
-size_t base_store_floats(int n)
+size_t base_store_bytes(int n)
 {
-    return n >= 3 ? 6 * (size_t)(n - 2) * (n - 2) * (n - 2) : 0;
+    return n >= 3 ? 6 * sizeof(float) * (size_t)(n - 2) * (n - 2) * (n - 2) : 0;
 }
 
-cudaError_t launch_base_colour(const float* hi, const float* lo, float* bstore, int n, double h, cudaStream_t s)
+size_t cm_points(int n) { return n >= 3 ? (size_t)(n - 2) * (n - 2) * (n - 2) : 0; }
+
+cudaError_t launch_base_colour(const float* hi, const float* lo, void* bstore, int n, double h, cudaStream_t s)
 {
     count_launches(1);
-    k_base_colour<<<grid_of(n), dim3(BX, BY), 0, s>>>(hi, lo, bstore, n, (float)(1.0 / (h * h)));
+    k_base_colour<<<grid_of(n), dim3(BX, BY), 0, s>>>(hi, lo, (float*)bstore, n, (float)(1.0 / (h * h)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_smooth_corr(float* e, const float* bstore, const float* rhs, int n, double h, int nsweeps,
+cudaError_t launch_to_cm(const float* nat, float* cm, int n, cudaStream_t s)
+{
+    count_launches(1);
+    k_to_cm<<<grid_of(n), dim3(BX, BY), 0, s>>>(nat, cm, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_smooth_corr(float* e, const void* bstore, const float* rhs_cm, int n, double h, int nsweeps,
                                unsigned long long* events, cudaStream_t s)
 {
     const float inv_h2 = (float)(1.0 / (h * h));
     const float h2half = (float)(0.5 * h * h);
+    const float* b = (const float*)bstore;
     for (int sw = 0; sw < nsweeps; ++sw) {
         cudaError_t e_;
-        if ((e_ = launch_colour_corr<0>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<1>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<2>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<3>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<4>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<5>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<6>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<7>(e, bstore, rhs, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<0>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<1>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<2>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<3>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<4>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<5>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<6>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        if ((e_ = launch_colour_corr<7>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
     }
     return cudaSuccess;
 }
 
-cudaError_t launch_residual_corr(const float* e, const float* hi, const float* lo, const float* rhs, float* res,
-                                 int n, double h, cudaStream_t s)
+cudaError_t launch_residual_corr(const float* e, const void* bstore, const float* rhs_cm, float* res, int n,
+                                 double h, cudaStream_t s)
 {
     count_launches(1);
-    k_residual_corr<<<grid_of(n), dim3(BX, BY), 0, s>>>(e, hi, lo, rhs, res, n, (float)(1.0 / (h * h)));
+    k_residual_corr<<<grid_of(n), dim3(BX, BY), 0, s>>>(e, (const float*)bstore, rhs_cm, res, n,
+                                                        (float)(1.0 / (h * h)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_rhs_corr(const float* w, const float* hi, const float* lo, const float* resc, float* rhs,
-                                   int nc, double H, cudaStream_t s)
+cudaError_t launch_coarse_rhs_corr(const float* w, const void* bstore, const float* resc, float* rhs_cm, int nc,
+                                   double H, cudaStream_t s)
 {
     count_launches(1);
-    k_coarse_rhs_corr<<<grid_of(nc), dim3(BX, BY), 0, s>>>(w, hi, lo, resc, rhs, nc, (float)(1.0 / (H * H)));
+    k_coarse_rhs_corr<<<grid_of(nc), dim3(BX, BY), 0, s>>>(w, (const float*)bstore, resc, rhs_cm, nc,
+                                                           (float)(1.0 / (H * H)));
     return cudaGetLastError();
 }
 
@@ -478,13 +525,18 @@ cudaError_t launch_inject_f32(const float* vf, int nf, float* vc, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_coarsest_corr(float* e, const float* hi, const float* lo, const float* rhs, int n, double h,
-                                 int sweeps, unsigned long long* events, cudaStream_t s)
+static size_t coarsest_corr_smem(int n)
 {
-    const size_t smem = 4 * sizeof(float) * (size_t)n * n * n;
+    return sizeof(float) * ((size_t)n * n * n + 7 * cm_points(n));
+}
+
+cudaError_t launch_coarsest_corr(float* e, const void* bstore, const float* rhs_cm, int n, double h, int sweeps,
+                                 unsigned long long* events, cudaStream_t s)
+{
     count_launches(1);
-    k_coarsest_corr<<<1, CT, smem, s>>>(e, hi, lo, rhs, n, (float)(1.0 / (h * h)), (float)(0.5 * h * h), sweeps,
-                                        events);
+    k_coarsest_corr<<<1, CT, coarsest_corr_smem(n), s>>>(e, (const float*)bstore, rhs_cm, n,
+                                                         (float)(1.0 / (h * h)), (float)(0.5 * h * h), sweeps,
+                                                         events);
     return cudaGetLastError();
 }
 
@@ -495,7 +547,7 @@ cudaError_t prepare_coarsest_kernels()
     cudaError_t e = prepare_coarsest_f64();
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_coarsest_corr, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(4 * sizeof(float) * 17 * 17 * 17));
+                                (int)coarsest_corr_smem(17));
 }
 
 cudaError_t launch_split_update(double* u, float* e, float* hi, float* lo, int n, int apply, cudaStream_t s)
@@ -506,13 +558,13 @@ cudaError_t launch_split_update(double* u, float* e, float* hi, float* lo, int n
     return cudaGetLastError();
 }
 
-cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r, int n, double h, double* partials,
-                                   cudaStream_t s)
+cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r_cm, int n, double h,
+                                   double* partials, cudaStream_t s)
 {
     const double h2 = h * h;
     count_launches(1);
     const dim3 g((n + BX - 1) / BX, (n + BY - 1) / BY, n < 16 ? n : 16);
-    k_residual64_to32<<<g, dim3(BX, BY), 0, s>>>(u, rhs, r, n, 1.0 / (64.0 * h2 * h2 * h2), partials);
+    k_residual64_to32<<<g, dim3(BX, BY), 0, s>>>(u, rhs, r_cm, n, 1.0 / (64.0 * h2 * h2 * h2), partials);
     return cudaGetLastError();
 }
 

@@ -71,8 +71,9 @@ _SIGS = {
     "ma_norm_scratch_bytes": [C.c_int, C.POINTER(C.c_size_t)],
     "ma_norm": [_vp, C.c_int, C.c_double, _vp, C.c_size_t, C.POINTER(C.c_double), _vp],
     "ma_kernel_launch_count": [C.POINTER(C.c_ulonglong)],
-    "ma_smooth_correction": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp, _vp],
-    "ma_residual_correction": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp],
+    "ma_correction_scratch_bytes": [C.c_int, C.POINTER(C.c_size_t)],
+    "ma_smooth_correction": [_vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp, C.c_size_t, _vp, _vp],
+    "ma_residual_correction": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp, C.c_size_t, _vp],
     "ma_norm_static": [_vp, C.c_int, C.c_double, C.POINTER(C.c_double), _vp],
 }
 # Declared in include/ma.h; the test suite checks that the library exports them.
@@ -222,15 +223,31 @@ def ma_coarsest_solve(u, rhs, n: int, h: float, sweeps: int = 0, events=None, st
     _check(load().ma_coarsest_solve(_ptr(u), _ptr(rhs), n, h, sweeps, _ptr(events), _stream(stream)))
 
 
-def ma_smooth_correction(e, b_scratch, u_hi, u_lo, rhs, n: int, h: float, nsweeps: int = 1, events=None,
-                         stream=None) -> None:
-    _check(load().ma_smooth_correction(_ptr(e), _ptr(b_scratch), _ptr(u_hi), _ptr(u_lo), _ptr(rhs), n, h, nsweeps,
-                                       _ptr(events), _stream(stream)))
+def ma_correction_scratch_bytes(n: int) -> int:
+    b = C.c_size_t(0)
+    _check(load().ma_correction_scratch_bytes(n, C.byref(b)))
+    return b.value
 
 
-def ma_residual_correction(e, u_hi, u_lo, rhs, res, n: int, h: float, stream=None) -> None:
+def ma_smooth_correction(e, u_hi, u_lo, rhs, n: int, h: float, nsweeps: int, scratch, scratch_bytes: int,
+                         events=None, stream=None) -> None:
+    _check(load().ma_smooth_correction(_ptr(e), _ptr(u_hi), _ptr(u_lo), _ptr(rhs), n, h, nsweeps, _ptr(scratch),
+                                       scratch_bytes, _ptr(events), _stream(stream)))
+
+
+def ma_residual_correction(e, u_hi, u_lo, rhs, res, n: int, h: float, scratch, scratch_bytes: int,
+                           stream=None) -> None:
     _check(load().ma_residual_correction(_ptr(e), _ptr(u_hi), _ptr(u_lo), _ptr(rhs), _ptr(res), n, h,
-                                         _stream(stream)))
+                                         _ptr(scratch), scratch_bytes, _stream(stream)))
+
+
+def correction_scratch(n: int, device=None):
+    """A 256-byte-aligned uint8 CUDA buffer for the correction step calls: (tensor, address, bytes)."""
+    import torch
+    nb = ma_correction_scratch_bytes(n)
+    t = torch.empty(nb + 256, dtype=torch.uint8, device=device or torch.device("cuda"))
+    addr = (t.data_ptr() + 255) // 256 * 256
+    return t, addr, nb
 
 
 def ma_norm_scratch_bytes(n: int) -> int:
@@ -271,7 +288,7 @@ class SolveResult:
 
 
 def make_desc(n: int, length: float = 1.0, x0=(0.0, 0.0, 0.0), nu1: int = 2, nu2: int = 2,
-              coarsest_n: int = 5, restrict_kind: int = MA_FULL_WEIGHTING,
+              coarsest_n: int = 3, restrict_kind: int = MA_FULL_WEIGHTING,
               approx_restrict: int = MA_APPROX_WEIGHTED, precision: int = MA_FP64,
               coarse_sweeps: int = 0, inner_cycles: int = 0) -> ma_hier_desc:
     d = ma_hier_desc()

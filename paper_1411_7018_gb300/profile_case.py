@@ -47,11 +47,11 @@ def main():
         hi = u.float()
         lo = (u - hi.double()).float()
         e = torch.zeros_like(hi)
-        b_scratch = torch.empty(6 * (a.n - 2) ** 3, dtype=torch.float32, device="cuda")
+        _keep, scr, nb = M.correction_scratch(a.n)
         rhs = (1e-6 * f).float()
         rhs[0], rhs[-1] = 0, 0
         for _ in range(a.reps):
-            M.ma_smooth_correction(e, b_scratch, hi, lo, rhs, a.n, pr.h, 1)
+            M.ma_smooth_correction(e, hi, lo, rhs, a.n, pr.h, 1, scr, nb)
     else:
         prec = M.MA_MIXED if a.precision == "mixed" else M.MA_FP64
         H = M.Hierarchy(M.make_desc(a.n, length=pr.length, precision=prec))

@@ -68,20 +68,26 @@ def test_correction_residual_matches_oracle_definition(name, n, amp):
     ref[0], ref[-1], ref[:, 0], ref[:, -1], ref[:, :, 0], ref[:, :, -1] = 0, 0, 0, 0, 0, 0
     hi, lo = split(u)
     res = torch.empty(u.shape, dtype=torch.float32, device="cuda")
-    M.ma_residual_correction(dev(e), dev(hi), dev(lo), dev(rhs), res, n, pr.h)
+    _keep, scr, nb = M.correction_scratch(n)
+    M.ma_residual_correction(dev(e), dev(hi), dev(lo), dev(rhs), res, n, pr.h, scr, nb)
     got = host(res).astype(np.float64)
     inner = (slice(1, -1),) * 3
     scale = np.max(np.abs(N_ref[inner])) + np.max(np.abs(rhs))
     assert np.max(np.abs(got - ref)) <= 2e-4 * scale
 
 
-@pytest.mark.parametrize("name,n,amp", [("exp", 33, 1e-4), ("cosine", 65, 1e-5)])
+@pytest.mark.parametrize("name,n,amp", [("exp", 33, 1e-4), ("cosine", 65, 1e-5), ("exp", 129, 1e-6)])
 def test_correction_sweep_matches_oracle_sweep(name, n, amp):
+    """One correction sweep against the oracle's Gauss-Seidel sweep on
+    w = u + e with right-hand side det(D^2_h u) + rhs, in the regime the
+    inner cycles run in (|rhs| ~ 1e-5 |f|, corrections of that order).  The
+    kernel's base Hessian comes from the FP32 hi/lo split (~1e-5 relative),
+    and e is FP32."""
     pr = P.make(name, n, seed=4)
     u = pr.u
     e = smooth_correction_field(n, amp, n + 1)
     rng = np.random.default_rng(2)
-    rhs = (1e-2 * rng.standard_normal(u.shape) * np.max(pr.f)).astype(np.float32)
+    rhs = (1e-5 * rng.standard_normal(u.shape) * np.max(pr.f)).astype(np.float32)
     rhs[0], rhs[-1] = 0, 0
     w = np.ascontiguousarray(u + e.astype(np.float64))
     ftot = O.discrete_ma(u, pr.h) + rhs.astype(np.float64)
@@ -89,7 +95,8 @@ def test_correction_sweep_matches_oracle_sweep(name, n, amp):
     e_ref = w - u
     hi, lo = split(u)
     ed = dev(e)
-    M.ma_smooth_correction(ed, torch.empty(6 * (n - 2) ** 3, dtype=torch.float32, device="cuda"), dev(hi), dev(lo), dev(rhs), n, pr.h, 1)
+    _keep, scr, nb = M.correction_scratch(n)
+    M.ma_smooth_correction(ed, dev(hi), dev(lo), dev(rhs), n, pr.h, 1, scr, nb)
     got = host(ed).astype(np.float64)
     change = np.max(np.abs(e_ref - e.astype(np.float64)))
     assert change > 0

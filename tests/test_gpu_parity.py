@@ -207,7 +207,7 @@ def test_norms_match_oracle(n):
 # whole cycles and solves
 # ---------------------------------------------------------------------------
 
-def _params(kind=M.MA_FULL_WEIGHTING, approx=M.MA_APPROX_WEIGHTED, coarsest=5, csweeps=0):
+def _params(kind=M.MA_FULL_WEIGHTING, approx=M.MA_APPROX_WEIGHTED, coarsest=3, csweeps=0):
     return O.Params(nu1=2, nu2=2, coarsest_n=coarsest, restrict_kind=kind, coarse_sweeps=csweeps,
                     approx_restrict=approx)
 
@@ -231,12 +231,15 @@ def test_vcycle_matches_oracle(name, n, kind, approx):
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("name,n", [("exp", 33), ("quadratic", 33), ("cosine", 65), ("exp", 129),
-                                    ("sine", 65)])
-def test_solve_matches_oracle(name, n):
+@pytest.mark.parametrize("name,n,coarsest", [("exp", 33, 5), ("quadratic", 33, 3), ("cosine", 65, 3),
+                                             ("exp", 129, 3), ("sine", 65, 5)])
+def test_solve_matches_oracle(name, n, coarsest):
+    """Whole FP64 solves (FMG + V(2,2) to 1e-10) against the oracle, with the
+    coarsest grid at 3^3 (Section 4's h0 = 1/2) or at 5^3 swept to
+    convergence."""
     pr = P.make(name, n, seed=7)
     length = pr.length
-    H = M.Hierarchy(M.make_desc(n, length=length))
+    H = M.Hierarchy(M.make_desc(n, length=length, coarsest_n=coarsest))
     H.set_rhs_bc(dev(pr.f), dev(pr.initial()))
     res = H.solve(tol=1e-10)
     u = torch.empty_like(dev(pr.f))
@@ -244,7 +247,7 @@ def test_solve_matches_oracle(name, n):
     got = host(u)
     H.close()
     ref = pr.initial()
-    info = O.solve(ref, pr.f, pr.h, tol=1e-10, params=_params())
+    info = O.solve(ref, pr.f, pr.h, tol=1e-10, params=_params(coarsest=coarsest))
     assert res.res <= 1e-10 and res.nonconvex_root_events == 0
     assert abs(res.cycles - info.cycles) <= 1
     assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
