@@ -138,6 +138,26 @@ ma_status ma_vcycle(ma_hierarchy *h, int ncycles);
  * every case. */
 ma_status ma_solve(ma_hierarchy *h, const ma_solve_opts *opts, ma_solve_result *result);
 
+/* The same solve without blocking, for callers that interleave many solves
+ * (batching, serving).  ma_solve_begin queues the initial iterate and its
+ * residual norm; each ma_solve_advance call returns at once: if the norms of
+ * the last queued step have reached the host it applies the stopping rule
+ * and, unless the solve is finished, queues the next cycle (one CUDA graph
+ * launch and one 40-byte read-back on the hierarchy's stream); *done is set
+ * to 1 when the solve has finished.  ma_solve_get_result then returns the
+ * result and its status, as ma_solve would.  ma_solve is begin + advance
+ * (waiting on the read-back) + get_result. */
+ma_status ma_solve_begin(ma_hierarchy *h, const ma_solve_opts *opts);
+ma_status ma_solve_advance(ma_hierarchy *h, int *done);
+ma_status ma_solve_get_result(const ma_hierarchy *h, ma_solve_result *result);
+
+/* Batched solve: every hierarchy in hs solves with opts, their cycles
+ * overlapping on the GPU (each hierarchy runs on the stream it was created
+ * with, so give them distinct streams).  Blocks until all have finished;
+ * results[b] is filled for every b.  Returns MA_OK if all converged, else the
+ * first non-MA_OK status. */
+ma_status ma_batch_solve(ma_hierarchy *const *hs, int count, const ma_solve_opts *opts, ma_solve_result *results);
+
 /* Norm of the fine-level FP64 residual f - det(D^2_h u) of the current
  * iterate (Algorithm 1 step 3; Section 4 norms).  Blocks on the stream. */
 ma_status ma_residual_norm(ma_hierarchy *h, int norm, double *out);

@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "ma.h"
 #include "ma_hier.h"
@@ -115,8 +116,9 @@ size_t layout(ma_hierarchy* H, const ma_hier_desc* d, char* base)
     H->L = L;
     H->npartials = ma::residual_partial_count(d->n);
     H->partials = (double*)take(2 * sizeof(double) * (size_t)H->npartials);
-    H->out2 = (double*)take(4 * sizeof(double));
-    H->events = (unsigned long long*)take(sizeof(unsigned long long));
+    H->rb = (double*)take(5 * sizeof(double));
+    H->out2 = H->rb;
+    H->events = base ? (unsigned long long*)(H->rb + 4) : nullptr;
     H->flag = (int*)take(sizeof(int));
     return off;
 }
@@ -316,18 +318,6 @@ ma_status fine_residual_norms(ma_hierarchy* H, double* mx, double* l2)
     return read_norms(H, mx, l2);
 }
 
-ma_status rhs_norms(ma_hierarchy* H, double* mx, double* l2)
-{
-    ma::Level& F = H->lev[0];
-    MA_CK(ma::launch_norm_partials(F.rhs, F.n, H->partials, H->s));
-    MA_CK(ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s));
-    MA_CK(cudaMemcpyAsync(H->host, H->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, H->s));
-    MA_CK(cudaStreamSynchronize(H->s));
-    *mx = H->host[0];
-    *l2 = H->host[1];
-    return MA_OK;
-}
-
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev)
@@ -390,7 +380,8 @@ ma_status ma_create_hierarchy(const ma_hier_desc* desc, void* dev_workspace, siz
     cudaError_t e = cudaGetDevice(&H->device);
     if (e == cudaSuccess) e = ma::prepare_coarsest_kernels();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&H->host, 4 * sizeof(double) + sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&H->host, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H->sv.ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(H->events, 0, sizeof(unsigned long long), H->s);
     for (int l = 0; l < H->L && e == cudaSuccess; ++l) {   // corrections start at zero (shell stays zero)
         const size_t pts = (size_t)H->lev[l].n * H->lev[l].n * H->lev[l].n;
@@ -399,6 +390,7 @@ ma_status ma_create_hierarchy(const ma_hier_desc* desc, void* dev_workspace, siz
     if (e != cudaSuccess) {
         if (H->host) cudaFreeHost(H->host);
         if (H->cap) cudaStreamDestroy(H->cap);
+        if (H->sv.ev) cudaEventDestroy(H->sv.ev);
         delete H;
         return fail(MA_ERR_CUDA, "create: %s", cudaGetErrorString(e));
     }
@@ -413,6 +405,7 @@ ma_status ma_destroy_hierarchy(ma_hierarchy* H)
     cudaError_t e = cudaStreamSynchronize(H->s);
     destroy_graphs(H);
     if (H->cap) cudaStreamDestroy(H->cap);
+    if (H->sv.ev) cudaEventDestroy(H->sv.ev);
     if (H->host) cudaFreeHost(H->host);
     delete H;
     if (e != cudaSuccess) return fail(MA_ERR_CUDA, "destroy: %s", cudaGetErrorString(e));
@@ -436,9 +429,9 @@ ma_status ma_set_rhs_bc(ma_hierarchy* H, const double* f_dev, const double* g_de
     MA_CK(cudaMemsetAsync(H->flag, 0, sizeof(int), H->s));
     MA_CK(ma::launch_copy_rhs_bc(f_dev, g_dev, F.rhs, F.u, F.n, H->flag, H->s));
     int bad = 0;
-    MA_CK(cudaMemcpyAsync(&H->host[2], H->flag, sizeof(int), cudaMemcpyDeviceToHost, H->s));
+    MA_CK(cudaMemcpyAsync(&H->host[6], H->flag, sizeof(int), cudaMemcpyDeviceToHost, H->s));
     MA_CK(cudaStreamSynchronize(H->s));
-    std::memcpy(&bad, &H->host[2], sizeof(int));
+    std::memcpy(&bad, &H->host[6], sizeof(int));
     if (bad) return fail(MA_ERR_INVALID_ARG, "%d grid values invalid (f must be finite and > 0 inside, g finite)", bad);
     return MA_OK;
 }
@@ -483,91 +476,206 @@ ma_status ma_set_solution(ma_hierarchy* H, const double* u_dev)
     return MA_OK;
 }
 
-ma_status ma_solve(ma_hierarchy* H, const ma_solve_opts* opts, ma_solve_result* res)
+static ma_status check_opts(const ma_solve_opts* o)
 {
-    if (!H || !opts || !res) return fail(MA_ERR_INVALID_ARG, "null argument");
-    if (!(opts->tol >= 0.0) || opts->max_cycles < 0 || (opts->norm != MA_NORM_MAX && opts->norm != MA_NORM_L2) ||
-        opts->init < MA_INIT_FMG || opts->init > MA_INIT_KEEP)
+    if (!(o->tol >= 0.0) || o->max_cycles < 0 || (o->norm != MA_NORM_MAX && o->norm != MA_NORM_L2) ||
+        o->init < MA_INIT_FMG || o->init > MA_INIT_KEEP)
         return fail(MA_ERR_INVALID_ARG, "bad solve options");
+    return MA_OK;
+}
+
+// Copies the read-back block to the pinned host buffer and marks it.
+static cudaError_t queue_readback(ma_hierarchy* H)
+{
+    cudaError_t e = cudaMemcpyAsync(H->host, H->rb, 5 * sizeof(double), cudaMemcpyDeviceToHost, H->s);
+    if (e != cudaSuccess) return e;
+    return cudaEventRecord(H->sv.ev, H->s);
+}
+
+ma_status ma_solve_begin(ma_hierarchy* H, const ma_solve_opts* opts)
+{
+    if (!H || !opts) return fail(MA_ERR_INVALID_ARG, "null argument");
+    ma_status st = check_opts(opts);
+    if (st != MA_OK) return st;
     DeviceGuard g(H->device);
-    std::memset(res, 0, sizeof *res);
+    H->sv.o = *opts;
+    H->sv.phase = 0;
+    H->sv.stagnant = 0;
+    H->sv.scale = 1.0;
+    H->sv.rel = 0.0;
+    std::memset(&H->sv.r, 0, sizeof H->sv.r);
     MA_CK(cudaMemsetAsync(H->events, 0, sizeof(unsigned long long), H->s));
-    double scale = 1.0;
-    if (opts->relative) {
-        double fm, f2;
-        ma_status st = rhs_norms(H, &fm, &f2);
-        if (st != MA_OK) return st;
-        scale = opts->norm == MA_NORM_MAX ? fm : f2;
-        if (!(scale > 0.0)) scale = 1.0;
-    }
     const bool mixed = H->d.precision == MA_MIXED;
-    // Initial iterate and its residual norm, then one graph per cycle.  In
+    // rhs norms, the initial iterate and its residual norm as one graph.  In
     // mixed precision the FMG pass stops at the interpolated finest iterate
     // and the FP32-corrected outer iterations take over from there.
     const int init = opts->init;
     MA_CK(run_graph(H, H->g_init[init], [&]() -> cudaError_t {
-        cudaError_t e = cudaSuccess;
-        if (init == MA_INIT_FMG) e = fmg(H, !mixed);
-        else if (init == MA_INIT_ZERO) e = ma::launch_zero_interior(H->lev[0].u, H->lev[0].n, H->s);
+        ma::Level& F = H->lev[0];
+        cudaError_t e = ma::launch_norm_partials(F.rhs, F.n, H->partials, H->s);
+        if (e == cudaSuccess) e = ma::launch_norm_final(H->partials, H->npartials, F.h, H->rb + 2, H->s);
+        if (e == cudaSuccess && init == MA_INIT_FMG) e = fmg(H, !mixed);
+        if (e == cudaSuccess && init == MA_INIT_ZERO) e = ma::launch_zero_interior(F.u, F.n, H->s);
         if (e != cudaSuccess) return e;
         if (mixed) {
             if ((e = refresh_base(H, 0)) != cudaSuccess) return e;
             return mixed_residual(H);
         }
-        ma::Level& F = H->lev[0];
         if ((e = ma::launch_residual(F.u, F.rhs, F.r, F.n, F.h, H->partials, H->s)) != cudaSuccess) return e;
         return ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s);
     }));
-    double mx, l2;
-    ma_status st = read_norms(H, &mx, &l2);
-    if (st != MA_OK) return st;
-    double rel = (opts->norm == MA_NORM_MAX ? mx : l2) / scale;
-    res->res0 = rel;
-    int stagnant = 0;
-    ma_status out = MA_OK;
-    while (true) {
-        if (!std::isfinite(rel)) { out = MA_ERR_NONFINITE; break; }
-        if (rel <= opts->tol) break;
-        if (res->cycles >= opts->max_cycles) { out = MA_ERR_NOT_CONVERGED; break; }
-        MA_CK(run_graph(H, H->g_cycle, [&]() -> cudaError_t {
-            cudaError_t e;
-            if (mixed) {
-                const int inner = H->d.inner_cycles > 0 ? H->d.inner_cycles : 3;
-                for (int c = 0; c < inner; ++c)
-                    if ((e = corr_vcycle(H)) != cudaSuccess) return e;
-                if ((e = refresh_base(H, 1)) != cudaSuccess) return e;
-                return mixed_residual(H);
-            }
-            if ((e = vcycle_from(H, 0)) != cudaSuccess) return e;
-            ma::Level& F = H->lev[0];
-            if ((e = ma::launch_residual(F.u, F.rhs, F.r, F.n, F.h, H->partials, H->s)) != cudaSuccess) return e;
-            return ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s);
-        }));
-        st = read_norms(H, &mx, &l2);
-        res->cycles += 1;
-        if (st != MA_OK) return st;
-        const double nrel = (opts->norm == MA_NORM_MAX ? mx : l2) / scale;
+    MA_CK(queue_readback(H));
+    H->sv.phase = 1;
+    return MA_OK;
+}
+
+// One cycle (FP64 V-cycle, or in mixed precision inner FP32 correction
+// cycles + FP64 update) and the new residual norm, as one graph.
+static cudaError_t launch_cycle(ma_hierarchy* H)
+{
+    const bool mixed = H->d.precision == MA_MIXED;
+    return run_graph(H, H->g_cycle, [&]() -> cudaError_t {
+        cudaError_t e;
+        if (mixed) {
+            const int inner = H->d.inner_cycles > 0 ? H->d.inner_cycles : 3;
+            for (int c = 0; c < inner; ++c)
+                if ((e = corr_vcycle(H)) != cudaSuccess) return e;
+            if ((e = refresh_base(H, 1)) != cudaSuccess) return e;
+            return mixed_residual(H);
+        }
+        if ((e = vcycle_from(H, 0)) != cudaSuccess) return e;
+        ma::Level& F = H->lev[0];
+        if ((e = ma::launch_residual(F.u, F.rhs, F.r, F.n, F.h, H->partials, H->s)) != cudaSuccess) return e;
+        return ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s);
+    });
+}
+
+ma_status ma_solve_advance(ma_hierarchy* H, int* done)
+{
+    if (!H || !done) return fail(MA_ERR_INVALID_ARG, "null argument");
+    *done = 0;
+    if (H->sv.phase == 0) return fail(MA_ERR_INVALID_ARG, "ma_solve_advance before ma_solve_begin");
+    if (H->sv.phase == 3) {
+        *done = 1;
+        return MA_OK;
+    }
+    DeviceGuard g(H->device);
+    const cudaError_t q = cudaEventQuery(H->sv.ev);
+    if (q == cudaErrorNotReady) return MA_OK;
+    if (q != cudaSuccess) return fail(MA_ERR_CUDA, "ma_solve_advance: %s", cudaGetErrorString(q));
+    const ma_solve_opts& o = H->sv.o;
+    const double resn = o.norm == MA_NORM_MAX ? H->host[0] : H->host[1];
+    ma_solve_result& r = H->sv.r;
+    if (H->sv.phase == 1) {
+        double sc = 1.0;
+        if (o.relative) {
+            sc = o.norm == MA_NORM_MAX ? H->host[2] : H->host[3];
+            if (!(sc > 0.0)) sc = 1.0;
+        }
+        H->sv.scale = sc;
+        H->sv.rel = resn / sc;
+        r.res0 = H->sv.rel;
+    } else {
+        const double nrel = resn / H->sv.scale;
+        r.cycles += 1;
         // three cycles in a row that barely reduce the residual: round-off floor
-        stagnant = (nrel > 0.8 * rel) ? stagnant + 1 : 0;
-        rel = nrel;
-        if (stagnant >= 3 && rel > opts->tol) {
-            res->floor_reached = 1;
-            out = MA_ERR_NOT_CONVERGED;
-            break;
+        H->sv.stagnant = (nrel > 0.8 * H->sv.rel) ? H->sv.stagnant + 1 : 0;
+        H->sv.rel = nrel;
+    }
+    const double rel = H->sv.rel;
+    int out = -1;
+    if (!std::isfinite(rel)) out = MA_ERR_NONFINITE;
+    else if (rel <= o.tol) out = MA_OK;
+    else if (r.cycles >= o.max_cycles) out = MA_ERR_NOT_CONVERGED;
+    else if (H->sv.stagnant >= 3) {
+        r.floor_reached = 1;
+        out = MA_ERR_NOT_CONVERGED;
+    }
+    if (out >= 0) {
+        unsigned long long ev = 0;
+        std::memcpy(&ev, H->host + 4, sizeof ev);
+        r.res = rel;
+        r.status = out;
+        r.nonconvex_root_events = (long long)ev;
+        H->sv.phase = 3;
+        *done = 1;
+        return MA_OK;
+    }
+    MA_CK(launch_cycle(H));
+    MA_CK(queue_readback(H));
+    H->sv.phase = 2;
+    return MA_OK;
+}
+
+ma_status ma_solve_get_result(const ma_hierarchy* H, ma_solve_result* res)
+{
+    if (!H || !res) return fail(MA_ERR_INVALID_ARG, "null argument");
+    if (H->sv.phase != 3) return fail(MA_ERR_INVALID_ARG, "solve not finished");
+    *res = H->sv.r;
+    const int out = H->sv.r.status;
+    if (out == MA_ERR_NONFINITE) return fail(MA_ERR_NONFINITE, "residual became non-finite after %d cycles", res->cycles);
+    if (out == MA_ERR_NOT_CONVERGED)
+        return fail(MA_ERR_NOT_CONVERGED, "not converged: residual %.3e > tol %.3e after %d cycles%s", res->res,
+                    H->sv.o.tol, res->cycles, res->floor_reached ? " (round-off floor)" : "");
+    return MA_OK;
+}
+
+ma_status ma_solve(ma_hierarchy* H, const ma_solve_opts* opts, ma_solve_result* res)
+{
+    if (!H || !opts || !res) return fail(MA_ERR_INVALID_ARG, "null argument");
+    std::memset(res, 0, sizeof *res);
+    ma_status st = ma_solve_begin(H, opts);
+    if (st != MA_OK) return st;
+    int done = 0;
+    while (!done) {
+        {
+            DeviceGuard g(H->device);
+            MA_CK(cudaEventSynchronize(H->sv.ev));
+        }
+        st = ma_solve_advance(H, &done);
+        if (st != MA_OK) return st;
+    }
+    return ma_solve_get_result(H, res);
+}
+
+ma_status ma_batch_solve(ma_hierarchy* const* hs, int count, const ma_solve_opts* opts, ma_solve_result* results)
+{
+    if (!hs || count < 0 || !opts || (count > 0 && !results)) return fail(MA_ERR_INVALID_ARG, "null argument");
+    for (int b = 0; b < count; ++b) {
+        if (!hs[b]) return fail(MA_ERR_INVALID_ARG, "null hierarchy %d", b);
+        std::memset(&results[b], 0, sizeof results[b]);
+    }
+    for (int b = 0; b < count; ++b) {
+        ma_status st = ma_solve_begin(hs[b], opts);
+        if (st != MA_OK) return st;
+    }
+    int remaining = count;
+    std::vector<char> done(count, 0);
+    while (remaining > 0) {
+        int first_pending = -1;
+        for (int b = 0; b < count; ++b) {
+            if (done[b]) continue;
+            int d = 0;
+            ma_status st = ma_solve_advance(hs[b], &d);
+            if (st != MA_OK) return st;
+            if (d) {
+                done[b] = 1;
+                --remaining;
+            } else if (first_pending < 0) {
+                first_pending = b;
+            }
+        }
+        if (first_pending >= 0) {   // wait for one pending read-back instead of spinning
+            DeviceGuard g(hs[first_pending]->device);
+            MA_CK(cudaEventSynchronize(hs[first_pending]->sv.ev));
         }
     }
-    res->res = rel;
-    unsigned long long ev = 0;
-    MA_CK(cudaMemcpyAsync(H->host + 3, H->events, sizeof ev, cudaMemcpyDeviceToHost, H->s));
-    MA_CK(cudaStreamSynchronize(H->s));
-    std::memcpy(&ev, H->host + 3, sizeof ev);
-    res->nonconvex_root_events = (long long)ev;
-    res->status = out;
-    if (out == MA_ERR_NONFINITE) return fail(out, "residual became non-finite after %d cycles", res->cycles);
-    if (out == MA_ERR_NOT_CONVERGED)
-        return fail(out, "not converged: residual %.3e > tol %.3e after %d cycles%s", rel, opts->tol, res->cycles,
-                    res->floor_reached ? " (round-off floor)" : "");
-    return MA_OK;
+    ma_status worst = MA_OK;
+    for (int b = 0; b < count; ++b) {
+        const ma_status st = ma_solve_get_result(hs[b], &results[b]);
+        if (st != MA_OK && worst == MA_OK) worst = st;
+    }
+    return worst;
 }
 
 // ---- single steps ----------------------------------------------------------

@@ -50,11 +50,24 @@ struct ma_hierarchy {
     size_t bytes = 0;
     double* partials = nullptr;          // norm partials (2 per block)
     int npartials = 0;
-    double* out2 = nullptr;              // device: reduced norms
-    unsigned long long* events = nullptr;  // device: nonconvex root events
+    // Device read-back block (5 x 8 bytes, copied to the host in one piece):
+    // [0..1] residual norms (max, L2), [2..3] rhs norms, [4] nonconvex root
+    // events (unsigned 64-bit).
+    double* rb = nullptr;
+    double* out2 = nullptr;                // = rb: where the residual norms land
+    unsigned long long* events = nullptr;  // = rb + 4
     int* flag = nullptr;                 // device: input validation count
-    double* host = nullptr;              // pinned host read-back (4 doubles + 1 counter)
+    double* host = nullptr;              // pinned host copy of the read-back block
     cudaStream_t cap = nullptr;          // private stream the graphs are captured on
     ma::GraphSlot g_init[3];             // per ma_solve init kind: init + first residual norm
     ma::GraphSlot g_cycle;               // one cycle + residual norm
+    // Non-blocking solve state (ma_solve_begin / ma_solve_advance).
+    struct {
+        ma_solve_opts o{};
+        int phase = 0;                   // 0 idle, 1 init norms pending, 2 cycle norms pending, 3 done
+        double scale = 1.0, rel = 0.0;
+        int stagnant = 0;
+        ma_solve_result r{};
+        cudaEvent_t ev = nullptr;        // marks the read-back of the latest norms
+    } sv;
 };

@@ -55,6 +55,10 @@ _SIGS = {
     "ma_set_rhs_bc": [_vp, _vp, _vp],
     "ma_vcycle": [_vp, C.c_int],
     "ma_solve": [_vp, C.POINTER(ma_solve_opts), C.POINTER(ma_solve_result)],
+    "ma_solve_begin": [_vp, C.POINTER(ma_solve_opts)],
+    "ma_solve_advance": [_vp, C.POINTER(C.c_int)],
+    "ma_solve_get_result": [_vp, C.POINTER(ma_solve_result)],
+    "ma_batch_solve": [C.POINTER(_vp), C.c_int, C.POINTER(ma_solve_opts), C.POINTER(ma_solve_result)],
     "ma_residual_norm": [_vp, C.c_int, C.POINTER(C.c_double)],
     "ma_get_solution": [_vp, _vp],
     "ma_set_solution": [_vp, _vp],
@@ -153,6 +157,34 @@ def ma_solve(hier: int, opts: ma_solve_opts, raise_on_error: bool = True) -> ma_
     if raise_on_error:
         _check(st)
     return res
+
+
+def ma_solve_begin(hier: int, opts: ma_solve_opts) -> None:
+    _check(load().ma_solve_begin(hier, C.byref(opts)))
+
+
+def ma_solve_advance(hier: int) -> bool:
+    done = C.c_int(0)
+    _check(load().ma_solve_advance(hier, C.byref(done)))
+    return bool(done.value)
+
+
+def ma_solve_get_result(hier: int, raise_on_error: bool = True) -> ma_solve_result:
+    res = ma_solve_result()
+    st = load().ma_solve_get_result(hier, C.byref(res))
+    if raise_on_error:
+        _check(st)
+    return res
+
+
+def ma_batch_solve(hiers, opts: ma_solve_opts, raise_on_error: bool = True):
+    n = len(hiers)
+    arr = (_vp * n)(*hiers)
+    res = (ma_solve_result * n)()
+    st = load().ma_batch_solve(arr, n, C.byref(opts), res)
+    if raise_on_error:
+        _check(st)
+    return list(res)
 
 
 def ma_residual_norm(hier: int, norm: int = MA_NORM_MAX) -> float:
