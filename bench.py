@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--problem", default="exp")
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+
 
     return ap.parse_args()
 
@@ -161,6 +163,93 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line), flush=True)
+
+
+def bench_batching(args, M, problems, dev):
+    """64 instances, sizes drawn by seed from {33, 65, 129}^3, each |x|^2/2
+    plus seeded cosine modes with amplitude drawn from [0.005, 0.02]; mixed
+    precision; solved together with ma_batch_solve (each hierarchy on its own
+    stream, cycles as CUDA graphs) versus the same hierarchies one at a time."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(2024)
+    sizes = rng.choice([33, 65, 129], size=64)
+    hs, keep = [], []
+    for b, n in enumerate(sizes):
+        f, g, _ = problems.make_on_device("cosine", int(n), seed=1000 + b, eps=(0.005, 0.02), device=dev)
+        H = M.Hierarchy(M.make_desc(int(n), precision=M.MA_MIXED), stream=torch.cuda.Stream(device=dev),
+                        device=dev)
+        torch.cuda.synchronize()
+        H.set_rhs_bc(f, g)
+        hs.append(H)
+        keep.append((f, g))
+    opts = M.ma_solve_opts(args.tol, M.MA_NORM_MAX, 1, 60, M.MA_INIT_FMG)
+    handles = [H.handle for H in hs]
+    M.ma_batch_solve(handles, opts)            # warm-up: graph capture
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = M.ma_batch_solve(handles, opts, raise_on_error=False)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for H in hs:
+        M.ma_solve(H.handle, opts, raise_on_error=False)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    unknowns = int(sum((int(n) - 2) ** 3 for n in sizes))
+    for H in hs:
+        H.close()
+    return {"instances": 64, "sizes": {str(k): int((sizes == k).sum()) for k in (33, 65, 129)},
+            "unknowns": unknowns, "tol": args.tol, "precision": "mixed",
+            "ms": t_batch * 1e3, "unknowns_per_s": unknowns / t_batch,
+            "sequential_ms": t_seq * 1e3, "sequential_unknowns_per_s": unknowns / t_seq,
+            "speedup_vs_sequential": t_seq / t_batch,
+            "converged": int(sum(1 for r in res if r.status == 0))}
+
+
+def bench_serving(args, M, problems, dev):
+    """Poisson arrivals (seeded, 200 req/s offered) of solves with sizes drawn
+    from {65, 129, 257}^3, |x|^2/2 plus seeded cosine modes, tol 1e-8
+    relative: continuous batching of mixed-precision solves versus FP64 solves
+    served one at a time, on the same request stream.  Latency = completion -
+    arrival (queueing included); the first requests that build the resident
+    hierarchies and capture their graphs are not counted."""
+    import numpy as np
+    import torch
+    from paper_1411_7018_gb300 import serve
+    sizes = (65, 129, 257)
+    keys = 2
+    inputs = {}
+    for n in sizes:
+        for k in range(keys):
+            inputs[(n, k)] = problems.make_on_device("cosine", n, seed=500 + 10 * n + k, eps=(0.005, 0.02),
+                                                     device=dev)
+    torch.cuda.synchronize()
+    out = {"offered_req_s": 200.0, "sizes": list(sizes), "tol": 1e-8,
+           "note": "200 req/s of this size mix exceeds one GPU's capacity, so latency there is mostly "
+                   "queueing; the *_60 runs offer 60 req/s"}
+    runs = (("mixed_continuous", M.MA_MIXED, args.serve_requests, 32, 200.0),
+            ("fp64_one_at_a_time", M.MA_FP64, max(50, args.serve_requests // 8), 1, 200.0),
+            ("mixed_continuous_60", M.MA_MIXED, max(100, args.serve_requests // 2), 32, 60.0),
+            ("fp64_one_at_a_time_60", M.MA_FP64, max(50, args.serve_requests // 8), 1, 60.0))
+    for label, precision, count, max_active, rate in runs:
+        be = serve.LibmaBackend(precision, inputs, device=dev)
+        srv = serve.Server(be, hbm_budget=48 << 30, max_active=max_active)
+        warm = [serve.Request(rid=-1 - i, n=n, arrival=0.0, key=(n, 0), tol=1e-8)
+                for i, n in enumerate(sizes * 2)]
+        srv.run(warm)
+        reqs = serve.poisson_stream(count, rate, sizes, keys, seed=77, tol=1e-8)
+        t0 = time.perf_counter()
+        done = srv.run(reqs)
+        wall = time.perf_counter() - t0
+        srv.close()
+        summ = serve.summarize(done, wall)
+        summ["max_active"] = max_active
+        summ["offered_req_s"] = rate
+        out[label] = summ
+    out["unknowns_per_s_mixed_vs_fp64"] = (out["mixed_continuous"]["unknowns_per_s"]
+                                          / out["fp64_one_at_a_time"]["unknowns_per_s"])
+    return out
 
 
 def main():
@@ -290,9 +379,19 @@ def main():
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
-    cpu = oracle_sample(pr, args.tol) if (rank == 0 and world == 1) else None
     for H in hier.values():
         H.close()
+    del hier
+    torch.cuda.empty_cache()
+    extras = {}
+    if world == 1:
+        for name, fn in (("batching", bench_batching), ("serving", bench_serving)):
+            try:
+                extras[name] = fn(args, M, problems, dev)
+            except Exception as exc:   # reported, not fatal: the headline line still prints
+                extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.empty_cache()
+    cpu = oracle_sample(pr, args.tol) if (rank == 0 and world == 1) else None
     if rank == 0:
         line = {
             "metric": "unknowns solved to tolerance per second",
@@ -326,6 +425,7 @@ def main():
                     "h2d_bytes_per_step": 2 * 8 * pr.n ** 3, "d2h_bytes_per_step": 8 * pr.n ** 3},
             "clocks": clocks,
             "gpu_launches": launches,
+            **extras,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

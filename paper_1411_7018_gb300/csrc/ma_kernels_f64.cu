@@ -17,6 +17,7 @@
 #include "ma_internal.h"
 #include "ma_point.cuh"
 #include "ma_transfer.cuh"
+#include "ma_residual.cuh"
 
 namespace ma {
 
@@ -93,32 +94,6 @@ __device__ __forceinline__ void block_reduce_store(double mx, double ss, double*
 constexpr int KZ = 16;   // z-blocks of the reduction grids; each loops over k
 
 dim3 reduce_grid(int n) { return dim3((n + BX - 1) / BX, (n + BY - 1) / BY, n < KZ ? n : KZ); }
-
-// r = rhs - det(D^2_h u) on the interior, 0 on the shell; optional
-// (max |r|, sum r^2) partials over the interior, one pair per block.
-__global__ void __launch_bounds__(BX * BY) k_residual(const double* __restrict__ u, const double* __restrict__ rhs,
-                                                      double* __restrict__ r, int n, double inv_h6,
-                                                      double* partials)
-{
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const long long sy = n, sz = (long long)n * n;
-    double mx = 0.0, ss = 0.0;
-    for (int k = blockIdx.z; k < n; k += gridDim.z) {
-        if (i < n && j < n) {
-            const long long p = lin(i, j, k, n);
-            double val = 0.0;
-            if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
-                const HessS H = gather_hess(u, p, sy, sz, u[p]);
-                val = fma(-det0(H), inv_h6, rhs[p]);   // inv_h6 = 1 / (64 h^6)
-                mx = fmax(mx, fabs(val));
-                ss = fma(val, val, ss);
-            }
-            r[p] = val;
-        }
-    }
-    if (partials) block_reduce_store(mx, ss, partials, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
-}
 
 __global__ void __launch_bounds__(BX * BY) k_norm_partials(const double* __restrict__ v, int n, double* partials)
 {
@@ -320,7 +295,10 @@ cudaError_t launch_residual(const double* u, const double* rhs, double* r, int n
                             double* partials, cudaStream_t s)
 {
     count_launches(1);
-    k_residual<<<reduce_grid(n), dim3(BX, BY), 0, s>>>(u, rhs, r, n, 1.0 / pow6(h), partials);
+    const dim3 g = reduce_grid(n);
+    const int kchunk = (n + (int)g.z - 1) / (int)g.z;
+    resid::k_residual_col<resid::NaturalF64Out><<<resid::grid_for(n, g.z), dim3(resid::RX, resid::RY), 0, s>>>(
+        u, rhs, resid::NaturalF64Out{r}, n, 1.0 / pow6(h), partials, kchunk);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@
 #include "ma_internal.h"
 #include "ma_point.cuh"
 #include "ma_transfer.cuh"
+#include "ma_residual.cuh"
 
 namespace ma {
 
@@ -176,15 +177,17 @@ __device__ __forceinline__ CmPos cm_pos(int i, int j, int k, int n)
     return r;
 }
 
+// B is read once per colour phase: streaming loads (evict-first) keep it from
+// pushing e, which every phase re-reads through its stencil, out of L2.
 __device__ __forceinline__ S3f load_b(const float* __restrict__ b, long long cnt)
 {
     S3f B;
-    B.xx = __ldg(b);
-    B.yy = __ldg(b + cnt);
-    B.zz = __ldg(b + 2 * cnt);
-    B.xy = __ldg(b + 3 * cnt);
-    B.xz = __ldg(b + 4 * cnt);
-    B.yz = __ldg(b + 5 * cnt);
+    B.xx = __ldcs(b);
+    B.yy = __ldcs(b + cnt);
+    B.zz = __ldcs(b + 2 * cnt);
+    B.xy = __ldcs(b + 3 * cnt);
+    B.xz = __ldcs(b + 4 * cnt);
+    B.yz = __ldcs(b + 5 * cnt);
     return B;
 }
 
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(BX * BY) k_smooth_corr(float* e, const float* 
     const float e0 = e[p];
     const S3f K = corr_hess(e, p, sy, sz, e0, inv_h2);
     bool nonconvex = false;
-    const float z = corr_root(B, K, __ldg(rc + idx), &nonconvex);
+    const float z = corr_root(B, K, __ldcs(rc + idx), &nonconvex);
     e[p] = fmaf(h2half, z, e0);
     if (nonconvex && events) atomicAdd(events, 1ull);
 }
@@ -397,47 +400,17 @@ __global__ void k_split_update(double* __restrict__ u, float* __restrict__ e, fl
     e[p] = 0.0f;
 }
 
-// FP64 fine residual r = rhs - det(D^2_h u), written as FP32 in colour-major
-// order (the correction problem's right-hand side), with the (max, sum of
-// squares) norm partials of the FP64 values.
-__global__ void __launch_bounds__(BX * BY) k_residual64_to32(const double* __restrict__ u,
-                                                             const double* __restrict__ rhs, float* __restrict__ r_cm,
-                                                             int n, double inv_h6, double* partials)
-{
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const long long sy = n, sz = (long long)n * n;
-    double mx = 0.0, ss = 0.0;
-    for (int k = blockIdx.z; k < n; k += gridDim.z) {
-        if (i < n && j < n) {
-            const long long p = lin(i, j, k, n);
-            double val = 0.0;
-            if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
-                const HessS H = gather_hess(u, p, sy, sz, u[p]);
-                val = fma(-det0(H), inv_h6, rhs[p]);   // inv_h6 = 1 / (64 h^6)
-                mx = fmax(mx, fabs(val));
-                ss = fma(val, val, ss);
-                const CmPos c = cm_pos(i, j, k, n);
-                r_cm[c.off + c.idx] = d2f_trunc(val);
-            }
-        }
+// FP64 fine residual, written as FP32 in colour-major order (the correction
+// problem's right-hand side); the shell is not stored.
+struct CmF32Out {
+    float* r;
+    __device__ __forceinline__ void put(long long, int i, int j, int k, int n, double, float v32) const
+    {
+        const CmPos c = cm_pos(i, j, k, n);
+        r[c.off + c.idx] = v32;
     }
-    __shared__ double smx[BX * BY / 32], sss[BX * BY / 32];
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-        ss += __shfl_down_sync(0xffffffffu, ss, o);
-    }
-    const int t = threadIdx.y * BX + threadIdx.x;
-    if ((t & 31) == 0) { smx[t >> 5] = mx; sss[t >> 5] = ss; }
-    __syncthreads();
-    if (t == 0) {
-        double a = smx[0], b = sss[0];
-        for (int w = 1; w < BX * BY / 32; ++w) { a = fmax(a, smx[w]); b += sss[w]; }
-        const int slot = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        partials[2 * slot] = a;
-        partials[2 * slot + 1] = b;
-    }
-}
+    __device__ __forceinline__ void zero(long long) const {}
+};
 
 }  // namespace
 
@@ -563,8 +536,10 @@ cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r_
 {
     const double h2 = h * h;
     count_launches(1);
-    const dim3 g((n + BX - 1) / BX, (n + BY - 1) / BY, n < 16 ? n : 16);
-    k_residual64_to32<<<g, dim3(BX, BY), 0, s>>>(u, rhs, r_cm, n, 1.0 / (64.0 * h2 * h2 * h2), partials);
+    const int kz = n < 16 ? n : 16;
+    const int kchunk = (n + kz - 1) / kz;
+    resid::k_residual_col<CmF32Out><<<resid::grid_for(n, kz), dim3(resid::RX, resid::RY), 0, s>>>(
+        u, rhs, CmF32Out{r_cm}, n, 1.0 / (64.0 * h2 * h2 * h2), partials, kchunk);
     return cudaGetLastError();
 }
 

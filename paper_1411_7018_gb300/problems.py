@@ -72,6 +72,54 @@ def cosine_modes(seed: int, eps: float | tuple = 0.02, modes: int = 8):
     return k, phi, amp
 
 
+def _cosine_fields(xp, x, y, z, k, phi, amp):
+    """u = |x|^2/2 + sum_m amp_m / (4 pi^2 |k_m|^2) cos(theta_m) and
+    f = det(I - sum_m amp_m cos(theta_m) k^_m k^_m^T), theta_m = 2 pi k_m.x + phi_m,
+    with array module xp (numpy or torch)."""
+    u = (x * x + y * y + z * z) / 2.0
+    hxx = xp.ones_like(u); hyy = xp.ones_like(u); hzz = xp.ones_like(u)
+    hxy = xp.zeros_like(u); hxz = xp.zeros_like(u); hyz = xp.zeros_like(u)
+    for m in range(k.shape[0]):
+        km = [float(v) for v in k[m]]
+        kk = km[0] ** 2 + km[1] ** 2 + km[2] ** 2
+        c = xp.cos(2.0 * np.pi * (km[0] * x + km[1] * y + km[2] * z) + float(phi[m]))
+        u = u + (float(amp[m]) / (4.0 * np.pi ** 2 * kk)) * c
+        w = (float(amp[m]) / kk) * c
+        hxx = hxx - (km[0] * km[0]) * w
+        hyy = hyy - (km[1] * km[1]) * w
+        hzz = hzz - (km[2] * km[2]) * w
+        hxy = hxy - (km[0] * km[1]) * w
+        hxz = hxz - (km[0] * km[2]) * w
+        hyz = hyz - (km[1] * km[2]) * w
+    f = hxx * (hyy * hzz - hyz * hyz) - hxy * (hxy * hzz - hyz * hxz) + hxz * (hxy * hyz - hyy * hxz)
+    return u, f
+
+
+def make_on_device(name: str, n: int, seed: int = 0, eps=0.02, device="cuda"):
+    """(f, g, length) as float64 torch tensors on `device`, g = u on the shell
+    and 0 inside: the same problems as make(), evaluated with torch (values
+    agree with make() to rounding).  For workloads that are only solved, not
+    compared with the CPU oracle."""
+    import torch
+    length = np.pi if name == "sine" else 1.0
+    h = length / (n - 1)
+    t = torch.arange(n, dtype=torch.float64, device=device) * h
+    z, y, x = torch.meshgrid(t, t, t, indexing="ij")
+    if name == "cosine":
+        u, f = _cosine_fields(torch, x, y, z, *cosine_modes(seed, eps))
+    elif name == "exp":
+        s = x * x + y * y + z * z
+        u, f = torch.exp(s / 2.0), (1.0 + s) * torch.exp(1.5 * s)
+    elif name == "quadratic":
+        u = (x * x + y * y + z * z) / 2.0
+        f = torch.ones_like(u)
+    else:
+        raise ValueError(f"unknown problem {name!r}")
+    g = u.clone()
+    g[1:-1, 1:-1, 1:-1] = 0.0
+    return f.contiguous(), g.contiguous(), length
+
+
 def make(name: str, n: int, seed: int = 0, eps=0.02) -> Problem:
     if name == "exp":
         x, y, z = grid_coords(n)
@@ -92,22 +140,6 @@ def make(name: str, n: int, seed: int = 0, eps=0.02) -> Problem:
         return Problem(name, n, length=L, u=u, f=f)
     if name == "cosine":
         x, y, z = grid_coords(n)
-        k, phi, amp = cosine_modes(seed, eps)
-        u = (x * x + y * y + z * z) / 2.0
-        Hm = np.zeros((3, 3) + x.shape)
-        for a in range(3):
-            Hm[a, a] = 1.0
-        for m in range(k.shape[0]):
-            km = k[m].astype(np.float64)
-            kk = float(km @ km)
-            theta = 2.0 * np.pi * (km[0] * x + km[1] * y + km[2] * z) + phi[m]
-            c = np.cos(theta)
-            u = u + amp[m] / (4.0 * np.pi ** 2 * kk) * c
-            for a in range(3):
-                for b in range(3):
-                    Hm[a, b] = Hm[a, b] - amp[m] * c * km[a] * km[b] / kk
-        f = (Hm[0, 0] * (Hm[1, 1] * Hm[2, 2] - Hm[1, 2] * Hm[2, 1])
-             - Hm[0, 1] * (Hm[1, 0] * Hm[2, 2] - Hm[1, 2] * Hm[2, 0])
-             + Hm[0, 2] * (Hm[1, 0] * Hm[2, 1] - Hm[1, 1] * Hm[2, 0]))
+        u, f = _cosine_fields(np, x, y, z, *cosine_modes(seed, eps))
         return Problem(name, n, u=u, f=f)
     raise ValueError(f"unknown problem {name!r}")
