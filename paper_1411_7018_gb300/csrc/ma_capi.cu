@@ -103,9 +103,12 @@ size_t layout(ma_hierarchy* H, const ma_hier_desc* d, char* base)
         lv.w = (double*)take(pts * sizeof(double));
         if (d->precision == MA_MIXED) {
             lv.e = (float*)take(pts * sizeof(float));
+            if (l < L - 1) lv.e2 = (float*)take(pts * sizeof(float));   // second buffer of the plane sweeps
             lv.bstore = (void*)take(ma::base_store_bytes(m));
-            lv.hi = (float*)take(pts * sizeof(float));
-            lv.lo = (float*)take(pts * sizeof(float));
+            if (l > 0) {   // the finest B comes from the FP64 residual
+                lv.hi = (float*)take(pts * sizeof(float));
+                lv.lo = (float*)take(pts * sizeof(float));
+            }
             lv.rhs32 = (float*)take(ma::cm_points(m) * sizeof(float));
             lv.res32 = (float*)take(pts * sizeof(float));
             lv.w32 = (float*)take(pts * sizeof(float));
@@ -177,22 +180,19 @@ cudaError_t fmg(ma_hierarchy* H, bool finest_vcycle = true)
 
 // ---- mixed precision: FP32 FAS cycle on the correction e --------------------
 
-// Base u = hi + lo on the finest level from the FP64 iterate (after u += e
-// when apply), e = 0; coarse bases by injection.
+// u += e on the finest level (apply != 0), e = 0, and the base Hessians B of
+// the coarse correction levels from the FP32 split of the injected iterate.
+// The finest B is written by the FP64 residual (mixed_residual), which
+// always follows.
 cudaError_t refresh_base(ma_hierarchy* H, int apply)
 {
     cudaStream_t s = H->s;
     cudaError_t e;
     ma::Level& F = H->lev[0];
-    if ((e = ma::launch_split_update(F.u, F.e, F.hi, F.lo, F.n, apply, s)) != cudaSuccess) return e;
-    for (int l = 0; l < H->L - 1; ++l) {
+    if ((e = ma::launch_update(F.u, F.e, F.n, apply, s)) != cudaSuccess) return e;
+    for (int l = 1; l < H->L; ++l) {
         ma::Level& A = H->lev[l];
-        ma::Level& C = H->lev[l + 1];
-        if ((e = ma::launch_inject_f32(A.hi, A.n, C.hi, s)) != cudaSuccess) return e;
-        if ((e = ma::launch_inject_f32(A.lo, A.n, C.lo, s)) != cudaSuccess) return e;
-    }
-    for (int l = 0; l < H->L; ++l) {
-        ma::Level& A = H->lev[l];
+        if ((e = ma::launch_split_inject(F.u, F.n, 1 << l, A.hi, A.lo, A.n, s)) != cudaSuccess) return e;
         if ((e = ma::launch_base_colour(A.hi, A.lo, A.bstore, A.n, A.h, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -208,7 +208,7 @@ cudaError_t corr_vcycle(ma_hierarchy* H)
     for (int l = 0; l < H->L - 1; ++l) {
         ma::Level& F = H->lev[l];
         ma::Level& C = H->lev[l + 1];
-        if ((e = ma::launch_smooth_corr(F.e, F.bstore, F.rhs32, F.n, F.h, d.nu1, H->events, s)) != cudaSuccess)
+        if ((e = ma::launch_smooth_corr(F.e, F.e2, F.bstore, F.rhs32, F.n, F.h, d.nu1, H->events, s)) != cudaSuccess)
             return e;
         if ((e = ma::launch_residual_corr(F.e, F.bstore, F.rhs32, F.res32, F.n, F.h, s)) != cudaSuccess) return e;
         if ((e = ma::launch_restrict_level_f32(F.e, F.res32, F.n, C.w32, C.e, C.res32, d.restrict_kind,
@@ -225,18 +225,19 @@ cudaError_t corr_vcycle(ma_hierarchy* H)
         ma::Level& F = H->lev[l];
         ma::Level& C = H->lev[l + 1];
         if ((e = ma::launch_prolong_add_f32(C.e, C.w32, C.n, F.e, s)) != cudaSuccess) return e;
-        if ((e = ma::launch_smooth_corr(F.e, F.bstore, F.rhs32, F.n, F.h, d.nu2, H->events, s)) != cudaSuccess)
+        if ((e = ma::launch_smooth_corr(F.e, F.e2, F.bstore, F.rhs32, F.n, F.h, d.nu2, H->events, s)) != cudaSuccess)
             return e;
     }
     return cudaSuccess;
 }
 
 // FP64 fine residual into rhs32 (the correction problem's right-hand side)
-// with norm partials; the caller reads the norms.
+// and the finest base Hessian B, with norm partials; the caller reads the
+// norms.
 cudaError_t mixed_residual(ma_hierarchy* H)
 {
     ma::Level& F = H->lev[0];
-    cudaError_t e = ma::launch_residual64_to32(F.u, F.rhs, F.rhs32, F.n, F.h, H->partials, H->s);
+    cudaError_t e = ma::launch_residual64_to32(F.u, F.rhs, F.rhs32, F.bstore, F.n, F.h, H->partials, H->s);
     if (e != cudaSuccess) return e;
     return ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s);
 }
@@ -378,14 +379,17 @@ ma_status ma_create_hierarchy(const ma_hier_desc* desc, void* dev_workspace, siz
     H->bytes = need;
     H->s = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&H->device);
-    if (e == cudaSuccess) e = ma::prepare_coarsest_kernels();
+    if (e == cudaSuccess) e = ma::prepare_kernels();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&H->host, 8 * sizeof(double));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H->sv.ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(H->events, 0, sizeof(unsigned long long), H->s);
-    for (int l = 0; l < H->L && e == cudaSuccess; ++l) {   // corrections start at zero (shell stays zero)
+    for (int l = 0; l < H->L && e == cudaSuccess; ++l) {
+        // corrections start at zero; the shells of e, e2 and res32 stay zero
         const size_t pts = (size_t)H->lev[l].n * H->lev[l].n * H->lev[l].n;
         if (H->lev[l].e) e = cudaMemsetAsync(H->lev[l].e, 0, pts * sizeof(float), H->s);
+        if (e == cudaSuccess && H->lev[l].e2) e = cudaMemsetAsync(H->lev[l].e2, 0, pts * sizeof(float), H->s);
+        if (e == cudaSuccess && H->lev[l].res32) e = cudaMemsetAsync(H->lev[l].res32, 0, pts * sizeof(float), H->s);
     }
     if (e != cudaSuccess) {
         if (H->host) cudaFreeHost(H->host);
@@ -740,19 +744,21 @@ ma_status ma_coarsest_solve(double* u, const double* rhs, int n, double h, int s
 {
     if (!u || !rhs || !valid_step_grid(n) || n > 17 || !(h > 0.0) || sweeps < 0 || sweeps > 1000)
         return fail(MA_ERR_INVALID_ARG, "ma_coarsest_solve: bad arguments (n <= 17)");
-    MA_CK(ma::prepare_coarsest_kernels());
+    MA_CK(ma::prepare_kernels());
     MA_CK(ma::launch_coarsest(u, rhs, n, h, sweeps, events, (cudaStream_t)stream));
     return MA_OK;
 }
 
-// Scratch of the correction step calls: the BF16 base-Hessian store, then the
-// colour-major right-hand side (256-byte aligned).
-static size_t corr_scratch_split(int n) { return align_up(ma::base_store_bytes(n)); }
+// Scratch of the correction step calls: the FP32 base-Hessian store, the
+// colour-major right-hand side, and the second e buffer of the plane sweeps
+// (each 256-byte aligned).
+static size_t corr_scratch_rhs(int n) { return align_up(ma::base_store_bytes(n)); }
+static size_t corr_scratch_e2(int n) { return corr_scratch_rhs(n) + align_up(ma::cm_points(n) * sizeof(float)); }
 
 ma_status ma_correction_scratch_bytes(int n, size_t* bytes)
 {
     if (!valid_step_grid(n) || !bytes) return fail(MA_ERR_INVALID_ARG, "ma_correction_scratch_bytes: bad arguments");
-    *bytes = corr_scratch_split(n) + ma::cm_points(n) * sizeof(float);
+    *bytes = corr_scratch_e2(n) + (size_t)n * n * n * sizeof(float);
     return MA_OK;
 }
 
@@ -764,7 +770,8 @@ static ma_status corr_setup(const float* hi, const float* lo, const float* rhs, 
     if (st != MA_OK) return st;
     if (scratch_bytes < need) return fail(MA_ERR_INVALID_ARG, "correction scratch %zu < %zu bytes", scratch_bytes, need);
     if (((uintptr_t)scratch) % kAlign != 0) return fail(MA_ERR_INVALID_ARG, "scratch not 256-byte aligned");
-    *rhs_cm = (float*)((char*)scratch + corr_scratch_split(n));
+    MA_CK(ma::prepare_kernels());
+    *rhs_cm = (float*)((char*)scratch + corr_scratch_rhs(n));
     MA_CK(ma::launch_base_colour(hi, lo, scratch, n, h, s));
     MA_CK(ma::launch_to_cm(rhs, *rhs_cm, n, s));
     return MA_OK;
@@ -780,7 +787,9 @@ ma_status ma_smooth_correction(float* e, const float* hi, const float* lo, const
     float* rhs_cm = nullptr;
     ma_status st = corr_setup(hi, lo, rhs, n, h, scratch, scratch_bytes, s, &rhs_cm);
     if (st != MA_OK) return st;
-    MA_CK(ma::launch_smooth_corr(e, scratch, rhs_cm, n, h, nsweeps, events, s));
+    float* e2 = (float*)((char*)scratch + corr_scratch_e2(n));
+    MA_CK(cudaMemsetAsync(e2, 0, (size_t)n * n * n * sizeof(float), s));
+    MA_CK(ma::launch_smooth_corr(e, e2, scratch, rhs_cm, n, h, nsweeps, events, s));
     return MA_OK;
 }
 
@@ -793,7 +802,84 @@ ma_status ma_residual_correction(const float* e, const float* hi, const float* l
     float* rhs_cm = nullptr;
     ma_status st = corr_setup(hi, lo, rhs, n, h, scratch, scratch_bytes, s, &rhs_cm);
     if (st != MA_OK) return st;
+    MA_CK(ma::launch_zero_shell_f32(res, n, s));
     MA_CK(ma::launch_residual_corr(e, scratch, rhs_cm, res, n, h, s));
+    return MA_OK;
+}
+
+ma_status ma_set_corr_tuning(int n, int smooth_choice, int residual_choice)
+{
+    if (smooth_choice < -1 || smooth_choice > MA_CORR_PLANE64 || residual_choice < -1 ||
+        residual_choice == MA_CORR_BY_COLOUR || residual_choice > MA_CORR_PLANE64)
+        return fail(MA_ERR_INVALID_ARG, "ma_set_corr_tuning: bad choice (%d, %d)", smooth_choice, residual_choice);
+    if (!ma::set_corr_tuning(n, smooth_choice, residual_choice))
+        return fail(MA_ERR_INVALID_ARG, "ma_set_corr_tuning: n - 1 = %d is not a power of two", n - 1);
+    return MA_OK;
+}
+
+ma_status ma_get_corr_tuning(int n, int* smooth_choice, int* residual_choice)
+{
+    if (!valid_step_grid(n)) return fail(MA_ERR_INVALID_ARG, "ma_get_corr_tuning: bad n %d", n);
+    if (smooth_choice) *smooth_choice = ma::corr_smooth_choice(n);
+    if (residual_choice) *residual_choice = ma::corr_resid_choice(n);
+    return MA_OK;
+}
+
+ma_status ma_tune_corr(float* e, const float* hi, const float* lo, const float* rhs, int n, double h, int reps,
+                       void* scratch, size_t scratch_bytes, double* us_smooth, double* us_residual,
+                       ma_stream_t stream)
+{
+    if (!e || !scratch || !hi || !lo || !rhs || !valid_step_grid(n) || n < 5 || !(h > 0.0) || reps < 1 ||
+        reps > 1000)
+        return fail(MA_ERR_INVALID_ARG, "ma_tune_corr: bad arguments");
+    const unsigned m = (unsigned)(n - 1);
+    if (m & (m - 1)) return fail(MA_ERR_INVALID_ARG, "ma_tune_corr: n - 1 = %d is not a power of two", n - 1);
+    cudaStream_t s = (cudaStream_t)stream;
+    float* rhs_cm = nullptr;
+    ma_status st = corr_setup(hi, lo, rhs, n, h, scratch, scratch_bytes, s, &rhs_cm);
+    if (st != MA_OK) return st;
+    float* e2 = (float*)((char*)scratch + corr_scratch_e2(n));
+    MA_CK(cudaMemsetAsync(e2, 0, (size_t)n * n * n * sizeof(float), s));
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    MA_CK(cudaEventCreate(&t0));
+    cudaError_t ce = cudaEventCreate(&t1);
+    double ts[4] = {0, 0, 0, 0}, tr[4] = {0, 0, 0, 0};
+    for (int c = MA_CORR_BY_COLOUR; c <= MA_CORR_PLANE64 && ce == cudaSuccess; ++c) {
+        ce = ma::launch_smooth_corr_choice(c, e, e2, scratch, rhs_cm, n, h, 2, nullptr, s);   // warm-up
+        if (ce == cudaSuccess) ce = cudaEventRecord(t0, s);
+        for (int r = 0; r < reps && ce == cudaSuccess; ++r)
+            ce = ma::launch_smooth_corr_choice(c, e, e2, scratch, rhs_cm, n, h, 2, nullptr, s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(t1, s);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(t1);
+        float ms = 0.0f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, t0, t1);
+        ts[c] = 1e3 * ms / (2.0 * reps);
+    }
+    // the residual writes into the second buffer's interior (its shell stays 0)
+    for (int c = MA_CORR_PLANE16; c <= MA_CORR_PLANE64 && ce == cudaSuccess; ++c) {
+        ce = ma::launch_residual_corr_choice(c, e, scratch, rhs_cm, e2, n, h, s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(t0, s);
+        for (int r = 0; r < reps && ce == cudaSuccess; ++r)
+            ce = ma::launch_residual_corr_choice(c, e, scratch, rhs_cm, e2, n, h, s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(t1, s);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(t1);
+        float ms = 0.0f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, t0, t1);
+        tr[c] = 1e3 * ms / reps;
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (ce != cudaSuccess) return fail(MA_ERR_CUDA, "ma_tune_corr: %s", cudaGetErrorString(ce));
+    int bs = MA_CORR_BY_COLOUR, br = MA_CORR_PLANE16;
+    for (int c = 1; c <= MA_CORR_PLANE64; ++c) {
+        if (ts[c] < ts[bs]) bs = c;
+        if (tr[c] < tr[br]) br = c;
+    }
+    ma::set_corr_tuning(n, bs, br);
+    for (int c = 0; c < 4; ++c) {
+        if (us_smooth) us_smooth[c] = ts[c];
+        if (us_residual) us_residual[c] = tr[c];
+    }
     return MA_OK;
 }
 

@@ -21,8 +21,9 @@ struct Level {
     double* w = nullptr;     // coarse levels: the restricted approximation w_H
     // mixed precision (FP32 correction cycle); null in FP64 mode
     float* e = nullptr;      // correction
-    void* bstore = nullptr;  // B = D^2_h u, colour-major BF16 (6 per interior point), refreshed per outer iteration
-    float* hi = nullptr;     // base u = hi + lo (FP32 split)
+    float* e2 = nullptr;     // second correction buffer of the plane sweeps (not on the coarsest level)
+    void* bstore = nullptr;  // B = D^2_h u, colour-major FP32 (6 per interior point), refreshed per outer iteration
+    float* hi = nullptr;     // coarse levels: base u = hi + lo (FP32 split of the injected iterate)
     float* lo = nullptr;
     float* rhs32 = nullptr;  // correction-problem right-hand side, colour-major (fine: the FP64 residual)
     float* res32 = nullptr;  // correction residual; on coarse levels the restricted one

@@ -9,9 +9,10 @@ namespace ma {
 // Kernel launches issued by this library in this process (all devices).
 void count_launches(unsigned long long k);
 void uncount_launches(unsigned long long k);
-// Sets the coarsest-grid kernels' shared-memory limits for grids up to n = 17
-// (call outside stream capture).
-cudaError_t prepare_coarsest_kernels();
+// Sets the shared-memory limits of the kernels that need more than 48 KB
+// (coarsest-grid solves up to n = 17, the 64-point plane tiles); call
+// outside stream capture, once per device.
+cudaError_t prepare_kernels();
 unsigned long long launch_count();
 
 // Sets the thread-local text ma_last_error_string() returns.
@@ -50,8 +51,21 @@ size_t base_store_bytes(int n);
 size_t cm_points(int n);
 cudaError_t launch_base_colour(const float* hi, const float* lo, void* bstore, int n, double h, cudaStream_t s);
 cudaError_t launch_to_cm(const float* nat, float* cm, int n, cudaStream_t s);
-cudaError_t launch_smooth_corr(float* e, const void* bstore, const float* rhs_cm, int n, double h, int nsweeps,
-                               unsigned long long* events, cudaStream_t s);
+// nsweeps 8-colour sweeps; pairs of sweeps run by k parity through the second
+// buffer e2 (n^3 floats, zero shell; null: every sweep by colour in place).
+cudaError_t launch_smooth_corr(float* e, float* e2, const void* bstore, const float* rhs_cm, int n, double h,
+                               int nsweeps, unsigned long long* events, cudaStream_t s);
+cudaError_t launch_zero_shell_f32(float* v, int n, cudaStream_t s);
+// Correction-smoother and residual variants (values of MA_CORR_* in ma.h) and
+// the per-size choice table the launchers above consult.
+constexpr int CORR_BY_COLOUR = 0, CORR_PLANE16 = 1, CORR_PLANE32 = 2, CORR_PLANE64 = 3;
+int corr_smooth_choice(int n);
+int corr_resid_choice(int n);
+bool set_corr_tuning(int n, int smooth, int resid);   // -1: built-in default; false if n - 1 is not 2^k
+cudaError_t launch_smooth_corr_choice(int choice, float* e, float* e2, const void* bstore, const float* rhs_cm, int n,
+                                      double h, int nsweeps, unsigned long long* events, cudaStream_t s);
+cudaError_t launch_residual_corr_choice(int choice, const float* e, const void* bstore, const float* rhs_cm,
+                                        float* res, int n, double h, cudaStream_t s);
 cudaError_t launch_residual_corr(const float* e, const void* bstore, const float* rhs_cm, float* res, int n,
                                  double h, cudaStream_t s);
 cudaError_t launch_coarse_rhs_corr(const float* w, const void* bstore, const float* resc, float* rhs_cm, int nc,
@@ -62,8 +76,9 @@ cudaError_t launch_prolong_add_f32(const float* ec, const float* wc, int nc, flo
 cudaError_t launch_inject_f32(const float* vf, int nf, float* vc, cudaStream_t s);
 cudaError_t launch_coarsest_corr(float* e, const void* bstore, const float* rhs_cm, int n, double h, int sweeps,
                                  unsigned long long* events, cudaStream_t s);
-cudaError_t launch_split_update(double* u, float* e, float* hi, float* lo, int n, int apply, cudaStream_t s);
-cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r_cm, int n, double h,
+cudaError_t launch_update(double* u, float* e, int n, int apply, cudaStream_t s);
+cudaError_t launch_split_inject(const double* u0, int n0, int stride, float* hi, float* lo, int nc, cudaStream_t s);
+cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r_cm, void* bstore, int n, double h,
                                    double* partials, cudaStream_t s);
 
 }  // namespace ma

@@ -354,7 +354,7 @@ cudaError_t launch_prolong_add(const double* uc, const double* wc, int nc, doubl
 {
     const int nf = 2 * nc - 1;
     count_launches(1);
-    xfer::k_prolong<double><<<grid_of(nf), dim3(BX, BY), 0, s>>>(uc, wc, nc, uf, nf, 1);
+    xfer::k_prolong<double><<<xfer::prolong_grid(nf), dim3(BX, BY), 0, s>>>(uc, wc, nc, uf, nf, 1);
     return cudaGetLastError();
 }
 
@@ -362,7 +362,7 @@ cudaError_t launch_interpolate(const double* uc, int nc, double* uf, cudaStream_
 {
     const int nf = 2 * nc - 1;
     count_launches(1);
-    xfer::k_prolong<double><<<grid_of(nf), dim3(BX, BY), 0, s>>>(uc, nullptr, nc, uf, nf, 0);
+    xfer::k_prolong<double><<<xfer::prolong_grid(nf), dim3(BX, BY), 0, s>>>(uc, nullptr, nc, uf, nf, 0);
     return cudaGetLastError();
 }
 

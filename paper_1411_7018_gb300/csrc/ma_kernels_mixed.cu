@@ -101,38 +101,60 @@ __device__ __forceinline__ float delta_det(const S3f& B, const S3f& K)
     return cof_dot(B, K) + cof_dot(K, B) + det3(K);
 }
 
-// Smallest-root update of the correction problem at one point; returns z with
-// e_new = e0 + h^2 z / 2.
-__device__ __forceinline__ float corr_root(const S3f& B, const S3f& K, float r, bool* nonconvex)
+// Smallest-root update of the correction problem at one point, z with
+// e_new = e0 + h^2 z / 2.  Fast path: FP32 Newton on
+// F(z) = det(G - zI) - det(B) - r from z = 0 (its first step is z = F(0) / M)
+// when G = B + K is positive definite and not near-degenerate; it stops once
+// a step is at most 1e-4 |z|: Newton converges quadratically there, so the
+// step just taken leaves an error of order (1e-4)^2 |z|, below FP32
+// resolution.  Returns false (z unset) when the point needs the FP64 path.
+__device__ __forceinline__ bool corr_root_fast(const S3f& B, const S3f& K, float r, float* zout)
 {
     S3f G;
     G.xx = B.xx + K.xx; G.yy = B.yy + K.yy; G.zz = B.zz + K.zz;
     G.xy = B.xy + K.xy; G.xz = B.xz + K.xz; G.yz = B.yz + K.yz;
     const float c = delta_det(B, K) - r;   // F(0)
     const float T = G.xx + G.yy + G.zz;
-    const float M = (G.xx * G.yy - G.xy * G.xy) + (G.xx * G.zz - G.xz * G.xz) + (G.yy * G.zz - G.yz * G.yz);
-    const float dG = det3(G);
-    const bool pd = G.xx > 0.0f && G.xx * G.yy - G.xy * G.xy > 0.0f && dG > 0.0f;
-    const float scale = fabsf(G.xx) + fabsf(G.yy) + fabsf(G.zz) + fabsf(G.xy) + fabsf(G.xz) + fabsf(G.yz);
-    if (pd && M > 0.05f * scale * scale) {
-        // F(z) = c - z M + z^2 T - z^3 = det(G - zI) - det(B) - r
-        float z = 0.0f;
-        for (int it = 0; it < 30; ++it) {
-            const float F = c - z * (M - z * (T - z));
-            const float Mz = M - z * (2.0f * T - 3.0f * z);
-            const float dz = __fdividef(F, Mz);
-            z += dz;
-            if (!isfinite(z)) break;
-            if (fabsf(dz) <= 1e-6f * fabsf(z) + 1e-12f * scale) return z;
+    const float m2 = G.xx * G.yy - G.xy * G.xy;
+    const float M = m2 + (G.xx * G.zz - G.xz * G.xz) + (G.yy * G.zz - G.yz * G.yz);
+    const bool pd = G.xx > 0.0f && m2 > 0.0f && det3(G) > 0.0f;
+    // with a positive diagonal, |G| summed entrywise is T + |off-diagonals|
+    const float scale = T + fabsf(G.xy) + fabsf(G.xz) + fabsf(G.yz);
+    if (!(pd && M > 0.05f * scale * scale)) return false;
+    // F(z) = c - z M + z^2 T - z^3
+    float z = __fdividef(c, M);
+    for (int it = 0; it < 30; ++it) {
+        const float F = c - z * (M - z * (T - z));
+        const float Mz = M - z * (2.0f * T - 3.0f * z);
+        const float dz = __fdividef(F, Mz);
+        z += dz;
+        if (fabsf(dz) <= 1e-4f * fabsf(z) + 1e-12f * scale) {
+            *zout = z;
+            return isfinite(z);
         }
     }
-    // FP64 on the same data: the target is det(G - zI) = det(B) + r.
+    return false;
+}
+
+// FP64 path on the same data (near-degenerate or indefinite G, or no FP32
+// convergence): the target is det(G - zI) = det(B) + r; rhs <= 0 takes the
+// smallest real root of the cubic and sets *nonconvex.
+__device__ __noinline__ float corr_root_slow(S3f B, S3f K, float r, bool* nonconvex)
+{
     HessS H;
-    H.A = G.xx; H.B = G.yy; H.C = G.zz; H.R = G.xy; H.S = G.xz; H.T = G.yz;
+    H.A = B.xx + K.xx; H.B = B.yy + K.yy; H.C = B.zz + K.zz;
+    H.R = B.xy + K.xy; H.S = B.xz + K.xz; H.T = B.yz + K.yz;
     const double tot = (double)det3(B) + (double)r;
     if (tot > 0.0) return (float)root_f64_monotone(H, tot);
     *nonconvex = true;
     return (float)root_f64_all_real_min(H, tot);
+}
+
+__device__ __forceinline__ float corr_root(const S3f& B, const S3f& K, float r, bool* nonconvex)
+{
+    float z;
+    if (corr_root_fast(B, K, r, &z)) return z;
+    return corr_root_slow(B, K, r, nonconvex);
 }
 
 __host__ __device__ __forceinline__ int colour_count(int n, int parity) { return parity ? (n - 1) / 2 : (n - 3) / 2; }
@@ -263,26 +285,264 @@ cudaError_t launch_colour_corr(float* e, const float* bstore, const float* rhs_c
     return cudaGetLastError();
 }
 
-// res = rhs - N(e) on the interior (natural layout), 0 on the shell.
-__global__ void __launch_bounds__(BX * BY) k_residual_corr(const float* __restrict__ e,
-                                                           const float* __restrict__ bstore,
-                                                           const float* __restrict__ rhs_cm,
-                                                           float* __restrict__ res, int n, float inv_h2)
+// ---------------------------------------------------------------------------
+// Plane-phase correction sweep.  Colours 0-3 lie on even planes k and colours
+// 4-7 on odd planes, and every neighbour of a point in planes k +- 1 has the
+// other k parity.  So during colours 0-3 of a sweep the even planes see only
+// old values of the odd planes and do not interact with each other; during
+// colours 4-7 the odd planes see only the (now final) even planes.  One sweep
+// is therefore two launches, one per k parity, each running the four in-plane
+// colour phases (i, j parities (0,0), (1,0), (0,1), (1,1)) of one PT x PT tile
+// of one plane per block, with __syncthreads between the phases.  In-plane
+// colour q needs the new values of colours < q at in-plane distance 1, so a
+// block also updates colour q on a halo of 3 - q points around its tile; it
+// does so from the same inputs and with the same arithmetic as the block that
+// owns those points, so the values agree bit for bit and the result is the
+// sequential 8-colour sweep.  Blocks read the old plane from `own` and write
+// their tile to `dst`, a second buffer, so that no block reads a neighbour's
+// new values in place of the old ones.  Phase k-even: own = nbr = src;
+// phase k-odd: own = src, nbr = dst (the new even planes).
+// ---------------------------------------------------------------------------
+// Tiles: PT x PT points (PT even), an e halo of PH = 4 in shared memory.  A
+// shared-memory row of PW = PT + 8 values keeps the even and the odd x = i - x0
+// in two halves, so the 32 lanes of a warp, which update points two apart in
+// i, read 32 consecutive words (no bank conflicts).
+constexpr int PH = 4;
+
+template <int PT>
+struct Tile {
+    static constexpr int PW = PT + 2 * PH;
+    static constexpr int PWH = PW / 2;
+    static constexpr int SMEM = 3 * PW * PW * (int)sizeof(float);
+};
+
+// Blocks per SM the launch bounds ask for: shared memory limits the 64-point
+// tile to 3; the smaller tiles allow 80 registers per thread.
+__host__ __device__ constexpr int plane_min_blocks(int pt, int nt) { return pt >= 64 ? 3 : 65536 / (80 * nt); }
+
+// 4-byte asynchronous global -> shared copy (cp.async); src_bytes 0 writes a
+// zero and reads nothing.
+__device__ __forceinline__ void cp_async_f32(float* dst_smem, const float* src, int src_bytes)
 {
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= n || j >= n) return;
-    const long long p = lin(i, j, k, n);
-    float v = 0.0f;
-    if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
-        const long long sy = n, sz = (long long)n * n;
-        const CmPos c = cm_pos(i, j, k, n);
-        const S3f B = load_b(bstore + 6 * c.off + c.idx, c.cnt);
-        const S3f K = corr_hess(e, p, sy, sz, e[p], inv_h2);
-        v = rhs_cm[c.off + c.idx] - delta_det(B, K);
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Loads planes k-1, k, k+1 of e over the tile and its halo into sp
+// ([3][PW][PW], parity-split rows) with asynchronous copies, one warp per
+// row.  Points outside the grid read as 0 and are never used.  Ends with the
+// copies complete and visible to the block.
+template <int PT, int NT>
+__device__ __forceinline__ void load_plane_tile(float* sp, const float* own, const float* nbr, int n, int k, int x0,
+                                                int y0)
+{
+    constexpr int PW = Tile<PT>::PW, PWH = Tile<PT>::PWH, NCH = (PW + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    bool xok[NCH];
+    int xs[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        const int x = lane + 32 * c;
+        xok[c] = x < PW && x0 + x >= 0 && x0 + x < n;
+        xs[c] = (x & 1) * PWH + (x >> 1);
     }
-    res[p] = v;
+    for (int r = threadIdx.x >> 5; r < 3 * PW; r += NT / 32) {
+        const int pl = r / PW, y = r - pl * PW;
+        const int gj = y0 + y;
+        const bool row_ok = gj >= 0 && gj < n;
+        const float* base = pl == 1 ? own : nbr;
+        const long long row = ((long long)(k - 1 + pl) * n + (row_ok ? gj : 0)) * n;
+        float* drow = sp + r * PW;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const int x = lane + 32 * c;
+            if (x < PW) {
+                const bool ok = row_ok && xok[c];
+                cp_async_f32(drow + xs[c], ok ? base + row + (x0 + x) : base, ok ? 4 : 0);
+            }
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+}
+
+// Points of in-plane colour Q (i parity Q & 1, j parity Q >> 1) of plane k
+// with i in [ia - hq, ia + PT - 1 + hq] and j likewise, inside the interior:
+// (a, b) -> i = ilo + 2a, j = jlo + 2b.
+struct ColourRegion {
+    int ilo, jlo, ci, cj;
+};
+
+__device__ __forceinline__ ColourRegion colour_region(int n, int ia, int ja, int pt, int hq, int pi, int pj)
+{
+    ColourRegion R;
+    R.ilo = max(1, ia - hq);
+    R.jlo = max(1, ja - hq);
+    const int ihi = min(n - 2, ia + pt - 1 + hq), jhi = min(n - 2, ja + pt - 1 + hq);
+    R.ilo += (R.ilo & 1) != pi;
+    R.jlo += (R.jlo & 1) != pj;
+    R.ci = ihi >= R.ilo ? (ihi - R.ilo) / 2 + 1 : 0;
+    R.cj = jhi >= R.jlo ? (jhi - R.jlo) / 2 + 1 : 0;
+    return R;
+}
+
+// One in-plane colour phase over a region of plane k (in shared memory), the
+// points spread over the block's NT threads.  SMOOTH: update each point by
+// the smallest-root rule; else write res = rhs - N(e) to global memory.
+// Returns the rhs <= 0 root events of this thread.
+template <int Q, int PT, int NT, bool SMOOTH>
+__device__ __forceinline__ unsigned colour_phase(float* sp, const float* __restrict__ bstore,
+                                                 const float* __restrict__ rhs_cm, float* __restrict__ res, int n,
+                                                 int pk, int kk, int k, int ia, int ja, int x0, int y0, int hq,
+                                                 float inv_h2, float h2half)
+{
+    constexpr int PW = Tile<PT>::PW, PWH = Tile<PT>::PWH;
+    constexpr int pi = Q & 1, pj = Q >> 1;
+    constexpr int XP = pi ^ 1;                       // parity of x = i - x0 (x0 = ia - 4 is odd)
+    static_assert(((PT + 6) / 2 + 1) * ((PT + 6) / 2 + 1) <= 32 * NT, "a thread's points of a colour must fit 32 bits");
+    constexpr int DXP = XP ? 1 - PWH : PWH;          // shared-memory offset of i + 1
+    constexpr int DXM = XP ? -PWH : PWH - 1;         // of i - 1
+    const ColourRegion R = colour_region(n, ia, ja, PT, hq, pi, pj);
+    const int total = R.ci * R.cj;
+    if (total == 0) return 0;
+    const int ni = colour_count(n, pi), nj = colour_count(n, pj);
+    const long long cnt = (long long)ni * nj * colour_count(n, pk);
+    const long long off = cm_offset(n, Q | (pk << 2));
+    const long long base = ((long long)kk * nj + ((R.jlo - (pj ? 1 : 2)) >> 1)) * ni + ((R.ilo - (pi ? 1 : 2)) >> 1);
+    const float* bq = bstore + 6 * off + base;
+    const float* rq = rhs_cm + off + base;
+    const int s0 = (PW + (R.jlo - y0)) * PW + XP * PWH + ((R.ilo - x0) >> 1);
+    int a = threadIdx.x % R.ci, b = threadIdx.x / R.ci;
+    const int da = NT % R.ci, db = NT / R.ci;
+    unsigned slow = 0;   // SMOOTH: iterations whose point needs the FP64 root (at most 32 per thread)
+    int it = 0;
+    for (int t = threadIdx.x; t < total; t += NT, ++it) {
+        const int rel = b * ni + a;
+        const S3f B = load_b(bq + rel, cnt);
+        const float rr = __ldcs(rq + rel);
+        const int sc = s0 + 2 * b * PW + a;
+        const float e0 = sp[sc];
+        const S3f K = hess_from_diff(
+            [&](int di, int dj, int dk) -> float {
+                return sp[sc + dk * PW * PW + dj * PW + (di > 0 ? DXP : (di < 0 ? DXM : 0))] - e0;
+            },
+            inv_h2);
+        if (SMOOTH) {
+            float z;
+            if (corr_root_fast(B, K, rr, &z)) sp[sc] = fmaf(h2half, z, e0);
+            else slow |= 1u << it;
+        } else {
+            res[((long long)k * n + (R.jlo + 2 * b)) * n + (R.ilo + 2 * a)] = rr - delta_det(B, K);
+        }
+        a += da;
+        b += db;
+        if (a >= R.ci) {
+            a -= R.ci;
+            ++b;
+        }
+    }
+    // points of this colour are independent, so the rare FP64 roots can
+    // follow the others (their neighbours have other colours)
+    unsigned ev = 0;
+    while (SMOOTH && slow) {
+        const int q = __ffs(slow) - 1;
+        slow &= slow - 1;
+        const int t = threadIdx.x + q * NT;
+        const int a2 = t % R.ci, b2 = t / R.ci;
+        const int rel = b2 * ni + a2;
+        const S3f B = load_b(bq + rel, cnt);
+        const int sc = s0 + 2 * b2 * PW + a2;
+        const float e0 = sp[sc];
+        const S3f K = hess_from_diff(
+            [&](int di, int dj, int dk) -> float {
+                return sp[sc + dk * PW * PW + dj * PW + (di > 0 ? DXP : (di < 0 ? DXM : 0))] - e0;
+            },
+            inv_h2);
+        bool nonconvex = false;
+        const float z = corr_root_slow(B, K, __ldcs(rq + rel), &nonconvex);
+        sp[sc] = fmaf(h2half, z, e0);
+        ev += nonconvex ? 1u : 0u;
+    }
+    return ev;
+}
+
+template <int PK, int PT, int NT>
+__global__ void __launch_bounds__(NT, plane_min_blocks(PT, NT))
+    k_smooth_corr_plane(const float* __restrict__ own, const float* __restrict__ nbr, float* __restrict__ dst,
+                        const float* __restrict__ bstore, const float* __restrict__ rhs_cm, int n, float inv_h2,
+                        float h2half, unsigned long long* events)
+{
+    extern __shared__ float sp[];
+    constexpr int PW = Tile<PT>::PW, PWH = Tile<PT>::PWH;
+    const int ia = 1 + PT * (int)blockIdx.x, ja = 1 + PT * (int)blockIdx.y;
+    const int kk = blockIdx.z;
+    const int k = (PK ? 1 : 2) + 2 * kk;
+    const int x0 = ia - PH, y0 = ja - PH;
+    load_plane_tile<PT, NT>(sp, own, nbr, n, k, x0, y0);
+    unsigned ev = colour_phase<0, PT, NT, true>(sp, bstore, rhs_cm, nullptr, n, PK, kk, k, ia, ja, x0, y0, 3, inv_h2,
+                                                h2half);
+    __syncthreads();
+    ev += colour_phase<1, PT, NT, true>(sp, bstore, rhs_cm, nullptr, n, PK, kk, k, ia, ja, x0, y0, 2, inv_h2,
+                                        h2half);
+    __syncthreads();
+    ev += colour_phase<2, PT, NT, true>(sp, bstore, rhs_cm, nullptr, n, PK, kk, k, ia, ja, x0, y0, 1, inv_h2,
+                                        h2half);
+    __syncthreads();
+    ev += colour_phase<3, PT, NT, true>(sp, bstore, rhs_cm, nullptr, n, PK, kk, k, ia, ja, x0, y0, 0, inv_h2,
+                                        h2half);
+    __syncthreads();
+    const int ihi = min(n - 2, ia + PT - 1), jhi = min(n - 2, ja + PT - 1);
+    for (int r = threadIdx.x >> 5; r <= jhi - ja; r += NT / 32) {
+        const int j = ja + r;
+        float* d = dst + ((long long)k * n + j) * n;
+        const float* srow = sp + (PW + (j - y0)) * PW;
+        for (int i = ia + (threadIdx.x & 31); i <= ihi; i += 32) {
+            const int x = i - x0;
+            d[i] = srow[(x & 1) * PWH + (x >> 1)];
+        }
+    }
+    if (events && ev) atomicAdd(events, (unsigned long long)ev);
+}
+
+// res = rhs - N(e) over one PT x PT tile of one interior plane: e staged in
+// shared memory, B and rhs read per in-plane colour (contiguous in the
+// colour-major store).
+template <int PT, int NT>
+__global__ void __launch_bounds__(NT, plane_min_blocks(PT, NT))
+    k_residual_corr_plane(const float* __restrict__ e, const float* __restrict__ bstore,
+                          const float* __restrict__ rhs_cm, float* __restrict__ res, int n, float inv_h2)
+{
+    extern __shared__ float sp[];
+    const int ia = 1 + PT * (int)blockIdx.x, ja = 1 + PT * (int)blockIdx.y;
+    const int k = 1 + (int)blockIdx.z;
+    const int pk = k & 1;
+    const int kk = (k - (pk ? 1 : 2)) >> 1;
+    const int x0 = ia - PH, y0 = ja - PH;
+    load_plane_tile<PT, NT>(sp, e, e, n, k, x0, y0);
+    colour_phase<0, PT, NT, false>(sp, bstore, rhs_cm, res, n, pk, kk, k, ia, ja, x0, y0, 0, inv_h2, 0.0f);
+    colour_phase<1, PT, NT, false>(sp, bstore, rhs_cm, res, n, pk, kk, k, ia, ja, x0, y0, 0, inv_h2, 0.0f);
+    colour_phase<2, PT, NT, false>(sp, bstore, rhs_cm, res, n, pk, kk, k, ia, ja, x0, y0, 0, inv_h2, 0.0f);
+    colour_phase<3, PT, NT, false>(sp, bstore, rhs_cm, res, n, pk, kk, k, ia, ja, x0, y0, 0, inv_h2, 0.0f);
+}
+
+// The shell of res (faces of the cube) is 0.
+__global__ void k_zero_shell(float* v, int n)
+{
+    const int a = blockIdx.x * BX + threadIdx.x, b = blockIdx.y * BY + threadIdx.y;
+    if (a >= n || b >= n) return;
+    const long long sz = (long long)n * n;
+    const int face = blockIdx.z;   // 0,1: k = 0, n-1; 2,3: j = 0, n-1; 4,5: i = 0, n-1
+    const int m = (face & 1) ? n - 1 : 0;
+    long long p;
+    if (face < 2) p = (long long)m * sz + (long long)b * n + a;
+    else if (face < 4) p = (long long)b * sz + (long long)m * n + a;
+    else p = (long long)b * sz + (long long)a * n + m;
+    v[p] = 0.0f;
 }
 
 // rhs_H = N_H(w_H) + res_H on the coarse interior, written colour-major.
@@ -381,36 +641,54 @@ __global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __r
     if (events && ev) atomicAdd(events, ev);
 }
 
-// u += e (optional), then u = hi + lo (FP32 split) and e = 0, over the whole grid.
-__global__ void k_split_update(double* __restrict__ u, float* __restrict__ e, float* __restrict__ hi,
-                               float* __restrict__ lo, long long m, int apply)
-{
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= m) return;
-    double v = u[p];
-    if (apply) {
-        v += f2d(e[p]);
-        u[p] = v;
-    }
-    // hi = v truncated to FP32; v - hi is exact in FP64 and below one FP32
-    // ulp of hi, so lo = its FP32 truncation keeps v = hi + lo to ~2^-47.
-    const float h = d2f_trunc(v);
-    hi[p] = h;
-    lo[p] = d2f_trunc(v - f2d(h));
-    e[p] = 0.0f;
-}
-
 // FP64 fine residual, written as FP32 in colour-major order (the correction
-// problem's right-hand side); the shell is not stored.
+// problem's right-hand side), and with it the fine base Hessian B = D^2_h u
+// of the correction operator, rounded to FP32 from the FP64 Hessian the
+// residual already formed; the shell is not stored.
 struct CmF32Out {
     float* r;
-    __device__ __forceinline__ void put(long long, int i, int j, int k, int n, double, float v32) const
+    float* b;        // colour-major B store of the level
+    float inv_4h2;   // 1 / (4 h^2)
+    __device__ __forceinline__ void put(long long, int i, int j, int k, int n, double, float v32,
+                                        const HessS& H4) const
     {
         const CmPos c = cm_pos(i, j, k, n);
         r[c.off + c.idx] = v32;
+        float* q = b + 6 * c.off + c.idx;
+        q[0] = d2f_trunc(H4.A) * inv_4h2;
+        q[c.cnt] = d2f_trunc(H4.B) * inv_4h2;
+        q[2 * c.cnt] = d2f_trunc(H4.C) * inv_4h2;
+        q[3 * c.cnt] = d2f_trunc(H4.R) * inv_4h2;
+        q[4 * c.cnt] = d2f_trunc(H4.S) * inv_4h2;
+        q[5 * c.cnt] = d2f_trunc(H4.T) * inv_4h2;
     }
     __device__ __forceinline__ void zero(long long) const {}
 };
+
+// u += e (optional) and e = 0 over the whole grid.
+__global__ void k_update(double* __restrict__ u, float* __restrict__ e, long long m, int apply)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m) return;
+    if (apply) u[p] += f2d(e[p]);
+    e[p] = 0.0f;
+}
+
+// Coarse-level FP32 split hi + lo of the injected FP64 iterate: coarse point
+// (I, J, K) takes fine point (sI, sJ, sK), s = 2^level.
+__global__ void __launch_bounds__(BX * BY) k_split_inject(const double* __restrict__ u0, int n0, int stride,
+                                                          float* __restrict__ hi, float* __restrict__ lo, int nc)
+{
+    const int I = blockIdx.x * BX + threadIdx.x;
+    const int J = blockIdx.y * BY + threadIdx.y;
+    const int K = blockIdx.z;
+    if (I >= nc || J >= nc) return;
+    const double v = u0[lin(stride * I, stride * J, stride * K, n0)];
+    const float h = d2f_trunc(v);
+    const long long pc = lin(I, J, K, nc);
+    hi[pc] = h;
+    lo[pc] = d2f_trunc(v - f2d(h));
+}
 
 }  // namespace
 
@@ -435,32 +713,178 @@ cudaError_t launch_to_cm(const float* nat, float* cm, int n, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_smooth_corr(float* e, const void* bstore, const float* rhs_cm, int n, double h, int nsweeps,
-                               unsigned long long* events, cudaStream_t s)
+// One sweep of in-place per-colour launches (8 launches).
+static cudaError_t colour_sweep_corr(float* e, const float* b, const float* rhs_cm, int n, float inv_h2, float h2half,
+                                     unsigned long long* events, cudaStream_t s)
+{
+    cudaError_t e_;
+    if ((e_ = launch_colour_corr<0>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+    if ((e_ = launch_colour_corr<1>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+    if ((e_ = launch_colour_corr<2>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+    if ((e_ = launch_colour_corr<3>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+    if ((e_ = launch_colour_corr<4>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+    if ((e_ = launch_colour_corr<5>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+    if ((e_ = launch_colour_corr<6>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+    return launch_colour_corr<7>(e, b, rhs_cm, n, inv_h2, h2half, events, s);
+}
+
+namespace {
+
+// ---- choice of smoother and residual kernels per level size ----------------
+// Tuning table: per grid size (n - 1 a power of two), the correction-smoother
+// variant (CORR_BY_COLOUR or a plane tile) and the residual tile, set by the
+// autotuner (ma_tune_corr) or by hand; -1 = the built-in default.
+constexpr int kTuneSlots = 16;
+std::atomic<int> g_smooth_choice[kTuneSlots];
+std::atomic<int> g_resid_choice[kTuneSlots];
+std::atomic<int> g_tune_init{0};
+
+int tune_slot(int n)
+{
+    if (n < 3) return -1;
+    const unsigned m = (unsigned)(n - 1);
+    if (m & (m - 1)) return -1;
+    int l = 0;
+    while ((1u << l) < m) ++l;
+    return l < kTuneSlots ? l : -1;
+}
+
+void tune_init()
+{
+    if (g_tune_init.load(std::memory_order_acquire)) return;
+    for (int i = 0; i < kTuneSlots; ++i) {
+        g_smooth_choice[i].store(-1, std::memory_order_relaxed);
+        g_resid_choice[i].store(-1, std::memory_order_relaxed);
+    }
+    g_tune_init.store(1, std::memory_order_release);
+}
+
+// Defaults before tuning: small grids are launch-latency bound, so the
+// plane-phase sweep (2 launches per sweep instead of 8) with small tiles.
+int default_smooth_choice(int n) { return n <= 33 ? CORR_PLANE16 : (n <= 65 ? CORR_PLANE32 : CORR_BY_COLOUR); }
+int default_resid_choice(int n) { return n <= 33 ? CORR_PLANE16 : (n <= 65 ? CORR_PLANE32 : CORR_PLANE64); }
+
+template <int PT>
+dim3 tile_grid(int n, int planes)
+{
+    const int t = (n - 2 + PT - 1) / PT;
+    return dim3(t, t, planes);
+}
+
+// One sweep by k parity (2 launches): src -> dst, both with a zero shell.
+template <int PT, int NT>
+cudaError_t plane_sweep_t(const float* src, float* dst, const float* b, const float* rhs_cm, int n, float inv_h2,
+                          float h2half, unsigned long long* events, cudaStream_t s)
+{
+    const int ne = colour_count(n, 0), no = colour_count(n, 1);
+    if (ne > 0) {
+        count_launches(1);
+        k_smooth_corr_plane<0, PT, NT><<<tile_grid<PT>(n, ne), NT, Tile<PT>::SMEM, s>>>(src, src, dst, b, rhs_cm, n,
+                                                                                         inv_h2, h2half, events);
+        cudaError_t e_ = cudaGetLastError();
+        if (e_ != cudaSuccess) return e_;
+    }
+    count_launches(1);
+    k_smooth_corr_plane<1, PT, NT><<<tile_grid<PT>(n, no), NT, Tile<PT>::SMEM, s>>>(src, dst, dst, b, rhs_cm, n,
+                                                                                     inv_h2, h2half, events);
+    return cudaGetLastError();
+}
+
+cudaError_t plane_sweep(int choice, const float* src, float* dst, const float* b, const float* rhs_cm, int n,
+                        float inv_h2, float h2half, unsigned long long* events, cudaStream_t s)
+{
+    switch (choice) {
+    case CORR_PLANE16: return plane_sweep_t<16, 128>(src, dst, b, rhs_cm, n, inv_h2, h2half, events, s);
+    case CORR_PLANE32: return plane_sweep_t<32, 128>(src, dst, b, rhs_cm, n, inv_h2, h2half, events, s);
+    default: return plane_sweep_t<64, 256>(src, dst, b, rhs_cm, n, inv_h2, h2half, events, s);
+    }
+}
+
+template <int PT, int NT>
+cudaError_t residual_t(const float* e, const float* b, const float* rhs_cm, float* res, int n, float inv_h2,
+                       cudaStream_t s)
+{
+    count_launches(1);
+    k_residual_corr_plane<PT, NT><<<tile_grid<PT>(n, n - 2), NT, Tile<PT>::SMEM, s>>>(e, b, rhs_cm, res, n, inv_h2);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int corr_smooth_choice(int n)
+{
+    tune_init();
+    const int sl = tune_slot(n);
+    const int c = sl >= 0 ? g_smooth_choice[sl].load(std::memory_order_relaxed) : -1;
+    return c >= 0 ? c : default_smooth_choice(n);
+}
+
+int corr_resid_choice(int n)
+{
+    tune_init();
+    const int sl = tune_slot(n);
+    const int c = sl >= 0 ? g_resid_choice[sl].load(std::memory_order_relaxed) : -1;
+    return c >= 0 ? c : default_resid_choice(n);
+}
+
+bool set_corr_tuning(int n, int smooth, int resid)
+{
+    tune_init();
+    const int sl = tune_slot(n);
+    if (sl < 0) return false;
+    g_smooth_choice[sl].store(smooth, std::memory_order_relaxed);
+    g_resid_choice[sl].store(resid, std::memory_order_relaxed);
+    return true;
+}
+
+cudaError_t launch_smooth_corr_choice(int choice, float* e, float* e2, const void* bstore, const float* rhs_cm, int n,
+                                      double h, int nsweeps, unsigned long long* events, cudaStream_t s)
 {
     const float inv_h2 = (float)(1.0 / (h * h));
     const float h2half = (float)(0.5 * h * h);
     const float* b = (const float*)bstore;
-    for (int sw = 0; sw < nsweeps; ++sw) {
-        cudaError_t e_;
-        if ((e_ = launch_colour_corr<0>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<1>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<2>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<3>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<4>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<5>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<6>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-        if ((e_ = launch_colour_corr<7>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
-    }
+    int sw = 0;
+    cudaError_t e_;
+    // pairs of sweeps e -> e2 -> e by k parity; the rest in place by colour
+    if (choice != CORR_BY_COLOUR && e2 && n >= 5)
+        for (; sw + 2 <= nsweeps; sw += 2) {
+            if ((e_ = plane_sweep(choice, e, e2, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+            if ((e_ = plane_sweep(choice, e2, e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        }
+    for (; sw < nsweeps; ++sw)
+        if ((e_ = colour_sweep_corr(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
     return cudaSuccess;
+}
+
+cudaError_t launch_smooth_corr(float* e, float* e2, const void* bstore, const float* rhs_cm, int n, double h,
+                               int nsweeps, unsigned long long* events, cudaStream_t s)
+{
+    return launch_smooth_corr_choice(corr_smooth_choice(n), e, e2, bstore, rhs_cm, n, h, nsweeps, events, s);
+}
+
+cudaError_t launch_residual_corr_choice(int choice, const float* e, const void* bstore, const float* rhs_cm,
+                                        float* res, int n, double h, cudaStream_t s)
+{
+    if (n < 3) return cudaSuccess;
+    const float inv_h2 = (float)(1.0 / (h * h));
+    const float* b = (const float*)bstore;
+    switch (choice) {
+    case CORR_PLANE16: return residual_t<16, 128>(e, b, rhs_cm, res, n, inv_h2, s);
+    case CORR_PLANE32: return residual_t<32, 128>(e, b, rhs_cm, res, n, inv_h2, s);
+    default: return residual_t<64, 256>(e, b, rhs_cm, res, n, inv_h2, s);
+    }
 }
 
 cudaError_t launch_residual_corr(const float* e, const void* bstore, const float* rhs_cm, float* res, int n,
                                  double h, cudaStream_t s)
 {
+    return launch_residual_corr_choice(corr_resid_choice(n), e, bstore, rhs_cm, res, n, h, s);
+}
+
+cudaError_t launch_zero_shell_f32(float* v, int n, cudaStream_t s)
+{
     count_launches(1);
-    k_residual_corr<<<grid_of(n), dim3(BX, BY), 0, s>>>(e, (const float*)bstore, rhs_cm, res, n,
-                                                        (float)(1.0 / (h * h)));
+    k_zero_shell<<<dim3((n + BX - 1) / BX, (n + BY - 1) / BY, 6), dim3(BX, BY), 0, s>>>(v, n);
     return cudaGetLastError();
 }
 
@@ -486,7 +910,7 @@ cudaError_t launch_prolong_add_f32(const float* ec, const float* wc, int nc, flo
 {
     const int nf = 2 * nc - 1;
     count_launches(1);
-    xfer::k_prolong<float><<<grid_of(nf), dim3(BX, BY), 0, s>>>(ec, wc, nc, ef, nf, 1);
+    xfer::k_prolong<float><<<xfer::prolong_grid(nf), dim3(BX, BY), 0, s>>>(ec, wc, nc, ef, nf, 1);
     return cudaGetLastError();
 }
 
@@ -515,23 +939,40 @@ cudaError_t launch_coarsest_corr(float* e, const void* bstore, const float* rhs_
 
 cudaError_t prepare_coarsest_f64();
 
-cudaError_t prepare_coarsest_kernels()
+cudaError_t prepare_kernels()
 {
     cudaError_t e = prepare_coarsest_f64();
     if (e != cudaSuccess) return e;
+    constexpr int big = Tile<64>::SMEM;
+    if ((e = cudaFuncSetAttribute(k_smooth_corr_plane<0, 64, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_smooth_corr_plane<1, 64, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_residual_corr_plane<64, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) !=
+        cudaSuccess)
+        return e;
     return cudaFuncSetAttribute(k_coarsest_corr, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)coarsest_corr_smem(17));
 }
 
-cudaError_t launch_split_update(double* u, float* e, float* hi, float* lo, int n, int apply, cudaStream_t s)
+cudaError_t launch_update(double* u, float* e, int n, int apply, cudaStream_t s)
 {
     const long long m = (long long)n * n * n;
     count_launches(1);
-    k_split_update<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(u, e, hi, lo, m, apply);
+    k_update<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(u, e, m, apply);
     return cudaGetLastError();
 }
 
-cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r_cm, int n, double h,
+cudaError_t launch_split_inject(const double* u0, int n0, int stride, float* hi, float* lo, int nc, cudaStream_t s)
+{
+    count_launches(1);
+    k_split_inject<<<grid_of(nc), dim3(BX, BY), 0, s>>>(u0, n0, stride, hi, lo, nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r_cm, void* bstore, int n, double h,
                                    double* partials, cudaStream_t s)
 {
     const double h2 = h * h;
@@ -539,7 +980,8 @@ cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r_
     const int kz = n < 16 ? n : 16;
     const int kchunk = (n + kz - 1) / kz;
     resid::k_residual_col<CmF32Out><<<resid::grid_for(n, kz), dim3(resid::RX, resid::RY), 0, s>>>(
-        u, rhs, CmF32Out{r_cm}, n, 1.0 / (64.0 * h2 * h2 * h2), partials, kchunk);
+        u, rhs, CmF32Out{r_cm, (float*)bstore, (float)(0.25 / h2)}, n, 1.0 / (64.0 * h2 * h2 * h2), partials,
+        kchunk);
     return cudaGetLastError();
 }
 

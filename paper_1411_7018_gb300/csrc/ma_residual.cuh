@@ -20,10 +20,14 @@ namespace resid {
 
 constexpr int RX = 32, RY = 4;
 
-// Writes the residual value of interior point (i, j, k), linear index p.
+// Writes the residual value of interior point (i, j, k), linear index p
+// (H4 = 4 h^2 D^2_h u at the point, for outputs that also store it).
 struct NaturalF64Out {
     double* r;
-    __device__ __forceinline__ void put(long long p, int, int, int, int, double v, float) const { r[p] = v; }
+    __device__ __forceinline__ void put(long long p, int, int, int, int, double v, float, const HessS&) const
+    {
+        r[p] = v;
+    }
     __device__ __forceinline__ void zero(long long p) const { r[p] = 0.0; }
 };
 
@@ -76,7 +80,7 @@ __global__ void __launch_bounds__(RX * RY) k_residual_col(const double* __restri
                     const float v32 = d2f_trunc(val);
                     mx = fmaxf(mx, fabsf(v32));
                     ss = fmaf(v32, v32, ss);
-                    out.put(p, i, j, k, n, val, v32);
+                    out.put(p, i, j, k, n, val, v32, H);
                     dxa = dxb; dya = dyb;
                     dxb = dxc; dyb = dyc;
                     continue;

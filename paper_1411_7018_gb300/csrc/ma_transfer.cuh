@@ -68,28 +68,48 @@ __global__ void __launch_bounds__(BX * BY) k_restrict(const T* __restrict__ uf, 
 }
 
 // Trilinear interpolation at fine interior points: along each axis an even
-// index sits on a coarse point, an odd one halfway between two.
+// index sits on a coarse point, an odd one halfway between two.  Thread
+// (I, j, k) writes fine points i = 2I + 1 and 2I + 2 of row (j, k): with
+// L(I) the coarse values d = uc - wc (add != 0) or d = uc (add == 0) summed
+// over the one, two or four coarse rows around (j, k) and scaled by their
+// weight, fine 2I + 2 gets L(I + 1) and fine 2I + 1 gets (L(I) + L(I + 1)) / 2.
+// A lane computes L(I + 1) and takes L(I) from the lane before it.
 // add != 0: uf += I(uc - wc) (coarse-grid correction); add == 0: uf = I(uc).
+// Grid: prolong_grid(nf), blocks of BX x BY.
 template <typename T>
 __global__ void __launch_bounds__(BX * BY) k_prolong(const T* __restrict__ uc, const T* __restrict__ wc, int nc,
                                                      T* __restrict__ uf, int nf, int add)
 {
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i < 1 || j < 1 || k < 1 || i > nf - 2 || j > nf - 2 || k > nf - 2) return;
-    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
-    const int oi = i & 1, oj = j & 1, ok = k & 1;
-    T s = T(0);
-    for (int dk = 0; dk <= ok; ++dk)
-        for (int dj = 0; dj <= oj; ++dj)
-            for (int di = 0; di <= oi; ++di) {
-                const long long q = lin(I0 + di, J0 + dj, K0 + dk, nc);
+    const int I = blockIdx.x * BX + threadIdx.x;
+    const int j = 1 + blockIdx.y * BY + threadIdx.y;
+    const int k = 1 + blockIdx.z;
+    const bool row = j <= nf - 2;   // uniform over the warp (BX = 32)
+    const int J0 = j >> 1, K0 = k >> 1, oj = j & 1, ok = k & 1;
+    const T w = T(1) / T(1 << (oj + ok));
+    auto line = [&](int Ic) -> T {
+        T s = T(0);
+        for (int dk = 0; dk <= ok; ++dk)
+            for (int dj = 0; dj <= oj; ++dj) {
+                const long long q = lin(Ic, J0 + dj, K0 + dk, nc);
                 s += add ? (uc[q] - wc[q]) : uc[q];
             }
-    const T w = T(1) / T(1 << (oi + oj + ok));
-    const long long p = lin(i, j, k, nf);
-    uf[p] = add ? (s * w + uf[p]) : s * w;
+        return s * w;
+    };
+    const bool act = row && I <= nc - 2;
+    const T b = act ? line(I + 1) : T(0);
+    T a = __shfl_up_sync(0xffffffffu, b, 1);
+    if (!act) return;
+    if (threadIdx.x == 0) a = line(I);
+    const long long p = lin(2 * I + 1, j, k, nf);
+    const T mid = (a + b) * T(0.5);
+    uf[p] = add ? uf[p] + mid : mid;
+    if (2 * I + 2 <= nf - 2) uf[p + 1] = add ? uf[p + 1] + b : b;
+}
+
+inline dim3 prolong_grid(int nf)
+{
+    const int nc = (nf + 1) / 2;
+    return dim3((nc - 1 + BX - 1) / BX, (nf - 2 + BY - 1) / BY, nf - 2);
 }
 
 template <typename T>

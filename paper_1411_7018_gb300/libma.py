@@ -20,6 +20,9 @@ MA_APPROX_INJECTION, MA_APPROX_WEIGHTED = 0, 1
 MA_FP64, MA_MIXED = 0, 1
 MA_NORM_MAX, MA_NORM_L2 = 0, 1
 MA_INIT_FMG, MA_INIT_ZERO, MA_INIT_KEEP = 0, 1, 2
+MA_CORR_BY_COLOUR, MA_CORR_PLANE16, MA_CORR_PLANE32, MA_CORR_PLANE64 = 0, 1, 2, 3
+CORR_NAMES = {MA_CORR_BY_COLOUR: "by_colour", MA_CORR_PLANE16: "plane16", MA_CORR_PLANE32: "plane32",
+              MA_CORR_PLANE64: "plane64"}
 
 STATUS_NAMES = {0: "MA_OK", 1: "MA_ERR_INVALID_ARG", 2: "MA_ERR_OOM", 3: "MA_ERR_CUDA",
                 4: "MA_ERR_NOT_CONVERGED", 5: "MA_ERR_NONFINITE"}
@@ -79,6 +82,10 @@ _SIGS = {
     "ma_smooth_correction": [_vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp, C.c_size_t, _vp, _vp],
     "ma_residual_correction": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp, C.c_size_t, _vp],
     "ma_norm_static": [_vp, C.c_int, C.c_double, C.POINTER(C.c_double), _vp],
+    "ma_set_corr_tuning": [C.c_int, C.c_int, C.c_int],
+    "ma_get_corr_tuning": [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "ma_tune_corr": [_vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp, C.c_size_t, C.POINTER(C.c_double),
+                     C.POINTER(C.c_double), _vp],
 }
 # Declared in include/ma.h; the test suite checks that the library exports them.
 EXPORTED = sorted(list(_SIGS) + ["ma_last_error_string"])
@@ -280,6 +287,67 @@ def correction_scratch(n: int, device=None):
     t = torch.empty(nb + 256, dtype=torch.uint8, device=device or torch.device("cuda"))
     addr = (t.data_ptr() + 255) // 256 * 256
     return t, addr, nb
+
+
+def ma_set_corr_tuning(n: int, smooth_choice: int, residual_choice: int) -> None:
+    _check(load().ma_set_corr_tuning(n, smooth_choice, residual_choice))
+
+
+def ma_get_corr_tuning(n: int):
+    a, b = C.c_int(0), C.c_int(0)
+    _check(load().ma_get_corr_tuning(n, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def ma_tune_corr(e, u_hi, u_lo, rhs, n: int, h: float, reps: int, scratch, scratch_bytes: int, stream=None):
+    """Runs the autotuner on one grid; returns (us_smooth[4], us_residual[4]) and records the fastest."""
+    us = (C.c_double * 4)()
+    ur = (C.c_double * 4)()
+    _check(load().ma_tune_corr(_ptr(e), _ptr(u_hi), _ptr(u_lo), _ptr(rhs), n, h, reps, _ptr(scratch), scratch_bytes,
+                               us, ur, _stream(stream)))
+    return list(us), list(ur)
+
+
+def autotune(sizes, reps: int = 5, device=None) -> dict:
+    """Autotunes the correction smoother and residual for each grid size in
+    `sizes` on Example 4 data (the base Hessian of u = exp(|x|^2/2), a small
+    smooth correction and right-hand side) and records the fastest variants
+    for this process.  Returns {n: {"smoother": name, "residual": name,
+    "us_per_sweep": {...}, "us_residual": {...}}}."""
+    import numpy as np
+    import torch
+    from . import problems
+    dev = device or torch.device("cuda")
+    out = {}
+    for n in sorted(set(int(v) for v in sizes)):
+        if n < 5:
+            continue
+        pr = problems.make("exp", n)
+        u = torch.from_numpy(pr.u).to(dev)
+        hi = u.float()
+        lo = (u - hi.double()).float()
+        x = torch.linspace(0.0, 1.0, n, device=dev, dtype=torch.float64)
+        s = torch.sin(np.pi * x)
+        e = (1e-6 * s[:, None, None] * s[None, :, None] * s[None, None, :]).float().contiguous()
+        rhs = (1e-6 * torch.from_numpy(pr.f).to(dev)).float()
+        rhs[0], rhs[-1] = 0, 0
+        keep, scr, nb = correction_scratch(n, device=dev)
+        us, ur = ma_tune_corr(e, hi, lo, rhs, n, pr.h, reps, scr, nb)
+        torch.cuda.synchronize(dev)
+        sm, rs = ma_get_corr_tuning(n)
+        out[n] = {"smoother": CORR_NAMES[sm], "residual": CORR_NAMES[rs],
+                  "us_per_sweep": {CORR_NAMES[c]: round(us[c], 2) for c in range(4)},
+                  "us_residual": {CORR_NAMES[c]: round(ur[c], 2) for c in range(1, 4)}}
+        del keep, u, hi, lo, e, rhs
+    return out
+
+
+def level_sizes(n: int, coarsest_n: int = 3):
+    """Grid sizes of the levels of a hierarchy on n points per side."""
+    out = [n]
+    while out[-1] > coarsest_n:
+        out.append((out[-1] + 1) // 2)
+    return out
 
 
 def ma_norm_scratch_bytes(n: int) -> int:

@@ -3,8 +3,9 @@
     python -m paper_1411_7018_gb300.profile_case --case smooth --n 257 --reps 2
 
 Cases: ``smooth`` (FP64 smoother sweeps, 8 colour launches each), ``residual``
-(the FP64 residual kernel), ``smooth_corr`` (FP32 correction-smoother sweeps
-of the mixed path on a small smooth correction), ``vcycle`` (whole V-cycles of
+(the FP64 residual kernel), ``smooth_corr`` (pairs of FP32 correction-smoother
+sweeps of the mixed path, two k-parity launches per sweep, on a small
+correction), ``vcycle`` (whole V-cycles of
 a resident hierarchy), ``solve`` (one FMG + V-cycle solve to 1e-10);
 ``--precision mixed`` runs the hierarchy cases in mixed precision.  The grid holds
 Example 4 (u = exp(|x|^2/2)) with a small seeded perturbation; fields of a
@@ -51,7 +52,7 @@ def main():
         rhs = (1e-6 * f).float()
         rhs[0], rhs[-1] = 0, 0
         for _ in range(a.reps):
-            M.ma_smooth_correction(e, hi, lo, rhs, a.n, pr.h, 1, scr, nb)
+            M.ma_smooth_correction(e, hi, lo, rhs, a.n, pr.h, 2, scr, nb)
     else:
         prec = M.MA_MIXED if a.precision == "mixed" else M.MA_FP64
         H = M.Hierarchy(M.make_desc(a.n, length=pr.length, precision=prec))

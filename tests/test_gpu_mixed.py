@@ -103,6 +103,81 @@ def test_correction_sweep_matches_oracle_sweep(name, n, amp):
     assert np.max(np.abs(got - e_ref)) <= 1e-3 * change + 1e-6 * np.max(np.abs(e_ref))
 
 
+@pytest.mark.parametrize("name,n", [("exp", 33), ("cosine", 129), ("exp", 257)])
+def test_plane_sweeps_equal_colour_sweeps_bitwise(name, n):
+    """Pairs of sweeps run by k parity (two launches per sweep, plane tiles
+    of 16, 32 or 64 points that recompute a halo, a second e buffer) give the
+    same bits as sweeps run colour by colour in place: all are the
+    sequential 8-colour sweep.  At 129^3 and 257^3 every tile size has
+    several tiles per plane edge."""
+    pr = P.make(name, n, seed=6)
+    u = pr.u
+    e = smooth_correction_field(n, 1e-5, n + 2)
+    rng = np.random.default_rng(3)
+    rhs = (1e-5 * rng.standard_normal(u.shape) * np.max(pr.f)).astype(np.float32)
+    hi, lo = (dev(a) for a in split(u))
+    rhs_d = dev(rhs)
+    _keep, scr, nb = M.correction_scratch(n)
+    try:
+        M.ma_set_corr_tuning(n, M.MA_CORR_BY_COLOUR, -1)
+        refs = {}
+        for sweeps in (2, 3):
+            b = dev(e)
+            for _ in range(sweeps):
+                M.ma_smooth_correction(b, hi, lo, rhs_d, n, pr.h, 1, scr, nb)
+            refs[sweeps] = b
+        for choice in (M.MA_CORR_PLANE16, M.MA_CORR_PLANE32, M.MA_CORR_PLANE64):
+            M.ma_set_corr_tuning(n, choice, -1)
+            for sweeps in (2, 3):
+                a = dev(e)
+                M.ma_smooth_correction(a, hi, lo, rhs_d, n, pr.h, sweeps, scr, nb)
+                torch.cuda.synchronize()
+                assert not torch.equal(a, dev(e))
+                d = (a - refs[sweeps]).abs().max().item()
+                assert torch.equal(a, refs[sweeps]), f"{M.CORR_NAMES[choice]}, {sweeps} sweeps: max diff {d}"
+    finally:
+        M.ma_set_corr_tuning(n, -1, -1)
+
+
+@pytest.mark.parametrize("choice", [1, 2, 3])
+def test_residual_tiles_agree(choice):
+    """The three residual tile sizes compute the same values (the same
+    arithmetic per point), with a zero shell."""
+    n = 129
+    pr = P.make("cosine", n, seed=7)
+    e = smooth_correction_field(n, 1e-5, 11)
+    rng = np.random.default_rng(4)
+    rhs = (1e-5 * rng.standard_normal(pr.u.shape)).astype(np.float32)
+    hi, lo = (dev(a) for a in split(pr.u))
+    _keep, scr, nb = M.correction_scratch(n)
+    outs = []
+    try:
+        for c in (M.MA_CORR_PLANE64, choice):
+            M.ma_set_corr_tuning(n, -1, c)
+            res = torch.full(pr.u.shape, 7.0, dtype=torch.float32, device="cuda")
+            M.ma_residual_correction(dev(e), hi, lo, dev(rhs), res, n, pr.h, scr, nb)
+            outs.append(host(res))
+    finally:
+        M.ma_set_corr_tuning(n, -1, -1)
+    assert np.array_equal(outs[0], outs[1])
+    sh = outs[1]
+    assert np.all(sh[0] == 0) and np.all(sh[-1] == 0) and np.all(sh[:, 0] == 0) and np.all(sh[:, :, -1] == 0)
+
+
+def test_autotune_records_a_choice_per_size():
+    table = M.autotune([17, 33, 65], reps=2)
+    try:
+        for n in (17, 33, 65):
+            t = table[n]
+            sm, rs = M.ma_get_corr_tuning(n)
+            assert M.CORR_NAMES[sm] == t["smoother"] and M.CORR_NAMES[rs] == t["residual"]
+            assert t["us_per_sweep"][t["smoother"]] == min(t["us_per_sweep"].values())
+            assert all(v > 0 for v in t["us_per_sweep"].values())
+    finally:
+        for n in (17, 33, 65):
+            M.ma_set_corr_tuning(n, -1, -1)
+
+
 @pytest.mark.parametrize("name,n", [("exp", 33), ("cosine", 65), ("exp", 129), ("quadratic", 65), ("sine", 65)])
 def test_mixed_solve_matches_fp64_oracle(name, n):
     pr = P.make(name, n, seed=5)
