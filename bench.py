@@ -273,6 +273,11 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
+    # autotune the correction smoother and residual tiles for every grid size
+    # the workloads use (before any hierarchy records its graphs)
+    tune_sizes = set(M.level_sizes(args.n)) | set(M.level_sizes(129)) | set(M.level_sizes(257))
+    tuning = M.autotune(sorted(tune_sizes), reps=5, device=dev)
+
     pr = problems.make(args.problem, args.n)
     f_dev = torch.from_numpy(pr.f).to(dev)
     g_dev = torch.from_numpy(pr.initial()).to(dev)
@@ -347,10 +352,15 @@ def main():
     M.ma_smooth_correction(e, hi, lo, rhs, n, h, 0, scr, nb)
     b1.record(stream)
     torch.cuda.synchronize()
-    # a sweep is two launches of k_smooth_corr_plane (even planes, then odd
-    # planes), each updating half of the points (four colours)
-    corr_launch_ms = (e0.elapsed_time(e1) - b0.elapsed_time(b1)) / (2 * sweeps)
-    corr_gbs = CORR_SMOOTH_BYTES_PER_POINT * ((n - 2) ** 3 / 2.0) / (corr_launch_ms / 1e3) / 1e9
+    # the variant in force at this size: by colour (8 launches per sweep, an
+    # eighth of the points each) or by k parity (2 launches, half the points)
+    corr_choice = M.ma_get_corr_tuning(n)[0]
+    corr_launches = 8 if corr_choice == M.MA_CORR_BY_COLOUR else 2
+    corr_kernel = ("k_smooth_corr (FP32 correction smoother, one colour phase)" if corr_launches == 8 else
+                   f"k_smooth_corr_plane (FP32 correction smoother, {M.CORR_NAMES[corr_choice]}, one k-parity "
+                   f"phase: four colours)")
+    corr_launch_ms = (e0.elapsed_time(e1) - b0.elapsed_time(b1)) / (corr_launches * sweeps)
+    corr_gbs = CORR_SMOOTH_BYTES_PER_POINT * ((n - 2) ** 3 / corr_launches) / (corr_launch_ms / 1e3) / 1e9
     pts_launch = (n - 2) ** 3 / 8.0
     u_tmp = u64.clone()
     M.ma_smooth(u_tmp, f_dev, n, h, 1)
@@ -412,7 +422,7 @@ def main():
             "mixed_vs_fp64": ms_fp64 / ms_mixed,
             "accuracy": {"max_err_vs_exact_mixed": err["mixed"], "max_err_vs_exact_fp64": err["fp64"],
                          "max_rel_diff_mixed_vs_fp64": diff},
-            "roofline": {"bound": "hbm", "kernel": "k_smooth_corr_plane (FP32 correction smoother, one k-parity phase: four colours, half the points)",
+            "roofline": {"bound": "hbm", "kernel": corr_kernel,
                          "achieved": corr_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                          "frac": corr_gbs / HBM_PEAK_GBS, "traffic": None,
                          "launch_ms": corr_launch_ms, "bytes_per_point": CORR_SMOOTH_BYTES_PER_POINT,
@@ -427,6 +437,8 @@ def main():
                     "h2d_bytes_per_step": 2 * 8 * pr.n ** 3, "d2h_bytes_per_step": 8 * pr.n ** 3},
             "clocks": clocks,
             "gpu_launches": launches,
+            "tuning": {str(k): {"smoother": v["smoother"], "residual": v["residual"],
+                                "us_per_sweep": v["us_per_sweep"]} for k, v in tuning.items()},
             **extras,
         }
         print(json.dumps(line), flush=True)

@@ -245,11 +245,14 @@ __global__ void __launch_bounds__(BX * BY) k_to_cm(const float* __restrict__ nat
 }
 
 // Correction smoother, one colour per launch: bc / rc point at this colour's
-// B and rhs boxes; e is in the natural layout (19-point stencil).
-template <int PI, int PJ, int PK>
-__global__ void __launch_bounds__(BX * BY) k_smooth_corr(float* e, const float* __restrict__ bc,
-                                                          const float* __restrict__ rc, int n, float inv_h2,
-                                                          float h2half, unsigned long long* events)
+// B and rhs boxes; e is in the natural layout (19-point stencil).  Idx is int
+// for grids up to 1289^3 (32-bit index arithmetic), long long above.  The
+// point solve is latency-bound, so the launch bounds ask for 10 resident
+// blocks per SM (48 registers).
+template <int PI, int PJ, int PK, typename Idx>
+__global__ void __launch_bounds__(BX * BY, 10) k_smooth_corr(float* e, const float* __restrict__ bc,
+                                                              const float* __restrict__ rc, int n, float inv_h2,
+                                                              float h2half, unsigned long long* events)
 {
     const int ii = blockIdx.x * BX + threadIdx.x;
     const int jj = blockIdx.y * BY + threadIdx.y;
@@ -257,16 +260,25 @@ __global__ void __launch_bounds__(BX * BY) k_smooth_corr(float* e, const float* 
     const int ni = colour_count(n, PI), nj = colour_count(n, PJ);
     if (ii >= ni || jj >= nj) return;
     const int i = (PI ? 1 : 2) + 2 * ii, j = (PJ ? 1 : 2) + 2 * jj, k = (PK ? 1 : 2) + 2 * kk;
-    const long long cnt = (long long)ni * nj * colour_count(n, PK);
-    const long long idx = ((long long)kk * nj + jj) * ni + ii;
-    const S3f B = load_b(bc + idx, cnt);
-    const long long sy = n, sz = (long long)n * n;
-    const long long p = lin(i, j, k, n);
-    const float e0 = e[p];
-    const S3f K = corr_hess(e, p, sy, sz, e0, inv_h2);
+    const Idx cnt = (Idx)ni * nj * colour_count(n, PK);
+    const Idx idx = ((Idx)kk * nj + jj) * ni + ii;
+    const float* bp = bc + idx;
+    S3f B;
+    B.xx = __ldcs(bp);
+    B.yy = __ldcs(bp + cnt);
+    B.zz = __ldcs(bp + 2 * cnt);
+    B.xy = __ldcs(bp + 3 * cnt);
+    B.xz = __ldcs(bp + 4 * cnt);
+    B.yz = __ldcs(bp + 5 * cnt);
+    const Idx sy = n, sz = (Idx)n * n;
+    float* q = e + (((Idx)k * n + j) * n + i);
+    const float e0 = q[0];
+    const S3f K =
+        hess_from_diff([&](int di, int dj, int dk) -> float { return __ldg(q + (di + dj * sy + dk * sz)) - e0; },
+                       inv_h2);
     bool nonconvex = false;
     const float z = corr_root(B, K, __ldcs(rc + idx), &nonconvex);
-    e[p] = fmaf(h2half, z, e0);
+    q[0] = fmaf(h2half, z, e0);
     if (nonconvex && events) atomicAdd(events, 1ull);
 }
 
@@ -280,8 +292,12 @@ cudaError_t launch_colour_corr(float* e, const float* bstore, const float* rhs_c
     dim3 grid((ni + BX - 1) / BX, (nj + BY - 1) / BY, nk);
     const long long off = cm_offset(n, C);
     count_launches(1);
-    k_smooth_corr<PI, PJ, PK><<<grid, dim3(BX, BY), 0, s>>>(e, bstore + 6 * off, rhs_cm + off, n, inv_h2, h2half,
-                                                             ev);
+    if (n <= 1289)
+        k_smooth_corr<PI, PJ, PK, int><<<grid, dim3(BX, BY), 0, s>>>(e, bstore + 6 * off, rhs_cm + off, n, inv_h2,
+                                                                      h2half, ev);
+    else
+        k_smooth_corr<PI, PJ, PK, long long><<<grid, dim3(BX, BY), 0, s>>>(e, bstore + 6 * off, rhs_cm + off, n,
+                                                                            inv_h2, h2half, ev);
     return cudaGetLastError();
 }
 
