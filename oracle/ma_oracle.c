@@ -47,6 +47,7 @@ enum { ORC_COLOUR8 = 0, ORC_LEXICOGRAPHIC = 1, ORC_COLOUR8_REVERSED = 2 };
 enum { ORC_HALF_WEIGHTING = 0, ORC_FULL_WEIGHTING = 1 };
 enum { ORC_NORM_MAX = 0, ORC_NORM_L2 = 1 };
 enum { ORC_APPROX_INJECTION = 0, ORC_APPROX_WEIGHTED = 1 };
+enum { ORC_FMG_TRILINEAR = 0, ORC_FMG_CUBIC = 1 };
 
 /* ------------------------------------------------------------------------ */
 /* Section 2: the stencil                                                    */
@@ -417,6 +418,60 @@ void orc_interpolate(const double *uc, int nc, double *uf, int nf)
                 AT(uf, nf, i, j, k) = trilinear_at(uc, nc, i, j, k);
 }
 
+/* Cubic interpolation along one axis (Algorithm 2 step 4, the cubic
+ * interpolation the paper recommends for FMG): the coarse points and weights
+ * that give fine index i.  An even i sits on coarse point i/2.  An odd i lies
+ * halfway between coarse points I0 = (i-1)/2 and I0 + 1 and takes the cubic
+ * through four neighbouring coarse points: I0-1 .. I0+2 (weights -1, 9, 9, -1
+ * over 16), or, next to the boundary, the four nearest ones (0..3 with 5, 15,
+ * -5, 1 over 16, and the mirror image at the far end).  A 3-point coarse grid
+ * has only a quadratic (3, 6, -1 over 8), a 2-point one a linear midpoint.
+ * Returns the number of points. */
+static int cubic_stencil(int i, int nc, int idx[4], double w[4])
+{
+    if (i % 2 == 0) { idx[0] = i / 2; w[0] = 1.0; return 1; }
+    const int I0 = (i - 1) / 2;
+    if (nc == 2) { idx[0] = 0; idx[1] = 1; w[0] = w[1] = 0.5; return 2; }
+    if (nc == 3) {
+        idx[0] = 0; idx[1] = 1; idx[2] = 2;
+        if (I0 == 0) { w[0] = 3.0 / 8; w[1] = 6.0 / 8; w[2] = -1.0 / 8; }
+        else         { w[0] = -1.0 / 8; w[1] = 6.0 / 8; w[2] = 3.0 / 8; }
+        return 3;
+    }
+    if (I0 == 0) {
+        for (int a = 0; a < 4; ++a) idx[a] = a;
+        w[0] = 5.0 / 16; w[1] = 15.0 / 16; w[2] = -5.0 / 16; w[3] = 1.0 / 16;
+    } else if (I0 == nc - 2) {
+        for (int a = 0; a < 4; ++a) idx[a] = nc - 4 + a;
+        w[0] = 1.0 / 16; w[1] = -5.0 / 16; w[2] = 15.0 / 16; w[3] = 5.0 / 16;
+    } else {
+        for (int a = 0; a < 4; ++a) idx[a] = I0 - 1 + a;
+        w[0] = -1.0 / 16; w[1] = 9.0 / 16; w[2] = 9.0 / 16; w[3] = -1.0 / 16;
+    }
+    return 4;
+}
+
+/* Algorithm 2 step 4 with tricubic interpolation: the tensor product of the
+ * per-axis cubic stencils, fine interior only (the shell keeps g). */
+void orc_interpolate_cubic(const double *uc, int nc, double *uf, int nf)
+{
+    for (int k = 1; k <= nf - 2; ++k)
+        for (int j = 1; j <= nf - 2; ++j)
+            for (int i = 1; i <= nf - 2; ++i) {
+                int ix[4], iy[4], iz[4];
+                double wx[4], wy[4], wz[4];
+                const int nx = cubic_stencil(i, nc, ix, wx);
+                const int ny = cubic_stencil(j, nc, iy, wy);
+                const int nz = cubic_stencil(k, nc, iz, wz);
+                double s = 0.0;
+                for (int c = 0; c < nz; ++c)
+                    for (int b = 0; b < ny; ++b)
+                        for (int a = 0; a < nx; ++a)
+                            s += wz[c] * wy[b] * wx[a] * AT(uc, nc, ix[a], iy[b], iz[c]);
+                AT(uf, nf, i, j, k) = s;
+            }
+}
+
 /* Algorithm 1 step 5: b_H = S_H(w_H) + r_H on the coarse interior (S_H the
  * same discrete operator with step H, Section 3); 0 on the shell. */
 void orc_coarse_rhs(const double *wc, const double *rc, double *bc, int nc, double H)
@@ -440,6 +495,7 @@ typedef struct {
                             0: sweep until max|du| <= 1e-14 max|u| (cap 100)     */
     int ordering;        /* sweep ordering (ORC_COLOUR8 ...)                     */
     int approx_restrict; /* ORC_APPROX_INJECTION or ORC_APPROX_WEIGHTED            */
+    int fmg_interp;      /* ORC_FMG_TRILINEAR or ORC_FMG_CUBIC (Algorithm 2 step 4) */
 } orc_params;
 
 typedef struct { int n; double h; double *u, *rhs, *r, *w; } orc_level;
@@ -544,7 +600,10 @@ static void fmg(orc_hier *H, int l)
     orc_inject(F->rhs, F->n, C->rhs, C->n);    /* (2) b_H = injection of b_h */
     orc_inject(F->u, F->n, C->u, C->n);        /*     coarse Dirichlet data  */
     fmg(H, l + 1);                             /* (3) */
-    orc_interpolate(C->u, C->n, F->u, F->n);   /* (4) */
+    if (H->p.fmg_interp == ORC_FMG_CUBIC)      /* (4) */
+        orc_interpolate_cubic(C->u, C->n, F->u, F->n);
+    else
+        orc_interpolate(C->u, C->n, F->u, F->n);
     fas_vcycle(H, l);                          /* (5) */
 }
 
@@ -585,26 +644,37 @@ long orc_fmg(double *u, const double *f, int n, double h, const orc_params *p)
 }
 
 /* Solve to tolerance: optional FMG initialisation (init = 1), then V-cycles
- * until ||f - S_h(u)|| / ||f|| <= tol (norm kind over the fine interior) or
- * max_cycles.  res_hist[0..cycles] receives the relative residual before the
- * first cycle and after each one.  Returns the number of cycles, or -1. */
+ * until ||f - S_h(u)|| / ref <= tol (norm kind over the fine interior) or
+ * max_cycles.  ref_kind 0: ref = ||f||; 1: ref = the residual norm of the
+ * initial iterate (Section 4's relative residual ||r^l|| / ||r^0||; with FMG
+ * the initial iterate is the zero interior that FMG starts from).
+ * res_hist[0..cycles] receives the relative residual after the
+ * initialisation and after each cycle.  Returns the number of cycles, or -1. */
 int orc_solve(double *u, const double *f, int n, double h, const orc_params *p,
-              double tol, int norm, int max_cycles, int init, double *res_hist, long *events)
+              double tol, int norm, int max_cycles, int init, int ref_kind, double *res_hist, long *events)
 {
     orc_hier H;
     if (load(&H, u, f, n, h, p) != 0) return -1;
     orc_level *F = &H.lev[0];
+    double ref = orc_norm(f, n, h, norm);
+    if (ref_kind == 1) {
+        if (init)
+            for (int k = 1; k <= n - 2; ++k)
+                for (int j = 1; j <= n - 2; ++j)
+                    for (int i = 1; i <= n - 2; ++i) AT(F->u, n, i, j, k) = 0.0;
+        orc_residual(F->u, F->rhs, F->r, n, h);
+        ref = orc_norm(F->r, n, h, norm);
+    }
     if (init) fmg(&H, 0);
-    const double fn = orc_norm(f, n, h, norm);
     orc_residual(F->u, F->rhs, F->r, n, h);
-    double rel = orc_norm(F->r, n, h, norm) / fn;
+    double rel = orc_norm(F->r, n, h, norm) / ref;
     if (res_hist) res_hist[0] = rel;
     int c = 0;
     while (rel > tol && c < max_cycles) {
         fas_vcycle(&H, 0);
         ++c;
         orc_residual(F->u, F->rhs, F->r, n, h);
-        rel = orc_norm(F->r, n, h, norm) / fn;
+        rel = orc_norm(F->r, n, h, norm) / ref;
         if (res_hist) res_hist[c] = rel;
     }
     memcpy(u, F->u, sizeof(double) * (size_t)n * n * n);

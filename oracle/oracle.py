@@ -18,6 +18,8 @@ COLOUR8, LEXICOGRAPHIC, COLOUR8_REVERSED = 0, 1, 2
 HALF_WEIGHTING, FULL_WEIGHTING = 0, 1
 NORM_MAX, NORM_L2 = 0, 1
 APPROX_INJECTION, APPROX_WEIGHTED = 0, 1
+FMG_TRILINEAR, FMG_CUBIC = 0, 1
+REF_RHS, REF_INITIAL = 0, 1
 
 _lib = None
 _dp = C.POINTER(C.c_double)
@@ -26,14 +28,15 @@ _dp = C.POINTER(C.c_double)
 class _Params(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("coarsest_n", C.c_int),
                 ("restrict_kind", C.c_int), ("coarse_sweeps", C.c_int), ("ordering", C.c_int),
-                ("approx_restrict", C.c_int)]
+                ("approx_restrict", C.c_int), ("fmg_interp", C.c_int)]
 
 
 @dataclass
 class Params:
     """FAS parameters: V(nu1, nu2), coarsest grid size, residual restriction
-    kind, coarsest sweeps (0 = sweep to convergence), smoother ordering and the
-    approximation restriction (injection or the residual's weighting)."""
+    kind, coarsest sweeps (0 = sweep to convergence), smoother ordering, the
+    approximation restriction (injection or the residual's weighting) and the
+    FMG interpolation (trilinear or tricubic)."""
     nu1: int = 2
     nu2: int = 2
     coarsest_n: int = 3
@@ -41,10 +44,18 @@ class Params:
     coarse_sweeps: int = 0
     ordering: int = COLOUR8
     approx_restrict: int = APPROX_WEIGHTED
+    fmg_interp: int = FMG_TRILINEAR
 
     def c(self) -> _Params:
         return _Params(self.nu1, self.nu2, self.coarsest_n, self.restrict_kind,
-                       self.coarse_sweeps, self.ordering, self.approx_restrict)
+                       self.coarse_sweeps, self.ordering, self.approx_restrict, self.fmg_interp)
+
+
+def paper_params(ordering: int = LEXICOGRAPHIC) -> "Params":
+    """The settings of Section 4: V(2,2), h0 = 1/2 (3^3 coarsest grid) with one
+    Gauss-Seidel sweep, tricubic FMG interpolation (lexicographic ordering by
+    default, as the paper's smoother)."""
+    return Params(nu1=2, nu2=2, coarsest_n=3, coarse_sweeps=1, ordering=ordering, fmg_interp=FMG_CUBIC)
 
 
 def lib():
@@ -65,8 +76,9 @@ def lib():
         L.orc_inject.argtypes = [_dp, C.c_int, _dp, C.c_int]
         L.orc_prolong_add.restype = None
         L.orc_prolong_add.argtypes = [_dp, _dp, C.c_int, _dp, C.c_int]
-        L.orc_interpolate.restype = None
-        L.orc_interpolate.argtypes = [_dp, C.c_int, _dp, C.c_int]
+        for name in ("orc_interpolate", "orc_interpolate_cubic"):
+            getattr(L, name).restype = None
+            getattr(L, name).argtypes = [_dp, C.c_int, _dp, C.c_int]
         L.orc_coarse_rhs.restype = None
         L.orc_coarse_rhs.argtypes = [_dp, _dp, _dp, C.c_int, C.c_double]
         L.orc_vcycle.restype = C.c_long
@@ -75,7 +87,7 @@ def lib():
         L.orc_fmg.argtypes = [_dp, _dp, C.c_int, C.c_double, C.POINTER(_Params)]
         L.orc_solve.restype = C.c_int
         L.orc_solve.argtypes = [_dp, _dp, C.c_int, C.c_double, C.POINTER(_Params), C.c_double,
-                                C.c_int, C.c_int, C.c_int, _dp, C.POINTER(C.c_long)]
+                                C.c_int, C.c_int, C.c_int, C.c_int, _dp, C.POINTER(C.c_long)]
         L.orc_smallest_root.restype = C.c_double
         L.orc_smallest_root.argtypes = [_dp, C.c_double]
         L.orc_point_update.restype = C.c_double
@@ -159,6 +171,11 @@ def interpolate(uc: np.ndarray, uf: np.ndarray) -> None:
     lib().orc_interpolate(_p(uc), _grid(uc), _p(uf), _grid(uf))
 
 
+def interpolate_cubic(uc: np.ndarray, uf: np.ndarray) -> None:
+    """Fine interior of uf := tricubic interpolation of uc (Algorithm 2 step 4), in place."""
+    lib().orc_interpolate_cubic(_p(uc), _grid(uc), _p(uf), _grid(uf))
+
+
 def coarse_rhs(wc: np.ndarray, rc: np.ndarray, H: float) -> np.ndarray:
     bc = np.empty_like(wc)
     lib().orc_coarse_rhs(_p(wc), _p(rc), _p(bc), _grid(wc), H)
@@ -191,13 +208,16 @@ class SolveInfo:
 
 
 def solve(u: np.ndarray, f: np.ndarray, h: float, tol: float = 1e-10, norm_kind: int = NORM_MAX,
-          max_cycles: int = 50, init_fmg: bool = True, params: Params | None = None) -> SolveInfo:
-    """FMG init then V-cycles until ||f - S_h u|| / ||f|| <= tol, in place on u."""
+          max_cycles: int = 50, init_fmg: bool = True, params: Params | None = None,
+          ref: int = REF_RHS) -> SolveInfo:
+    """FMG init then V-cycles until ||f - S_h u|| / ref <= tol, in place on u;
+    ref = ||f|| (REF_RHS) or the residual norm of the initial iterate
+    (REF_INITIAL, the relative residual of Section 4)."""
     p = (params or Params()).c()
     hist = np.full(max_cycles + 1, np.nan)
     ev = C.c_long(0)
     c = lib().orc_solve(_p(u), _p(f), _grid(u), h, C.byref(p), tol, norm_kind, max_cycles,
-                        1 if init_fmg else 0, _p(hist), C.byref(ev))
+                        1 if init_fmg else 0, ref, _p(hist), C.byref(ev))
     if c < 0:
         raise ValueError("grid size does not coarsen to the coarsest grid")
     return SolveInfo(cycles=c, res_hist=hist[: c + 1], events=ev.value)

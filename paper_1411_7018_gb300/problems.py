@@ -14,6 +14,10 @@ Examples (Section 4):
   * ``quadratic``  u = |x|^2/2, f = 1 (the centred scheme is exact for it).
   * ``sine``       Example 5 on (0, pi)^3: u = -sum sin x_a + |x|^2/2,
                    f = prod (sin x_a + 1).
+  * ``ex6``        Example 6: u = |x|^{3/2} / 3, f = |x|^{-3/2} / 16 (singular at
+                   the corner x = 0, a boundary point).
+  * ``ex7``        Example 7: u = -sqrt(3 - |x|^2), f = 3 (3 - |x|^2)^{-5/2}
+                   (unbounded gradient at the corner x = (1, 1, 1)).
   * ``cosine``     |x|^2/2 plus eight seeded cosine modes (a synthetic
                    perturbation used for the GPU workloads; not in the paper):
                    u = |x|^2/2 + sum_m e_m / (4 pi^2 |k_m|^2) cos(2 pi k_m.x + phi_m)
@@ -113,6 +117,14 @@ def make_on_device(name: str, n: int, seed: int = 0, eps=0.02, device="cuda"):
     elif name == "quadratic":
         u = (x * x + y * y + z * z) / 2.0
         f = torch.ones_like(u)
+    elif name == "ex6":
+        s = x * x + y * y + z * z
+        u = s ** 0.75 / 3.0
+        f = torch.where(s > 0, s.clamp_min(1e-300) ** -0.75 / 16.0, torch.full_like(s, float("inf")))
+    elif name == "ex7":
+        s = 3.0 - (x * x + y * y + z * z)
+        u = -torch.sqrt(s)
+        f = torch.where(s > 0, 3.0 * s.clamp_min(1e-300) ** -2.5, torch.full_like(s, float("inf")))
     else:
         raise ValueError(f"unknown problem {name!r}")
     g = u.clone()
@@ -141,5 +153,19 @@ def make(name: str, n: int, seed: int = 0, eps=0.02) -> Problem:
     if name == "cosine":
         x, y, z = grid_coords(n)
         u, f = _cosine_fields(np, x, y, z, *cosine_modes(seed, eps))
+        return Problem(name, n, u=u, f=f)
+    if name == "ex6":
+        x, y, z = grid_coords(n)
+        s = x * x + y * y + z * z
+        u = s ** 0.75 / 3.0
+        with np.errstate(divide="ignore"):
+            f = np.where(s > 0, s ** -0.75 / 16.0, np.inf)   # f is only read on the interior
+        return Problem(name, n, u=u, f=f)
+    if name == "ex7":
+        x, y, z = grid_coords(n)
+        s = 3.0 - (x * x + y * y + z * z)
+        u = -np.sqrt(s)
+        with np.errstate(divide="ignore"):
+            f = np.where(s > 0, 3.0 * s ** -2.5, np.inf)
         return Problem(name, n, u=u, f=f)
     raise ValueError(f"unknown problem {name!r}")
