@@ -63,6 +63,15 @@ enum { MA_NORM_MAX = 0, MA_NORM_L2 = 1 };
 /* Initial iterate for ma_solve: one FMG pass (Algorithm 2), the Dirichlet
  * data with a zero interior, or the current iterate. */
 enum { MA_INIT_FMG = 0, MA_INIT_ZERO = 1, MA_INIT_KEEP = 2 };
+/* Interpolation of the FMG pass (Algorithm 2 step 4): trilinear, or the
+ * tricubic interpolation Section 3 recommends so that one FMG pass reaches
+ * discretisation accuracy (one-sided cubics next to the boundary). */
+enum { MA_FMG_TRILINEAR = 0, MA_FMG_CUBIC = 1 };
+/* Reference of the stopping rule: none (absolute), ||f|| over the interior,
+ * or the residual norm of the initial iterate (Section 4's relative residual
+ * ||r^l|| / ||r^0||; with MA_INIT_FMG or MA_INIT_ZERO the initial iterate is
+ * the Dirichlet data with a zero interior, which FMG starts from). */
+enum { MA_REL_NONE = 0, MA_REL_RHS = 1, MA_REL_INITIAL = 2 };
 
 /* A cudaStream_t (NULL = the legacy default stream). */
 typedef void *ma_stream_t;
@@ -84,21 +93,23 @@ typedef struct {
                             1); 0: sweep until max|du| <= 1e-14 max|u| (cap 100)        */
     int inner_cycles;    /* MA_MIXED: FP32 correction V-cycles per FP64 residual and
                             update (0: the default, 3); ignored in MA_FP64              */
+    int fmg_interp;      /* MA_FMG_TRILINEAR | MA_FMG_CUBIC                            */
 } ma_hier_desc;
 
 /* Stopping rule for ma_solve.  Converged when ||f - det(D^2_h u)|| <= tol *
- * (relative ? ||f|| : 1), norm over the fine interior, evaluated in FP64. */
+ * reference (MA_REL_*), norm over the fine interior, evaluated in FP64. */
 typedef struct {
     double tol;
     int norm;            /* MA_NORM_MAX | MA_NORM_L2                        */
-    int relative;        /* 1: relative to ||f|| on the interior; 0: absolute */
+    int relative;        /* MA_REL_NONE | MA_REL_RHS | MA_REL_INITIAL         */
     int max_cycles;      /* V-cycles (outer iterations in MA_MIXED) at most    */
     int init;            /* MA_INIT_FMG | MA_INIT_ZERO | MA_INIT_KEEP          */
 } ma_solve_opts;
 
 typedef struct {
     int cycles;                       /* V-cycles run after the initial iterate        */
-    double res0;                      /* residual norm of the initial iterate           */
+    double res0;                      /* residual norm after the initialisation (FMG)
+                                         over the reference, as res                     */
     double res;                       /* final residual norm (same scaling as tol)      */
     int status;                       /* the ma_status ma_solve returned                */
     int floor_reached;                /* 1 if stopped because the residual stagnated at
@@ -230,6 +241,16 @@ ma_status ma_prolong_add(const double *uc_dev, const double *wc_dev, int nc, dou
 /* Fine interior := trilinear interpolation of the coarse solution (Algorithm
  * 2 step 4 with trilinear in place of cubic interpolation); shell untouched. */
 ma_status ma_interpolate(const double *uc_dev, int nc, double *uf_dev, ma_stream_t stream);
+
+/* Device scratch bytes of ma_interpolate_cubic for a coarse grid of nc. */
+ma_status ma_interpolate_cubic_scratch_bytes(int nc, size_t *bytes);
+
+/* Fine interior := tricubic interpolation of the coarse solution (Algorithm
+ * 2 step 4, MA_FMG_CUBIC), as three one-axis passes through scratch_dev
+ * (>= ma_interpolate_cubic_scratch_bytes(nc) bytes, 8-byte aligned); the fine
+ * shell is untouched.  nc >= 3. */
+ma_status ma_interpolate_cubic(const double *uc_dev, int nc, double *uf_dev, void *scratch_dev, size_t scratch_bytes,
+                               ma_stream_t stream);
 
 /* Approximate solve on a coarsest grid (Algorithm 1 step 1), one thread
  * block: sweeps > 0 runs that many sweeps, 0 sweeps until

@@ -77,6 +77,8 @@ ma_status check_desc(const ma_hier_desc* d)
         return fail(MA_ERR_INVALID_ARG, "coarse_sweeps must be in [0, 1000]");
     if (d->inner_cycles < 0 || d->inner_cycles > 16)
         return fail(MA_ERR_INVALID_ARG, "inner_cycles must be in [0, 16]");
+    if (d->fmg_interp != MA_FMG_TRILINEAR && d->fmg_interp != MA_FMG_CUBIC)
+        return fail(MA_ERR_INVALID_ARG, "bad fmg_interp %d", d->fmg_interp);
     return MA_OK;
 }
 
@@ -171,7 +173,12 @@ cudaError_t fmg(ma_hierarchy* H, bool finest_vcycle = true)
     if ((e = ma::launch_zero_interior(B.u, B.n, s)) != cudaSuccess) return e;
     if ((e = ma::launch_coarsest(B.u, B.rhs, B.n, B.h, H->d.coarse_sweeps, H->events, s)) != cudaSuccess) return e;
     for (int l = H->L - 2; l >= 0; --l) {
-        if ((e = ma::launch_interpolate(H->lev[l + 1].u, H->lev[l + 1].n, H->lev[l].u, s)) != cudaSuccess) return e;
+        ma::Level& F = H->lev[l];
+        ma::Level& C = H->lev[l + 1];
+        // the fine level's r is free here and large enough for the cubic passes
+        e = H->d.fmg_interp == MA_FMG_CUBIC ? ma::launch_interpolate_cubic(C.u, C.n, F.u, F.r, s)
+                                            : ma::launch_interpolate(C.u, C.n, F.u, s);
+        if (e != cudaSuccess) return e;
         if (l == 0 && !finest_vcycle) break;
         if ((e = vcycle_from(H, l)) != cudaSuccess) return e;
     }
@@ -279,7 +286,8 @@ cudaError_t run_graph(ma_hierarchy* H, ma::GraphSlot& gs, F body)
 
 void destroy_graphs(ma_hierarchy* H)
 {
-    ma::GraphSlot* slots[4] = {&H->g_init[0], &H->g_init[1], &H->g_init[2], &H->g_cycle};
+    ma::GraphSlot* slots[7] = {&H->g_init[0], &H->g_init[1], &H->g_init[2], &H->g_init[3],
+                               &H->g_init[4], &H->g_init[5], &H->g_cycle};
     for (ma::GraphSlot* gs : slots) {
         if (gs->exec) cudaGraphExecDestroy(gs->exec);
         if (gs->graph) cudaGraphDestroy(gs->graph);
@@ -483,7 +491,7 @@ ma_status ma_set_solution(ma_hierarchy* H, const double* u_dev)
 static ma_status check_opts(const ma_solve_opts* o)
 {
     if (!(o->tol >= 0.0) || o->max_cycles < 0 || (o->norm != MA_NORM_MAX && o->norm != MA_NORM_L2) ||
-        o->init < MA_INIT_FMG || o->init > MA_INIT_KEEP)
+        o->init < MA_INIT_FMG || o->init > MA_INIT_KEEP || o->relative < MA_REL_NONE || o->relative > MA_REL_INITIAL)
         return fail(MA_ERR_INVALID_ARG, "bad solve options");
     return MA_OK;
 }
@@ -514,9 +522,18 @@ ma_status ma_solve_begin(ma_hierarchy* H, const ma_solve_opts* opts)
     // mixed precision the FMG pass stops at the interpolated finest iterate
     // and the FP32-corrected outer iterations take over from there.
     const int init = opts->init;
-    MA_CK(run_graph(H, H->g_init[init], [&]() -> cudaError_t {
+    const bool ref_initial = opts->relative == MA_REL_INITIAL;
+    MA_CK(run_graph(H, H->g_init[init + (ref_initial ? 3 : 0)], [&]() -> cudaError_t {
         ma::Level& F = H->lev[0];
-        cudaError_t e = ma::launch_norm_partials(F.rhs, F.n, H->partials, H->s);
+        cudaError_t e = cudaSuccess;
+        if (ref_initial) {
+            // reference: the residual of the initial iterate (zero interior
+            // unless the current iterate is kept)
+            if (init != MA_INIT_KEEP) e = ma::launch_zero_interior(F.u, F.n, H->s);
+            if (e == cudaSuccess) e = ma::launch_residual(F.u, F.rhs, F.r, F.n, F.h, H->partials, H->s);
+        } else {
+            e = ma::launch_norm_partials(F.rhs, F.n, H->partials, H->s);
+        }
         if (e == cudaSuccess) e = ma::launch_norm_final(H->partials, H->npartials, F.h, H->rb + 2, H->s);
         if (e == cudaSuccess && init == MA_INIT_FMG) e = fmg(H, !mixed);
         if (e == cudaSuccess && init == MA_INIT_ZERO) e = ma::launch_zero_interior(F.u, F.n, H->s);
@@ -746,6 +763,25 @@ ma_status ma_coarsest_solve(double* u, const double* rhs, int n, double h, int s
         return fail(MA_ERR_INVALID_ARG, "ma_coarsest_solve: bad arguments (n <= 17)");
     MA_CK(ma::prepare_kernels());
     MA_CK(ma::launch_coarsest(u, rhs, n, h, sweeps, events, (cudaStream_t)stream));
+    return MA_OK;
+}
+
+ma_status ma_interpolate_cubic_scratch_bytes(int nc, size_t* bytes)
+{
+    if (!bytes || nc < 3 || nc > 2049) return fail(MA_ERR_INVALID_ARG, "ma_interpolate_cubic_scratch_bytes: bad arguments");
+    *bytes = ma::interpolate_cubic_scratch(nc);
+    return MA_OK;
+}
+
+ma_status ma_interpolate_cubic(const double* uc, int nc, double* uf, void* scratch, size_t scratch_bytes,
+                               ma_stream_t stream)
+{
+    if (!uc || !uf || !scratch || nc < 3 || nc > 2049 || ((uintptr_t)scratch) % 8 != 0)
+        return fail(MA_ERR_INVALID_ARG, "ma_interpolate_cubic: bad arguments");
+    if (scratch_bytes < ma::interpolate_cubic_scratch(nc))
+        return fail(MA_ERR_INVALID_ARG, "ma_interpolate_cubic: scratch %zu < %zu bytes", scratch_bytes,
+                    ma::interpolate_cubic_scratch(nc));
+    MA_CK(ma::launch_interpolate_cubic(uc, nc, uf, (double*)scratch, (cudaStream_t)stream));
     return MA_OK;
 }
 

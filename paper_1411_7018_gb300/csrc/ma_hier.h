@@ -60,7 +60,7 @@ struct ma_hierarchy {
     int* flag = nullptr;                 // device: input validation count
     double* host = nullptr;              // pinned host copy of the read-back block
     cudaStream_t cap = nullptr;          // private stream the graphs are captured on
-    ma::GraphSlot g_init[3];             // per ma_solve init kind: init + first residual norm
+    ma::GraphSlot g_init[6];             // per ma_solve init kind (and reference kind): init + first residual norm
     ma::GraphSlot g_cycle;               // one cycle + residual norm
     // Non-blocking solve state (ma_solve_begin / ma_solve_advance).
     struct {

@@ -36,6 +36,8 @@ cudaError_t launch_coarse_rhs(const double* wc, const double* rc, double* bc, in
                               cudaStream_t s);
 cudaError_t launch_prolong_add(const double* uc, const double* wc, int nc, double* uf, cudaStream_t s);
 cudaError_t launch_interpolate(const double* uc, int nc, double* uf, cudaStream_t s);
+size_t interpolate_cubic_scratch(int nc);
+cudaError_t launch_interpolate_cubic(const double* uc, int nc, double* uf, double* scratch, cudaStream_t s);
 cudaError_t launch_inject(const double* vf, int nf, double* vc, cudaStream_t s);
 cudaError_t launch_zero_interior(double* u, int n, cudaStream_t s);
 cudaError_t launch_coarsest(double* u, const double* rhs, int n, double h, int sweeps,

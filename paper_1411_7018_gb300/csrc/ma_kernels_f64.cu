@@ -366,6 +366,27 @@ cudaError_t launch_interpolate(const double* uc, int nc, double* uf, cudaStream_
     return cudaGetLastError();
 }
 
+size_t interpolate_cubic_scratch(int nc)
+{
+    const size_t nf = 2 * (size_t)nc - 1;
+    return sizeof(double) * (nf * nc * nc + nf * nf * nc);
+}
+
+// Tricubic interpolation (Algorithm 2 step 4): passes x, y, z through the
+// scratch t (interpolate_cubic_scratch(nc) bytes); the fine shell is kept.
+cudaError_t launch_interpolate_cubic(const double* uc, int nc, double* uf, double* t, cudaStream_t s)
+{
+    const int nf = 2 * nc - 1;
+    double* t1 = t;                                  // nc x nc x nf
+    double* t2 = t + (size_t)nf * nc * nc;           // nc x nf x nf
+    auto grid = [](int ox, int oy, int oz) { return dim3((ox + BX - 1) / BX, (oy + BY - 1) / BY, oz); };
+    count_launches(3);
+    xfer::k_cubic_pass<0><<<grid(nf, nc, nc), dim3(BX, BY), 0, s>>>(uc, t1, nc, nf, nc, nc, 0);
+    xfer::k_cubic_pass<1><<<grid(nf, nf, nc), dim3(BX, BY), 0, s>>>(t1, t2, nc, nf, nf, nc, 0);
+    xfer::k_cubic_pass<2><<<grid(nf, nf, nf), dim3(BX, BY), 0, s>>>(t2, uf, nc, nf, nf, nf, 1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_inject(const double* vf, int nf, double* vc, cudaStream_t s)
 {
     const int nc = (nf + 1) / 2;

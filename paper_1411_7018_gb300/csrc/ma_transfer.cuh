@@ -112,6 +112,73 @@ inline dim3 prolong_grid(int nf)
     return dim3((nc - 1 + BX - 1) / BX, (nf - 2 + BY - 1) / BY, nf - 2);
 }
 
+// Cubic interpolation (Algorithm 2 step 4) as three 1-D passes, x then y
+// then z.  Along an axis, fine index i on a coarse grid of nc points: even i
+// is coarse point i/2; odd i, halfway between coarse I0 = (i-1)/2 and I0 + 1,
+// takes the cubic through four coarse neighbours -- I0-1 .. I0+2 with weights
+// (-1, 9, 9, -1)/16, or the four nearest ones next to either end ((5, 15, -5,
+// 1)/16 from the left end, mirrored at the right) -- a 3-point grid the
+// quadratic (3, 6, -1)/8 (mirrored for the second interval), a 2-point grid
+// the midpoint.  Returns the first coarse index and fills up to 4 weights.
+__device__ __forceinline__ int cubic_axis(int i, int nc, double w[4], int* cnt)
+{
+    if ((i & 1) == 0) {
+        w[0] = 1.0;
+        *cnt = 1;
+        return i >> 1;
+    }
+    const int I0 = i >> 1;
+    if (nc == 2) {
+        w[0] = w[1] = 0.5;
+        *cnt = 2;
+        return 0;
+    }
+    if (nc == 3) {
+        *cnt = 3;
+        if (I0 == 0) { w[0] = 0.375; w[1] = 0.75; w[2] = -0.125; }
+        else { w[0] = -0.125; w[1] = 0.75; w[2] = 0.375; }
+        return 0;
+    }
+    *cnt = 4;
+    if (I0 == 0) {
+        w[0] = 0.3125; w[1] = 0.9375; w[2] = -0.3125; w[3] = 0.0625;
+        return 0;
+    }
+    if (I0 == nc - 2) {
+        w[0] = 0.0625; w[1] = -0.3125; w[2] = 0.9375; w[3] = 0.3125;
+        return nc - 4;
+    }
+    w[0] = -0.0625; w[1] = 0.5625; w[2] = 0.5625; w[3] = -0.0625;
+    return I0 - 1;
+}
+
+// One pass along axis AX (0 = x, 1 = y, 2 = z): out has dims ox x oy x oz
+// ([z][y][x], x fastest), in has the same dims except nc along AX.  A thread
+// per output point (threads run along x); interior_only writes only points
+// with every index in 1 .. dim-2 (the last pass, which keeps the Dirichlet
+// shell of the target).
+template <int AX>
+__global__ void __launch_bounds__(BX * BY) k_cubic_pass(const double* __restrict__ in, double* __restrict__ out,
+                                                        int nc, int ox, int oy, int oz, int interior_only)
+{
+    const int x = blockIdx.x * BX + threadIdx.x;
+    const int y = blockIdx.y * BY + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= ox || y >= oy) return;
+    if (interior_only && (x < 1 || x > ox - 2 || y < 1 || y > oy - 2 || z < 1 || z > oz - 2)) return;
+    const int ix = AX == 0 ? nc : ox, iy = AX == 1 ? nc : oy;
+    const int a = AX == 0 ? x : (AX == 1 ? y : z);
+    double w[4];
+    int cnt;
+    const int I = cubic_axis(a, nc, w, &cnt);
+    const long long step = AX == 0 ? 1 : (AX == 1 ? (long long)ix : (long long)ix * iy);
+    const int xi = AX == 0 ? I : x, yi = AX == 1 ? I : y, zi = AX == 2 ? I : z;
+    const double* src = in + ((long long)zi * iy + yi) * ix + xi;
+    double s = w[0] * src[0];
+    for (int q = 1; q < cnt; ++q) s = fma(w[q], src[q * step], s);
+    out[((long long)z * oy + y) * ox + x] = s;
+}
+
 template <typename T>
 __global__ void k_inject(const T* __restrict__ vf, int nf, T* __restrict__ vc, int nc)
 {

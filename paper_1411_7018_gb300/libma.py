@@ -20,6 +20,8 @@ MA_APPROX_INJECTION, MA_APPROX_WEIGHTED = 0, 1
 MA_FP64, MA_MIXED = 0, 1
 MA_NORM_MAX, MA_NORM_L2 = 0, 1
 MA_INIT_FMG, MA_INIT_ZERO, MA_INIT_KEEP = 0, 1, 2
+MA_FMG_TRILINEAR, MA_FMG_CUBIC = 0, 1
+MA_REL_NONE, MA_REL_RHS, MA_REL_INITIAL = 0, 1, 2
 MA_CORR_BY_COLOUR, MA_CORR_PLANE16, MA_CORR_PLANE32, MA_CORR_PLANE64 = 0, 1, 2, 3
 CORR_NAMES = {MA_CORR_BY_COLOUR: "by_colour", MA_CORR_PLANE16: "plane16", MA_CORR_PLANE32: "plane32",
               MA_CORR_PLANE64: "plane64"}
@@ -38,7 +40,7 @@ class ma_hier_desc(C.Structure):
     _fields_ = [("n", C.c_int), ("x0", C.c_double * 3), ("len", C.c_double), ("nu1", C.c_int),
                 ("nu2", C.c_int), ("coarsest_n", C.c_int), ("restrict_kind", C.c_int),
                 ("approx_restrict", C.c_int), ("precision", C.c_int), ("coarse_sweeps", C.c_int),
-                ("inner_cycles", C.c_int)]
+                ("inner_cycles", C.c_int), ("fmg_interp", C.c_int)]
 
 
 class ma_solve_opts(C.Structure):
@@ -83,6 +85,8 @@ _SIGS = {
     "ma_residual_correction": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp, C.c_size_t, _vp],
     "ma_norm_static": [_vp, C.c_int, C.c_double, C.POINTER(C.c_double), _vp],
     "ma_set_corr_tuning": [C.c_int, C.c_int, C.c_int],
+    "ma_interpolate_cubic_scratch_bytes": [C.c_int, C.POINTER(C.c_size_t)],
+    "ma_interpolate_cubic": [_vp, C.c_int, _vp, _vp, C.c_size_t, _vp],
     "ma_get_corr_tuning": [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "ma_tune_corr": [_vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp, C.c_size_t, C.POINTER(C.c_double),
                      C.POINTER(C.c_double), _vp],
@@ -258,6 +262,16 @@ def ma_interpolate(uc, nc: int, uf, stream=None) -> None:
     _check(load().ma_interpolate(_ptr(uc), nc, _ptr(uf), _stream(stream)))
 
 
+def ma_interpolate_cubic_scratch_bytes(nc: int) -> int:
+    b = C.c_size_t(0)
+    _check(load().ma_interpolate_cubic_scratch_bytes(nc, C.byref(b)))
+    return b.value
+
+
+def ma_interpolate_cubic(uc, nc: int, uf, scratch, scratch_bytes: int, stream=None) -> None:
+    _check(load().ma_interpolate_cubic(_ptr(uc), nc, _ptr(uf), _ptr(scratch), scratch_bytes, _stream(stream)))
+
+
 def ma_coarsest_solve(u, rhs, n: int, h: float, sweeps: int = 0, events=None, stream=None) -> None:
     _check(load().ma_coarsest_solve(_ptr(u), _ptr(rhs), n, h, sweeps, _ptr(events), _stream(stream)))
 
@@ -390,7 +404,7 @@ class SolveResult:
 def make_desc(n: int, length: float = 1.0, x0=(0.0, 0.0, 0.0), nu1: int = 2, nu2: int = 2,
               coarsest_n: int = 3, restrict_kind: int = MA_FULL_WEIGHTING,
               approx_restrict: int = MA_APPROX_WEIGHTED, precision: int = MA_FP64,
-              coarse_sweeps: int = 0, inner_cycles: int = 0) -> ma_hier_desc:
+              coarse_sweeps: int = 0, inner_cycles: int = 0, fmg_interp: int = MA_FMG_TRILINEAR) -> ma_hier_desc:
     d = ma_hier_desc()
     d.n = n
     d.x0[0], d.x0[1], d.x0[2] = x0
@@ -402,7 +416,15 @@ def make_desc(n: int, length: float = 1.0, x0=(0.0, 0.0, 0.0), nu1: int = 2, nu2
     d.precision = precision
     d.coarse_sweeps = coarse_sweeps
     d.inner_cycles = inner_cycles
+    d.fmg_interp = fmg_interp
     return d
+
+
+def paper_desc(n: int, length: float = 1.0, precision: int = MA_FP64) -> ma_hier_desc:
+    """The settings of Section 4 on the GPU: V(2,2), h0 = 1/2 (3^3) with one
+    sweep, tricubic FMG interpolation; full-weighting restriction (the
+    8-colour smoother diverges with half weighting from 33^3 up)."""
+    return make_desc(n, length=length, coarsest_n=3, coarse_sweeps=1, precision=precision, fmg_interp=MA_FMG_CUBIC)
 
 
 class Hierarchy:
@@ -425,9 +447,11 @@ class Hierarchy:
     def vcycle(self, ncycles: int = 1):
         ma_vcycle(self.handle, ncycles)
 
-    def solve(self, tol: float = 1e-10, norm: int = MA_NORM_MAX, relative: bool = True,
+    def solve(self, tol: float = 1e-10, norm: int = MA_NORM_MAX, relative=True,
               max_cycles: int = 50, init: int = MA_INIT_FMG, raise_on_error: bool = True) -> SolveResult:
-        o = ma_solve_opts(tol, norm, 1 if relative else 0, max_cycles, init)
+        """relative: True / MA_REL_RHS (||f||), False / MA_REL_NONE, or MA_REL_INITIAL."""
+        rel = int(relative) if not isinstance(relative, bool) else (MA_REL_RHS if relative else MA_REL_NONE)
+        o = ma_solve_opts(tol, norm, rel, max_cycles, init)
         r = ma_solve(self.handle, o, raise_on_error)
         return SolveResult(r.cycles, r.res0, r.res, r.status, bool(r.floor_reached), r.nonconvex_root_events)
 
