@@ -85,6 +85,18 @@ _SIGS = {
     "ma_residual_correction": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp, C.c_size_t, _vp],
     "ma_norm_static": [_vp, C.c_int, C.c_double, C.POINTER(C.c_double), _vp],
     "ma_set_corr_tuning": [C.c_int, C.c_int, C.c_int],
+    "ma2d_hierarchy_footprint": [C.c_void_p, C.POINTER(C.c_size_t)],
+    "ma2d_create_hierarchy": [C.c_void_p, _vp, C.c_size_t, _vp, C.POINTER(_vp)],
+    "ma2d_set_rhs_bc": [_vp, _vp, _vp],
+    "ma2d_vcycle": [_vp, C.c_int],
+    "ma2d_solve": [_vp, C.POINTER(ma_solve_opts), C.POINTER(ma_solve_result)],
+    "ma2d_get_solution": [_vp, _vp],
+    "ma2d_destroy_hierarchy": [_vp],
+    "ma2d_smooth": [_vp, _vp, C.c_int, C.c_double, C.c_int, C.c_int, _vp, _vp, _vp],
+    "ma2d_residual": [_vp, _vp, _vp, C.c_int, C.c_double, _vp],
+    "ma2d_restrict_residual": [_vp, C.c_int, _vp, C.c_int, _vp],
+    "ma2d_prolong_add": [_vp, _vp, C.c_int, _vp, _vp],
+    "ma2d_interpolate": [_vp, C.c_int, _vp, C.c_int, _vp],
     "ma_interpolate_cubic_scratch_bytes": [C.c_int, C.POINTER(C.c_size_t)],
     "ma_interpolate_cubic": [_vp, C.c_int, _vp, _vp, C.c_size_t, _vp],
     "ma_get_corr_tuning": [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)],
@@ -474,3 +486,91 @@ class Hierarchy:
             self.close()
         except Exception:
             pass
+
+
+# ---- the 2D version of the method (include/ma2d.h) ------------------------------
+
+MA2D_REDBLACK, MA2D_COLOUR4 = 0, 2
+
+
+class ma2d_desc(C.Structure):
+    _fields_ = [("n", C.c_int), ("len", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int), ("coarsest_n", C.c_int),
+                ("restrict_kind", C.c_int), ("approx_restrict", C.c_int), ("coarse_sweeps", C.c_int),
+                ("ordering", C.c_int), ("fmg_interp", C.c_int)]
+
+
+def make_desc2d(n: int, length: float = 1.0, nu1: int = 2, nu2: int = 2, coarsest_n: int = 3,
+                restrict_kind: int = MA_FULL_WEIGHTING, approx_restrict: int = MA_APPROX_WEIGHTED,
+                coarse_sweeps: int = 0, ordering: int = MA2D_REDBLACK, fmg_interp: int = MA_FMG_TRILINEAR):
+    return ma2d_desc(n, length, nu1, nu2, coarsest_n, restrict_kind, approx_restrict, coarse_sweeps, ordering,
+                     fmg_interp)
+
+
+def paper_desc2d(n: int, ordering: int = MA2D_REDBLACK):
+    """Section 4's settings in 2D: V(2,2), h0 = 1/2 with one sweep, bicubic FMG,
+    full weighting (the weighting the errors of Table 1 match)."""
+    return make_desc2d(n, coarsest_n=3, coarse_sweeps=1, ordering=ordering, fmg_interp=MA_FMG_CUBIC)
+
+
+class Hierarchy2D:
+    """A 2D hierarchy in a torch-owned device workspace, on one stream."""
+
+    def __init__(self, desc, stream=None, device=None):
+        import torch
+        self.desc = desc
+        self.device = device or torch.device("cuda")
+        b = C.c_size_t(0)
+        _check(load().ma2d_hierarchy_footprint(C.byref(desc), C.byref(b)))
+        self.nbytes = b.value
+        self.ws = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+        addr = (self.ws.data_ptr() + 255) // 256 * 256
+        self.stream = stream
+        h = _vp()
+        _check(load().ma2d_create_hierarchy(C.byref(desc), addr, self.nbytes, _stream(stream), C.byref(h)))
+        self.handle = h.value
+
+    def set_rhs_bc(self, f, g):
+        _check(load().ma2d_set_rhs_bc(self.handle, _ptr(f), _ptr(g)))
+
+    def vcycle(self, n: int = 1):
+        _check(load().ma2d_vcycle(self.handle, n))
+
+    def solve(self, tol: float = 1e-10, norm: int = MA_NORM_MAX, relative=True, max_cycles: int = 50,
+              init: int = MA_INIT_FMG, raise_on_error: bool = True):
+        rel = int(relative) if not isinstance(relative, bool) else (MA_REL_RHS if relative else MA_REL_NONE)
+        o = ma_solve_opts(tol, norm, rel, max_cycles, init)
+        r = ma_solve_result()
+        st = load().ma2d_solve(self.handle, C.byref(o), C.byref(r))
+        if raise_on_error:
+            _check(st)
+        return SolveResult(r.cycles, r.res0, r.res, r.status, bool(r.floor_reached), r.nonconvex_root_events)
+
+    def get_solution(self, out):
+        _check(load().ma2d_get_solution(self.handle, _ptr(out)))
+
+    def close(self):
+        if self.handle:
+            _check(load().ma2d_destroy_hierarchy(self.handle))
+            self.handle = None
+
+
+def ma2d_smooth(u, rhs, n: int, h: float, nsweeps: int, ordering: int = MA2D_REDBLACK, scratch=None, events=None,
+                stream=None):
+    _check(load().ma2d_smooth(_ptr(u), _ptr(rhs), n, h, nsweeps, ordering, _ptr(scratch), _ptr(events),
+                              _stream(stream)))
+
+
+def ma2d_residual(u, rhs, r, n: int, h: float, stream=None):
+    _check(load().ma2d_residual(_ptr(u), _ptr(rhs), _ptr(r), n, h, _stream(stream)))
+
+
+def ma2d_restrict_residual(rf, nf: int, rc, kind: int = MA_FULL_WEIGHTING, stream=None):
+    _check(load().ma2d_restrict_residual(_ptr(rf), nf, _ptr(rc), kind, _stream(stream)))
+
+
+def ma2d_prolong_add(uc, wc, nc: int, uf, stream=None):
+    _check(load().ma2d_prolong_add(_ptr(uc), _ptr(wc), nc, _ptr(uf), _stream(stream)))
+
+
+def ma2d_interpolate(uc, nc: int, uf, cubic: bool = False, stream=None):
+    _check(load().ma2d_interpolate(_ptr(uc), nc, _ptr(uf), 1 if cubic else 0, _stream(stream)))

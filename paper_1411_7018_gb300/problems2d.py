@@ -65,3 +65,28 @@ def make2d(name: str, n: int) -> Problem2D:
         else:
             raise ValueError(f"unknown 2D problem {name!r}")
     return Problem2D(name, n, u=u, f=f)
+
+
+def make2d_on_device(name: str, n: int, device="cuda"):
+    """(u_exact, f, g) as float64 torch tensors on `device` (g = u on the
+    boundary, 0 inside): the problems of make2d evaluated with torch, for grids
+    too large to build on the host."""
+    import torch
+    t = torch.arange(n, dtype=torch.float64, device=device) / (n - 1)
+    y, x = torch.meshgrid(t, t, indexing="ij")
+    s = x * x + y * y
+    if name == "ex1":
+        u, f = torch.exp(s / 2.0), (1.0 + s) * torch.exp(s)
+    elif name == "ex2":
+        u = (2.0 * 2.0 ** 0.5 / 3.0) * s ** 0.75
+        f = torch.where(s > 0, 1.0 / torch.sqrt(s.clamp_min(1e-300)), torch.full_like(s, float("inf")))
+    elif name == "ex3":
+        u = -torch.sqrt(2.0 - s)
+        f = torch.where(s < 2.0, 2.0 / (2.0 - s).clamp_min(1e-300) ** 2, torch.full_like(s, float("inf")))
+    elif name == "quadratic":
+        u, f = s / 2.0, torch.ones_like(s)
+    else:
+        raise ValueError(f"unknown 2D problem {name!r}")
+    g = u.clone()
+    g[1:-1, 1:-1] = 0.0
+    return u.contiguous(), f.contiguous(), g.contiguous()
