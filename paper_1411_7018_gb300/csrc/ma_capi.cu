@@ -519,8 +519,9 @@ ma_status ma_solve_begin(ma_hierarchy* H, const ma_solve_opts* opts)
     MA_CK(cudaMemsetAsync(H->events, 0, sizeof(unsigned long long), H->s));
     const bool mixed = H->d.precision == MA_MIXED;
     // rhs norms, the initial iterate and its residual norm as one graph.  In
-    // mixed precision the FMG pass stops at the interpolated finest iterate
-    // and the FP32-corrected outer iterations take over from there.
+    // mixed precision the FMG pass runs its FP64 V-cycles below the finest
+    // level and completes with one outer iteration (FP32 correction cycles
+    // and the FP64 update) in place of the finest FP64 V-cycle.
     const int init = opts->init;
     const bool ref_initial = opts->relative == MA_REL_INITIAL;
     MA_CK(run_graph(H, H->g_init[init + (ref_initial ? 3 : 0)], [&]() -> cudaError_t {
@@ -540,6 +541,14 @@ ma_status ma_solve_begin(ma_hierarchy* H, const ma_solve_opts* opts)
         if (e != cudaSuccess) return e;
         if (mixed) {
             if ((e = refresh_base(H, 0)) != cudaSuccess) return e;
+            if ((e = mixed_residual(H)) != cudaSuccess) return e;
+            if (init != MA_INIT_FMG) return cudaSuccess;
+            // Algorithm 2 step 5 on the finest level: one outer iteration
+            // (the FP32 correction cycles) completes the FMG pass
+            const int inner = H->d.inner_cycles > 0 ? H->d.inner_cycles : 3;
+            for (int c = 0; c < inner; ++c)
+                if ((e = corr_vcycle(H)) != cudaSuccess) return e;
+            if ((e = refresh_base(H, 1)) != cudaSuccess) return e;
             return mixed_residual(H);
         }
         if ((e = ma::launch_residual(F.u, F.rhs, F.r, F.n, F.h, H->partials, H->s)) != cudaSuccess) return e;

@@ -136,18 +136,111 @@ __device__ __forceinline__ bool corr_root_fast(const S3f& B, const S3f& K, float
     return false;
 }
 
-// FP64 path on the same data (near-degenerate or indefinite G, or no FP32
-// convergence): the target is det(G - zI) = det(B) + r; rhs <= 0 takes the
-// smallest real root of the cubic and sets *nonconvex.
+// The correction cubic in FP64 from the FP32 data: with G = B + K,
+//     F(z) = det(G - zI) - det(B) - r = c - M z + T z^2 - z^3,
+// c = tr(cof(B) K) + tr(B cof(K)) + det(K) - r, evaluated without the
+// subtraction of two O(f) numbers (det(B) in FP32 would put an error of
+// ~1e-7 f into the target and stall defect correction there).
+struct CorrCubic {
+    double c, M, T, tot;   // tot = det(B) + r = det(G) - c: the sign decides the branch
+    double g[6];           // G: xx, yy, zz, xy, xz, yz
+};
+
+__device__ __forceinline__ double cof_dot_d(const double* A, const double* X)
+{
+    const double cxx = A[1] * A[2] - A[5] * A[5];
+    const double cyy = A[0] * A[2] - A[4] * A[4];
+    const double czz = A[0] * A[1] - A[3] * A[3];
+    const double cxy = A[4] * A[5] - A[3] * A[2];
+    const double cxz = A[3] * A[5] - A[4] * A[1];
+    const double cyz = A[3] * A[4] - A[0] * A[5];
+    return cxx * X[0] + cyy * X[1] + czz * X[2] + 2.0 * (cxy * X[3] + cxz * X[4] + cyz * X[5]);
+}
+
+__device__ __forceinline__ double det3_d(const double* A)
+{
+    return A[0] * (A[1] * A[2] - A[5] * A[5]) - A[3] * (A[3] * A[2] - A[4] * A[5]) +
+           A[4] * (A[3] * A[5] - A[1] * A[4]);
+}
+
+__device__ __forceinline__ CorrCubic corr_cubic(const S3f& B, const S3f& K, float r)
+{
+    const double b[6] = {B.xx, B.yy, B.zz, B.xy, B.xz, B.yz};
+    const double k[6] = {K.xx, K.yy, K.zz, K.xy, K.xz, K.yz};
+    CorrCubic C;
+    for (int q = 0; q < 6; ++q) C.g[q] = b[q] + k[q];
+    C.c = cof_dot_d(b, k) + cof_dot_d(k, b) + det3_d(k) - (double)r;
+    C.T = C.g[0] + C.g[1] + C.g[2];
+    C.M = (C.g[0] * C.g[1] - C.g[3] * C.g[3]) + (C.g[0] * C.g[2] - C.g[4] * C.g[4]) +
+          (C.g[1] * C.g[2] - C.g[5] * C.g[5]);
+    C.tot = det3_d(C.g) - C.c;
+    return C;
+}
+
+__device__ __forceinline__ double corr_F(const CorrCubic& C, double z) { return C.c - z * (C.M - z * (C.T - z)); }
+__device__ __forceinline__ double corr_Mz(const CorrCubic& C, double z) { return C.M - z * (2.0 * C.T - 3.0 * z); }
+
+// FP64 path (near-degenerate or indefinite G, or no FP32 convergence).
+// tot > 0: F is decreasing and convex left of the smallest eigenvalue of G
+// and has its unique root there; monotone Newton from the Gershgorin bound
+// minus tot^(1/3), where F >= 0.  tot <= 0: Eq. (realroots) taken
+// literally, the smallest real root of the cubic (trigonometric form for three
+// real roots, Cardano's formula for one, two Newton polishes), counted in
+// *nonconvex.
 __device__ __noinline__ float corr_root_slow(S3f B, S3f K, float r, bool* nonconvex)
 {
-    HessS H;
-    H.A = B.xx + K.xx; H.B = B.yy + K.yy; H.C = B.zz + K.zz;
-    H.R = B.xy + K.xy; H.S = B.xz + K.xz; H.T = B.yz + K.yz;
-    const double tot = (double)det3(B) + (double)r;
-    if (tot > 0.0) return (float)root_f64_monotone(H, tot);
+    const CorrCubic C = corr_cubic(B, K, r);
+    if (C.tot > 0.0) {
+        const double g0 = C.g[0] - fabs(C.g[3]) - fabs(C.g[4]);
+        const double g1 = C.g[1] - fabs(C.g[3]) - fabs(C.g[5]);
+        const double g2 = C.g[2] - fabs(C.g[4]) - fabs(C.g[5]);
+        double z = fmin(g0, fmin(g1, g2)) - cbrt(C.tot);
+        for (int it = 0; it < 200; ++it) {
+            const double F = corr_F(C, z);
+            const double m = corr_Mz(C, z);
+            if (!(F > 0.0) || !(m > 0.0)) break;
+            const double zn = z + F / m;
+            if (!(zn > z)) break;
+            z = zn;
+        }
+        return (float)z;
+    }
     *nonconvex = true;
-    return (float)root_f64_all_real_min(H, tot);
+    // z^3 + a2 z^2 + a1 z + a0 = -F(z)
+    const double a2 = -C.T, a1 = C.M, a0 = -C.c;
+    const double p = a1 - a2 * a2 / 3.0;
+    const double q = 2.0 * a2 * a2 * a2 / 27.0 - a2 * a1 / 3.0 + a0;
+    const double disc = 0.25 * q * q + p * p * p / 27.0;
+    double roots[3];
+    int nr;
+    if (p < 0.0 && disc <= 0.0) {
+        const double m = 2.0 * sqrt(-p / 3.0);
+        double arg = 1.5 * q / p * sqrt(-3.0 / p);
+        arg = fmin(1.0, fmax(-1.0, arg));
+        const double phi = acos(arg) / 3.0;
+        const double tp = 2.0943951023931954923;   // 2 pi / 3
+        roots[0] = m * cos(phi) - a2 / 3.0;
+        roots[1] = m * cos(phi - tp) - a2 / 3.0;
+        roots[2] = m * cos(phi - 2.0 * tp) - a2 / 3.0;
+        nr = 3;
+    } else {
+        const double sq = sqrt(fmax(disc, 0.0));
+        roots[0] = cbrt(-0.5 * q + sq) + cbrt(-0.5 * q - sq) - a2 / 3.0;
+        nr = 1;
+    }
+    double best = INFINITY;
+    for (int k = 0; k < nr; ++k) {
+        double z = roots[k];
+        for (int it = 0; it < 2; ++it) {
+            const double m = corr_Mz(C, z);
+            if (m == 0.0) break;
+            const double zn = z + corr_F(C, z) / m;
+            if (!isfinite(zn)) break;
+            z = zn;
+        }
+        best = fmin(best, z);
+    }
+    return (float)best;
 }
 
 __device__ __forceinline__ float corr_root(const S3f& B, const S3f& K, float r, bool* nonconvex)
