@@ -209,6 +209,41 @@ def bench_paper_mode(args, M, problems, dev):
     return out
 
 
+def bench_fp32_mode(args, M, problems, dev):
+    """The full-FP32 mode on Example 4 at 129^3 and 257^3: time, the FP32
+    residual floor it stops at, and its error against the exact solution and
+    against the FP64 discrete solution (the round-off floor per N)."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    out = {"mode": "FP32 FAS cycles on the solution, stop at the FP32 residual floor (3 stagnant cycles)"}
+    for n in (129, 257):
+        f, g, length = problems.make_on_device("exp", n, device=dev)
+        u_ex = torch.from_numpy(problems.make("exp", n).u).to(dev)
+        res = {}
+        for prec, key in ((M.MA_FP64, "fp64"), (M.MA_FP32, "fp32")):
+            H = M.Hierarchy(M.make_desc(n, length=length, precision=prec), device=dev)
+            ts = []
+            for _ in range(3):
+                H.set_rhs_bc(f, g)
+                ms, r = _timed_solve(H, torch, stream, tol=1e-10 if prec == M.MA_FP64 else 1e-12, max_cycles=40,
+                                     raise_on_error=False)
+                ts.append(ms)
+            u = torch.empty_like(f)
+            H.get_solution(u)
+            H.close()
+            res[key] = (u, r, min(ts))
+        u32, r32, ms32 = res["fp32"]
+        umax = u_ex.abs().max().item()
+        out[str(n)] = {"ms": ms32, "unknowns_per_s": (n - 2) ** 3 / (ms32 / 1e3), "cycles": r32.cycles,
+                       "residual_floor": r32.res, "error_vs_exact": (u32 - u_ex).abs().max().item(),
+                       "fp64_error_vs_exact": (res["fp64"][0] - u_ex).abs().max().item(),
+                       "rel_diff_vs_fp64_solution": (u32 - res["fp64"][0]).abs().max().item() / umax,
+                       "fp64_ms": res["fp64"][2]}
+        del f, g, u_ex, res, u32
+        torch.cuda.empty_cache()
+    return out
+
+
 def bench_2d(args, M, problems, dev):
     """The 2D version (Section 4.1): Example 1 at N = 8192 in Section 4's
     configuration (red-black smoother, bicubic FMG), against Table 1's row
@@ -467,7 +502,7 @@ def main():
     extras = {}
     if world == 1:
         for name, fn in (("batching", bench_batching), ("serving", bench_serving), ("paper_mode", bench_paper_mode),
-                         ("two_d", bench_2d)):
+                         ("two_d", bench_2d), ("fp32_mode", bench_fp32_mode)):
             try:
                 extras[name] = fn(args, M, problems, dev)
             except Exception as exc:   # reported, not fatal: the headline line still prints

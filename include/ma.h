@@ -54,9 +54,12 @@ enum { MA_HALF_WEIGHTING = 0, MA_FULL_WEIGHTING = 1 };
  * (Section 3), or the residual's own weighting applied to u.  The coarse
  * iterate u_H starts equal to w_H in both cases. */
 enum { MA_APPROX_INJECTION = 0, MA_APPROX_WEIGHTED = 1 };
-/* Arithmetic: everything in FP64, or FP32 correction cycles under an FP64
- * fine-grid residual and update (defect correction). */
-enum { MA_FP64 = 0, MA_MIXED = 1 };
+/* Arithmetic: everything in FP64; FP32 correction cycles under an FP64
+ * fine-grid residual and update (defect correction); or everything in FP32
+ * (the FP32 cycles on the solution itself, stopping on the FP32 residual): a
+ * throughput mode whose accuracy is limited by FP32 round-off of the second
+ * differences, ~eps_32 |u| / h^2 in the Hessian, which grows with N. */
+enum { MA_FP64 = 0, MA_MIXED = 1, MA_FP32 = 2 };
 /* Norms over the fine interior: max, or discrete L2 sqrt(h^3 sum v^2)
  * (stopping rule of Section 4). */
 enum { MA_NORM_MAX = 0, MA_NORM_L2 = 1 };
@@ -88,7 +91,7 @@ typedef struct {
                             exactly) or 5, 9, 17                                       */
     int restrict_kind;   /* MA_HALF_WEIGHTING | MA_FULL_WEIGHTING                      */
     int approx_restrict; /* MA_APPROX_INJECTION | MA_APPROX_WEIGHTED                   */
-    int precision;       /* MA_FP64 | MA_MIXED                                         */
+    int precision;       /* MA_FP64 | MA_MIXED | MA_FP32                               */
     int coarse_sweeps;   /* > 0: that many sweeps on the coarsest grid (Section 4 uses
                             1); 0: sweep until max|du| <= 1e-14 max|u| (cap 100)        */
     int inner_cycles;    /* MA_MIXED: FP32 correction V-cycles per FP64 residual and

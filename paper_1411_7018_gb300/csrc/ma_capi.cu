@@ -71,7 +71,7 @@ ma_status check_desc(const ma_hier_desc* d)
         return fail(MA_ERR_INVALID_ARG, "bad restrict_kind %d", d->restrict_kind);
     if (d->approx_restrict != MA_APPROX_INJECTION && d->approx_restrict != MA_APPROX_WEIGHTED)
         return fail(MA_ERR_INVALID_ARG, "bad approx_restrict %d", d->approx_restrict);
-    if (d->precision != MA_FP64 && d->precision != MA_MIXED)
+    if (d->precision != MA_FP64 && d->precision != MA_MIXED && d->precision != MA_FP32)
         return fail(MA_ERR_INVALID_ARG, "bad precision %d", d->precision);
     if (d->coarse_sweeps < 0 || d->coarse_sweeps > 1000)
         return fail(MA_ERR_INVALID_ARG, "coarse_sweeps must be in [0, 1000]");
@@ -103,11 +103,11 @@ size_t layout(ma_hierarchy* H, const ma_hier_desc* d, char* base)
         lv.rhs = (double*)take(pts * sizeof(double));
         lv.r = (double*)take(pts * sizeof(double));
         lv.w = (double*)take(pts * sizeof(double));
-        if (d->precision == MA_MIXED) {
+        if (d->precision == MA_MIXED || d->precision == MA_FP32) {
             lv.e = (float*)take(pts * sizeof(float));
             if (l < L - 1) lv.e2 = (float*)take(pts * sizeof(float));   // second buffer of the plane sweeps
             lv.bstore = (void*)take(ma::base_store_bytes(m));
-            if (l > 0) {   // the finest B comes from the FP64 residual
+            if (l > 0 && d->precision == MA_MIXED) {   // the finest B comes from the FP64 residual
                 lv.hi = (float*)take(pts * sizeof(float));
                 lv.lo = (float*)take(pts * sizeof(float));
             }
@@ -205,14 +205,14 @@ cudaError_t refresh_base(ma_hierarchy* H, int apply)
     return cudaSuccess;
 }
 
-// One FAS V-cycle (Algorithm 1 structure) for N(e) = rhs32 on every level,
-// starting from the current e on the finest level.
-cudaError_t corr_vcycle(ma_hierarchy* H)
+// One FAS V-cycle (Algorithm 1 structure) for N(e) = rhs32 from level l0
+// down and back, starting from the current e on level l0.
+cudaError_t corr_vcycle_from(ma_hierarchy* H, int l0)
 {
     cudaStream_t s = H->s;
     const ma_hier_desc& d = H->d;
     cudaError_t e;
-    for (int l = 0; l < H->L - 1; ++l) {
+    for (int l = l0; l < H->L - 1; ++l) {
         ma::Level& F = H->lev[l];
         ma::Level& C = H->lev[l + 1];
         if ((e = ma::launch_smooth_corr(F.e, F.e2, F.bstore, F.rhs32, F.n, F.h, d.nu1, H->events, s)) != cudaSuccess)
@@ -228,7 +228,7 @@ cudaError_t corr_vcycle(ma_hierarchy* H)
     if ((e = ma::launch_coarsest_corr(B.e, B.bstore, B.rhs32, B.n, B.h, d.coarse_sweeps, H->events, s)) !=
         cudaSuccess)
         return e;
-    for (int l = H->L - 2; l >= 0; --l) {
+    for (int l = H->L - 2; l >= l0; --l) {
         ma::Level& F = H->lev[l];
         ma::Level& C = H->lev[l + 1];
         if ((e = ma::launch_prolong_add_f32(C.e, C.w32, C.n, F.e, s)) != cudaSuccess) return e;
@@ -236,6 +236,70 @@ cudaError_t corr_vcycle(ma_hierarchy* H)
             return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t corr_vcycle(ma_hierarchy* H) { return corr_vcycle_from(H, 0); }
+
+// ---- FP32 mode: the correction machinery with B = 0 -------------------------
+// With B = 0 the correction operator N(e) = det(B + K(e)) - det(B) is
+// det(D^2_h e) itself, so the FP32 FAS cycles solve det(D^2_h e) = f for the
+// solution: e carries the Dirichlet data on its shell and rhs32 holds f.  No
+// FP64 residual or update: the result carries FP32 round-off of the second
+// differences, ~eps_32 |u| / h^2 in the Hessian.
+
+// e = FP32(u) and rhs32 = FP32(f) (colour-major) on every level, f and the
+// boundary data injected down in FP64 first; e2 gets e's shell.
+cudaError_t fp32_prepare(ma_hierarchy* H)
+{
+    cudaStream_t s = H->s;
+    cudaError_t e;
+    for (int l = 0; l < H->L - 1; ++l) {
+        ma::Level& F = H->lev[l];
+        ma::Level& C = H->lev[l + 1];
+        if ((e = ma::launch_inject(F.rhs, F.n, C.rhs, s)) != cudaSuccess) return e;
+        if ((e = ma::launch_inject(F.u, F.n, C.u, s)) != cudaSuccess) return e;
+    }
+    for (int l = 0; l < H->L; ++l) {
+        ma::Level& A = H->lev[l];
+        if ((e = ma::launch_f64_to_f32(A.u, A.e, A.n, s)) != cudaSuccess) return e;
+        if ((e = ma::launch_f64_to_f32(A.rhs, A.res32, A.n, s)) != cudaSuccess) return e;
+        if ((e = ma::launch_to_cm(A.res32, A.rhs32, A.n, s)) != cudaSuccess) return e;
+        if (A.e2 && (e = cudaMemcpyAsync(A.e2, A.e, sizeof(float) * (size_t)A.n * A.n * A.n,
+                                         cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+// Algorithm 2 in FP32: zero coarsest interior, coarsest solve, then up the
+// levels: interpolate and one cycle from that level.
+cudaError_t fp32_fmg(ma_hierarchy* H)
+{
+    cudaStream_t s = H->s;
+    cudaError_t e;
+    ma::Level& B = H->lev[H->L - 1];
+    if ((e = ma::launch_zero_interior_f32(B.e, B.n, s)) != cudaSuccess) return e;
+    if ((e = ma::launch_coarsest_corr(B.e, B.bstore, B.rhs32, B.n, B.h, H->d.coarse_sweeps, H->events, s)) !=
+        cudaSuccess)
+        return e;
+    for (int l = H->L - 2; l >= 0; --l) {
+        ma::Level& F = H->lev[l];
+        ma::Level& C = H->lev[l + 1];
+        if ((e = ma::launch_interpolate_f32(C.e, C.n, F.e, s)) != cudaSuccess) return e;
+        if ((e = corr_vcycle_from(H, l)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// The FP32 residual f - det(D^2_h e) and its norms into out2; u = e in FP64.
+cudaError_t fp32_residual(ma_hierarchy* H)
+{
+    ma::Level& F = H->lev[0];
+    cudaError_t e = ma::launch_residual_corr(F.e, F.bstore, F.rhs32, F.res32, F.n, F.h, H->s);
+    if (e == cudaSuccess) e = ma::launch_norm_partials_f32(F.res32, F.n, H->partials, H->s);
+    if (e == cudaSuccess) e = ma::launch_norm_final(H->partials, H->npartials, F.h, H->out2, H->s);
+    if (e == cudaSuccess) e = ma::launch_f32_to_f64(F.e, F.u, F.n, H->s);
+    return e;
 }
 
 // FP64 fine residual into rhs32 (the correction problem's right-hand side)
@@ -398,6 +462,8 @@ ma_status ma_create_hierarchy(const ma_hier_desc* desc, void* dev_workspace, siz
         if (H->lev[l].e) e = cudaMemsetAsync(H->lev[l].e, 0, pts * sizeof(float), H->s);
         if (e == cudaSuccess && H->lev[l].e2) e = cudaMemsetAsync(H->lev[l].e2, 0, pts * sizeof(float), H->s);
         if (e == cudaSuccess && H->lev[l].res32) e = cudaMemsetAsync(H->lev[l].res32, 0, pts * sizeof(float), H->s);
+        if (e == cudaSuccess && desc->precision == MA_FP32)   // B = 0: the operator is det(D^2_h e)
+            e = cudaMemsetAsync(H->lev[l].bstore, 0, ma::base_store_bytes(H->lev[l].n), H->s);
     }
     if (e != cudaSuccess) {
         if (H->host) cudaFreeHost(H->host);
@@ -452,6 +518,12 @@ ma_status ma_vcycle(ma_hierarchy* H, int ncycles)
 {
     if (!H || ncycles < 0) return fail(MA_ERR_INVALID_ARG, "bad arguments");
     DeviceGuard g(H->device);
+    if (H->d.precision == MA_FP32) {
+        MA_CK(fp32_prepare(H));
+        for (int c = 0; c < ncycles; ++c) MA_CK(corr_vcycle(H));
+        MA_CK(ma::launch_f32_to_f64(H->lev[0].e, H->lev[0].u, H->lev[0].n, H->s));
+        return MA_OK;
+    }
     for (int c = 0; c < ncycles; ++c) {
         if (H->d.precision == MA_MIXED) MA_CK(mixed_iteration(H));
         else MA_CK(vcycle_from(H, 0));
@@ -536,7 +608,14 @@ ma_status ma_solve_begin(ma_hierarchy* H, const ma_solve_opts* opts)
             e = ma::launch_norm_partials(F.rhs, F.n, H->partials, H->s);
         }
         if (e == cudaSuccess) e = ma::launch_norm_final(H->partials, H->npartials, F.h, H->rb + 2, H->s);
-        if (e == cudaSuccess && init == MA_INIT_FMG) e = fmg(H, !mixed);
+        if (e != cudaSuccess) return e;
+        if (H->d.precision == MA_FP32) {
+            if ((e = fp32_prepare(H)) != cudaSuccess) return e;
+            if (init == MA_INIT_FMG && (e = fp32_fmg(H)) != cudaSuccess) return e;
+            if (init == MA_INIT_ZERO && (e = ma::launch_zero_interior_f32(F.e, F.n, H->s)) != cudaSuccess) return e;
+            return fp32_residual(H);
+        }
+        if (init == MA_INIT_FMG) e = fmg(H, !mixed);
         if (e == cudaSuccess && init == MA_INIT_ZERO) e = ma::launch_zero_interior(F.u, F.n, H->s);
         if (e != cudaSuccess) return e;
         if (mixed) {
@@ -566,6 +645,10 @@ static cudaError_t launch_cycle(ma_hierarchy* H)
     const bool mixed = H->d.precision == MA_MIXED;
     return run_graph(H, H->g_cycle, [&]() -> cudaError_t {
         cudaError_t e;
+        if (H->d.precision == MA_FP32) {
+            if ((e = corr_vcycle(H)) != cudaSuccess) return e;
+            return fp32_residual(H);
+        }
         if (mixed) {
             const int inner = H->d.inner_cycles > 0 ? H->d.inner_cycles : 3;
             for (int c = 0; c < inner; ++c)

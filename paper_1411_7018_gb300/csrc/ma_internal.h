@@ -79,6 +79,12 @@ cudaError_t launch_inject_f32(const float* vf, int nf, float* vc, cudaStream_t s
 cudaError_t launch_coarsest_corr(float* e, const void* bstore, const float* rhs_cm, int n, double h, int sweeps,
                                  unsigned long long* events, cudaStream_t s);
 cudaError_t launch_update(double* u, float* e, int n, int apply, cudaStream_t s);
+// FP32 mode (the correction machinery with B = 0 on the solution itself)
+cudaError_t launch_f64_to_f32(const double* u, float* e, int n, cudaStream_t s);
+cudaError_t launch_f32_to_f64(const float* e, double* u, int n, cudaStream_t s);
+cudaError_t launch_interpolate_f32(const float* ec, int nc, float* ef, cudaStream_t s);
+cudaError_t launch_zero_interior_f32(float* e, int n, cudaStream_t s);
+cudaError_t launch_norm_partials_f32(const float* v, int n, double* partials, cudaStream_t s);
 cudaError_t launch_split_inject(const double* u0, int n0, int stride, float* hi, float* lo, int nc, cudaStream_t s);
 cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r_cm, void* bstore, int n, double h,
                                    double* partials, cudaStream_t s);

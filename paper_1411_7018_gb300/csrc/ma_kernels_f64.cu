@@ -95,14 +95,15 @@ constexpr int KZ = 16;   // z-blocks of the reduction grids; each loops over k
 
 dim3 reduce_grid(int n) { return dim3((n + BX - 1) / BX, (n + BY - 1) / BY, n < KZ ? n : KZ); }
 
-__global__ void __launch_bounds__(BX * BY) k_norm_partials(const double* __restrict__ v, int n, double* partials)
+template <typename T>
+__global__ void __launch_bounds__(BX * BY) k_norm_partials(const T* __restrict__ v, int n, double* partials)
 {
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
     double mx = 0.0, ss = 0.0;
     for (int k = blockIdx.z; k < n; k += gridDim.z) {
         if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
-            const double x = v[lin(i, j, k, n)];
+            const double x = (double)v[lin(i, j, k, n)];
             mx = fmax(mx, fabs(x));
             ss = fma(x, x, ss);
         }
@@ -305,7 +306,14 @@ cudaError_t launch_residual(const double* u, const double* rhs, double* r, int n
 cudaError_t launch_norm_partials(const double* v, int n, double* partials, cudaStream_t s)
 {
     count_launches(1);
-    k_norm_partials<<<reduce_grid(n), dim3(BX, BY), 0, s>>>(v, n, partials);
+    k_norm_partials<double><<<reduce_grid(n), dim3(BX, BY), 0, s>>>(v, n, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm_partials_f32(const float* v, int n, double* partials, cudaStream_t s)
+{
+    count_launches(1);
+    k_norm_partials<float><<<reduce_grid(n), dim3(BX, BY), 0, s>>>(v, n, partials);
     return cudaGetLastError();
 }
 

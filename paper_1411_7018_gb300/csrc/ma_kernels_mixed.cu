@@ -750,6 +750,19 @@ __global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __r
     if (events && ev) atomicAdd(events, ev);
 }
 
+// FP64 <-> FP32 copies of whole grids (the FP32 mode's iterate and data).
+__global__ void k_f64_to_f32(const double* __restrict__ u, float* __restrict__ e, long long m)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < m) e[p] = __double2float_rn(u[p]);
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ e, double* __restrict__ u, long long m)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < m) u[p] = (double)e[p];
+}
+
 // FP64 fine residual, written as FP32 in colour-major order (the correction
 // problem's right-hand side), and with it the fine base Hessian B = D^2_h u
 // of the correction operator, rounded to FP32 from the FP64 Hessian the
@@ -1071,6 +1084,37 @@ cudaError_t launch_update(double* u, float* e, int n, int apply, cudaStream_t s)
     const long long m = (long long)n * n * n;
     count_launches(1);
     k_update<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(u, e, m, apply);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f64_to_f32(const double* u, float* e, int n, cudaStream_t s)
+{
+    const long long m = (long long)n * n * n;
+    count_launches(1);
+    k_f64_to_f32<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(u, e, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_f64(const float* e, double* u, int n, cudaStream_t s)
+{
+    const long long m = (long long)n * n * n;
+    count_launches(1);
+    k_f32_to_f64<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(e, u, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interpolate_f32(const float* ec, int nc, float* ef, cudaStream_t s)
+{
+    const int nf = 2 * nc - 1;
+    count_launches(1);
+    xfer::k_prolong<float><<<xfer::prolong_grid(nf), dim3(BX, BY), 0, s>>>(ec, nullptr, nc, ef, nf, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_interior_f32(float* e, int n, cudaStream_t s)
+{
+    count_launches(1);
+    xfer::k_zero_interior<float><<<grid_of(n), dim3(BX, BY), 0, s>>>(e, n);
     return cudaGetLastError();
 }
 

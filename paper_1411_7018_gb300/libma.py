@@ -17,7 +17,7 @@ from . import build as _build
 MA_OK, MA_ERR_INVALID_ARG, MA_ERR_OOM, MA_ERR_CUDA, MA_ERR_NOT_CONVERGED, MA_ERR_NONFINITE = range(6)
 MA_HALF_WEIGHTING, MA_FULL_WEIGHTING = 0, 1
 MA_APPROX_INJECTION, MA_APPROX_WEIGHTED = 0, 1
-MA_FP64, MA_MIXED = 0, 1
+MA_FP64, MA_MIXED, MA_FP32 = 0, 1, 2
 MA_NORM_MAX, MA_NORM_L2 = 0, 1
 MA_INIT_FMG, MA_INIT_ZERO, MA_INIT_KEEP = 0, 1, 2
 MA_FMG_TRILINEAR, MA_FMG_CUBIC = 0, 1
