@@ -53,22 +53,28 @@ __device__ __forceinline__ double s_h(const double* u, int n, int i, int j, doub
 }
 
 // Red-black phase: dst = src with the points of one colour (i + j parity)
-// updated from src.
+// updated from src.  A thread takes the pair i = 2 i2, 2 i2 + 1 of row j: it
+// solves the point of this colour and copies the other, so every lane of a
+// warp runs the root (colours alternate along a row).
 __global__ void __launch_bounds__(TX * TY) k_rb_phase(const double* __restrict__ src, double* __restrict__ dst,
                                                        const double* __restrict__ rhs, int n, double h4, int colour,
                                                        unsigned long long* events)
 {
-    const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
-    if (i >= n || j >= n) return;
-    const long long p = (long long)j * n + i;
-    if (i > 0 && j > 0 && i < n - 1 && j < n - 1 && ((i + j) & 1) == colour) {
+    const int i0 = 2 * (int)(blockIdx.x * TX + threadIdx.x), j = blockIdx.y * TY + threadIdx.y;
+    if (i0 >= n || j >= n) return;
+    const long long row = (long long)j * n;
+    const int ic = i0 + ((j + colour) & 1);   // (ic + j) & 1 == colour
+    const int io = ic == i0 ? i0 + 1 : i0;
+    if (io < n) dst[row + io] = src[row + io];
+    if (ic >= n) return;
+    if (ic > 0 && j > 0 && ic < n - 1 && j < n - 1) {
         double a, b, r;
-        sums2(src, n, i, j, a, b, r);
+        sums2(src, n, ic, j, a, b, r);
         bool neg = false;
-        dst[p] = quad_root(a, b, r, h4, rhs[p], &neg);
+        dst[row + ic] = quad_root(a, b, r, h4, rhs[row + ic], &neg);
         if (neg && events) atomicAdd(events, 1ull);
     } else {
-        dst[p] = src[p];
+        dst[row + ic] = src[row + ic];
     }
 }
 
@@ -376,8 +382,9 @@ cudaError_t smooth2(double* u, double* t, const double* rhs, int n, double h, in
             }
         } else {
             ma::count_launches(2);
-            k_rb_phase<<<grid2(n, n), dim3(TX, TY), 0, s>>>(u, t, rhs, n, h4, 0, ev);
-            k_rb_phase<<<grid2(n, n), dim3(TX, TY), 0, s>>>(t, u, rhs, n, h4, 1, ev);
+            const dim3 g = grid2((n + 1) / 2, n);
+            k_rb_phase<<<g, dim3(TX, TY), 0, s>>>(u, t, rhs, n, h4, 0, ev);
+            k_rb_phase<<<g, dim3(TX, TY), 0, s>>>(t, u, rhs, n, h4, 1, ev);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -6,7 +6,8 @@ Cases: ``smooth`` (FP64 smoother sweeps, 8 colour launches each), ``residual``
 (the FP64 residual kernel), ``smooth_corr`` (pairs of FP32 correction-smoother
 sweeps of the mixed path, two k-parity launches per sweep, on a small
 correction), ``vcycle`` (whole V-cycles of
-a resident hierarchy), ``solve`` (one FMG + V-cycle solve to 1e-10);
+a resident hierarchy), ``solve`` (one FMG + V-cycle solve to 1e-10), ``solve2d`` (the 2D paper-configuration solve of
+Example 1 on an n x n grid), ``smooth2d`` (2D red-black sweeps on that grid);
 ``--precision mixed`` runs the hierarchy cases in mixed precision.  The grid holds
 Example 4 (u = exp(|x|^2/2)) with a small seeded perturbation; fields of a
 257^3 grid are 136 MB each, larger than L2.  Prints nothing but a one-line
@@ -25,12 +26,34 @@ from . import problems
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["smooth", "residual", "smooth_corr", "vcycle", "solve"], default="smooth")
+    ap.add_argument("--case", choices=["smooth", "residual", "smooth_corr", "vcycle", "solve", "solve2d", "smooth2d"],
+                    default="smooth")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--problem", default="exp")
     a = ap.parse_args()
+    if a.case == "smooth2d":
+        from . import problems2d
+        u_ex, f2, g2 = problems2d.make2d_on_device("ex1", a.n)
+        u2 = u_ex.clone()
+        t2 = torch.empty_like(u2)
+        for _ in range(a.reps):
+            M.ma2d_smooth(u2, f2, a.n, 1.0 / (a.n - 1), 1, M.MA2D_REDBLACK, t2)
+        torch.cuda.synchronize()
+        print(f"profile_case {a.case} n={a.n} reps={a.reps} done")
+        return
+    if a.case == "solve2d":
+        from . import problems2d
+        u_ex, f2, g2 = problems2d.make2d_on_device("ex1", a.n)
+        H = M.Hierarchy2D(M.paper_desc2d(a.n))
+        for _ in range(a.reps):
+            H.set_rhs_bc(f2, g2)
+            H.solve(tol=1e-6, norm=M.MA_NORM_L2, relative=M.MA_REL_INITIAL, max_cycles=30)
+        H.close()
+        torch.cuda.synchronize()
+        print(f"profile_case {a.case} n={a.n} reps={a.reps} done")
+        return
     pr = problems.make(a.problem, a.n)
     rng = np.random.default_rng(0)
     u0 = pr.u.copy()
