@@ -47,8 +47,8 @@ cudaError_t launch_copy_rhs_bc(const double* f, const double* g, double* rhs, do
 
 // Mixed-precision kernels (ma_kernels_mixed.cu).  e, res, w are n^3 floats
 // in the natural layout; hi + lo is the FP32 split of the FP64 iterate; the
-// base Hessian store (BF16, base_store_bytes) and the correction right-hand
-// side (cm_points floats) are in colour-major order.
+// base Hessian store (FP32, six per interior point, base_store_bytes) and the
+// correction right-hand side (cm_points floats) are in colour-major order.
 size_t base_store_bytes(int n);
 size_t cm_points(int n);
 cudaError_t launch_base_colour(const float* hi, const float* lo, void* bstore, int n, double h, cudaStream_t s);
