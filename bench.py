@@ -366,11 +366,9 @@ def main():
     import torch.distributed as dist
 
     from paper_1411_7018_gb300 import libma as M
-    from paper_1411_7018_gb300 import problems
+    from paper_1411_7018_gb300 import problems, replicas
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, local, world = replicas.rank_info()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -398,8 +396,7 @@ def main():
         for _ in range(args.warmup):
             step(H)
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        replicas.barrier()
         l0 = M.ma_kernel_launch_count()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -411,19 +408,16 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         launches = M.ma_kernel_launch_count() - l0
-        ms = e0.elapsed_time(e1) / steps
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dist.barrier()
-        return float(t.item()), statistics.mean(cyc), r, launches
+        ms = replicas.max_over_ranks(e0.elapsed_time(e1) / steps, device=dev)
+        replicas.barrier()
+        return ms, statistics.mean(cyc), r, launches
 
     sampler = ClockSampler(local)
     sampler.start()
     ms_mixed, cyc_mixed, res_mixed, launches = timed(hier["mixed"], args.steps)
     clocks = sampler.stop()
     ms_fp64, cyc_fp64, res_fp64, _ = timed(hier["fp64"], max(1, args.steps // 2))
-    value = world * pr.unknowns / (ms_mixed / 1e3)
+    value = replicas.whole_job_rate(pr.unknowns, ms_mixed / 1e3, world)
     sols = {}
     for k, H in hier.items():
         u = torch.empty_like(f_dev)
