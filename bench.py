@@ -44,6 +44,10 @@ FP64_PEAK_GOPS = 629.0   # 2 FP64 ops/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 
 # once per sweep for the stencils, counted at its own update).
 CORR_SMOOTH_BYTES_PER_POINT = 36
 HBM_PEAK_GBS = 6663.9    # MEASURED_PEAKS.json hbm_gbs (copy bandwidth)
+# DRAM bytes (read + write) per launch of the by-colour correction smoother at
+# 257^3, from one ncu capture of the current kernel with a warm L2
+# (--cache-control none): 103.0 MB read + 34.7 MB written.
+CORR_SMOOTH_TRAFFIC_257 = 137.7e6
 
 
 def parse():
@@ -470,6 +474,23 @@ def main():
     f64_gops = SMOOTH_FP64_OPS_PER_POINT * pts_launch / (f64_launch_ms / 1e3) / 1e9
     del u_tmp, hi, lo, e, rhs, _keep
 
+    # V-cycles per second on the resident 257^3 hierarchies: an FP64 FAS
+    # V-cycle, and an FP32 correction V-cycle (an outer iteration of the
+    # mixed solve is inner_cycles of them plus the FP64 residual and update)
+    vc = {}
+    for key in ("fp64", "mixed"):
+        H = hier[key]
+        H.set_rhs_bc(f_dev, g_dev)
+        H.solve(tol=args.tol, max_cycles=60)
+        H.vcycle(1)
+        e0.record(stream)
+        H.vcycle(3)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per = e0.elapsed_time(e1) / 3.0
+        inner = 3 if key == "mixed" else 1
+        vc[key] = {"ms_per_cycle": per / inner, "vcycles_per_s": 1e3 * inner / per}
+
     # end to end through the C ABI with host buffers (pinned), mixed precision
     H = hier["mixed"]
     f_host = torch.from_numpy(pr.f).pin_memory()
@@ -523,7 +544,9 @@ def main():
                          "max_rel_diff_mixed_vs_fp64": diff},
             "roofline": {"bound": "hbm", "kernel": corr_kernel,
                          "achieved": corr_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                         "frac": corr_gbs / HBM_PEAK_GBS, "traffic": None,
+                         "frac": corr_gbs / HBM_PEAK_GBS,
+                         "traffic": CORR_SMOOTH_TRAFFIC_257 if (n == 257 and corr_launches == 8) else None,
+                         "traffic_note": "ncu dram bytes per launch, warm L2; algorithmic 36 B x (n-2)^3/8 = 74 MB",
                          "launch_ms": corr_launch_ms, "bytes_per_point": CORR_SMOOTH_BYTES_PER_POINT,
                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
             "roofline_fp64_smoother": {"bound": "alu", "kernel": "k_smooth_colour (FP64 smoother, one colour phase)",
@@ -536,6 +559,8 @@ def main():
                     "h2d_bytes_per_step": 2 * 8 * pr.n ** 3, "d2h_bytes_per_step": 8 * pr.n ** 3},
             "clocks": clocks,
             "gpu_launches": launches,
+            "vcycles": {"fp64_fas_vcycle": vc["fp64"],
+                        "fp32_correction_vcycle_with_fp64_update_share": vc["mixed"]},
             "tuning": {str(k): {"smoother": v["smoother"], "residual": v["residual"],
                                 "us_per_sweep": v["us_per_sweep"]} for k, v in tuning.items()},
             **extras,
