@@ -148,28 +148,6 @@ static double q_eval(const double lam[3], double rhs, double z, double *dq)
     return p0 * p1 * p2 - rhs;
 }
 
-/* All real roots of z^3 + A z^2 + B z + C (trigonometric / Cardano form of the
- * cubic formula); returns their count (1 or 3). */
-static int cubic_real_roots(double A, double B, double C, double z[3])
-{
-    const double p = B - A * A / 3.0;
-    const double q = 2.0 * A * A * A / 27.0 - A * B / 3.0 + C;
-    const double shift = -A / 3.0;
-    const double disc = q * q / 4.0 + p * p * p / 27.0;
-    if (p < 0.0 && disc <= 0.0) {
-        const double m = 2.0 * sqrt(-p / 3.0);
-        double arg = (3.0 * q / (2.0 * p)) * sqrt(-3.0 / p);
-        if (arg > 1.0) arg = 1.0;
-        if (arg < -1.0) arg = -1.0;
-        const double phi = acos(arg) / 3.0;
-        for (int k = 0; k < 3; ++k)
-            z[k] = m * cos(phi - 2.0 * M_PI * k / 3.0) + shift;
-        return 3;
-    }
-    const double sq = sqrt(disc > 0.0 ? disc : 0.0);
-    z[0] = cbrt(-q / 2.0 + sq) + cbrt(-q / 2.0 - sq) + shift;
-    return 1;
-}
 
 /* Eq. (realroots): the smallest real root z of Q(z) = det(H - z I) - rhs.
  *
@@ -200,26 +178,33 @@ static double smallest_root(const double H[3][3], double rhs, long *nonconvex)
         return z;
     }
     if (nonconvex) *nonconvex += 1;
-    /* (l1 - z)(l2 - z)(l3 - z) = rhs  <=>  z^3 - e1 z^2 + e2 z - e3 + rhs = 0 */
-    const double e1 = lam[0] + lam[1] + lam[2];
-    const double e2 = lam[0] * lam[1] + lam[0] * lam[2] + lam[1] * lam[2];
-    const double e3 = lam[0] * lam[1] * lam[2];
-    double z[3];
-    const int m = cubic_real_roots(-e1, e2, rhs - e3, z);
-    double best = INFINITY;
-    for (int k = 0; k < m; ++k) {
-        double x = z[k];
-        for (int it = 0; it < 4; ++it) {
-            double dq;
-            const double qx = q_eval(lam, rhs, x, &dq);
-            if (dq == 0.0) break;
-            const double xn = x - qx / dq;
-            if (!isfinite(xn)) break;
-            x = xn;
-        }
-        if (x < best) best = x;
+    /* rhs <= 0: Eq. (realroots) literally, the smallest real root of
+     * q(z) = (l1 - z)(l2 - z)(l3 - z) - rhs.  q > 0 below l1 and q(l1) =
+     * q(l2) = -rhs >= 0; between l1 and l2 q dips to its minimum at
+     * z* = (T - sqrt(S)) / 3 (T = l1 + l2 + l3, S = T^2 - 3 (l1 l2 + l1 l3 +
+     * l2 l3) = ((l1-l2)^2 + (l1-l3)^2 + (l2-l3)^2) / 2), and it is positive
+     * between l2 and l3 and decreasing beyond l3.  So the smallest root is l1
+     * if rhs = 0, else in [l1, z*] if q(z*) <= 0 (a double root when = 0),
+     * else the single root in (l3, l3 + (-rhs)^(1/3)].  Found by bisection
+     * on the product form, which keeps double and triple roots exact. */
+    if (rhs == 0.0) return lam[0];
+    const double T = lam[0] + lam[1] + lam[2];
+    const double S = 0.5 * ((lam[0] - lam[1]) * (lam[0] - lam[1]) + (lam[0] - lam[2]) * (lam[0] - lam[2]) +
+                            (lam[1] - lam[2]) * (lam[1] - lam[2]));
+    double zs = (T - sqrt(S)) / 3.0;
+    if (zs < lam[0]) zs = lam[0];
+    if (zs > lam[1]) zs = lam[1];
+    double lo, hi;
+    if (q_eval(lam, rhs, zs, NULL) <= 0.0) { lo = lam[0]; hi = zs; }
+    else { lo = lam[2]; hi = lam[2] + cbrt(-rhs); }
+    /* q(lo) >= 0 >= q(hi), q decreasing on [lo, hi] */
+    for (int it = 0; it < 400; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        if (q_eval(lam, rhs, mid, NULL) > 0.0) lo = mid;
+        else hi = mid;
     }
-    return best;
+    return q_eval(lam, rhs, lo, NULL) <= 0.0 ? lo : hi;
 }
 
 /* One nonlinear Gauss-Seidel point update (Section 2, Eq. realroots): the new

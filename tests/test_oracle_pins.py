@@ -65,6 +65,26 @@ def test_point_update_is_smallest_real_root_of_printed_cubic(seed):
     assert checked > 200
 
 
+@pytest.mark.parametrize("mu", [(1.0, 1.0, 1.0), (0.7, 0.7, 2.0), (0.5, 1.5, 1.5), (0.9, 0.9, 0.9)])
+def test_point_update_at_multiple_roots(mu):
+    """Double and triple roots, where companion-matrix root finders lose
+    accuracy: with f = 0 the printed cubic is det(M - 2v I) for the symmetric
+    stencil matrix M = [[a, r, s], [r, b, t], [s, t, c]], whose roots are
+    v = mu_i / 2 (mu_i the eigenvalues, repeated ones included), so the
+    smallest is min(mu) / 2; with M = mu I and f > 0 the unique real root is
+    (mu - (h^6 f)^{1/3}) / 2."""
+    rng = np.random.default_rng(int(100 * sum(mu)))
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    Mx = Q @ np.diag(mu) @ Q.T
+    q = [Mx[0, 0], Mx[1, 1], Mx[2, 2], Mx[0, 1], Mx[0, 2], Mx[1, 2]]
+    v = O.point_update(q, 0.3, 1.0, 0.0)
+    assert abs(v - min(mu) / 2.0) <= 1e-10
+    if mu[0] == mu[1] == mu[2]:
+        for f in (1e-3, 0.2, 3.0):
+            v = O.point_update([mu[0]] * 3 + [0.0] * 3, 0.1, 0.5, f)
+            assert abs(v - (mu[0] - np.cbrt(0.5 ** 6 * f)) / 2.0) <= 1e-12
+
+
 def test_point_update_on_fine_step_vs_extended_precision():
     """At a small step h the printed monomial form cancels; compare with the
     smallest real root computed by numpy's roots on the cubic in the shifted
