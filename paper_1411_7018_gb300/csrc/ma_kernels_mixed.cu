@@ -206,41 +206,13 @@ __device__ __noinline__ float corr_root_slow(S3f B, S3f K, float r, bool* noncon
         return (float)z;
     }
     *nonconvex = true;
-    // z^3 + a2 z^2 + a1 z + a0 = -F(z)
-    const double a2 = -C.T, a1 = C.M, a0 = -C.c;
-    const double p = a1 - a2 * a2 / 3.0;
-    const double q = 2.0 * a2 * a2 * a2 / 27.0 - a2 * a1 / 3.0 + a0;
-    const double disc = 0.25 * q * q + p * p * p / 27.0;
-    double roots[3];
-    int nr;
-    if (p < 0.0 && disc <= 0.0) {
-        const double m = 2.0 * sqrt(-p / 3.0);
-        double arg = 1.5 * q / p * sqrt(-3.0 / p);
-        arg = fmin(1.0, fmax(-1.0, arg));
-        const double phi = acos(arg) / 3.0;
-        const double tp = 2.0943951023931954923;   // 2 pi / 3
-        roots[0] = m * cos(phi) - a2 / 3.0;
-        roots[1] = m * cos(phi - tp) - a2 / 3.0;
-        roots[2] = m * cos(phi - 2.0 * tp) - a2 / 3.0;
-        nr = 3;
-    } else {
-        const double sq = sqrt(fmax(disc, 0.0));
-        roots[0] = cbrt(-0.5 * q + sq) + cbrt(-0.5 * q - sq) - a2 / 3.0;
-        nr = 1;
-    }
-    double best = INFINITY;
-    for (int k = 0; k < nr; ++k) {
-        double z = roots[k];
-        for (int it = 0; it < 2; ++it) {
-            const double m = corr_Mz(C, z);
-            if (m == 0.0) break;
-            const double zn = z + corr_F(C, z) / m;
-            if (!isfinite(zn)) break;
-            z = zn;
-        }
-        best = fmin(best, z);
-    }
-    return (float)best;
+    const double glo = fmin(C.g[0] - fabs(C.g[3]) - fabs(C.g[4]),
+                            fmin(C.g[1] - fabs(C.g[3]) - fabs(C.g[5]), C.g[2] - fabs(C.g[4]) - fabs(C.g[5])));
+    const double ghi = fmax(C.g[0] + fabs(C.g[3]) + fabs(C.g[4]),
+                            fmax(C.g[1] + fabs(C.g[3]) + fabs(C.g[5]), C.g[2] + fabs(C.g[4]) + fabs(C.g[5])));
+    double scale = 0.0;
+    for (int q = 0; q < 6; ++q) scale += fabs(C.g[q]);
+    return (float)smallest_root_nonpositive([&](double z) { return corr_F(C, z); }, C.T, C.M, glo, ghi, C.tot, scale);
 }
 
 __device__ __forceinline__ float corr_root(const S3f& B, const S3f& K, float r, bool* nonconvex)

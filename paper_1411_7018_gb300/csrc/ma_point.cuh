@@ -162,51 +162,49 @@ static __device__ __noinline__ double root_f64_monotone(const HessS H, double rh
     return z;
 }
 
-// rhs <= 0: no root lies below l1; Eq. (realroots) taken literally -- the
-// smallest real root of det(Hs - z I) = rhs6, i.e. of
-// z^3 - T z^2 + M z - (D - rhs6) with T, M, D the trace, minor sum and
-// determinant of Hs.  Trigonometric form when there are three real roots,
-// Cardano's formula when there is one, then two FP64 Newton polishes.
+// Smallest real root of q(z) = c - M z + T z^2 - z^3 = 0 for a symmetric 3x3
+// matrix X with trace T, principal-minor sum M and Gershgorin bounds [lo, hi]
+// of its eigenvalues, when q(z) = det(X - z I) - t with t <= 0 (Eq.
+// (realroots) taken literally: no root lies below the smallest eigenvalue).
+// q > 0 below the eigenvalues; det(X - z I) has its local minimum at
+// za = (T - sqrt(T^2 - 3M)) / 3, between the two smallest eigenvalues, and its
+// local maximum at zb = (T + sqrt(T^2 - 3M)) / 3.  If q(za) <= 0 (within
+// rounding: a double root) the smallest root is in [lo, za], else it is the
+// root beyond zb, below hi + (-t)^(1/3).  Bisection on the bracket.
+template <typename Q>
+__device__ __forceinline__ double smallest_root_nonpositive(Q q, double T, double M, double glo, double ghi, double t,
+                                                            double scale)
+{
+    const double sq = sqrt(fmax(T * T - 3.0 * M, 0.0));
+    const double za = (T - sq) / 3.0, zb = (T + sq) / 3.0;
+    const double tiny = 64.0 * 2.220446049250313e-16 * scale * scale * scale;
+    double lo, hi;
+    if (q(za) <= tiny) {
+        lo = fmin(glo, za);
+        hi = za;
+    } else {
+        lo = zb;
+        hi = fmax(ghi, zb) + cbrt(fmax(-t, 0.0)) + tiny;
+    }
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        if (q(mid) > 0.0) lo = mid;
+        else hi = mid;
+    }
+    return q(lo) <= 0.0 ? lo : hi;
+}
+
+// rhs <= 0 for the FP64 smoother: the smallest real root of
+// det(Hs - z I) = rhs6.
 static __device__ __noinline__ double root_f64_all_real_min(const HessS H, double rhs6)
 {
     const double T = H.A + H.B + H.C;
     const double M = minors_shift(H, 0.0);
-    const double D = det0(H);
-    const double a2 = -T, a1 = M, a0 = rhs6 - D;   // z^3 + a2 z^2 + a1 z + a0
-    const double p = a1 - a2 * a2 / 3.0;
-    const double q = 2.0 * a2 * a2 * a2 / 27.0 - a2 * a1 / 3.0 + a0;
-    const double disc = 0.25 * q * q + p * p * p / 27.0;
-    double roots[3];
-    int nr;
-    if (p < 0.0 && disc <= 0.0) {
-        const double m = 2.0 * sqrt(-p / 3.0);
-        double arg = 1.5 * q / p * sqrt(-3.0 / p);
-        arg = fmin(1.0, fmax(-1.0, arg));
-        const double phi = acos(arg) / 3.0;
-        const double tp = 2.0943951023931954923;   // 2 pi / 3
-        roots[0] = m * cos(phi) - a2 / 3.0;
-        roots[1] = m * cos(phi - tp) - a2 / 3.0;
-        roots[2] = m * cos(phi - 2.0 * tp) - a2 / 3.0;
-        nr = 3;
-    } else {
-        const double sq = sqrt(fmax(disc, 0.0));
-        roots[0] = cbrt(-0.5 * q + sq) + cbrt(-0.5 * q - sq) - a2 / 3.0;
-        nr = 1;
-    }
-    double best = INFINITY;
-    for (int k = 0; k < nr; ++k) {
-        double z = roots[k];
-        for (int it = 0; it < 2; ++it) {
-            const double g = det_shift(H, z) - rhs6;
-            const double m = minors_shift(H, z);
-            if (m == 0.0) break;
-            const double zn = z + g / m;
-            if (!isfinite(zn)) break;
-            z = zn;
-        }
-        best = fmin(best, z);
-    }
-    return best;
+    const double glo = gershgorin_low<HessS, double>(H);
+    const double ghi = fmax(H.A + fabs(H.R) + fabs(H.S), fmax(H.B + fabs(H.R) + fabs(H.T), H.C + fabs(H.S) + fabs(H.T)));
+    const double scale = fabs(H.A) + fabs(H.B) + fabs(H.C) + fabs(H.R) + fabs(H.S) + fabs(H.T);
+    return smallest_root_nonpositive([&](double z) { return det_shift(H, z) - rhs6; }, T, M, glo, ghi, rhs6, scale);
 }
 
 // Smallest real root zeta of det(Hs - zeta I) = rhs6 (rhs6 = h^6 rhs).
