@@ -299,14 +299,14 @@ ma_status ma_residual_correction(const float *e_dev, const float *u_hi_dev, cons
  * all odd planes, 2 launches, in tiles of 16, 32 or 64 points per plane edge
  * with a recomputed halo and a second e buffer); both give the same bits.  The
  * correction residual runs in plane tiles of 16, 32 or 64.  The choice is
- * kept per grid size n (n - 1 a power of two) for the whole process; hierarchy
+ * kept per grid size n (odd, 3 .. 4097) for the whole process; hierarchy
  * calls take it when they first record their CUDA graphs, so set or tune
  * before the first solve. */
 enum { MA_CORR_BY_COLOUR = 0, MA_CORR_PLANE16 = 1, MA_CORR_PLANE32 = 2, MA_CORR_PLANE64 = 3 };
 
 /* Sets the choice for grid size n (-1 restores the built-in default: plane
  * tiles of 16 up to n = 33, 32 at n = 65, by colour above; residual tiles
- * 16 / 32 / 64).  MA_ERR_INVALID_ARG if n - 1 is not a power of two or a choice
+ * 16 / 32 / 64).  MA_ERR_INVALID_ARG if n is not odd in [3, 4097] or a choice
  * is out of range (the residual has no MA_CORR_BY_COLOUR). */
 ma_status ma_set_corr_tuning(int n, int smooth_choice, int residual_choice);
 

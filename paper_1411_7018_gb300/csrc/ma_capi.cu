@@ -941,7 +941,7 @@ ma_status ma_set_corr_tuning(int n, int smooth_choice, int residual_choice)
         residual_choice == MA_CORR_BY_COLOUR || residual_choice > MA_CORR_PLANE64)
         return fail(MA_ERR_INVALID_ARG, "ma_set_corr_tuning: bad choice (%d, %d)", smooth_choice, residual_choice);
     if (!ma::set_corr_tuning(n, smooth_choice, residual_choice))
-        return fail(MA_ERR_INVALID_ARG, "ma_set_corr_tuning: n - 1 = %d is not a power of two", n - 1);
+        return fail(MA_ERR_INVALID_ARG, "ma_set_corr_tuning: n = %d is not an odd size in [3, 4097]", n);
     return MA_OK;
 }
 
@@ -960,8 +960,6 @@ ma_status ma_tune_corr(float* e, const float* hi, const float* lo, const float* 
     if (!e || !scratch || !hi || !lo || !rhs || !valid_step_grid(n) || n < 5 || !(h > 0.0) || reps < 1 ||
         reps > 1000)
         return fail(MA_ERR_INVALID_ARG, "ma_tune_corr: bad arguments");
-    const unsigned m = (unsigned)(n - 1);
-    if (m & (m - 1)) return fail(MA_ERR_INVALID_ARG, "ma_tune_corr: n - 1 = %d is not a power of two", n - 1);
     cudaStream_t s = (cudaStream_t)stream;
     float* rhs_cm = nullptr;
     ma_status st = corr_setup(hi, lo, rhs, n, h, scratch, scratch_bytes, s, &rhs_cm);

@@ -63,7 +63,7 @@ cudaError_t launch_zero_shell_f32(float* v, int n, cudaStream_t s);
 constexpr int CORR_BY_COLOUR = 0, CORR_PLANE16 = 1, CORR_PLANE32 = 2, CORR_PLANE64 = 3;
 int corr_smooth_choice(int n);
 int corr_resid_choice(int n);
-bool set_corr_tuning(int n, int smooth, int resid);   // -1: built-in default; false if n - 1 is not 2^k
+bool set_corr_tuning(int n, int smooth, int resid);   // -1: built-in default; false unless n is odd in [3, 4097]
 cudaError_t launch_smooth_corr_choice(int choice, float* e, float* e2, const void* bstore, const float* rhs_cm, int n,
                                       double h, int nsweeps, unsigned long long* events, cudaStream_t s);
 cudaError_t launch_residual_corr_choice(int choice, const float* e, const void* bstore, const float* rhs_cm,

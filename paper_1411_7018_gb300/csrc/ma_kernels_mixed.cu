@@ -825,28 +825,20 @@ static cudaError_t colour_sweep_corr(float* e, const float* b, const float* rhs_
 namespace {
 
 // ---- choice of smoother and residual kernels per level size ----------------
-// Tuning table: per grid size (n - 1 a power of two), the correction-smoother
+// Tuning table: per grid size n (odd, 3 .. 4097), the correction-smoother
 // variant (CORR_BY_COLOUR or a plane tile) and the residual tile, set by the
 // autotuner (ma_tune_corr) or by hand; -1 = the built-in default.
-constexpr int kTuneSlots = 16;
-std::atomic<int> g_smooth_choice[kTuneSlots];
-std::atomic<int> g_resid_choice[kTuneSlots];
+constexpr int kTuneMaxN = 4097;
+std::atomic<int> g_smooth_choice[kTuneMaxN + 1];
+std::atomic<int> g_resid_choice[kTuneMaxN + 1];
 std::atomic<int> g_tune_init{0};
 
-int tune_slot(int n)
-{
-    if (n < 3) return -1;
-    const unsigned m = (unsigned)(n - 1);
-    if (m & (m - 1)) return -1;
-    int l = 0;
-    while ((1u << l) < m) ++l;
-    return l < kTuneSlots ? l : -1;
-}
+int tune_slot(int n) { return (n >= 3 && n <= kTuneMaxN && (n & 1)) ? n : -1; }
 
 void tune_init()
 {
     if (g_tune_init.load(std::memory_order_acquire)) return;
-    for (int i = 0; i < kTuneSlots; ++i) {
+    for (int i = 0; i <= kTuneMaxN; ++i) {
         g_smooth_choice[i].store(-1, std::memory_order_relaxed);
         g_resid_choice[i].store(-1, std::memory_order_relaxed);
     }

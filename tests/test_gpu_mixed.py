@@ -76,7 +76,8 @@ def test_correction_residual_matches_oracle_definition(name, n, amp):
     assert np.max(np.abs(got - ref)) <= 2e-4 * scale
 
 
-@pytest.mark.parametrize("name,n,amp", [("exp", 33, 1e-4), ("cosine", 65, 1e-5), ("exp", 129, 1e-6)])
+@pytest.mark.parametrize("name,n,amp", [("exp", 33, 1e-4), ("cosine", 65, 1e-5), ("exp", 129, 1e-6),
+                                        ("exp", 45, 1e-5)])
 def test_correction_sweep_matches_oracle_sweep(name, n, amp):
     """One correction sweep against the oracle's Gauss-Seidel sweep on
     w = u + e with right-hand side det(D^2_h u) + rhs, in the regime the
@@ -103,7 +104,8 @@ def test_correction_sweep_matches_oracle_sweep(name, n, amp):
     assert np.max(np.abs(got - e_ref)) <= 1e-3 * change + 1e-6 * np.max(np.abs(e_ref))
 
 
-@pytest.mark.parametrize("name,n", [("exp", 33), ("cosine", 129), ("exp", 257)])
+@pytest.mark.parametrize("name,n", [("exp", 33), ("cosine", 129), ("exp", 257), ("exp", 37), ("cosine", 71),
+                                    ("exp", 135)])   # ragged last tiles for every tile size
 def test_plane_sweeps_equal_colour_sweeps_bitwise(name, n):
     """Pairs of sweeps run by k parity (two launches per sweep, plane tiles
     of 16, 32 or 64 points that recompute a halo, a second e buffer) give the
@@ -139,11 +141,11 @@ def test_plane_sweeps_equal_colour_sweeps_bitwise(name, n):
         M.ma_set_corr_tuning(n, -1, -1)
 
 
+@pytest.mark.parametrize("n", [129, 71])
 @pytest.mark.parametrize("choice", [1, 2, 3])
-def test_residual_tiles_agree(choice):
+def test_residual_tiles_agree(choice, n):
     """The three residual tile sizes compute the same values (the same
     arithmetic per point), with a zero shell."""
-    n = 129
     pr = P.make("cosine", n, seed=7)
     e = smooth_correction_field(n, 1e-5, 11)
     rng = np.random.default_rng(4)

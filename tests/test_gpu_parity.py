@@ -52,7 +52,8 @@ def perturbed(name, n, amp, seed=0):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("name,n,amp", [("exp", 17, 1e-4), ("exp", 33, 1e-5), ("cosine", 65, 1e-6),
-                                        ("exp", 129, 1e-7), ("sine", 33, 1e-4)])
+                                        ("exp", 129, 1e-7), ("sine", 33, 1e-4),
+                                        ("exp", 23, 1e-4), ("cosine", 71, 1e-6)])   # ragged: n - 1 not 2^k
 def test_smooth_one_sweep_matches_oracle(name, n, amp):
     pr, u0 = perturbed(name, n, amp)
     ref = u0.copy()
@@ -109,7 +110,8 @@ def _residual_bound(u, h, name):
     return 64.0 * EPS * np.max(np.abs(u)) / h ** 2 * hmax ** 2
 
 
-@pytest.mark.parametrize("name,n", [("exp", 17), ("exp", 65), ("cosine", 129), ("sine", 33)])
+@pytest.mark.parametrize("name,n", [("exp", 17), ("exp", 65), ("cosine", 129), ("sine", 33), ("exp", 23),
+                                    ("cosine", 71)])
 def test_residual_matches_oracle(name, n):
     pr, u0 = perturbed(name, n, 1e-6)
     ref = O.residual(u0, pr.f, pr.h)
@@ -129,7 +131,7 @@ def test_residual_of_quadratic_is_exactly_zero():
     assert np.all(host(r) == 0.0)
 
 
-@pytest.mark.parametrize("nf", [9, 33, 129])
+@pytest.mark.parametrize("nf", [9, 33, 129, 23, 71])
 @pytest.mark.parametrize("kind", [M.MA_HALF_WEIGHTING, M.MA_FULL_WEIGHTING])
 def test_restrictions_match_oracle(nf, kind):
     rng = np.random.default_rng(nf + kind)
@@ -145,7 +147,7 @@ def test_restrictions_match_oracle(nf, kind):
     assert np.array_equal(host(uc), O.inject(v))
 
 
-@pytest.mark.parametrize("nc", [5, 17, 65])
+@pytest.mark.parametrize("nc", [5, 17, 65, 13, 37])
 def test_prolong_interpolate_coarse_rhs_match_oracle(nc):
     nf = 2 * nc - 1
     rng = np.random.default_rng(nc)
