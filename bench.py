@@ -136,6 +136,16 @@ def oracle_sample(pr, tol, problem_cycles=None):
             "est_solve_s": est, "cycles": problem_cycles}
 
 
+def workload_config(args, world: int = 1) -> dict:
+    """The benchmark's workload description, shared by both arms."""
+    return {"workload": f"Example 4 exp(|x|^2/2) {args.n}^3, FMG + FAS V(2,2), 8-colour nonlinear GS, "
+                        f"tol {args.tol:g} relative max-norm residual (FP64)",
+            "n": args.n, "tol": args.tol,
+            "precision": "mixed: FP32 correction V-cycles x3 per FP64 fine residual and update",
+            "restrict": "full weighting", "parallelism": f"replicas x{world}",
+            "l2": "working set larger than L2 (no flush needed)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -159,9 +169,7 @@ def run_reference(args):
             "unit": "unknowns/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.problem} {args.n}^3 FMG-FAS V(2,2) 8-colour GS, tol {args.tol:g} "
-                                   "relative max-norm", "tol": args.tol, "n": args.n,
-                       "l2": "working set larger than L2"},
+            "config": workload_config(args),
             "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": s["cores"], "kind": "oracle",
                              "sample": s["sample"]},
             "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -530,12 +538,7 @@ def main():
             "value": value, "unit": "unknowns/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"Example 4 exp(|x|^2/2) {args.n}^3, FMG + FAS V(2,2), 8-colour nonlinear GS, "
-                                   f"tol {args.tol:g} relative max-norm residual (FP64)",
-                       "n": args.n, "tol": args.tol,
-                       "precision": "mixed: FP32 correction V-cycles x3 per FP64 fine residual and update",
-                       "restrict": "full weighting", "parallelism": f"replicas x{world}",
-                       "l2": "working set larger than L2 (no flush needed)"},
+            "config": workload_config(args, world),
             "cycles_per_solve": cyc_mixed, "residual": res_mixed.res,
             "fp64": {"value": world * pr.unknowns / (ms_fp64 / 1e3), "unit": "unknowns/s",
                      "ms_per_step": ms_fp64, "cycles_per_solve": cyc_fp64, "residual": res_fp64.res},
