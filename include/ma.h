@@ -313,6 +313,13 @@ ma_status ma_set_corr_tuning(int n, int smooth_choice, int residual_choice);
 /* The choices in force for grid size n. */
 ma_status ma_get_corr_tuning(int n, int *smooth_choice, int *residual_choice);
 
+/* The levels of a correction cycle with n <= 17 (down to the coarsest grid)
+ * run as one single-block launch with the same arithmetic as the separate
+ * kernels (enable = 1, the default), or level by level (0).  Both give the
+ * same bits; hierarchies take the setting when they first record their CUDA
+ * graphs. */
+ma_status ma_set_corr_tail(int enable);
+
 /* Autotuner: times every smoother variant (reps pairs of sweeps each) and
  * every residual tile on the caller's data of one grid (the arguments of
  * ma_smooth_correction; e is overwritten by the sweeps), records the fastest

@@ -206,16 +206,23 @@ cudaError_t refresh_base(ma_hierarchy* H, int apply)
 }
 
 // One FAS V-cycle (Algorithm 1 structure) for N(e) = rhs32 from level l0
-// down and back, starting from the current e on level l0.
+// down and back, starting from the current e on level l0.  The levels with
+// n <= 17 (the tail, down to the coarsest grid) run as one single-block
+// launch with the same arithmetic.
 cudaError_t corr_vcycle_from(ma_hierarchy* H, int l0)
 {
     cudaStream_t s = H->s;
     const ma_hier_desc& d = H->d;
     cudaError_t e;
-    for (int l = l0; l < H->L - 1; ++l) {
+    int lt = H->L - 1;   // first level of the fused tail
+    while (lt > l0 && H->lev[lt - 1].n <= ma::corr_tail_max_n()) --lt;
+    const bool fused = H->lev[lt].n <= ma::corr_tail_max_n();
+    if (!fused) lt = H->L - 1;
+    for (int l = l0; l < lt; ++l) {
         ma::Level& F = H->lev[l];
         ma::Level& C = H->lev[l + 1];
-        if ((e = ma::launch_smooth_corr(F.e, F.e2, F.bstore, F.rhs32, F.n, F.h, d.nu1, H->events, s)) != cudaSuccess)
+        if ((e = ma::launch_smooth_corr(F.e, F.e2, F.bstore, F.rhs32, F.n, F.h, d.nu1, H->events, s)) !=
+            cudaSuccess)
             return e;
         if ((e = ma::launch_residual_corr(F.e, F.bstore, F.rhs32, F.res32, F.n, F.h, s)) != cudaSuccess) return e;
         if ((e = ma::launch_restrict_level_f32(F.e, F.res32, F.n, C.w32, C.e, C.res32, d.restrict_kind,
@@ -224,15 +231,28 @@ cudaError_t corr_vcycle_from(ma_hierarchy* H, int l0)
         if ((e = ma::launch_coarse_rhs_corr(C.w32, C.bstore, C.res32, C.rhs32, C.n, C.h, s)) != cudaSuccess)
             return e;
     }
-    ma::Level& B = H->lev[H->L - 1];
-    if ((e = ma::launch_coarsest_corr(B.e, B.bstore, B.rhs32, B.n, B.h, d.coarse_sweeps, H->events, s)) !=
-        cudaSuccess)
-        return e;
-    for (int l = H->L - 2; l >= l0; --l) {
+    if (fused) {
+        ma::TailSpec spec[4];
+        const int nlev = H->L - lt;
+        for (int q = 0; q < nlev; ++q) {
+            ma::Level& A = H->lev[lt + q];
+            spec[q] = ma::TailSpec{A.n, A.h, A.e, A.bstore, A.rhs32};
+        }
+        if ((e = ma::launch_corr_vcycle_tail(spec, nlev, d.nu1, d.nu2, d.restrict_kind, d.approx_restrict,
+                                             d.coarse_sweeps, H->events, s)) != cudaSuccess)
+            return e;
+    } else {
+        ma::Level& B = H->lev[H->L - 1];
+        if ((e = ma::launch_coarsest_corr(B.e, B.bstore, B.rhs32, B.n, B.h, d.coarse_sweeps, H->events, s)) !=
+            cudaSuccess)
+            return e;
+    }
+    for (int l = lt - 1; l >= l0; --l) {
         ma::Level& F = H->lev[l];
         ma::Level& C = H->lev[l + 1];
         if ((e = ma::launch_prolong_add_f32(C.e, C.w32, C.n, F.e, s)) != cudaSuccess) return e;
-        if ((e = ma::launch_smooth_corr(F.e, F.e2, F.bstore, F.rhs32, F.n, F.h, d.nu2, H->events, s)) != cudaSuccess)
+        if ((e = ma::launch_smooth_corr(F.e, F.e2, F.bstore, F.rhs32, F.n, F.h, d.nu2, H->events, s)) !=
+            cudaSuccess)
             return e;
     }
     return cudaSuccess;
@@ -932,6 +952,12 @@ ma_status ma_residual_correction(const float* e, const float* hi, const float* l
     if (st != MA_OK) return st;
     MA_CK(ma::launch_zero_shell_f32(res, n, s));
     MA_CK(ma::launch_residual_corr(e, scratch, rhs_cm, res, n, h, s));
+    return MA_OK;
+}
+
+ma_status ma_set_corr_tail(int enable)
+{
+    ma::set_corr_tail(enable);
     return MA_OK;
 }
 

@@ -66,6 +66,20 @@ int corr_resid_choice(int n);
 bool set_corr_tuning(int n, int smooth, int resid);   // -1: built-in default; false unless n is odd in [3, 4097]
 cudaError_t launch_smooth_corr_choice(int choice, float* e, float* e2, const void* bstore, const float* rhs_cm, int n,
                                       double h, int nsweeps, unsigned long long* events, cudaStream_t s);
+// One correction V-cycle over the levels with n <= corr_tail_max_n() (the
+// first entry is the level the cycle enters there, the last the coarsest
+// grid), in one single-block launch.
+struct TailSpec {
+    int n;
+    double h;
+    float* e;
+    const void* bstore;
+    const float* rhs_cm;
+};
+int corr_tail_max_n();            // 0 when the fused tail is switched off
+void set_corr_tail(int enable);
+cudaError_t launch_corr_vcycle_tail(const TailSpec* lv, int nlev, int nu1, int nu2, int kind, int approx,
+                                    int coarse_sweeps, unsigned long long* events, cudaStream_t s);
 cudaError_t launch_residual_corr_choice(int choice, const float* e, const void* bstore, const float* rhs_cm,
                                         float* res, int n, double h, cudaStream_t s);
 cudaError_t launch_residual_corr(const float* e, const void* bstore, const float* rhs_cm, float* res, int n,

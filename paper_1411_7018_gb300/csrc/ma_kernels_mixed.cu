@@ -77,22 +77,32 @@ __device__ __forceinline__ S3f corr_hess(const float* __restrict__ e, long long 
         [&](int di, int dj, int dk) -> float { return __ldg(e + p + di + dj * sy + dk * sz) - e0; }, inv_h2);
 }
 
+// The FP32 products below are written as explicit fused multiply-adds in a
+// fixed order, so that every kernel that inlines them (by-colour and plane
+// sweeps, residuals, the fused tail) rounds identically: the compiler may
+// otherwise contract a*b + c*d either way depending on the surrounding code.
+__device__ __forceinline__ float mdiff(float a, float b, float c, float d) { return fmaf(a, b, -(c * d)); }   // ab - cd
+
 __device__ __forceinline__ float det3(const S3f& A)
 {
-    return A.xx * (A.yy * A.zz - A.yz * A.yz) - A.xy * (A.xy * A.zz - A.xz * A.yz) +
-           A.xz * (A.xy * A.yz - A.yy * A.xz);
+    const float c1 = mdiff(A.yy, A.zz, A.yz, A.yz);
+    const float c2 = mdiff(A.xy, A.zz, A.xz, A.yz);
+    const float c3 = mdiff(A.xy, A.yz, A.yy, A.xz);
+    return fmaf(A.xz, c3, fmaf(A.xx, c1, -(A.xy * c2)));
 }
 
 // tr(cof(A) X) for symmetric A, X.
 __device__ __forceinline__ float cof_dot(const S3f& A, const S3f& X)
 {
-    const float cxx = A.yy * A.zz - A.yz * A.yz;
-    const float cyy = A.xx * A.zz - A.xz * A.xz;
-    const float czz = A.xx * A.yy - A.xy * A.xy;
-    const float cxy = A.xz * A.yz - A.xy * A.zz;
-    const float cxz = A.xy * A.yz - A.xz * A.yy;
-    const float cyz = A.xy * A.xz - A.xx * A.yz;
-    return cxx * X.xx + cyy * X.yy + czz * X.zz + 2.0f * (cxy * X.xy + cxz * X.xz + cyz * X.yz);
+    const float cxx = mdiff(A.yy, A.zz, A.yz, A.yz);
+    const float cyy = mdiff(A.xx, A.zz, A.xz, A.xz);
+    const float czz = mdiff(A.xx, A.yy, A.xy, A.xy);
+    const float cxy = mdiff(A.xz, A.yz, A.xy, A.zz);
+    const float cxz = mdiff(A.xy, A.yz, A.xz, A.yy);
+    const float cyz = mdiff(A.xy, A.xz, A.xx, A.yz);
+    const float diag = fmaf(czz, X.zz, fmaf(cyy, X.yy, cxx * X.xx));
+    const float off = fmaf(cyz, X.yz, fmaf(cxz, X.xz, cxy * X.xy));
+    return fmaf(2.0f, off, diag);
 }
 
 // N = det(B + K) - det(B) by the 3x3 expansion.
@@ -115,20 +125,21 @@ __device__ __forceinline__ bool corr_root_fast(const S3f& B, const S3f& K, float
     G.xy = B.xy + K.xy; G.xz = B.xz + K.xz; G.yz = B.yz + K.yz;
     const float c = delta_det(B, K) - r;   // F(0)
     const float T = G.xx + G.yy + G.zz;
-    const float m2 = G.xx * G.yy - G.xy * G.xy;
-    const float M = m2 + (G.xx * G.zz - G.xz * G.xz) + (G.yy * G.zz - G.yz * G.yz);
+    const float m2 = mdiff(G.xx, G.yy, G.xy, G.xy);
+    const float M = m2 + mdiff(G.xx, G.zz, G.xz, G.xz) + mdiff(G.yy, G.zz, G.yz, G.yz);
     const bool pd = G.xx > 0.0f && m2 > 0.0f && det3(G) > 0.0f;
     // with a positive diagonal, |G| summed entrywise is T + |off-diagonals|
     const float scale = T + fabsf(G.xy) + fabsf(G.xz) + fabsf(G.yz);
-    if (!(pd && M > 0.05f * scale * scale)) return false;
-    // F(z) = c - z M + z^2 T - z^3
+    if (!(pd && M > 0.05f * (scale * scale))) return false;
+    // F(z) = c - z M + z^2 T - z^3 = c - z (M - z (T - z));  M(z) = -F'(z)
     float z = __fdividef(c, M);
+    const float T2 = 2.0f * T;
     for (int it = 0; it < 30; ++it) {
-        const float F = c - z * (M - z * (T - z));
-        const float Mz = M - z * (2.0f * T - 3.0f * z);
+        const float F = fmaf(-z, fmaf(-z, T - z, M), c);
+        const float Mz = fmaf(-z, fmaf(-3.0f, z, T2), M);
         const float dz = __fdividef(F, Mz);
         z += dz;
-        if (fabsf(dz) <= 1e-4f * fabsf(z) + 1e-12f * scale) {
+        if (fabsf(dz) <= fmaf(1e-4f, fabsf(z), 1e-12f * scale)) {
             *zout = z;
             return isfinite(z);
         }
@@ -722,6 +733,255 @@ __global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __r
     if (events && ev) atomicAdd(events, ev);
 }
 
+// ---------------------------------------------------------------------------
+// The tail of a correction V-cycle in one block: every level with n <= 17,
+// from the level the cycle enters there down to the coarsest grid and back,
+// with e, w, the residual, B and rhs of those levels in shared memory.  Each
+// step does the per-point arithmetic of its separate kernel -- the sweeps of
+// k_smooth_corr, the residual of k_residual_corr_plane, the restriction of
+// xfer::k_restrict, the right-hand side of k_coarse_rhs_corr, the coarsest
+// solve of k_coarsest_corr, the prolongation of xfer::k_prolong -- so the
+// result is the same bits; it replaces the ~25-40 launches of these latency-
+// bound levels by one.
+// ---------------------------------------------------------------------------
+constexpr int kTailMaxN = 17;
+constexpr int TT = 1024;
+
+struct TailLevel {
+    int n;
+    float inv_h2, h2half;
+    float* e;            // global iterate (read on the top level, written back there)
+    const float* b;      // global colour-major B store
+    const float* rhs;    // global colour-major rhs (read on the top level)
+};
+
+struct TailArgs {
+    int nlev;
+    TailLevel lev[4];
+    int nu1, nu2, kind, approx, coarse_sweeps;
+    unsigned long long* events;
+};
+
+__host__ __device__ inline int tail_level_floats(int n, bool top)
+{
+    const int m = n * n * n, mi = (n - 2) * (n - 2) * (n - 2);
+    return m /* e */ + (top ? 0 : m) /* w */ + m /* res */ + 6 * mi /* B */ + mi /* rhs */;
+}
+
+struct TailSmem {
+    float *e, *w, *r, *b, *rhs;
+};
+
+__device__ __forceinline__ void tail_smooth(const TailSmem& S, int n, float inv_h2, float h2half, int nsw,
+                                            unsigned long long* ev)
+{
+    for (int sw = 0; sw < nsw; ++sw) {
+        int off = 0;
+        for (int c = 0; c < 8; ++c) {
+            const int pi = c & 1, pj = (c >> 1) & 1, pk = (c >> 2) & 1;
+            const int ni = colour_count(n, pi), nj = colour_count(n, pj), nk = colour_count(n, pk);
+            const int cnt = (ni > 0 && nj > 0 && nk > 0) ? ni * nj * nk : 0;
+            for (int t = threadIdx.x; t < cnt; t += TT) {
+                const int i = (pi ? 1 : 2) + 2 * (t % ni);
+                const int j = (pj ? 1 : 2) + 2 * ((t / ni) % nj);
+                const int k = (pk ? 1 : 2) + 2 * (t / (ni * nj));
+                const int p = (k * n + j) * n + i;
+                const float* bp = S.b + 6 * off + t;
+                S3f B;
+                B.xx = bp[0]; B.yy = bp[cnt]; B.zz = bp[2 * cnt]; B.xy = bp[3 * cnt]; B.xz = bp[4 * cnt];
+                B.yz = bp[5 * cnt];
+                const float e0 = S.e[p];
+                const S3f K = corr_hess_sm(S.e, p, n, n * n, e0, inv_h2);
+                bool nonconvex = false;
+                const float z = corr_root(B, K, S.rhs[off + t], &nonconvex);
+                S.e[p] = fmaf(h2half, z, e0);
+                *ev += nonconvex ? 1ull : 0ull;
+            }
+            off += cnt;
+            __syncthreads();
+        }
+    }
+}
+
+// B and rhs of interior point (i, j, k) in the colour-major shared copies.
+__device__ __forceinline__ int tail_cm(int i, int j, int k, int n, int* cnt)
+{
+    const CmPos c = cm_pos(i, j, k, n);
+    *cnt = (int)c.cnt;
+    return (int)(c.off + c.idx);
+}
+
+__device__ __forceinline__ S3f tail_b(const float* b, int i, int j, int k, int n)
+{
+    const CmPos c = cm_pos(i, j, k, n);
+    const float* bp = b + 6 * c.off + c.idx;
+    const int cnt = (int)c.cnt;
+    S3f B;
+    B.xx = bp[0]; B.yy = bp[cnt]; B.zz = bp[2 * cnt]; B.xy = bp[3 * cnt]; B.xz = bp[4 * cnt]; B.yz = bp[5 * cnt];
+    return B;
+}
+
+__device__ __forceinline__ float tail_line(const float* uc, const float* wc, int nc, int Ic, int J0, int K0, int oj,
+                                           int ok, float w)
+{
+    float s = 0.0f;
+    for (int dk = 0; dk <= ok; ++dk)
+        for (int dj = 0; dj <= oj; ++dj) {
+            const int q = ((K0 + dk) * nc + (J0 + dj)) * nc + Ic;
+            s += uc[q] - wc[q];
+        }
+    return s * w;
+}
+
+__global__ void __launch_bounds__(TT, 1) k_corr_vcycle_tail(TailArgs A)
+{
+    extern __shared__ float tsm[];
+    TailSmem S[4];
+    {
+        float* q = tsm;
+        for (int l = 0; l < A.nlev; ++l) {
+            const int n = A.lev[l].n, m = n * n * n, mi = (n - 2) * (n - 2) * (n - 2);
+            S[l].e = q; q += m;
+            S[l].w = l > 0 ? q : nullptr; q += l > 0 ? m : 0;
+            S[l].r = q; q += m;
+            S[l].b = q; q += 6 * mi;
+            S[l].rhs = q; q += mi;
+        }
+    }
+    // inputs: the top level's iterate and rhs, every level's B; residual
+    // shells 0 (restrictions only read the interior, as in the separate path)
+    for (int l = 0; l < A.nlev; ++l) {
+        const int n = A.lev[l].n, m = n * n * n, mi = (n - 2) * (n - 2) * (n - 2);
+        for (int q = threadIdx.x; q < 6 * mi; q += TT) S[l].b[q] = A.lev[l].b[q];
+        for (int q = threadIdx.x; q < m; q += TT) S[l].r[q] = 0.0f;
+        if (l == 0) {
+            for (int q = threadIdx.x; q < m; q += TT) S[0].e[q] = A.lev[0].e[q];
+            for (int q = threadIdx.x; q < mi; q += TT) S[0].rhs[q] = A.lev[0].rhs[q];
+        }
+    }
+    __syncthreads();
+    unsigned long long ev = 0;
+    const int L = A.nlev;
+    for (int l = 0; l < L - 1; ++l) {
+        const TailSmem& F = S[l];
+        const TailSmem& C = S[l + 1];
+        const int nf = A.lev[l].n, nc = A.lev[l + 1].n;
+        tail_smooth(F, nf, A.lev[l].inv_h2, A.lev[l].h2half, A.nu1, &ev);
+        // residual on the fine interior
+        for (int q = threadIdx.x; q < (nf - 2) * (nf - 2) * (nf - 2); q += TT) {
+            const int i = 1 + q % (nf - 2), j = 1 + (q / (nf - 2)) % (nf - 2), k = 1 + q / ((nf - 2) * (nf - 2));
+            const int p = (k * nf + j) * nf + i;
+            int cnt;
+            const int cm = tail_cm(i, j, k, nf, &cnt);
+            const S3f B = tail_b(F.b, i, j, k, nf);
+            const S3f K = corr_hess_sm(F.e, p, nf, nf * nf, F.e[p], A.lev[l].inv_h2);
+            F.r[p] = F.rhs[cm] - delta_det(B, K);
+        }
+        __syncthreads();
+        // restriction: coarse residual, approximation restriction of e
+        for (int pc = threadIdx.x; pc < nc * nc * nc; pc += TT) {
+            const int I = pc % nc, J = (pc / nc) % nc, K = pc / (nc * nc);
+            const int pf = ((2 * K) * nf + 2 * J) * nf + 2 * I;
+            const bool inside = I > 0 && J > 0 && K > 0 && I < nc - 1 && J < nc - 1 && K < nc - 1;
+            C.r[pc] = inside ? xfer::weighted_restrict(F.r, pf, nf, (long long)nf * nf, A.kind) : 0.0f;
+            const float w = (inside && A.approx == 1) ? xfer::weighted_restrict(F.e, pf, nf, (long long)nf * nf, A.kind)
+                                                     : F.e[pf];
+            C.w[pc] = w;
+            C.e[pc] = w;
+        }
+        __syncthreads();
+        // coarse right-hand side N_H(w_H) + res_H, colour-major
+        for (int q = threadIdx.x; q < (nc - 2) * (nc - 2) * (nc - 2); q += TT) {
+            const int i = 1 + q % (nc - 2), j = 1 + (q / (nc - 2)) % (nc - 2), k = 1 + q / ((nc - 2) * (nc - 2));
+            const int p = (k * nc + j) * nc + i;
+            int cnt;
+            const int cm = tail_cm(i, j, k, nc, &cnt);
+            const S3f B = tail_b(C.b, i, j, k, nc);
+            const S3f K = corr_hess_sm(C.w, p, nc, nc * nc, C.w[p], A.lev[l + 1].inv_h2);
+            C.rhs[cm] = delta_det(B, K) + C.r[p];
+        }
+        __syncthreads();
+    }
+    {   // coarsest grid: sweeps until max|de| <= 2e-6 max|e| (at most 40), or a fixed count
+        const TailSmem& Bt = S[L - 1];
+        const int n = A.lev[L - 1].n;
+        __shared__ float red[TT / 32][2];
+        __shared__ int stop;
+        const int max_sweeps = A.coarse_sweeps > 0 ? A.coarse_sweeps : 40;
+        for (int s = 0; s < max_sweeps; ++s) {
+            float du = 0.0f, um = 0.0f;
+            int off = 0;
+            for (int c = 0; c < 8; ++c) {
+                const int pi = c & 1, pj = (c >> 1) & 1, pk = (c >> 2) & 1;
+                const int ni = colour_count(n, pi), nj = colour_count(n, pj), nk = colour_count(n, pk);
+                const int cnt = (ni > 0 && nj > 0 && nk > 0) ? ni * nj * nk : 0;
+                for (int t = threadIdx.x; t < cnt; t += TT) {
+                    const int i = (pi ? 1 : 2) + 2 * (t % ni);
+                    const int j = (pj ? 1 : 2) + 2 * ((t / ni) % nj);
+                    const int k = (pk ? 1 : 2) + 2 * (t / (ni * nj));
+                    const int p = (k * n + j) * n + i;
+                    const float e0 = Bt.e[p];
+                    const float* b = Bt.b + 6 * off + t;
+                    S3f Bm;
+                    Bm.xx = b[0]; Bm.yy = b[cnt]; Bm.zz = b[2 * cnt]; Bm.xy = b[3 * cnt]; Bm.xz = b[4 * cnt];
+                    Bm.yz = b[5 * cnt];
+                    const S3f K = corr_hess_sm(Bt.e, p, n, n * n, e0, A.lev[L - 1].inv_h2);
+                    bool nonconvex = false;
+                    const float z = corr_root(Bm, K, Bt.rhs[off + t], &nonconvex);
+                    const float v = fmaf(A.lev[L - 1].h2half, z, e0);
+                    Bt.e[p] = v;
+                    du = fmaxf(du, fabsf(v - e0));
+                    um = fmaxf(um, fabsf(v));
+                    ev += nonconvex ? 1ull : 0ull;
+                }
+                off += cnt;
+                __syncthreads();
+            }
+            if (A.coarse_sweeps > 0) continue;
+            for (int o = 16; o > 0; o >>= 1) {
+                du = fmaxf(du, __shfl_down_sync(0xffffffffu, du, o));
+                um = fmaxf(um, __shfl_down_sync(0xffffffffu, um, o));
+            }
+            if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5][0] = du; red[threadIdx.x >> 5][1] = um; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float a = 0.0f, b = 0.0f;
+                for (int w = 0; w < TT / 32; ++w) { a = fmaxf(a, red[w][0]); b = fmaxf(b, red[w][1]); }
+                stop = (a <= 2e-6f * b) ? 1 : 0;
+            }
+            __syncthreads();
+            if (stop) break;
+        }
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        const TailSmem& F = S[l];
+        const TailSmem& C = S[l + 1];
+        const int nf = A.lev[l].n, nc = A.lev[l + 1].n;
+        // prolongation e_h += I(e_H - w_H) on the fine interior (the pair form of xfer::k_prolong)
+        for (int q = threadIdx.x; q < (nf - 2) * (nf - 2) * (nf - 2); q += TT) {
+            const int i = 1 + q % (nf - 2), j = 1 + (q / (nf - 2)) % (nf - 2), k = 1 + q / ((nf - 2) * (nf - 2));
+            const int J0 = j >> 1, K0 = k >> 1, oj = j & 1, ok = k & 1;
+            const float w = 1.0f / (float)(1 << (oj + ok));
+            float v;
+            if (i & 1) {
+                const int I = i >> 1;
+                const float a = tail_line(C.e, C.w, nc, I, J0, K0, oj, ok, w);
+                const float b = tail_line(C.e, C.w, nc, I + 1, J0, K0, oj, ok, w);
+                v = (a + b) * 0.5f;
+            } else {
+                v = tail_line(C.e, C.w, nc, i >> 1, J0, K0, oj, ok, w);
+            }
+            const int p = (k * nf + j) * nf + i;
+            F.e[p] = F.e[p] + v;
+        }
+        __syncthreads();
+        tail_smooth(F, nf, A.lev[l].inv_h2, A.lev[l].h2half, A.nu2, &ev);
+    }
+    const int m0 = A.lev[0].n * A.lev[0].n * A.lev[0].n;
+    for (int q = threadIdx.x; q < m0; q += TT) A.lev[0].e[q] = S[0].e[q];
+    if (A.events && ev) atomicAdd(A.events, ev);
+}
+
 // FP64 <-> FP32 copies of whole grids (the FP32 mode's iterate and data).
 __global__ void k_f64_to_f32(const double* __restrict__ u, float* __restrict__ e, long long m)
 {
@@ -1023,6 +1283,46 @@ cudaError_t launch_coarsest_corr(float* e, const void* bstore, const float* rhs_
     return cudaGetLastError();
 }
 
+int tail_smem_bytes(const int* ns, int nlev)
+{
+    int f = 0;
+    for (int l = 0; l < nlev; ++l) f += tail_level_floats(ns[l], l == 0);
+    return f * (int)sizeof(float);
+}
+
+std::atomic<int> g_tail_enabled{1};
+
+int corr_tail_max_n() { return g_tail_enabled.load(std::memory_order_relaxed) ? kTailMaxN : 0; }
+
+void set_corr_tail(int enable) { g_tail_enabled.store(enable ? 1 : 0, std::memory_order_relaxed); }
+
+cudaError_t launch_corr_vcycle_tail(const TailSpec* lv, int nlev, int nu1, int nu2, int kind, int approx,
+                                    int coarse_sweeps, unsigned long long* events, cudaStream_t s)
+{
+    if (nlev < 1 || nlev > 4) return cudaErrorInvalidValue;
+    TailArgs A;
+    A.nlev = nlev;
+    int ns[4];
+    for (int l = 0; l < nlev; ++l) {
+        const double h = lv[l].h;
+        A.lev[l].n = ns[l] = lv[l].n;
+        A.lev[l].inv_h2 = (float)(1.0 / (h * h));
+        A.lev[l].h2half = (float)(0.5 * h * h);
+        A.lev[l].e = lv[l].e;
+        A.lev[l].b = (const float*)lv[l].bstore;
+        A.lev[l].rhs = lv[l].rhs_cm;
+    }
+    A.nu1 = nu1;
+    A.nu2 = nu2;
+    A.kind = kind;
+    A.approx = approx;
+    A.coarse_sweeps = coarse_sweeps;
+    A.events = events;
+    count_launches(1);
+    k_corr_vcycle_tail<<<1, TT, tail_smem_bytes(ns, nlev), s>>>(A);
+    return cudaGetLastError();
+}
+
 cudaError_t prepare_coarsest_f64();
 
 cudaError_t prepare_kernels()
@@ -1038,6 +1338,10 @@ cudaError_t prepare_kernels()
         return e;
     if ((e = cudaFuncSetAttribute(k_residual_corr_plane<64, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) !=
         cudaSuccess)
+        return e;
+    const int tail_ns[4] = {17, 9, 5, 3};
+    if ((e = cudaFuncSetAttribute(k_corr_vcycle_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tail_smem_bytes(tail_ns, 4))) != cudaSuccess)
         return e;
     return cudaFuncSetAttribute(k_coarsest_corr, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)coarsest_corr_smem(17));

@@ -17,28 +17,33 @@ __device__ __forceinline__ long long lin(int i, int j, int k, int n)
     return ((long long)k * n + j) * n + i;
 }
 
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
 // Restriction I_h^H at a fine point p with strides sy, sz.  kind 0: the
 // printed 7-point half weighting (6 centre + 6 faces) / 12; kind 1: 27-point
-// full weighting, separable (1 2 1)/4 along each axis.
+// full weighting, separable (1 2 1)/4 along each axis.  Written with explicit
+// fused multiply-adds in a fixed order so that every kernel that inlines it
+// rounds identically.
 template <typename T>
 __device__ __forceinline__ T weighted_restrict(const T* __restrict__ v, long long p, long long sy, long long sz,
                                                int kind)
 {
     if (kind == 0) {
         const T faces = (v[p + 1] + v[p - 1]) + (v[p + sy] + v[p - sy]) + (v[p + sz] + v[p - sz]);
-        return (T(6) * v[p] + faces) * (T(1) / T(12));
+        return fma_t(T(6), v[p], faces) * (T(1) / T(12));
     }
     T acc = T(0);
-    #pragma unroll
+#pragma unroll
     for (int dk = -1; dk <= 1; ++dk) {
         T plane = T(0);
-        #pragma unroll
+#pragma unroll
         for (int dj = -1; dj <= 1; ++dj) {
             const long long q = p + dk * sz + dj * sy;
-            const T row = v[q - 1] + T(2) * v[q] + v[q + 1];
-            plane += (dj == 0 ? T(2) : T(1)) * row;
+            const T row = fma_t(T(2), v[q], v[q - 1] + v[q + 1]);
+            plane = fma_t(dj == 0 ? T(2) : T(1), row, plane);
         }
-        acc += (dk == 0 ? T(2) : T(1)) * plane;
+        acc = fma_t(dk == 0 ? T(2) : T(1), plane, acc);
     }
     return acc * (T(1) / T(64));
 }
