@@ -320,6 +320,15 @@ ma_status ma_get_corr_tuning(int n, int *smooth_choice, int *residual_choice);
  * graphs. */
 ma_status ma_set_corr_tail(int enable);
 
+/* The same for the FP64 V-cycles (ma_vcycle, the FP64 solves and FMG below
+ * the finest level of every precision): the levels with n <= 17 run as one
+ * single-block launch with u, w, r and rhs of those levels in shared memory
+ * (enable = 1, the default), or level by level (0).  Both give the same
+ * bits; the coarse levels' arrays in the workspace are then left as they
+ * were (nothing outside the cycle reads them).  Hierarchies take the setting
+ * when they first record their CUDA graphs. */
+ma_status ma_set_vcycle_tail(int enable);
+
 /* Autotuner: times every smoother variant (reps pairs of sweeps each) and
  * every residual tile on the caller's data of one grid (the arguments of
  * ma_smooth_correction; e is overwritten by the sweeps), records the fastest

@@ -128,13 +128,19 @@ size_t layout(ma_hierarchy* H, const ma_hier_desc* d, char* base)
     return off;
 }
 
-// Algorithm 1 from level l0 down to the coarsest grid and back.
+// Algorithm 1 from level l0 down to the coarsest grid and back.  The levels
+// with n <= 17 (the tail, down to the coarsest grid) run as one single-block
+// launch with the same arithmetic.
 cudaError_t vcycle_from(ma_hierarchy* H, int l0)
 {
     cudaStream_t s = H->s;
     const ma_hier_desc& d = H->d;
     cudaError_t e;
-    for (int l = l0; l < H->L - 1; ++l) {
+    int lt = H->L - 1;   // first level of the fused tail
+    while (lt > l0 && H->lev[lt - 1].n <= ma::vcycle_tail_max_n()) --lt;
+    const bool fused = H->lev[lt].n <= ma::vcycle_tail_max_n();
+    if (!fused) lt = H->L - 1;
+    for (int l = l0; l < lt; ++l) {
         ma::Level& F = H->lev[l];
         ma::Level& C = H->lev[l + 1];
         if ((e = ma::launch_smooth(F.u, F.rhs, F.n, F.h, d.nu1, H->events, s)) != cudaSuccess) return e;   // (2)
@@ -144,9 +150,22 @@ cudaError_t vcycle_from(ma_hierarchy* H, int l0)
             return e;                                                                                        // (3)-(4)
         if ((e = ma::launch_coarse_rhs(C.w, C.r, C.rhs, C.n, C.h, s)) != cudaSuccess) return e;             // (5)
     }
-    ma::Level& B = H->lev[H->L - 1];
-    if ((e = ma::launch_coarsest(B.u, B.rhs, B.n, B.h, d.coarse_sweeps, H->events, s)) != cudaSuccess) return e;  // (1)
-    for (int l = H->L - 2; l >= l0; --l) {
+    if (fused) {
+        ma::TailSpec64 spec[4];
+        const int nlev = H->L - lt;
+        for (int q = 0; q < nlev; ++q) {
+            ma::Level& A = H->lev[lt + q];
+            spec[q] = ma::TailSpec64{A.n, A.h, A.u, A.rhs};
+        }
+        if ((e = ma::launch_vcycle_tail(spec, nlev, d.nu1, d.nu2, d.restrict_kind, d.approx_restrict,
+                                        d.coarse_sweeps, H->events, s)) != cudaSuccess)
+            return e;
+    } else {
+        ma::Level& B = H->lev[H->L - 1];
+        if ((e = ma::launch_coarsest(B.u, B.rhs, B.n, B.h, d.coarse_sweeps, H->events, s)) != cudaSuccess)
+            return e;                                                                                      // (1)
+    }
+    for (int l = lt - 1; l >= l0; --l) {
         ma::Level& F = H->lev[l];
         ma::Level& C = H->lev[l + 1];
         if ((e = ma::launch_prolong_add(C.u, C.w, C.n, F.u, s)) != cudaSuccess) return e;                  // (7)-(8)
@@ -958,6 +977,12 @@ ma_status ma_residual_correction(const float* e, const float* hi, const float* l
 ma_status ma_set_corr_tail(int enable)
 {
     ma::set_corr_tail(enable);
+    return MA_OK;
+}
+
+ma_status ma_set_vcycle_tail(int enable)
+{
+    ma::set_vcycle_tail(enable);
     return MA_OK;
 }
 

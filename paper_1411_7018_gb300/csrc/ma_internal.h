@@ -44,6 +44,19 @@ cudaError_t launch_coarsest(double* u, const double* rhs, int n, double h, int s
                             unsigned long long* events, cudaStream_t s);
 cudaError_t launch_copy_rhs_bc(const double* f, const double* g, double* rhs, double* u, int n,
                                int* bad, cudaStream_t s);
+// One FP64 V-cycle over the levels with n <= vcycle_tail_max_n() (the first
+// entry is the level the cycle enters there, the last the coarsest grid), in
+// one single-block launch; the coarse levels' u, w, r, rhs stay on chip.
+struct TailSpec64 {
+    int n;
+    double h;
+    double* u;
+    const double* rhs;
+};
+int vcycle_tail_max_n();          // 0 when the fused tail is switched off
+void set_vcycle_tail(int enable);
+cudaError_t launch_vcycle_tail(const TailSpec64* lv, int nlev, int nu1, int nu2, int kind, int approx,
+                               int coarse_sweeps, unsigned long long* events, cudaStream_t s);
 
 // Mixed-precision kernels (ma_kernels_mixed.cu).  e, res, w are n^3 floats
 // in the natural layout; hi + lo is the FP32 split of the FP64 iterate; the

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(BX * BY) k_smooth_colour(double* u, const doub
     const double v0 = u[p];
     const HessS H = gather_hess(u, p, sy, sz, v0);
     bool nonconvex = false;
-    const double z = smallest_root(H, h6 * rhs[p], &nonconvex);   // h6 = 64 h^6: the 4 Hs scaling
+    const double z = smallest_root(H, __dmul_rn(h6, rhs[p]), &nonconvex);   // h6 = 64 h^6: the 4 Hs scaling
     u[p] = fma(0.125, z, v0);
     if (nonconvex && events) atomicAdd(events, 1ull);
 }
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(COARSE_THREADS) k_coarsest(double* u, const do
                 const double v0 = su[p];
                 const HessS H = gather_hess_plain(su, p, n, n * n, v0);
                 bool nonconvex = false;
-                const double z = smallest_root_precise(H, h6 * sr[p], &nonconvex);
+                const double z = smallest_root_precise(H, __dmul_rn(h6, sr[p]), &nonconvex);
                 const double v = fma(0.125, z, v0);
                 su[p] = v;
                 du = fmax(du, fabs(v - v0));
@@ -251,6 +251,244 @@ __global__ void __launch_bounds__(COARSE_THREADS) k_coarsest(double* u, const do
     }
     for (int q = threadIdx.x; q < m; q += COARSE_THREADS) u[q] = su[q];
     if (events && ev) atomicAdd(events, ev);
+}
+
+// ---------------------------------------------------------------------------
+// The tail of an FP64 V-cycle in one block: every level with n <= 17, from
+// the level the cycle enters there down to the coarsest grid and back, with
+// u, w, r and rhs of those levels in shared memory.  Each step repeats the
+// per-point arithmetic of its separate kernel -- the colour sweeps of
+// k_smooth_colour, the residual of resid::k_residual_col (its column
+// grouping of the cross differences), the restriction of xfer::k_restrict,
+// the tau-corrected right-hand side of k_coarse_rhs, the coarsest solve of
+// k_coarsest, the prolongation of xfer::k_prolong -- so the result is the
+// same bits; it replaces the ~100 launches these latency-bound levels take
+// (8 colour launches per sweep) by one.  FMG runs such a cycle from every
+// level, so it pays most there.
+// ---------------------------------------------------------------------------
+constexpr int T64 = 512;
+
+struct Tail64Level {
+    int n;
+    double h6, inv_h6;   // 64 h^6 (the 4 Hs scaling) and its reciprocal
+    double* u;           // global iterate (read on the top level, written back there)
+    const double* rhs;   // global right-hand side (read on the top level)
+};
+
+struct Tail64Args {
+    int nlev;
+    Tail64Level lev[4];
+    int nu1, nu2, kind, approx, coarse_sweeps;
+    unsigned long long* events;
+};
+
+__host__ __device__ inline int tail64_level_doubles(int n, bool top)
+{
+    const int m = n * n * n;
+    return m /* u */ + (top ? 0 : m) /* w */ + m /* r */ + m /* rhs */;
+}
+
+struct Tail64Smem {
+    double *u, *w, *r, *rhs;
+};
+
+__device__ __forceinline__ void tail64_smooth(const Tail64Smem& S, int n, double h6, int nsw, unsigned long long* ev)
+{
+    for (int sw = 0; sw < nsw; ++sw) {
+        for (int c = 0; c < 8; ++c) {
+            const int pi = c & 1, pj = (c >> 1) & 1, pk = (c >> 2) & 1;
+            const int ni = colour_count(n, pi), nj = colour_count(n, pj), nk = colour_count(n, pk);
+            const int cnt = (ni > 0 && nj > 0 && nk > 0) ? ni * nj * nk : 0;
+            for (int t = threadIdx.x; t < cnt; t += T64) {
+                const int i = (pi ? 1 : 2) + 2 * (t % ni);
+                const int j = (pj ? 1 : 2) + 2 * ((t / ni) % nj);
+                const int k = (pk ? 1 : 2) + 2 * (t / (ni * nj));
+                const int p = (k * n + j) * n + i;
+                const double v0 = S.u[p];
+                const HessS H = gather_hess_plain(S.u, p, n, n * n, v0);
+                bool nonconvex = false;
+                const double z = smallest_root(H, __dmul_rn(h6, S.rhs[p]), &nonconvex);
+                S.u[p] = fma(0.125, z, v0);
+                *ev += nonconvex ? 1ull : 0ull;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// rhs - det(D^2_h u) at interior point p, the cross differences grouped as
+// the column-marching residual kernel forms them.
+__device__ __forceinline__ double tail64_residual(const double* u, int p, int n, double rhs, double inv_h6)
+{
+    const int sy = n, sz = n * n;
+    const double* q = u + p;
+    const double a = q[1] + q[-1];
+    const double b = q[sy] + q[-sy];
+    const double c = q[sz] + q[-sz];
+    const double r4 = (q[sy + 1] - q[sy - 1]) - (q[-sy + 1] - q[-sy - 1]);
+    const double dxc = q[sz + 1] - q[sz - 1], dxa = q[-sz + 1] - q[-sz - 1];
+    const double dyc = q[sz + sy] - q[sz - sy], dya = q[-sz + sy] - q[-sz - sy];
+    HessS H;
+    const double m8v = -8.0 * q[0];
+    H.A = fma(4.0, a, m8v);
+    H.B = fma(4.0, b, m8v);
+    H.C = fma(4.0, c, m8v);
+    H.R = r4;
+    H.S = dxc - dxa;
+    H.T = dyc - dya;
+    return fma(-det0(H), inv_h6, rhs);
+}
+
+__device__ __forceinline__ double tail64_line(const double* uc, const double* wc, int nc, int Ic, int J0, int K0,
+                                              int oj, int ok, double w)
+{
+    double s = 0.0;
+    for (int dk = 0; dk <= ok; ++dk)
+        for (int dj = 0; dj <= oj; ++dj) {
+            const int q = ((K0 + dk) * nc + (J0 + dj)) * nc + Ic;
+            s += uc[q] - wc[q];
+        }
+    return s * w;
+}
+
+__global__ void __launch_bounds__(T64, 1) k_vcycle_tail(Tail64Args A)
+{
+    extern __shared__ double t64sm[];
+    Tail64Smem S[4];
+    {
+        double* q = t64sm;
+        for (int l = 0; l < A.nlev; ++l) {
+            const int m = A.lev[l].n * A.lev[l].n * A.lev[l].n;
+            S[l].u = q; q += m;
+            S[l].w = l > 0 ? q : nullptr; q += l > 0 ? m : 0;
+            S[l].r = q; q += m;
+            S[l].rhs = q; q += m;
+        }
+    }
+    // inputs: the top level's iterate and right-hand side; residual shells 0
+    // (the restriction reads only the interior, as in the separate path)
+    for (int l = 0; l < A.nlev; ++l) {
+        const int m = A.lev[l].n * A.lev[l].n * A.lev[l].n;
+        for (int q = threadIdx.x; q < m; q += T64) S[l].r[q] = 0.0;
+        if (l == 0)
+            for (int q = threadIdx.x; q < m; q += T64) { S[0].u[q] = A.lev[0].u[q]; S[0].rhs[q] = A.lev[0].rhs[q]; }
+    }
+    __syncthreads();
+    unsigned long long ev = 0;
+    const int L = A.nlev;
+    for (int l = 0; l < L - 1; ++l) {
+        const Tail64Smem& F = S[l];
+        const Tail64Smem& C = S[l + 1];
+        const int nf = A.lev[l].n, nc = A.lev[l + 1].n;
+        tail64_smooth(F, nf, A.lev[l].h6, A.nu1, &ev);                                       // (2)
+        for (int q = threadIdx.x; q < (nf - 2) * (nf - 2) * (nf - 2); q += T64) {        // (3)
+            const int i = 1 + q % (nf - 2), j = 1 + (q / (nf - 2)) % (nf - 2), k = 1 + q / ((nf - 2) * (nf - 2));
+            const int p = (k * nf + j) * nf + i;
+            F.r[p] = tail64_residual(F.u, p, nf, F.rhs[p], A.lev[l].inv_h6);
+        }
+        __syncthreads();
+        for (int pc = threadIdx.x; pc < nc * nc * nc; pc += T64) {                        // (3)-(4)
+            const int I = pc % nc, J = (pc / nc) % nc, K = pc / (nc * nc);
+            const int pf = ((2 * K) * nf + 2 * J) * nf + 2 * I;
+            const bool inside = I > 0 && J > 0 && K > 0 && I < nc - 1 && J < nc - 1 && K < nc - 1;
+            C.r[pc] = inside ? xfer::weighted_restrict(F.r, pf, nf, (long long)nf * nf, A.kind) : 0.0;
+            const double w = (inside && A.approx == 1) ? xfer::weighted_restrict(F.u, pf, nf, (long long)nf * nf, A.kind)
+                                                      : F.u[pf];
+            C.w[pc] = w;
+            C.u[pc] = w;
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < nc * nc * nc; p += T64) {                           // (5)
+            const int I = p % nc, J = (p / nc) % nc, K = p / (nc * nc);
+            double b = 0.0;
+            if (I > 0 && J > 0 && K > 0 && I < nc - 1 && J < nc - 1 && K < nc - 1) {
+                const HessS H = gather_hess_plain(C.w, p, nc, nc * nc, C.w[p]);
+                b = fma(det0(H), A.lev[l + 1].inv_h6, C.r[p]);
+            }
+            C.rhs[p] = b;
+        }
+        __syncthreads();
+    }
+    {   // (1) coarsest grid: sweeps until max|du| <= 1e-14 max|u| (at most 100), or a fixed count
+        const Tail64Smem& Bt = S[L - 1];
+        const int n = A.lev[L - 1].n;
+        const double h6 = A.lev[L - 1].h6;
+        __shared__ double red[T64 / 32][2];
+        __shared__ int stop;
+        const int max_sweeps = A.coarse_sweeps > 0 ? A.coarse_sweeps : 100;
+        for (int s = 0; s < max_sweeps; ++s) {
+            double du = 0.0, um = 0.0;
+            for (int c = 0; c < 8; ++c) {
+                const int pi = c & 1, pj = (c >> 1) & 1, pk = (c >> 2) & 1;
+                const int ni = colour_count(n, pi), nj = colour_count(n, pj), nk = colour_count(n, pk);
+                const int cnt = (ni > 0 && nj > 0 && nk > 0) ? ni * nj * nk : 0;
+                for (int t = threadIdx.x; t < cnt; t += T64) {
+                    const int i = (pi ? 1 : 2) + 2 * (t % ni);
+                    const int j = (pj ? 1 : 2) + 2 * ((t / ni) % nj);
+                    const int k = (pk ? 1 : 2) + 2 * (t / (ni * nj));
+                    const int p = (k * n + j) * n + i;
+                    const double v0 = Bt.u[p];
+                    const HessS H = gather_hess_plain(Bt.u, p, n, n * n, v0);
+                    bool nonconvex = false;
+                    const double z = smallest_root_precise(H, __dmul_rn(h6, Bt.rhs[p]), &nonconvex);
+                    const double v = fma(0.125, z, v0);
+                    Bt.u[p] = v;
+                    du = fmax(du, fabs(v - v0));
+                    um = fmax(um, fabs(v));
+                    ev += nonconvex ? 1ull : 0ull;
+                }
+                __syncthreads();
+            }
+            if (A.coarse_sweeps > 0) continue;
+            for (int o = 16; o > 0; o >>= 1) {
+                du = fmax(du, __shfl_down_sync(0xffffffffu, du, o));
+                um = fmax(um, __shfl_down_sync(0xffffffffu, um, o));
+            }
+            if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5][0] = du; red[threadIdx.x >> 5][1] = um; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double a = 0.0, b = 0.0;
+                for (int w = 0; w < T64 / 32; ++w) { a = fmax(a, red[w][0]); b = fmax(b, red[w][1]); }
+                stop = (a <= 1e-14 * b) ? 1 : 0;
+            }
+            __syncthreads();
+            if (stop) break;
+        }
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        const Tail64Smem& F = S[l];
+        const Tail64Smem& C = S[l + 1];
+        const int nf = A.lev[l].n, nc = A.lev[l + 1].n;
+        // (7)-(8) u_h += I(u_H - w_H) on the fine interior (the pair form of xfer::k_prolong)
+        for (int q = threadIdx.x; q < (nf - 2) * (nf - 2) * (nf - 2); q += T64) {
+            const int i = 1 + q % (nf - 2), j = 1 + (q / (nf - 2)) % (nf - 2), k = 1 + q / ((nf - 2) * (nf - 2));
+            const int J0 = j >> 1, K0 = k >> 1, oj = j & 1, ok = k & 1;
+            const double w = 1.0 / (double)(1 << (oj + ok));
+            double v;
+            if (i & 1) {
+                const int I = i >> 1;
+                const double a = tail64_line(C.u, C.w, nc, I, J0, K0, oj, ok, w);
+                const double b = tail64_line(C.u, C.w, nc, I + 1, J0, K0, oj, ok, w);
+                v = (a + b) * 0.5;
+            } else {
+                v = tail64_line(C.u, C.w, nc, i >> 1, J0, K0, oj, ok, w);
+            }
+            const int p = (k * nf + j) * nf + i;
+            F.u[p] = F.u[p] + v;
+        }
+        __syncthreads();
+        tail64_smooth(F, nf, A.lev[l].h6, A.nu2, &ev);                                      // (9)
+    }
+    const int m0 = A.lev[0].n * A.lev[0].n * A.lev[0].n;
+    for (int q = threadIdx.x; q < m0; q += T64) A.lev[0].u[q] = S[0].u[q];
+    if (A.events && ev) atomicAdd(A.events, ev);
+}
+
+int tail64_smem_bytes(const int* ns, int nlev)
+{
+    int d = 0;
+    for (int l = 0; l < nlev; ++l) d += tail64_level_doubles(ns[l], l == 0);
+    return d * (int)sizeof(double);
 }
 
 }  // namespace
@@ -427,10 +665,46 @@ cudaError_t launch_coarsest(double* u, const double* rhs, int n, double h, int s
     return cudaGetLastError();
 }
 
+static std::atomic<int> g_vtail_enabled{1};
+
+int vcycle_tail_max_n() { return g_vtail_enabled.load(std::memory_order_relaxed) ? 17 : 0; }
+
+void set_vcycle_tail(int enable) { g_vtail_enabled.store(enable ? 1 : 0, std::memory_order_relaxed); }
+
+cudaError_t launch_vcycle_tail(const TailSpec64* lv, int nlev, int nu1, int nu2, int kind, int approx,
+                               int coarse_sweeps, unsigned long long* events, cudaStream_t s)
+{
+    if (nlev < 1 || nlev > 4) return cudaErrorInvalidValue;
+    Tail64Args A;
+    A.nlev = nlev;
+    int ns[4];
+    for (int l = 0; l < nlev; ++l) {
+        if (lv[l].n > 17 || (l > 0 && lv[l].n != (lv[l - 1].n + 1) / 2)) return cudaErrorInvalidValue;
+        A.lev[l].n = ns[l] = lv[l].n;
+        A.lev[l].h6 = pow6(lv[l].h);
+        A.lev[l].inv_h6 = 1.0 / pow6(lv[l].h);
+        A.lev[l].u = lv[l].u;
+        A.lev[l].rhs = lv[l].rhs;
+    }
+    A.nu1 = nu1;
+    A.nu2 = nu2;
+    A.kind = kind;
+    A.approx = approx;
+    A.coarse_sweeps = coarse_sweeps;
+    A.events = events;
+    count_launches(1);
+    k_vcycle_tail<<<1, T64, tail64_smem_bytes(ns, nlev), s>>>(A);
+    return cudaGetLastError();
+}
+
 cudaError_t prepare_coarsest_f64()
 {
-    return cudaFuncSetAttribute(k_coarsest, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(2 * sizeof(double) * 17 * 17 * 17));
+    cudaError_t e = cudaFuncSetAttribute(k_coarsest, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * sizeof(double) * 17 * 17 * 17));
+    if (e != cudaSuccess) return e;
+    const int tail_ns[4] = {17, 9, 5, 3};
+    return cudaFuncSetAttribute(k_vcycle_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tail64_smem_bytes(tail_ns, 4));
 }
 
 }  // namespace ma

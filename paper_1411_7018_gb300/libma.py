@@ -86,6 +86,7 @@ _SIGS = {
     "ma_norm_static": [_vp, C.c_int, C.c_double, C.POINTER(C.c_double), _vp],
     "ma_set_corr_tuning": [C.c_int, C.c_int, C.c_int],
     "ma_set_corr_tail": [C.c_int],
+    "ma_set_vcycle_tail": [C.c_int],
     "ma2d_hierarchy_footprint": [C.c_void_p, C.POINTER(C.c_size_t)],
     "ma2d_create_hierarchy": [C.c_void_p, _vp, C.c_size_t, _vp, C.POINTER(_vp)],
     "ma2d_set_rhs_bc": [_vp, _vp, _vp],
@@ -322,6 +323,10 @@ def ma_set_corr_tuning(n: int, smooth_choice: int, residual_choice: int) -> None
 
 def ma_set_corr_tail(enable: bool) -> None:
     _check(load().ma_set_corr_tail(1 if enable else 0))
+
+
+def ma_set_vcycle_tail(enable: bool) -> None:
+    _check(load().ma_set_vcycle_tail(1 if enable else 0))
 
 
 def ma_get_corr_tuning(n: int):

@@ -1,0 +1,109 @@
+"""The fused tail of the FP64 V-cycle (Algorithm 1): the levels with n <= 17
+run as one single-block launch with the arithmetic of the separate kernels,
+so every solve that runs FP64 cycles -- FP64 solves, the paper's FMG
+configuration, FMG below the finest level of the mixed-precision solve --
+gives the same bits and cycle count with the tail fused or level by level,
+in fewer kernel launches.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1411_7018_gb300 import libma as M
+from paper_1411_7018_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    M.load()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _both(desc_fn, name, n, solve_kw, vcycles=0):
+    """Runs the same solve with the tail fused and level by level; returns
+    [(u, cycles, res, launches)] for (fused, separate)."""
+    pr = P.make(name, n)
+    outs = []
+    try:
+        for enable in (True, False):
+            M.ma_set_vcycle_tail(enable)
+            H = M.Hierarchy(desc_fn(pr))
+            H.set_rhs_bc(dev(pr.f), dev(pr.initial()))
+            torch.cuda.synchronize()
+            c0 = M.ma_kernel_launch_count()
+            if vcycles:
+                H.vcycle(vcycles)
+                cycles, res = vcycles, 0.0
+            else:
+                r = H.solve(raise_on_error=False, **solve_kw)
+                cycles, res = r.cycles, r.res
+            u = torch.empty_like(dev(pr.f))
+            H.get_solution(u)
+            launches = M.ma_kernel_launch_count() - c0
+            outs.append((host(u), cycles, res, launches))
+            H.close()
+    finally:
+        M.ma_set_vcycle_tail(True)
+    return outs
+
+
+@pytest.mark.parametrize("name,n,coarsest", [("exp", 65, 3), ("cosine", 17, 3), ("exp", 33, 5), ("sine", 129, 3),
+                                             ("exp", 9, 3), ("cosine", 33, 17)])
+def test_fp64_fused_tail_is_bitwise_the_level_by_level_solve(name, n, coarsest):
+    outs = _both(lambda pr: M.make_desc(n, length=pr.length, coarsest_n=coarsest), name, n,
+                 dict(tol=1e-12, max_cycles=40))
+    (uf, cf, rf, lf), (us, cs, rs, ls) = outs
+    assert cf == cs and rf == rs
+    assert np.array_equal(uf, us)
+    # with a 17^3 coarsest grid the tail is the coarsest solve alone: one launch either way
+    assert lf < ls if coarsest < 17 else lf == ls
+
+
+@pytest.mark.parametrize("name,n", [("exp", 33), ("ex6", 33), ("sine", 65)])
+def test_fp64_fused_tail_bitwise_in_the_paper_configuration(name, n):
+    """Tricubic FMG, 3^3 coarsest grid with one sweep, the relative-L2 stop of
+    Section 4: FMG runs a V-cycle from every level, all through the tail on
+    the levels up to 17^3."""
+    outs = _both(lambda pr: M.paper_desc(n, length=pr.length), name, n,
+                 dict(tol=1e-6, norm=M.MA_NORM_L2, relative=M.MA_REL_INITIAL, max_cycles=30))
+    (uf, cf, rf, lf), (us, cs, rs, ls) = outs
+    assert cf == cs and rf == rs
+    assert np.array_equal(uf, us)
+    assert lf < ls
+
+
+@pytest.mark.parametrize("precision", [M.MA_MIXED, M.MA_FP32])
+def test_fused_fp64_tail_bitwise_under_the_other_precisions(precision):
+    """The mixed solve runs FP64 FMG below the finest level; the FP32 mode
+    runs no FP64 cycle (the switch must not change anything there)."""
+    outs = _both(lambda pr: M.make_desc(65, length=pr.length, precision=precision), "exp", 65,
+                 dict(tol=1e-10 if precision == M.MA_MIXED else 1e-5, max_cycles=40))
+    (uf, cf, rf, _), (us, cs, rs, _) = outs
+    assert cf == cs and rf == rs
+    assert np.array_equal(uf, us)
+
+
+def test_fp64_fused_tail_bitwise_for_plain_vcycles_with_half_weighting():
+    """ma_vcycle from the Dirichlet data, half weighting with injected
+    approximation, V(1,3), a fixed count of coarsest sweeps."""
+    outs = _both(lambda pr: M.make_desc(33, length=pr.length, nu1=1, nu2=3, restrict_kind=M.MA_HALF_WEIGHTING,
+                                        approx_restrict=M.MA_APPROX_INJECTION, coarse_sweeps=4),
+                 "exp", 33, {}, vcycles=3)
+    (uf, _, _, lf), (us, _, _, ls) = outs
+    assert np.array_equal(uf, us)
+    assert lf < ls
