@@ -281,6 +281,41 @@ def bench_2d(args, M, problems, dev):
             "table1": {"error": 1.0e-9, "iter": 1, "cpu_s_matlab_laptop": 67.1}}
 
 
+def bench_precision(args, M, problems, dev):
+    """The precision workload at full size: 257^3 and 513^3, the three seeded
+    exact solutions (Example 4, |x|^2/2, random cosine), mixed precision and
+    plain FP64 to the same tolerance; per case the solve time, unknowns/s,
+    cycles, final residual, max-norm error against the exact solution, and
+    the mixed-vs-FP64 difference relative to max|u| (the FP64 GPU path is the
+    FP64 solution the oracle pins at smaller sizes)."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    out = {"tol": args.tol, "timing": "one solve after one warm-up solve, CUDA events on the solve stream"}
+    for n in (257, 513):
+        for name in ("exp", "quadratic", "cosine"):
+            f, g, length, u_ex = problems.make_on_device(name, n, device=dev, exact=True)
+            unknowns = (n - 2) ** 3
+            row, sols = {}, {}
+            for prec, key in ((M.MA_MIXED, "mixed"), (M.MA_FP64, "fp64")):
+                H = M.Hierarchy(M.make_desc(n, length=length, precision=prec), device=dev)
+                for _ in range(2):
+                    H.set_rhs_bc(f, g)
+                    ms, r = _timed_solve(H, torch, stream, tol=args.tol, max_cycles=60, raise_on_error=False)
+                u = torch.empty_like(f)
+                H.get_solution(u)
+                H.close()
+                sols[key] = u
+                row[key] = {"ms": ms, "unknowns_per_s": unknowns / (ms / 1e3), "cycles": r.cycles,
+                            "residual": r.res, "status": r.status, "floor_reached": r.floor_reached,
+                            "max_err_vs_exact": float((u - u_ex).abs().max())}
+            row["mixed_vs_fp64_speed"] = row["fp64"]["ms"] / row["mixed"]["ms"]
+            row["max_rel_diff_mixed_vs_fp64"] = float((sols["mixed"] - sols["fp64"]).abs().max() / u_ex.abs().max())
+            out[f"{name}_{n}"] = row
+            del f, g, u_ex, sols
+            torch.cuda.empty_cache()
+    return out
+
+
 def bench_batching(args, M, problems, dev):
     """64 instances, sizes drawn by seed from {33, 65, 129}^3, each |x|^2/2
     plus seeded cosine modes with amplitude drawn from [0.005, 0.02]; mixed
@@ -389,7 +424,7 @@ def main():
 
     # autotune the correction smoother and residual tiles for every grid size
     # the workloads use (before any hierarchy records its graphs)
-    tune_sizes = set(M.level_sizes(args.n)) | set(M.level_sizes(129)) | set(M.level_sizes(257))
+    tune_sizes = set(M.level_sizes(args.n)) | set(M.level_sizes(129)) | set(M.level_sizes(257)) | {513}
     tuning = M.autotune(sorted(tune_sizes), reps=5, device=dev)
 
     pr = problems.make(args.problem, args.n)
@@ -524,8 +559,8 @@ def main():
     torch.cuda.empty_cache()
     extras = {}
     if world == 1:
-        for name, fn in (("batching", bench_batching), ("serving", bench_serving), ("paper_mode", bench_paper_mode),
-                         ("two_d", bench_2d), ("fp32_mode", bench_fp32_mode)):
+        for name, fn in (("precision", bench_precision), ("batching", bench_batching), ("serving", bench_serving),
+                         ("paper_mode", bench_paper_mode), ("two_d", bench_2d), ("fp32_mode", bench_fp32_mode)):
             try:
                 extras[name] = fn(args, M, problems, dev)
             except Exception as exc:   # reported, not fatal: the headline line still prints

@@ -313,21 +313,24 @@ ma_status ma_set_corr_tuning(int n, int smooth_choice, int residual_choice);
 /* The choices in force for grid size n. */
 ma_status ma_get_corr_tuning(int n, int *smooth_choice, int *residual_choice);
 
-/* The levels of a correction cycle with n <= 17 (down to the coarsest grid)
- * run as one single-block launch with the same arithmetic as the separate
- * kernels (enable = 1, the default), or level by level (0).  Both give the
- * same bits; hierarchies take the setting when they first record their CUDA
- * graphs. */
-ma_status ma_set_corr_tail(int enable);
+/* Fused tails.  The levels of a V-cycle with n <= max_n, down to the
+ * coarsest grid, run as one single-block launch that keeps their grids in
+ * shared memory and repeats the per-point arithmetic of the separate kernels,
+ * so both forms give the same bits.  It saves the launches of those latency-
+ * bound levels, but puts all their points on one SM: the default, 9, is the
+ * fastest bound on whole solves (at 17 one SM takes longer over the 17^3
+ * level than the launches it replaces).  max_n: 0 (level by level), 1 (the
+ * default), or 3, 5, 9 or 17; MA_ERR_INVALID_ARG otherwise.  Hierarchies
+ * take the setting when they first record their CUDA graphs.
+ *
+ * ma_set_corr_tail: the FP32 correction cycles of the mixed and FP32 modes. */
+ma_status ma_set_corr_tail(int max_n);
 
-/* The same for the FP64 V-cycles (ma_vcycle, the FP64 solves and FMG below
- * the finest level of every precision): the levels with n <= 17 run as one
- * single-block launch with u, w, r and rhs of those levels in shared memory
- * (enable = 1, the default), or level by level (0).  Both give the same
- * bits; the coarse levels' arrays in the workspace are then left as they
- * were (nothing outside the cycle reads them).  Hierarchies take the setting
- * when they first record their CUDA graphs. */
-ma_status ma_set_vcycle_tail(int enable);
+/* ma_set_vcycle_tail: the FP64 V-cycles (ma_vcycle, the FP64 solves and FMG
+ * below the finest level of every precision), with u, w, r and rhs of the
+ * tail levels in shared memory.  The coarse levels' arrays in the workspace
+ * are then left as they were; nothing outside the cycle reads them. */
+ma_status ma_set_vcycle_tail(int max_n);
 
 /* Autotuner: times every smoother variant (reps pairs of sweeps each) and
  * every residual tile on the caller's data of one grid (the arguments of

@@ -974,15 +974,15 @@ ma_status ma_residual_correction(const float* e, const float* hi, const float* l
     return MA_OK;
 }
 
-ma_status ma_set_corr_tail(int enable)
+ma_status ma_set_corr_tail(int max_n)
 {
-    ma::set_corr_tail(enable);
+    if (!ma::set_corr_tail(max_n)) return fail(MA_ERR_INVALID_ARG, "ma_set_corr_tail: bad value %d", max_n);
     return MA_OK;
 }
 
-ma_status ma_set_vcycle_tail(int enable)
+ma_status ma_set_vcycle_tail(int max_n)
 {
-    ma::set_vcycle_tail(enable);
+    if (!ma::set_vcycle_tail(max_n)) return fail(MA_ERR_INVALID_ARG, "ma_set_vcycle_tail: bad value %d", max_n);
     return MA_OK;
 }
 

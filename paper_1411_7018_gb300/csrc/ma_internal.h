@@ -54,7 +54,7 @@ struct TailSpec64 {
     const double* rhs;
 };
 int vcycle_tail_max_n();          // 0 when the fused tail is switched off
-void set_vcycle_tail(int enable);
+bool set_vcycle_tail(int max_n);  // 0 off, 1 default, or 3 / 5 / 9 / 17; false otherwise
 cudaError_t launch_vcycle_tail(const TailSpec64* lv, int nlev, int nu1, int nu2, int kind, int approx,
                                int coarse_sweeps, unsigned long long* events, cudaStream_t s);
 
@@ -90,7 +90,7 @@ struct TailSpec {
     const float* rhs_cm;
 };
 int corr_tail_max_n();            // 0 when the fused tail is switched off
-void set_corr_tail(int enable);
+bool set_corr_tail(int max_n);     // 0 off, 1 default, or 3 / 5 / 9 / 17; false otherwise
 cudaError_t launch_corr_vcycle_tail(const TailSpec* lv, int nlev, int nu1, int nu2, int kind, int approx,
                                     int coarse_sweeps, unsigned long long* events, cudaStream_t s);
 cudaError_t launch_residual_corr_choice(int choice, const float* e, const void* bstore, const float* rhs_cm,

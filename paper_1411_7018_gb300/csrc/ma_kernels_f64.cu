@@ -665,11 +665,22 @@ cudaError_t launch_coarsest(double* u, const double* rhs, int n, double h, int s
     return cudaGetLastError();
 }
 
-static std::atomic<int> g_vtail_enabled{1};
+// Largest level of the fused FP64 tail.  One block runs the tail on one SM,
+// whose FP64 pipe then does all the point solves: at 17^3 (3375 points a
+// sweep) that costs more than 8 colour launches spread over the GPU, at 9^3
+// and below the launches cost more.
+constexpr int kVTailDefault = 9;
+static std::atomic<int> g_vtail_max{kVTailDefault};
 
-int vcycle_tail_max_n() { return g_vtail_enabled.load(std::memory_order_relaxed) ? 17 : 0; }
+int vcycle_tail_max_n() { return g_vtail_max.load(std::memory_order_relaxed); }
 
-void set_vcycle_tail(int enable) { g_vtail_enabled.store(enable ? 1 : 0, std::memory_order_relaxed); }
+bool set_vcycle_tail(int max_n)
+{
+    if (max_n == 1) max_n = kVTailDefault;
+    if (!(max_n == 0 || max_n == 3 || max_n == 5 || max_n == 9 || max_n == 17)) return false;
+    g_vtail_max.store(max_n, std::memory_order_relaxed);
+    return true;
+}
 
 cudaError_t launch_vcycle_tail(const TailSpec64* lv, int nlev, int nu1, int nu2, int kind, int approx,
                                int coarse_sweeps, unsigned long long* events, cudaStream_t s)

@@ -195,9 +195,9 @@ __device__ __forceinline__ double corr_Mz(const CorrCubic& C, double z) { return
 // tot > 0: F is decreasing and convex left of the smallest eigenvalue of G
 // and has its unique root there; monotone Newton from the Gershgorin bound
 // minus tot^(1/3), where F >= 0.  tot <= 0: Eq. (realroots) taken
-// literally, the smallest real root of the cubic (trigonometric form for three
-// real roots, Cardano's formula for one, two Newton polishes), counted in
-// *nonconvex.
+// literally, the smallest real root of the cubic, bracketed between the
+// Gershgorin bounds and the stationary points of det(G - zI) and found by
+// bisection (smallest_root_nonpositive), counted in *nonconvex.
 __device__ __noinline__ float corr_root_slow(S3f B, S3f K, float r, bool* nonconvex)
 {
     const CorrCubic C = corr_cubic(B, K, r);
@@ -734,8 +734,9 @@ __global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __r
 }
 
 // ---------------------------------------------------------------------------
-// The tail of a correction V-cycle in one block: every level with n <= 17,
-// from the level the cycle enters there down to the coarsest grid and back,
+// The tail of a correction V-cycle in one block: every level with n <= 17
+// (or a smaller bound set by set_corr_tail), from the level the cycle enters
+// there down to the coarsest grid and back,
 // with e, w, the residual, B and rhs of those levels in shared memory.  Each
 // step does the per-point arithmetic of its separate kernel -- the sweeps of
 // k_smooth_corr, the residual of k_residual_corr_plane, the restriction of
@@ -1290,11 +1291,21 @@ int tail_smem_bytes(const int* ns, int nlev)
     return f * (int)sizeof(float);
 }
 
-std::atomic<int> g_tail_enabled{1};
+// Default largest level of the fused tail: at 17^3 one SM's serial colour
+// phases take longer than the launches they replace, at 9^3 and below the
+// launches cost more (measured on whole solves from 33^3 to 257^3).
+constexpr int kTailDefault = 9;
+std::atomic<int> g_tail_max{kTailDefault};
 
-int corr_tail_max_n() { return g_tail_enabled.load(std::memory_order_relaxed) ? kTailMaxN : 0; }
+int corr_tail_max_n() { return g_tail_max.load(std::memory_order_relaxed); }
 
-void set_corr_tail(int enable) { g_tail_enabled.store(enable ? 1 : 0, std::memory_order_relaxed); }
+bool set_corr_tail(int max_n)
+{
+    if (max_n == 1) max_n = kTailDefault;
+    if (!(max_n == 0 || max_n == 3 || max_n == 5 || max_n == 9 || max_n == 17)) return false;
+    g_tail_max.store(max_n, std::memory_order_relaxed);
+    return true;
+}
 
 cudaError_t launch_corr_vcycle_tail(const TailSpec* lv, int nlev, int nu1, int nu2, int kind, int approx,
                                     int coarse_sweeps, unsigned long long* events, cudaStream_t s)

@@ -321,12 +321,14 @@ def ma_set_corr_tuning(n: int, smooth_choice: int, residual_choice: int) -> None
     _check(load().ma_set_corr_tuning(n, smooth_choice, residual_choice))
 
 
-def ma_set_corr_tail(enable: bool) -> None:
-    _check(load().ma_set_corr_tail(1 if enable else 0))
+def ma_set_corr_tail(max_n) -> None:
+    """True / 1: the default; False / 0: level by level; 3, 5, 9, 17: the largest fused level."""
+    _check(load().ma_set_corr_tail(int(max_n)))
 
 
-def ma_set_vcycle_tail(enable: bool) -> None:
-    _check(load().ma_set_vcycle_tail(1 if enable else 0))
+def ma_set_vcycle_tail(max_n) -> None:
+    """True / 1: the default; False / 0: level by level; 3, 5, 9, 17: the largest fused level."""
+    _check(load().ma_set_vcycle_tail(int(max_n)))
 
 
 def ma_get_corr_tuning(n: int):

@@ -99,11 +99,12 @@ def _cosine_fields(xp, x, y, z, k, phi, amp):
     return u, f
 
 
-def make_on_device(name: str, n: int, seed: int = 0, eps=0.02, device="cuda"):
+def make_on_device(name: str, n: int, seed: int = 0, eps=0.02, device="cuda", exact: bool = False):
     """(f, g, length) as float64 torch tensors on `device`, g = u on the shell
     and 0 inside: the same problems as make(), evaluated with torch (values
     agree with make() to rounding).  For workloads that are only solved, not
-    compared with the CPU oracle."""
+    compared with the CPU oracle.  exact=True appends the exact solution u
+    on the whole grid."""
     import torch
     length = np.pi if name == "sine" else 1.0
     h = length / (n - 1)
@@ -129,6 +130,8 @@ def make_on_device(name: str, n: int, seed: int = 0, eps=0.02, device="cuda"):
         raise ValueError(f"unknown problem {name!r}")
     g = u.clone()
     g[1:-1, 1:-1, 1:-1] = 0.0
+    if exact:
+        return f.contiguous(), g.contiguous(), length, u.contiguous()
     return f.contiguous(), g.contiguous(), length
 
 
