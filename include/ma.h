@@ -172,6 +172,44 @@ ma_status ma_solve_get_result(const ma_hierarchy *h, ma_solve_result *result);
  * first non-MA_OK status. */
 ma_status ma_batch_solve(ma_hierarchy *const *hs, int count, const ma_solve_opts *opts, ma_solve_result *results);
 
+/* Shared per-level batch.  Binds `count` MA_MIXED hierarchies of any sizes
+ * (n <= 1025; equal nu1, nu2, restrict_kind, approx_restrict, coarse_sweeps,
+ * inner_cycles; one device; each at most once) so that their solves share
+ * kernel launches.  ma_batch_run starts every hierarchy as ma_solve_begin
+ * does (FMG and the first outer iteration, each on its own stream), then runs
+ * the outer iterations (Algorithm 1 V-cycles on the correction, the FP64
+ * update and residual) of all hierarchies still iterating as one CUDA graph
+ * on `stream`: each of its kernels covers one level depth of every
+ * hierarchy (its blocks find their hierarchy in a job table kept in the
+ * workspace), the levels <= the fused-tail bound of every hierarchy take one
+ * launch, and a hierarchy that has met the stopping rule is skipped.  Each
+ * hierarchy executes the per-point operations of its own solve, so
+ * results[b] and its solution are those ma_solve gives for it alone.
+ *
+ * ma_batch_footprint: device bytes the batch needs (job tables, flags and
+ * norms; a few KB per hierarchy).  ma_create_batch: the caller owns the
+ * 256-byte-aligned workspace, and the hierarchies, which must outlive the
+ * batch and not be used by other calls while ma_batch_run runs; it reads the
+ * fused-tail setting (ma_set_corr_tail) once, here.  MA_ERR_INVALID_ARG for a
+ * null or repeated hierarchy, mismatched settings or a small workspace.
+ * ma_batch_run blocks until every solve has finished; returns MA_OK if all
+ * converged, else the first non-MA_OK status (results[b] is filled for every
+ * b).  Later work on a hierarchy's own stream follows the batch's. */
+typedef struct ma_batch ma_batch;
+ma_status ma_batch_footprint(ma_hierarchy *const *hs, int count, size_t *bytes);
+ma_status ma_create_batch(ma_hierarchy *const *hs, int count, void *dev_workspace, size_t bytes, ma_stream_t stream,
+                          ma_batch **out);
+ma_status ma_batch_run(ma_batch *b, const ma_solve_opts *opts, ma_solve_result *results);
+ma_status ma_destroy_batch(ma_batch *b);
+
+/* Batches split their hierarchies (by decreasing size, dealt in turn) into
+ * min(count, groups) groups, each replayed as its own graph on its own stream
+ * in every outer iteration, so that the groups' kernels overlap (an FP64
+ * residual of one beside the FP32 sweeps of another).  1..16, default 2;
+ * read by ma_batch_footprint and ma_create_batch.  The results do not
+ * depend on it. */
+ma_status ma_set_batch_groups(int groups);
+
 /* Norm of the fine-level FP64 residual f - det(D^2_h u) of the current
  * iterate (Algorithm 1 step 3; Section 4 norms).  Blocks on the stream. */
 ma_status ma_residual_norm(ma_hierarchy *h, int norm, double *out);

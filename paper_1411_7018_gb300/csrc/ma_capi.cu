@@ -4,6 +4,8 @@
 // single-step entry points.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdarg>
@@ -702,19 +704,11 @@ static cudaError_t launch_cycle(ma_hierarchy* H)
     });
 }
 
-ma_status ma_solve_advance(ma_hierarchy* H, int* done)
+// Applies the stopping rule to the norms in the host read-back block (after
+// the start, phase 1, or after a cycle, phase 2); returns true, with the
+// result filled and phase 3, when the solve is finished.
+static bool absorb_norms(ma_hierarchy* H)
 {
-    if (!H || !done) return fail(MA_ERR_INVALID_ARG, "null argument");
-    *done = 0;
-    if (H->sv.phase == 0) return fail(MA_ERR_INVALID_ARG, "ma_solve_advance before ma_solve_begin");
-    if (H->sv.phase == 3) {
-        *done = 1;
-        return MA_OK;
-    }
-    DeviceGuard g(H->device);
-    const cudaError_t q = cudaEventQuery(H->sv.ev);
-    if (q == cudaErrorNotReady) return MA_OK;
-    if (q != cudaSuccess) return fail(MA_ERR_CUDA, "ma_solve_advance: %s", cudaGetErrorString(q));
     const ma_solve_opts& o = H->sv.o;
     const double resn = o.norm == MA_NORM_MAX ? H->host[0] : H->host[1];
     ma_solve_result& r = H->sv.r;
@@ -750,6 +744,25 @@ ma_status ma_solve_advance(ma_hierarchy* H, int* done)
         r.status = out;
         r.nonconvex_root_events = (long long)ev;
         H->sv.phase = 3;
+        return true;
+    }
+    return false;
+}
+
+ma_status ma_solve_advance(ma_hierarchy* H, int* done)
+{
+    if (!H || !done) return fail(MA_ERR_INVALID_ARG, "null argument");
+    *done = 0;
+    if (H->sv.phase == 0) return fail(MA_ERR_INVALID_ARG, "ma_solve_advance before ma_solve_begin");
+    if (H->sv.phase == 3) {
+        *done = 1;
+        return MA_OK;
+    }
+    DeviceGuard g(H->device);
+    const cudaError_t q = cudaEventQuery(H->sv.ev);
+    if (q == cudaErrorNotReady) return MA_OK;
+    if (q != cudaSuccess) return fail(MA_ERR_CUDA, "ma_solve_advance: %s", cudaGetErrorString(q));
+    if (absorb_norms(H)) {
         *done = 1;
         return MA_OK;
     }
@@ -828,6 +841,324 @@ ma_status ma_batch_solve(ma_hierarchy* const* hs, int count, const ma_solve_opts
         if (st != MA_OK && worst == MA_OK) worst = st;
     }
     return worst;
+}
+
+// ---- shared per-level batches ----------------------------------------------
+
+}  // extern "C"
+
+struct ma_batch_group {
+    std::vector<int> ids;             // the hierarchies of this group (indices into the batch)
+    ma::BatchPlan* plan = nullptr;
+    cudaStream_t s = nullptr;         // group 0: the batch's stream; others: created here
+    cudaStream_t cap = nullptr;       // private capture stream
+    ma::GraphSlot g;                  // one outer iteration of the group
+    cudaEvent_t done = nullptr;
+};
+
+struct ma_batch {
+    std::vector<ma_hierarchy*> hs;
+    int device = 0;
+    cudaStream_t s = nullptr;        // the caller's stream
+    int* active_dev = nullptr;       // per hierarchy: 1 while it iterates
+    double* packed_dev = nullptr;    // per hierarchy: (max, L2, -, -, events) after an iteration
+    int* active_host = nullptr;      // pinned
+    double* packed_host = nullptr;   // pinned
+    std::vector<ma_batch_group> grp;
+    cudaEvent_t flags_ev = nullptr;
+    cudaEvent_t done_ev = nullptr;
+};
+
+namespace {
+
+std::atomic<int> g_batch_groups{2};
+
+ma_status batch_describe(ma_hierarchy* const* hs, int count, std::vector<ma::BatchInstance>* in,
+                         ma::BatchParams* p)
+{
+    if (!hs || count < 1) return fail(MA_ERR_INVALID_ARG, "batch: need at least one hierarchy");
+    in->assign(count, ma::BatchInstance());
+    for (int b = 0; b < count; ++b) {
+        const ma_hierarchy* H = hs[b];
+        if (!H) return fail(MA_ERR_INVALID_ARG, "batch: null hierarchy %d", b);
+        for (int c = 0; c < b; ++c)
+            if (hs[c] == H) return fail(MA_ERR_INVALID_ARG, "batch: hierarchy %d appears twice", b);
+        const ma_hier_desc& d = H->d;
+        const ma_hier_desc& d0 = hs[0]->d;
+        if (d.precision != MA_MIXED) return fail(MA_ERR_INVALID_ARG, "batch: hierarchy %d is not MA_MIXED", b);
+        if (d.n > 1025) return fail(MA_ERR_INVALID_ARG, "batch: n = %d exceeds 1025", d.n);
+        if (d.nu1 != d0.nu1 || d.nu2 != d0.nu2 || d.restrict_kind != d0.restrict_kind ||
+            d.approx_restrict != d0.approx_restrict || d.coarse_sweeps != d0.coarse_sweeps ||
+            d.inner_cycles != d0.inner_cycles || H->device != hs[0]->device)
+            return fail(MA_ERR_INVALID_ARG, "batch: hierarchy %d differs from hierarchy 0 in its cycle settings "
+                                            "or device", b);
+        ma::BatchInstance& I = (*in)[b];
+        I.id = b;
+        I.L = H->L;
+        for (int l = 0; l < H->L; ++l) {
+            const ma::Level& A = H->lev[l];
+            ma::BatchLevel& V = I.lev[l];
+            V.n = A.n;
+            V.h = A.h;
+            V.u = A.u;
+            V.rhs = A.rhs;
+            V.e = A.e;
+            V.e2 = A.e2;
+            V.res32 = A.res32;
+            V.w32 = A.w32;
+            V.hi = A.hi;
+            V.lo = A.lo;
+            V.rhs32 = A.rhs32;
+            V.bstore = A.bstore;
+        }
+        I.partials = H->partials;
+        I.npartials = H->npartials;
+        I.out2 = H->out2;
+        I.events = H->events;
+    }
+    const ma_hier_desc& d0 = hs[0]->d;
+    p->nu1 = d0.nu1;
+    p->nu2 = d0.nu2;
+    p->kind = d0.restrict_kind;
+    p->approx = d0.approx_restrict;
+    p->coarse_sweeps = d0.coarse_sweeps;
+    p->inner = d0.inner_cycles > 0 ? d0.inner_cycles : 3;
+    p->tail_max = ma::corr_tail_max_n();
+    return MA_OK;
+}
+
+// Groups of the batch: the hierarchies by decreasing size, dealt in turn to
+// min(count, batch groups) groups, so that the groups carry similar work.
+std::vector<std::vector<int>> batch_grouping(const std::vector<ma::BatchInstance>& in)
+{
+    const int count = (int)in.size();
+    const int G = std::max(1, std::min(count, g_batch_groups.load(std::memory_order_relaxed)));
+    std::vector<int> order(count);
+    for (int b = 0; b < count; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return in[x].lev[0].n > in[y].lev[0].n; });
+    std::vector<std::vector<int>> grp(G);
+    for (int q = 0; q < count; ++q) grp[q % G].push_back(order[q]);
+    return grp;
+}
+
+std::vector<ma::BatchInstance> subset(const std::vector<ma::BatchInstance>& in, const std::vector<int>& ids)
+{
+    std::vector<ma::BatchInstance> out;
+    for (int b : ids) out.push_back(in[b]);
+    return out;
+}
+
+// Workspace: active flags, packed norms, then the job tables of each group.
+size_t batch_layout(const std::vector<ma::BatchInstance>& in, const ma::BatchParams& p,
+                    const std::vector<std::vector<int>>& grp, size_t* off_packed, std::vector<size_t>* off_tables)
+{
+    const size_t count = in.size();
+    *off_packed = align_up(sizeof(int) * count);
+    size_t off = *off_packed + align_up(5 * sizeof(double) * count);
+    off_tables->clear();
+    for (const std::vector<int>& ids : grp) {
+        off_tables->push_back(off);
+        const std::vector<ma::BatchInstance> sub = subset(in, ids);
+        off += align_up(ma::batch_tables_bytes(sub.data(), (int)sub.size(), p));
+    }
+    return off;
+}
+
+cudaError_t group_replay(ma_batch_group& G)
+{
+    if (!G.g.exec) {
+        const unsigned long long before = ma::launch_count();
+        cudaError_t e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        const cudaError_t eb = ma::batch_plan_iteration(G.plan, G.cap);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(G.cap, &g);
+        const unsigned long long captured = ma::launch_count() - before;
+        ma::uncount_launches(captured);
+        if (eb != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return eb != cudaSuccess ? eb : e;
+        }
+        e = cudaGraphInstantiate(&G.g.exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            G.g.exec = nullptr;
+            return e;
+        }
+        G.g.graph = g;
+        G.g.launches = captured;
+    }
+    ma::count_launches(G.g.launches);
+    return cudaGraphLaunch(G.g.exec, G.s);
+}
+
+}  // namespace
+
+extern "C" {
+
+ma_status ma_set_batch_groups(int groups)
+{
+    if (groups < 1 || groups > 16) return fail(MA_ERR_INVALID_ARG, "ma_set_batch_groups: %d not in [1, 16]", groups);
+    g_batch_groups.store(groups, std::memory_order_relaxed);
+    return MA_OK;
+}
+
+ma_status ma_batch_footprint(ma_hierarchy* const* hs, int count, size_t* bytes)
+{
+    if (!bytes) return fail(MA_ERR_INVALID_ARG, "null bytes");
+    std::vector<ma::BatchInstance> in;
+    ma::BatchParams p;
+    ma_status st = batch_describe(hs, count, &in, &p);
+    if (st != MA_OK) return st;
+    size_t op;
+    std::vector<size_t> ot;
+    *bytes = batch_layout(in, p, batch_grouping(in), &op, &ot);
+    return MA_OK;
+}
+
+ma_status ma_create_batch(ma_hierarchy* const* hs, int count, void* dev_workspace, size_t bytes, ma_stream_t stream,
+                          ma_batch** out)
+{
+    if (!out) return fail(MA_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    std::vector<ma::BatchInstance> in;
+    ma::BatchParams p;
+    ma_status st = batch_describe(hs, count, &in, &p);
+    if (st != MA_OK) return st;
+    if (!dev_workspace || ((uintptr_t)dev_workspace) % kAlign != 0)
+        return fail(MA_ERR_INVALID_ARG, "batch workspace null or not 256-byte aligned");
+    const std::vector<std::vector<int>> grouping = batch_grouping(in);
+    size_t op;
+    std::vector<size_t> ot;
+    const size_t need = batch_layout(in, p, grouping, &op, &ot);
+    if (bytes < need) return fail(MA_ERR_INVALID_ARG, "batch workspace of %zu bytes < footprint %zu", bytes, need);
+    DeviceGuard g(hs[0]->device);
+    ma_batch* B = new (std::nothrow) ma_batch();
+    if (!B) return fail(MA_ERR_OOM, "host allocation failed");
+    B->hs.assign(hs, hs + count);
+    B->device = hs[0]->device;
+    B->s = (cudaStream_t)stream;
+    char* ws = (char*)dev_workspace;
+    B->active_dev = (int*)ws;
+    B->packed_dev = (double*)(ws + op);
+    B->grp.resize(grouping.size());
+    cudaError_t e = cudaMallocHost((void**)&B->active_host, sizeof(int) * (size_t)count);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&B->packed_host, 5 * sizeof(double) * (size_t)count);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->flags_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->done_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, ot.empty() ? 0 : ot[0], B->s);
+    for (size_t q = 0; q < grouping.size() && e == cudaSuccess; ++q) {
+        ma_batch_group& G = B->grp[q];
+        G.ids = grouping[q];
+        if (q == 0) G.s = B->s;
+        else e = cudaStreamCreateWithFlags(&G.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) break;
+        const std::vector<ma::BatchInstance> sub = subset(in, G.ids);
+        G.plan = ma::batch_plan_create(sub.data(), (int)sub.size(), p, ws + ot[q], B->active_dev, B->packed_dev, B->s,
+                                       &e);
+        if (!G.plan && e == cudaSuccess) e = cudaErrorMemoryAllocation;
+    }
+    if (e != cudaSuccess) {
+        ma_destroy_batch(B);
+        return fail(MA_ERR_CUDA, "create batch: %s", cudaGetErrorString(e));
+    }
+    *out = B;
+    return MA_OK;
+}
+
+ma_status ma_batch_run(ma_batch* B, const ma_solve_opts* opts, ma_solve_result* results)
+{
+    if (!B || !opts || !results) return fail(MA_ERR_INVALID_ARG, "null argument");
+    ma_status st = check_opts(opts);
+    if (st != MA_OK) return st;
+    const int count = (int)B->hs.size();
+    DeviceGuard g(B->device);
+    // every hierarchy's start (FMG and the first outer iteration, with the
+    // residual norms) on its own stream, concurrently
+    for (int b = 0; b < count; ++b) {
+        std::memset(&results[b], 0, sizeof results[b]);
+        if ((st = ma_solve_begin(B->hs[b], opts)) != MA_OK) return st;
+    }
+    std::vector<char> done(count, 0);
+    for (int b = 0; b < count; ++b) {
+        ma_hierarchy* H = B->hs[b];
+        MA_CK(cudaStreamWaitEvent(B->s, H->sv.ev, 0));
+        MA_CK(cudaEventSynchronize(H->sv.ev));
+        done[b] = absorb_norms(H) ? 1 : 0;
+        if (!done[b]) H->sv.phase = 2;
+    }
+    // then each outer iteration of all hierarchies still iterating: one
+    // graph per group, the groups' graphs running concurrently
+    for (;;) {
+        int active = 0;
+        for (int b = 0; b < count; ++b) {
+            B->active_host[b] = done[b] ? 0 : 1;
+            active += B->active_host[b];
+        }
+        if (!active) break;
+        MA_CK(cudaMemcpyAsync(B->active_dev, B->active_host, sizeof(int) * (size_t)count, cudaMemcpyHostToDevice,
+                              B->s));
+        MA_CK(cudaEventRecord(B->flags_ev, B->s));
+        for (ma_batch_group& G : B->grp) {
+            bool any = false;
+            for (int b : G.ids) any = any || !done[b];
+            if (!any) continue;
+            if (G.s != B->s) MA_CK(cudaStreamWaitEvent(G.s, B->flags_ev, 0));
+            MA_CK(group_replay(G));
+            if (G.s != B->s) {
+                MA_CK(cudaEventRecord(G.done, G.s));
+                MA_CK(cudaStreamWaitEvent(B->s, G.done, 0));
+            }
+        }
+        MA_CK(cudaMemcpyAsync(B->packed_host, B->packed_dev, 5 * sizeof(double) * (size_t)count,
+                              cudaMemcpyDeviceToHost, B->s));
+        MA_CK(cudaStreamSynchronize(B->s));
+        for (int b = 0; b < count; ++b) {
+            if (done[b]) continue;
+            ma_hierarchy* H = B->hs[b];
+            H->host[0] = B->packed_host[5 * b];
+            H->host[1] = B->packed_host[5 * b + 1];
+            H->host[4] = B->packed_host[5 * b + 4];
+            done[b] = absorb_norms(H) ? 1 : 0;
+        }
+    }
+    // later work on a hierarchy's own stream follows the batch's
+    MA_CK(cudaEventRecord(B->done_ev, B->s));
+    ma_status worst = MA_OK;
+    for (int b = 0; b < count; ++b) {
+        MA_CK(cudaStreamWaitEvent(B->hs[b]->s, B->done_ev, 0));
+        const ma_status sb = ma_solve_get_result(B->hs[b], &results[b]);
+        if (sb != MA_OK && worst == MA_OK) worst = sb;
+    }
+    return worst;
+}
+
+ma_status ma_destroy_batch(ma_batch* B)
+{
+    if (!B) return MA_OK;
+    DeviceGuard g(B->device);
+    cudaError_t e = cudaSuccess;
+    for (ma_batch_group& G : B->grp) {
+        if (G.s) {
+            const cudaError_t es = cudaStreamSynchronize(G.s);
+            if (e == cudaSuccess) e = es;
+        }
+        if (G.g.exec) cudaGraphExecDestroy(G.g.exec);
+        if (G.g.graph) cudaGraphDestroy(G.g.graph);
+        if (G.cap) cudaStreamDestroy(G.cap);
+        if (G.s && G.s != B->s) cudaStreamDestroy(G.s);
+        if (G.done) cudaEventDestroy(G.done);
+        ma::batch_plan_destroy(G.plan);
+    }
+    if (B->flags_ev) cudaEventDestroy(B->flags_ev);
+    if (B->done_ev) cudaEventDestroy(B->done_ev);
+    if (B->active_host) cudaFreeHost(B->active_host);
+    if (B->packed_host) cudaFreeHost(B->packed_host);
+    delete B;
+    if (e != cudaSuccess) return fail(MA_ERR_CUDA, "destroy batch: %s", cudaGetErrorString(e));
+    return MA_OK;
 }
 
 // ---- single steps ----------------------------------------------------------

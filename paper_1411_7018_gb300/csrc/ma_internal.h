@@ -116,4 +116,45 @@ cudaError_t launch_split_inject(const double* u0, int n0, int stride, float* hi,
 cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r_cm, void* bstore, int n, double h,
                                    double* partials, cudaStream_t s);
 
+// Batched launches (ma_kernels_mixed.cu).  One outer iteration of the mixed-
+// precision solve -- `inner` FP32 correction V-cycles, the update u += e with
+// the coarse base refresh, the FP64 fine residual and its norms -- for several
+// hierarchies of any sizes, as one launch per kernel and level depth over all
+// of them: a block finds its hierarchy in a job table, and hierarchies whose
+// active flag is 0 are skipped.  Every hierarchy runs exactly the per-point
+// operations of its own cycle, so the results are those of solving it alone.
+constexpr int kBatchMaxLevels = 16;
+struct BatchLevel {
+    int n;
+    double h;
+    double* u;             // FP64 iterate (level 0)
+    const double* rhs;     // FP64 right-hand side (level 0)
+    float *e, *e2, *res32, *w32, *hi, *lo, *rhs32;   // e2: second buffer of the plane sweeps (null on the coarsest level)
+    void* bstore;
+};
+struct BatchInstance {
+    int id;                // index of the hierarchy in the batch (active flags, packed norms)
+    int L;
+    BatchLevel lev[kBatchMaxLevels];
+    double* partials;      // norm partials of the fine residual
+    int npartials;
+    double* out2;          // the hierarchy's (max, L2) residual norms
+    unsigned long long* events;
+};
+struct BatchParams {
+    int nu1, nu2, kind, approx, coarse_sweeps, inner, tail_max;
+};
+struct BatchPlan;
+// Bytes of the device job tables of a batch.
+size_t batch_tables_bytes(const BatchInstance* in, int count, const BatchParams& p);
+// Builds the job tables into tables_dev (batch_tables_bytes, 256-byte
+// aligned; uploaded on s, which is synchronised) and returns the plan, or null
+// with *err set.  active_dev: count ints; packed_dev: 5 doubles per instance,
+// where each iteration leaves (max, L2, -, -, events).
+BatchPlan* batch_plan_create(const BatchInstance* in, int count, const BatchParams& p, void* tables_dev,
+                             const int* active_dev, double* packed_dev, cudaStream_t s, cudaError_t* err);
+cudaError_t batch_plan_iteration(const BatchPlan* plan, cudaStream_t s);
+unsigned long long batch_plan_launches(const BatchPlan* plan);
+void batch_plan_destroy(BatchPlan* plan);
+
 }  // namespace ma

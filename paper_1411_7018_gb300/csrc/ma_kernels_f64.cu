@@ -112,29 +112,10 @@ __global__ void __launch_bounds__(BX * BY) k_norm_partials(const T* __restrict__
 }
 
 // One block folds the partials in a fixed order: out2 = (max, sqrt(h^3 sum)).
-__global__ void __launch_bounds__(256) k_norm_final(const double* __restrict__ partials, int count, double h3,
-                                                    double* out2)
+__global__ void __launch_bounds__(resid::NF) k_norm_final(const double* __restrict__ partials, int count, double h3,
+                                                          double* out2)
 {
-    __shared__ double smx[256], sss[256];
-    double mx = 0.0, ss = 0.0;
-    for (int q = threadIdx.x; q < count; q += 256) {
-        mx = fmax(mx, partials[2 * q]);
-        ss += partials[2 * q + 1];
-    }
-    smx[threadIdx.x] = mx;
-    sss[threadIdx.x] = ss;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) {
-            smx[threadIdx.x] = fmax(smx[threadIdx.x], smx[threadIdx.x + w]);
-            sss[threadIdx.x] += sss[threadIdx.x + w];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        out2[0] = smx[0];
-        out2[1] = sqrt(h3 * sss[0]);
-    }
+    resid::norm_final_block(partials, count, h3, out2);
 }
 
 // b_H = det(D^2_H w_H) + r_H on the interior, 0 on the shell.
@@ -558,7 +539,7 @@ cudaError_t launch_norm_partials_f32(const float* v, int n, double* partials, cu
 cudaError_t launch_norm_final(const double* partials, int count, double h, double* out2, cudaStream_t s)
 {
     count_launches(1);
-    k_norm_final<<<1, 256, 0, s>>>(partials, count, h * h * h, out2);
+    k_norm_final<<<1, resid::NF, 0, s>>>(partials, count, h * h * h, out2);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,9 @@
 // eigenvalue of G; FP32 Newton from z = 0 when G is positive definite, else
 // the FP64 routines of ma_point.cuh on the same data.
 #include <atomic>
+#include <cstring>
+#include <new>
+#include <vector>
 
 #include "ma_internal.h"
 #include "ma_point.cuh"
@@ -290,12 +293,12 @@ __device__ __forceinline__ S3f load_b(const float* __restrict__ b, long long cnt
 }
 
 // B from the hi/lo split, stored at the point's colour-major slot.
-__global__ void __launch_bounds__(BX * BY) k_base_colour(const float* __restrict__ hi, const float* __restrict__ lo,
-                                                         float* __restrict__ bstore, int n, float inv_h2)
+__device__ __forceinline__ void base_colour_block(const float* __restrict__ hi, const float* __restrict__ lo,
+                                                  float* __restrict__ bstore, int n, float inv_h2, uint3 bid)
 {
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z;
+    const int i = bid.x * BX + threadIdx.x;
+    const int j = bid.y * BY + threadIdx.y;
+    const int k = bid.z;
     if (i < 1 || j < 1 || k < 1 || i > n - 2 || j > n - 2 || k > n - 2) return;
     const long long sy = n, sz = (long long)n * n;
     const S3f B = base_hess(hi, lo, lin(i, j, k, n), sy, sz, inv_h2);
@@ -307,6 +310,12 @@ __global__ void __launch_bounds__(BX * BY) k_base_colour(const float* __restrict
     b[3 * c.cnt] = B.xy;
     b[4 * c.cnt] = B.xz;
     b[5 * c.cnt] = B.yz;
+}
+
+__global__ void __launch_bounds__(BX * BY) k_base_colour(const float* __restrict__ hi, const float* __restrict__ lo,
+                                                         float* __restrict__ bstore, int n, float inv_h2)
+{
+    base_colour_block(hi, lo, bstore, n, inv_h2, blockIdx);
 }
 
 // Natural-layout interior values -> colour-major order.
@@ -326,13 +335,13 @@ __global__ void __launch_bounds__(BX * BY) k_to_cm(const float* __restrict__ nat
 // point solve is latency-bound, so the launch bounds ask for 10 resident
 // blocks per SM (48 registers).
 template <int PI, int PJ, int PK, typename Idx>
-__global__ void __launch_bounds__(BX * BY, 10) k_smooth_corr(float* e, const float* __restrict__ bc,
-                                                              const float* __restrict__ rc, int n, float inv_h2,
-                                                              float h2half, unsigned long long* events)
+__device__ __forceinline__ void smooth_corr_block(float* e, const float* __restrict__ bc, const float* __restrict__ rc,
+                                                  int n, float inv_h2, float h2half, unsigned long long* events,
+                                                  uint3 bid)
 {
-    const int ii = blockIdx.x * BX + threadIdx.x;
-    const int jj = blockIdx.y * BY + threadIdx.y;
-    const int kk = blockIdx.z;
+    const int ii = bid.x * BX + threadIdx.x;
+    const int jj = bid.y * BY + threadIdx.y;
+    const int kk = bid.z;
     const int ni = colour_count(n, PI), nj = colour_count(n, PJ);
     if (ii >= ni || jj >= nj) return;
     const int i = (PI ? 1 : 2) + 2 * ii, j = (PJ ? 1 : 2) + 2 * jj, k = (PK ? 1 : 2) + 2 * kk;
@@ -356,6 +365,14 @@ __global__ void __launch_bounds__(BX * BY, 10) k_smooth_corr(float* e, const flo
     const float z = corr_root(B, K, __ldcs(rc + idx), &nonconvex);
     q[0] = fmaf(h2half, z, e0);
     if (nonconvex && events) atomicAdd(events, 1ull);
+}
+
+template <int PI, int PJ, int PK, typename Idx>
+__global__ void __launch_bounds__(BX * BY, 10) k_smooth_corr(float* e, const float* __restrict__ bc,
+                                                              const float* __restrict__ rc, int n, float inv_h2,
+                                                              float h2half, unsigned long long* events)
+{
+    smooth_corr_block<PI, PJ, PK, Idx>(e, bc, rc, n, inv_h2, h2half, events, blockIdx);
 }
 
 template <int C>
@@ -558,21 +575,24 @@ __device__ __forceinline__ unsigned colour_phase(float* sp, const float* __restr
         bool nonconvex = false;
         const float z = corr_root_slow(B, K, __ldcs(rq + rel), &nonconvex);
         sp[sc] = fmaf(h2half, z, e0);
-        ev += nonconvex ? 1u : 0u;
+        // count each point once: halo points are the neighbouring block's
+        const int i2 = R.ilo + 2 * a2, j2 = R.jlo + 2 * b2;
+        const bool owned = i2 >= ia && i2 < ia + PT && j2 >= ja && j2 < ja + PT;
+        ev += (nonconvex && owned) ? 1u : 0u;
     }
     return ev;
 }
 
 template <int PK, int PT, int NT>
-__global__ void __launch_bounds__(NT, plane_min_blocks(PT, NT))
-    k_smooth_corr_plane(const float* __restrict__ own, const float* __restrict__ nbr, float* __restrict__ dst,
-                        const float* __restrict__ bstore, const float* __restrict__ rhs_cm, int n, float inv_h2,
-                        float h2half, unsigned long long* events)
+__device__ __forceinline__ void smooth_corr_plane_block(const float* __restrict__ own, const float* __restrict__ nbr,
+                                                        float* __restrict__ dst, const float* __restrict__ bstore,
+                                                        const float* __restrict__ rhs_cm, int n, float inv_h2,
+                                                        float h2half, unsigned long long* events, uint3 bid)
 {
     extern __shared__ float sp[];
     constexpr int PW = Tile<PT>::PW, PWH = Tile<PT>::PWH;
-    const int ia = 1 + PT * (int)blockIdx.x, ja = 1 + PT * (int)blockIdx.y;
-    const int kk = blockIdx.z;
+    const int ia = 1 + PT * (int)bid.x, ja = 1 + PT * (int)bid.y;
+    const int kk = bid.z;
     const int k = (PK ? 1 : 2) + 2 * kk;
     const int x0 = ia - PH, y0 = ja - PH;
     load_plane_tile<PT, NT>(sp, own, nbr, n, k, x0, y0);
@@ -601,17 +621,26 @@ __global__ void __launch_bounds__(NT, plane_min_blocks(PT, NT))
     if (events && ev) atomicAdd(events, (unsigned long long)ev);
 }
 
+template <int PK, int PT, int NT>
+__global__ void __launch_bounds__(NT, plane_min_blocks(PT, NT))
+    k_smooth_corr_plane(const float* __restrict__ own, const float* __restrict__ nbr, float* __restrict__ dst,
+                        const float* __restrict__ bstore, const float* __restrict__ rhs_cm, int n, float inv_h2,
+                        float h2half, unsigned long long* events)
+{
+    smooth_corr_plane_block<PK, PT, NT>(own, nbr, dst, bstore, rhs_cm, n, inv_h2, h2half, events, blockIdx);
+}
+
 // res = rhs - N(e) over one PT x PT tile of one interior plane: e staged in
 // shared memory, B and rhs read per in-plane colour (contiguous in the
 // colour-major store).
 template <int PT, int NT>
-__global__ void __launch_bounds__(NT, plane_min_blocks(PT, NT))
-    k_residual_corr_plane(const float* __restrict__ e, const float* __restrict__ bstore,
-                          const float* __restrict__ rhs_cm, float* __restrict__ res, int n, float inv_h2)
+__device__ __forceinline__ void residual_corr_plane_block(const float* __restrict__ e, const float* __restrict__ bstore,
+                                                          const float* __restrict__ rhs_cm, float* __restrict__ res,
+                                                          int n, float inv_h2, uint3 bid)
 {
     extern __shared__ float sp[];
-    const int ia = 1 + PT * (int)blockIdx.x, ja = 1 + PT * (int)blockIdx.y;
-    const int k = 1 + (int)blockIdx.z;
+    const int ia = 1 + PT * (int)bid.x, ja = 1 + PT * (int)bid.y;
+    const int k = 1 + (int)bid.z;
     const int pk = k & 1;
     const int kk = (k - (pk ? 1 : 2)) >> 1;
     const int x0 = ia - PH, y0 = ja - PH;
@@ -620,6 +649,14 @@ __global__ void __launch_bounds__(NT, plane_min_blocks(PT, NT))
     colour_phase<1, PT, NT, false>(sp, bstore, rhs_cm, res, n, pk, kk, k, ia, ja, x0, y0, 0, inv_h2, 0.0f);
     colour_phase<2, PT, NT, false>(sp, bstore, rhs_cm, res, n, pk, kk, k, ia, ja, x0, y0, 0, inv_h2, 0.0f);
     colour_phase<3, PT, NT, false>(sp, bstore, rhs_cm, res, n, pk, kk, k, ia, ja, x0, y0, 0, inv_h2, 0.0f);
+}
+
+template <int PT, int NT>
+__global__ void __launch_bounds__(NT, plane_min_blocks(PT, NT))
+    k_residual_corr_plane(const float* __restrict__ e, const float* __restrict__ bstore,
+                          const float* __restrict__ rhs_cm, float* __restrict__ res, int n, float inv_h2)
+{
+    residual_corr_plane_block<PT, NT>(e, bstore, rhs_cm, res, n, inv_h2, blockIdx);
 }
 
 // The shell of res (faces of the cube) is 0.
@@ -638,14 +675,13 @@ __global__ void k_zero_shell(float* v, int n)
 }
 
 // rhs_H = N_H(w_H) + res_H on the coarse interior, written colour-major.
-__global__ void __launch_bounds__(BX * BY) k_coarse_rhs_corr(const float* __restrict__ w,
-                                                             const float* __restrict__ bstore,
-                                                             const float* __restrict__ resc,
-                                                             float* __restrict__ rhs_cm, int n, float inv_h2)
+__device__ __forceinline__ void coarse_rhs_corr_block(const float* __restrict__ w, const float* __restrict__ bstore,
+                                                      const float* __restrict__ resc, float* __restrict__ rhs_cm,
+                                                      int n, float inv_h2, uint3 bid)
 {
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z;
+    const int i = bid.x * BX + threadIdx.x;
+    const int j = bid.y * BY + threadIdx.y;
+    const int k = bid.z;
     if (i < 1 || j < 1 || k < 1 || i > n - 2 || j > n - 2 || k > n - 2) return;
     const long long p = lin(i, j, k, n);
     const long long sy = n, sz = (long long)n * n;
@@ -653,6 +689,14 @@ __global__ void __launch_bounds__(BX * BY) k_coarse_rhs_corr(const float* __rest
     const S3f B = load_b(bstore + 6 * c.off + c.idx, c.cnt);
     const S3f K = corr_hess(w, p, sy, sz, w[p], inv_h2);
     rhs_cm[c.off + c.idx] = delta_det(B, K) + resc[p];
+}
+
+__global__ void __launch_bounds__(BX * BY) k_coarse_rhs_corr(const float* __restrict__ w,
+                                                             const float* __restrict__ bstore,
+                                                             const float* __restrict__ resc,
+                                                             float* __restrict__ rhs_cm, int n, float inv_h2)
+{
+    coarse_rhs_corr_block(w, bstore, resc, rhs_cm, n, inv_h2, blockIdx);
 }
 
 // Coarsest correction grid: one block, shared memory, FP32 sweeps until
@@ -668,9 +712,9 @@ __device__ __forceinline__ S3f corr_hess_sm(const float* e, int p, int sy, int s
 
 // smem: e (n^3, natural), B (6 floats per interior point, colour-major),
 // rhs (colour-major).
-__global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __restrict__ bstore,
-                                                      const float* __restrict__ rhs_cm, int n, float inv_h2,
-                                                      float h2half, int sweeps, unsigned long long* events)
+__device__ __forceinline__ void coarsest_corr_body(float* e, const float* __restrict__ bstore,
+                                                   const float* __restrict__ rhs_cm, int n, float inv_h2, float h2half,
+                                                   int sweeps, unsigned long long* events)
 {
     extern __shared__ float smf[];
     const int m = n * n * n;
@@ -731,6 +775,13 @@ __global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __r
     }
     for (int q = threadIdx.x; q < m; q += CT) e[q] = se[q];
     if (events && ev) atomicAdd(events, ev);
+}
+
+__global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __restrict__ bstore,
+                                                      const float* __restrict__ rhs_cm, int n, float inv_h2,
+                                                      float h2half, int sweeps, unsigned long long* events)
+{
+    coarsest_corr_body(e, bstore, rhs_cm, n, inv_h2, h2half, sweeps, events);
 }
 
 // ---------------------------------------------------------------------------
@@ -834,7 +885,7 @@ __device__ __forceinline__ float tail_line(const float* uc, const float* wc, int
     return s * w;
 }
 
-__global__ void __launch_bounds__(TT, 1) k_corr_vcycle_tail(TailArgs A)
+__device__ __forceinline__ void corr_tail_body(const TailArgs& A)
 {
     extern __shared__ float tsm[];
     TailSmem S[4];
@@ -983,6 +1034,8 @@ __global__ void __launch_bounds__(TT, 1) k_corr_vcycle_tail(TailArgs A)
     if (A.events && ev) atomicAdd(A.events, ev);
 }
 
+__global__ void __launch_bounds__(TT, 1) k_corr_vcycle_tail(TailArgs A) { corr_tail_body(A); }
+
 // FP64 <-> FP32 copies of whole grids (the FP32 mode's iterate and data).
 __global__ void k_f64_to_f32(const double* __restrict__ u, float* __restrict__ e, long long m)
 {
@@ -1021,28 +1074,42 @@ struct CmF32Out {
 };
 
 // u += e (optional) and e = 0 over the whole grid.
-__global__ void k_update(double* __restrict__ u, float* __restrict__ e, long long m, int apply)
+constexpr int UT = 256;   // threads of the k_update blocks
+
+__device__ __forceinline__ void update_block(double* __restrict__ u, float* __restrict__ e, long long m, int apply,
+                                             unsigned bx)
 {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long p = (long long)bx * UT + threadIdx.x;
     if (p >= m) return;
     if (apply) u[p] += f2d(e[p]);
     e[p] = 0.0f;
 }
 
+__global__ void __launch_bounds__(UT) k_update(double* __restrict__ u, float* __restrict__ e, long long m, int apply)
+{
+    update_block(u, e, m, apply, blockIdx.x);
+}
+
 // Coarse-level FP32 split hi + lo of the injected FP64 iterate: coarse point
 // (I, J, K) takes fine point (sI, sJ, sK), s = 2^level.
-__global__ void __launch_bounds__(BX * BY) k_split_inject(const double* __restrict__ u0, int n0, int stride,
-                                                          float* __restrict__ hi, float* __restrict__ lo, int nc)
+__device__ __forceinline__ void split_inject_block(const double* __restrict__ u0, int n0, int stride,
+                                                   float* __restrict__ hi, float* __restrict__ lo, int nc, uint3 bid)
 {
-    const int I = blockIdx.x * BX + threadIdx.x;
-    const int J = blockIdx.y * BY + threadIdx.y;
-    const int K = blockIdx.z;
+    const int I = bid.x * BX + threadIdx.x;
+    const int J = bid.y * BY + threadIdx.y;
+    const int K = bid.z;
     if (I >= nc || J >= nc) return;
     const double v = u0[lin(stride * I, stride * J, stride * K, n0)];
     const float h = d2f_trunc(v);
     const long long pc = lin(I, J, K, nc);
     hi[pc] = h;
     lo[pc] = d2f_trunc(v - f2d(h));
+}
+
+__global__ void __launch_bounds__(BX * BY) k_split_inject(const double* __restrict__ u0, int n0, int stride,
+                                                          float* __restrict__ hi, float* __restrict__ lo, int nc)
+{
+    split_inject_block(u0, n0, stride, hi, lo, nc, blockIdx);
 }
 
 }  // namespace
@@ -1302,7 +1369,7 @@ int corr_tail_max_n() { return g_tail_max.load(std::memory_order_relaxed); }
 bool set_corr_tail(int max_n)
 {
     if (max_n == 1) max_n = kTailDefault;
-    if (!(max_n == 0 || max_n == 3 || max_n == 5 || max_n == 9 || max_n == 17)) return false;
+    if (!(max_n == 0 || max_n == 3 || max_n == 5 || max_n == 9 || max_n == kTailMaxN)) return false;
     g_tail_max.store(max_n, std::memory_order_relaxed);
     return true;
 }
@@ -1335,11 +1402,13 @@ cudaError_t launch_corr_vcycle_tail(const TailSpec* lv, int nlev, int nu1, int n
 }
 
 cudaError_t prepare_coarsest_f64();
+cudaError_t prepare_batched_kernels();
 
 cudaError_t prepare_kernels()
 {
     cudaError_t e = prepare_coarsest_f64();
     if (e != cudaSuccess) return e;
+    if ((e = prepare_batched_kernels()) != cudaSuccess) return e;
     constexpr int big = Tile<64>::SMEM;
     if ((e = cudaFuncSetAttribute(k_smooth_corr_plane<0, 64, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)) !=
         cudaSuccess)
@@ -1362,7 +1431,7 @@ cudaError_t launch_update(double* u, float* e, int n, int apply, cudaStream_t s)
 {
     const long long m = (long long)n * n * n;
     count_launches(1);
-    k_update<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(u, e, m, apply);
+    k_update<<<(unsigned)((m + UT - 1) / UT), UT, 0, s>>>(u, e, m, apply);
     return cudaGetLastError();
 }
 
@@ -1415,6 +1484,677 @@ cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r_
         u, rhs, CmF32Out{r_cm, (float*)bstore, (float)(0.25 / h2)}, n, 1.0 / (64.0 * h2 * h2 * h2), partials,
         kchunk);
     return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched launches: the kernels of a mixed-precision outer iteration over the
+// levels of several hierarchies at once.  A launch carries a table of jobs
+// (one per hierarchy that has work at this step) and the first block of each;
+// block b finds its job by binary search, skips it when the hierarchy's
+// active flag is 0, and runs the same block body as the single-grid kernel
+// with its block index inside that job's grid.  The levels are aligned by
+// depth: the descents of all hierarchies run depth by depth, every
+// hierarchy's fused tail (or coarsest solve) in one launch, then the ascents.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ uint3 split_block(int q, int gx, int gy)
+{
+    const int gxy = gx * gy;
+    const int bz = q / gxy, r = q - bz * gxy;
+    const int by = r / gx, bx = r - by * gx;
+    return make_uint3((unsigned)bx, (unsigned)by, (unsigned)bz);
+}
+
+template <typename Op>
+__global__ void __launch_bounds__(Op::NT, Op::MINB)
+    k_batched(const typename Op::Job* __restrict__ jobs, const int* __restrict__ start, int njobs,
+              const int* __restrict__ active)
+{
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const typename Op::Job& J = jobs[lo];
+    if (!active[J.inst]) return;   // uniform over the block
+    Op::run(J, b - start[lo]);
+}
+
+struct SmoothJob {
+    int inst, n, gx, gy;
+    float inv_h2, h2half;
+    float* e;
+    const float* bc;
+    const float* rc;
+    unsigned long long* events;
+};
+
+template <int C>
+struct OpSmooth {
+    static constexpr int NT = BX * BY, MINB = 10;
+    using Job = SmoothJob;
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        smooth_corr_block<C & 1, (C >> 1) & 1, (C >> 2) & 1, int>(J.e, J.bc, J.rc, J.n, J.inv_h2, J.h2half, J.events,
+                                                                  split_block(q, J.gx, J.gy));
+    }
+};
+
+struct PlaneSmoothJob {
+    int inst, n, gx, gy;
+    float inv_h2, h2half;
+    const float* own;
+    const float* nbr;
+    float* dst;
+    const float* b;
+    const float* rhs;
+    unsigned long long* events;
+};
+
+struct PlaneResidJob {
+    int inst, n, gx, gy;
+    float inv_h2;
+    const float* e;
+    const float* b;
+    const float* rhs;
+    float* res;
+};
+
+template <int PK, int PT, int NTH>
+struct OpPlaneSmooth {
+    static constexpr int NT = NTH, MINB = plane_min_blocks(PT, NTH);
+    using Job = PlaneSmoothJob;
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        smooth_corr_plane_block<PK, PT, NTH>(J.own, J.nbr, J.dst, J.b, J.rhs, J.n, J.inv_h2, J.h2half, J.events,
+                                             split_block(q, J.gx, J.gy));
+    }
+};
+
+template <int PT, int NTH>
+struct OpPlaneResid {
+    static constexpr int NT = NTH, MINB = plane_min_blocks(PT, NTH);
+    using Job = PlaneResidJob;
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        residual_corr_plane_block<PT, NTH>(J.e, J.b, J.rhs, J.res, J.n, J.inv_h2, split_block(q, J.gx, J.gy));
+    }
+};
+
+struct OpRestrict {
+    static constexpr int NT = BX * BY, MINB = 1;
+    struct Job {
+        int inst, nf, nc, kind, approx, gx, gy;
+        const float* ef;
+        const float* rf;
+        float* wc;
+        float* ec;
+        float* rc;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        xfer::restrict_block<float>(J.ef, J.rf, J.nf, J.wc, J.ec, J.rc, J.nc, J.kind, J.approx,
+                                    split_block(q, J.gx, J.gy));
+    }
+};
+
+struct OpCoarseRhs {
+    static constexpr int NT = BX * BY, MINB = 1;
+    struct Job {
+        int inst, n, gx, gy;
+        float inv_h2;
+        const float* w;
+        const float* b;
+        const float* resc;
+        float* rhs;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        coarse_rhs_corr_block(J.w, J.b, J.resc, J.rhs, J.n, J.inv_h2, split_block(q, J.gx, J.gy));
+    }
+};
+
+struct OpProlong {
+    static constexpr int NT = BX * BY, MINB = 1;
+    struct Job {
+        int inst, nc, nf, gx, gy;
+        const float* ec;
+        const float* wc;
+        float* ef;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        xfer::prolong_block<float>(J.ec, J.wc, J.nc, J.ef, J.nf, 1, split_block(q, J.gx, J.gy));
+    }
+};
+
+struct OpTail {
+    static constexpr int NT = TT, MINB = 1;
+    struct Job {
+        int inst;
+        TailArgs A;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int) { corr_tail_body(J.A); }
+};
+
+struct OpCoarsest {
+    static constexpr int NT = CT, MINB = 1;
+    struct Job {
+        int inst, n, sweeps;
+        float inv_h2, h2half;
+        float* e;
+        const float* b;
+        const float* rhs;
+        unsigned long long* events;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int)
+    {
+        coarsest_corr_body(J.e, J.b, J.rhs, J.n, J.inv_h2, J.h2half, J.sweeps, J.events);
+    }
+};
+
+struct OpUpdate {
+    static constexpr int NT = UT, MINB = 1;
+    struct Job {
+        int inst;
+        long long m;
+        double* u;
+        float* e;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q) { update_block(J.u, J.e, J.m, 1, (unsigned)q); }
+};
+
+struct OpSplit {
+    static constexpr int NT = BX * BY, MINB = 1;
+    struct Job {
+        int inst, n0, stride, nc, gx, gy;
+        const double* u0;
+        float* hi;
+        float* lo;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        split_inject_block(J.u0, J.n0, J.stride, J.hi, J.lo, J.nc, split_block(q, J.gx, J.gy));
+    }
+};
+
+struct OpBase {
+    static constexpr int NT = BX * BY, MINB = 1;
+    struct Job {
+        int inst, n, gx, gy;
+        float inv_h2;
+        const float* hi;
+        const float* lo;
+        float* b;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        base_colour_block(J.hi, J.lo, J.b, J.n, J.inv_h2, split_block(q, J.gx, J.gy));
+    }
+};
+
+struct OpRes64 {
+    static constexpr int NT = resid::RX * resid::RY, MINB = 1;
+    struct Job {
+        int inst, n, kchunk, gx, gy, gz;
+        double inv_h6;
+        const double* u;
+        const double* rhs;
+        double* partials;
+        CmF32Out out;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        resid::residual_col_block<CmF32Out>(J.u, J.rhs, J.out, J.n, J.inv_h6, J.partials, J.kchunk,
+                                            split_block(q, J.gx, J.gy),
+                                            make_uint3((unsigned)J.gx, (unsigned)J.gy, (unsigned)J.gz));
+    }
+};
+
+struct OpNorm {
+    static constexpr int NT = resid::NF, MINB = 1;
+    struct Job {
+        int inst, count;
+        double h3;
+        const double* partials;
+        double* out2;
+        double* packed;   // 5 doubles of this instance
+        const unsigned long long* events;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int)
+    {
+        resid::norm_final_block(J.partials, J.count, J.h3, J.out2);
+        if (threadIdx.x == 0) {
+            J.packed[0] = J.out2[0];
+            J.packed[1] = J.out2[1];
+            unsigned long long ev = J.events ? *J.events : 0ull;
+            double d;
+            memcpy(&d, &ev, sizeof d);
+            J.packed[4] = d;
+        }
+    }
+};
+
+enum BatchOpId {
+    B_SMOOTH0 = 0,   // .. B_SMOOTH0 + 7
+    B_RESTRICT = 8, B_COARSE_RHS, B_PROLONG, B_TAIL, B_COARSEST, B_UPDATE, B_SPLIT, B_BASE, B_RES64, B_NORM,
+    B_PSMOOTH16_0, B_PSMOOTH16_1, B_PSMOOTH32_0, B_PSMOOTH32_1,   // k-parity sweeps, tiles of 16 / 32, parity 0 / 1
+    B_PRESID16, B_PRESID32, B_PRESID64                            // residual in plane tiles
+};
+
+struct BLaunch {
+    int op, njobs, blocks, smem;
+    size_t jobs_off, starts_off;
+};
+
+dim3 batch_grid2(int n) { return dim3((n + BX - 1) / BX, (n + BY - 1) / BY, n); }
+
+}  // namespace
+
+struct BatchPlan {
+    std::vector<BLaunch> seq;
+    char* dev = nullptr;
+    const int* active = nullptr;
+};
+
+namespace {
+
+// Accumulates the job tables of a plan in host memory, each table (jobs,
+// then njobs + 1 block starts) 256-byte aligned.
+struct TableBuilder {
+    std::vector<char> buf;
+    std::vector<BLaunch> seq;
+    size_t align(size_t x) { return (x + 255) / 256 * 256; }
+    template <typename Job>
+    void emit(int op, const std::vector<Job>& jobs, const std::vector<int>& blocks, int smem)
+    {
+        if (jobs.empty()) return;
+        BLaunch L;
+        L.op = op;
+        L.njobs = (int)jobs.size();
+        L.smem = smem;
+        L.jobs_off = align(buf.size());
+        L.starts_off = align(L.jobs_off + sizeof(Job) * jobs.size());
+        buf.resize(align(L.starts_off + sizeof(int) * (jobs.size() + 1)), 0);
+        std::memcpy(buf.data() + L.jobs_off, jobs.data(), sizeof(Job) * jobs.size());
+        int* st = (int*)(buf.data() + L.starts_off);
+        int acc = 0;
+        for (size_t q = 0; q < jobs.size(); ++q) {
+            st[q] = acc;
+            acc += blocks[q];
+        }
+        st[jobs.size()] = acc;
+        L.blocks = acc;
+        if (acc > 0) seq.push_back(L);
+    }
+};
+
+struct LevelRefs {
+    const BatchLevel* lv;
+    float inv_h2, h2half;
+};
+
+int tail_start(const BatchInstance& I, int tmax)
+{
+    int lt = I.L - 1;
+    while (lt > 0 && I.lev[lt - 1].n <= tmax) --lt;
+    return I.lev[lt].n <= tmax ? lt : -1;   // -1: no fused tail (coarsest solve alone)
+}
+
+void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const BatchParams& p, double* packed)
+{
+    const auto inv_h2 = [](double h) { return (float)(1.0 / (h * h)); };
+    const auto h2half = [](double h) { return (float)(0.5 * h * h); };
+    // first level of each instance's tail (or its coarsest level)
+    std::vector<int> lt(count);
+    std::vector<int> fused(count);
+    int D = 0;
+    for (int b = 0; b < count; ++b) {
+        const int t = tail_start(in[b], p.tail_max);
+        fused[b] = t >= 0;
+        lt[b] = t >= 0 ? t : in[b].L - 1;
+        D = lt[b] > D ? lt[b] : D;
+    }
+    // Sweeps at depth d: by k parity through e2 (pairs of sweeps, 4 launches
+    // a pair) when every grid at this depth has n <= 65, where launches cost
+    // more than the sweeps' work; by colour otherwise.  Both are the same
+    // sequential 8-colour sweep, bit for bit.
+    auto max_n_at = [&](int d) {
+        int m = 0;
+        for (int b = 0; b < count; ++b)
+            if (d < lt[b]) m = in[b].lev[d].n > m ? in[b].lev[d].n : m;
+        return m;
+    };
+    auto plane_pair = [&](int d) {
+        const int mx = max_n_at(d);
+        const int PT = mx <= 33 ? 16 : 32;
+        for (int half = 0; half < 2; ++half)          // e -> e2, then e2 -> e
+            for (int pk = 0; pk < 2; ++pk) {
+                std::vector<PlaneSmoothJob> jobs;
+                std::vector<int> blocks;
+                for (int b = 0; b < count; ++b) {
+                    if (d >= lt[b]) continue;
+                    const BatchLevel& F = in[b].lev[d];
+                    const int n = F.n;
+                    const int planes = colour_count(n, pk);
+                    if (planes <= 0) continue;
+                    float* src = half == 0 ? F.e : F.e2;
+                    float* dst = half == 0 ? F.e2 : F.e;
+                    PlaneSmoothJob J;
+                    J.inst = in[b].id;
+                    J.n = n;
+                    J.gx = J.gy = (n - 2 + PT - 1) / PT;
+                    J.inv_h2 = inv_h2(F.h);
+                    J.h2half = h2half(F.h);
+                    J.own = src;
+                    J.nbr = pk == 0 ? src : dst;
+                    J.dst = dst;
+                    J.b = (const float*)F.bstore;
+                    J.rhs = F.rhs32;
+                    J.events = in[b].events;
+                    jobs.push_back(J);
+                    blocks.push_back(J.gx * J.gy * planes);
+                }
+                const int op = PT == 16 ? (pk ? B_PSMOOTH16_1 : B_PSMOOTH16_0) : (pk ? B_PSMOOTH32_1 : B_PSMOOTH32_0);
+                T.emit(op, jobs, blocks, PT == 16 ? Tile<16>::SMEM : Tile<32>::SMEM);
+            }
+    };
+    auto smooth = [&](int d, int nsweeps) {
+        int sw = 0;
+        bool plane = max_n_at(d) <= 65;
+        for (int b = 0; b < count && plane; ++b)
+            if (d < lt[b] && (!in[b].lev[d].e2 || in[b].lev[d].n < 5)) plane = false;
+        if (plane)
+            for (; sw + 2 <= nsweeps; sw += 2) plane_pair(d);
+        for (; sw < nsweeps; ++sw)
+            for (int c = 0; c < 8; ++c) {
+                std::vector<SmoothJob> jobs;
+                std::vector<int> blocks;
+                for (int b = 0; b < count; ++b) {
+                    if (d >= lt[b]) continue;
+                    const BatchLevel& F = in[b].lev[d];
+                    const int n = F.n;
+                    const int ni = colour_count(n, c & 1), nj = colour_count(n, (c >> 1) & 1),
+                              nk = colour_count(n, (c >> 2) & 1);
+                    if (ni <= 0 || nj <= 0 || nk <= 0) continue;
+                    const long long off = cm_offset(n, c);
+                    SmoothJob J;
+                    J.inst = in[b].id;
+                    J.n = n;
+                    J.gx = (ni + BX - 1) / BX;
+                    J.gy = (nj + BY - 1) / BY;
+                    J.inv_h2 = inv_h2(F.h);
+                    J.h2half = h2half(F.h);
+                    J.e = F.e;
+                    J.bc = (const float*)F.bstore + 6 * off;
+                    J.rc = F.rhs32 + off;
+                    J.events = in[b].events;
+                    jobs.push_back(J);
+                    blocks.push_back(J.gx * J.gy * nk);
+                }
+                T.emit(B_SMOOTH0 + c, jobs, blocks, 0);
+            }
+    };
+    for (int cyc = 0; cyc < p.inner; ++cyc) {
+        for (int d = 0; d < D; ++d) {
+            smooth(d, p.nu1);
+            std::vector<PlaneResidJob> rj;
+            std::vector<OpRestrict::Job> sj;
+            std::vector<OpCoarseRhs::Job> cj;
+            std::vector<int> rb, sb, cb;
+            const int mx = max_n_at(d);
+            const int RT = mx >= 129 ? 64 : (mx >= 65 ? 32 : 16);   // residual tile
+            for (int b = 0; b < count; ++b) {
+                if (d >= lt[b]) continue;
+                const BatchLevel& F = in[b].lev[d];
+                const BatchLevel& C = in[b].lev[d + 1];
+                const dim3 gc = batch_grid2(C.n);
+                const int t = (F.n - 2 + RT - 1) / RT;
+                PlaneResidJob r{in[b].id, F.n, t, t, inv_h2(F.h), F.e, (const float*)F.bstore, F.rhs32,
+                                                      F.res32};
+                rj.push_back(r);
+                rb.push_back(t * t * (F.n - 2));
+                OpRestrict::Job s{in[b].id, F.n, C.n, p.kind, p.approx, (int)gc.x, (int)gc.y, F.e, F.res32, C.w32, C.e,
+                                  C.res32};
+                sj.push_back(s);
+                sb.push_back((int)(gc.x * gc.y * gc.z));
+                OpCoarseRhs::Job q{in[b].id, C.n, (int)gc.x, (int)gc.y, inv_h2(C.h), C.w32, (const float*)C.bstore,
+                                   C.res32, C.rhs32};
+                cj.push_back(q);
+                cb.push_back((int)(gc.x * gc.y * gc.z));
+            }
+            T.emit(RT == 64 ? B_PRESID64 : (RT == 32 ? B_PRESID32 : B_PRESID16), rj, rb,
+                   RT == 64 ? Tile<64>::SMEM : (RT == 32 ? Tile<32>::SMEM : Tile<16>::SMEM));
+            T.emit(B_RESTRICT, sj, sb, 0);
+            T.emit(B_COARSE_RHS, cj, cb, 0);
+        }
+        {   // every hierarchy's tail (or coarsest solve), one launch
+            std::vector<OpTail::Job> tj;
+            std::vector<OpCoarsest::Job> kj;
+            std::vector<int> tb, kb;
+            int tsmem = 0, ksmem = 0;
+            for (int b = 0; b < count; ++b) {
+                const BatchInstance& I = in[b];
+                if (fused[b]) {
+                    OpTail::Job J;
+                    std::memset(&J, 0, sizeof J);
+                    J.inst = in[b].id;
+                    TailArgs& A = J.A;
+                    A.nlev = I.L - lt[b];
+                    int ns[4] = {0, 0, 0, 0};
+                    for (int q = 0; q < A.nlev; ++q) {
+                        const BatchLevel& V = I.lev[lt[b] + q];
+                        ns[q] = V.n;
+                        A.lev[q].n = V.n;
+                        A.lev[q].inv_h2 = inv_h2(V.h);
+                        A.lev[q].h2half = h2half(V.h);
+                        A.lev[q].e = V.e;
+                        A.lev[q].b = (const float*)V.bstore;
+                        A.lev[q].rhs = V.rhs32;
+                    }
+                    A.nu1 = p.nu1;
+                    A.nu2 = p.nu2;
+                    A.kind = p.kind;
+                    A.approx = p.approx;
+                    A.coarse_sweeps = p.coarse_sweeps;
+                    A.events = I.events;
+                    const int sm = tail_smem_bytes(ns, A.nlev);
+                    tsmem = sm > tsmem ? sm : tsmem;
+                    tj.push_back(J);
+                    tb.push_back(1);
+                } else {
+                    const BatchLevel& V = I.lev[I.L - 1];
+                    OpCoarsest::Job J{in[b].id, V.n, p.coarse_sweeps, inv_h2(V.h), h2half(V.h), V.e,
+                                      (const float*)V.bstore, V.rhs32, I.events};
+                    const int sm = (int)coarsest_corr_smem(V.n);
+                    ksmem = sm > ksmem ? sm : ksmem;
+                    kj.push_back(J);
+                    kb.push_back(1);
+                }
+            }
+            T.emit(B_TAIL, tj, tb, tsmem);
+            T.emit(B_COARSEST, kj, kb, ksmem);
+        }
+        for (int d = D - 1; d >= 0; --d) {
+            std::vector<OpProlong::Job> pj;
+            std::vector<int> pb;
+            for (int b = 0; b < count; ++b) {
+                if (d >= lt[b]) continue;
+                const BatchLevel& F = in[b].lev[d];
+                const BatchLevel& C = in[b].lev[d + 1];
+                const dim3 g = xfer::prolong_grid(F.n);
+                OpProlong::Job J{in[b].id, C.n, F.n, (int)g.x, (int)g.y, C.e, C.w32, F.e};
+                pj.push_back(J);
+                pb.push_back((int)(g.x * g.y * g.z));
+            }
+            T.emit(B_PROLONG, pj, pb, 0);
+            smooth(d, p.nu2);
+        }
+    }
+    // u += e, e = 0; the coarse base Hessians of the new iterate
+    {
+        std::vector<OpUpdate::Job> uj;
+        std::vector<int> ub;
+        for (int b = 0; b < count; ++b) {
+            const BatchLevel& F = in[b].lev[0];
+            const long long m = (long long)F.n * F.n * F.n;
+            uj.push_back(OpUpdate::Job{in[b].id, m, F.u, F.e});
+            ub.push_back((int)((m + UT - 1) / UT));
+        }
+        T.emit(B_UPDATE, uj, ub, 0);
+    }
+    int Lmax = 0;
+    for (int b = 0; b < count; ++b) Lmax = in[b].L > Lmax ? in[b].L : Lmax;
+    for (int l = 1; l < Lmax; ++l) {
+        std::vector<OpSplit::Job> sj;
+        std::vector<OpBase::Job> bj;
+        std::vector<int> sb, bb;
+        for (int b = 0; b < count; ++b) {
+            if (l >= in[b].L) continue;
+            const BatchLevel& F = in[b].lev[0];
+            const BatchLevel& A = in[b].lev[l];
+            const dim3 g = batch_grid2(A.n);
+            sj.push_back(OpSplit::Job{in[b].id, F.n, 1 << l, A.n, (int)g.x, (int)g.y, F.u, A.hi, A.lo});
+            sb.push_back((int)(g.x * g.y * g.z));
+            bj.push_back(OpBase::Job{in[b].id, A.n, (int)g.x, (int)g.y, inv_h2(A.h), A.hi, A.lo, (float*)A.bstore});
+            bb.push_back((int)(g.x * g.y * g.z));
+        }
+        T.emit(B_SPLIT, sj, sb, 0);
+        T.emit(B_BASE, bj, bb, 0);
+    }
+    // FP64 fine residual (the next correction rhs and the fine B) and its norms
+    {
+        std::vector<OpRes64::Job> rj;
+        std::vector<OpNorm::Job> nj;
+        std::vector<int> rb, nb;
+        for (int b = 0; b < count; ++b) {
+            const BatchInstance& I = in[b];
+            const BatchLevel& F = I.lev[0];
+            const int n = F.n;
+            const double h2 = F.h * F.h;
+            const int kz = n < 16 ? n : 16;
+            const dim3 g = resid::grid_for(n, kz);
+            OpRes64::Job J;
+            std::memset(&J, 0, sizeof J);
+            J.inst = in[b].id;
+            J.n = n;
+            J.kchunk = (n + kz - 1) / kz;
+            J.gx = (int)g.x;
+            J.gy = (int)g.y;
+            J.gz = (int)g.z;
+            J.inv_h6 = 1.0 / (64.0 * h2 * h2 * h2);
+            J.u = F.u;
+            J.rhs = F.rhs;
+            J.partials = I.partials;
+            J.out = CmF32Out{F.rhs32, (float*)F.bstore, (float)(0.25 / h2)};
+            rj.push_back(J);
+            rb.push_back((int)(g.x * g.y * g.z));
+            OpNorm::Job N{in[b].id, I.npartials, F.h * F.h * F.h, I.partials, I.out2, packed + 5 * in[b].id, I.events};
+            nj.push_back(N);
+            nb.push_back(1);
+        }
+        T.emit(B_RES64, rj, rb, 0);
+        T.emit(B_NORM, nj, nb, 0);
+    }
+}
+
+template <typename Op>
+cudaError_t launch_batched(const BatchPlan* P, const BLaunch& L, dim3 block, cudaStream_t s)
+{
+    count_launches(1);
+    k_batched<Op><<<L.blocks, block, L.smem, s>>>((const typename Op::Job*)(P->dev + L.jobs_off),
+                                                  (const int*)(P->dev + L.starts_off), L.njobs, P->active);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t batch_tables_bytes(const BatchInstance* in, int count, const BatchParams& p)
+{
+    TableBuilder T;
+    build_sequence(T, in, count, p, nullptr);
+    return T.buf.size();
+}
+
+BatchPlan* batch_plan_create(const BatchInstance* in, int count, const BatchParams& p, void* tables_dev,
+                             const int* active_dev, double* packed_dev, cudaStream_t s, cudaError_t* err)
+{
+    TableBuilder T;
+    build_sequence(T, in, count, p, packed_dev);
+    *err = cudaSuccess;
+    if (!T.buf.empty()) {
+        *err = cudaMemcpyAsync(tables_dev, T.buf.data(), T.buf.size(), cudaMemcpyHostToDevice, s);
+        if (*err == cudaSuccess) *err = cudaStreamSynchronize(s);
+    }
+    if (*err != cudaSuccess) return nullptr;
+    BatchPlan* P = new (std::nothrow) BatchPlan();
+    if (!P) {
+        *err = cudaErrorMemoryAllocation;
+        return nullptr;
+    }
+    P->seq = std::move(T.seq);
+    P->dev = (char*)tables_dev;
+    P->active = active_dev;
+    return P;
+}
+
+cudaError_t batch_plan_iteration(const BatchPlan* P, cudaStream_t s)
+{
+    const dim3 b2(BX, BY);
+    for (const BLaunch& L : P->seq) {
+        cudaError_t e;
+        switch (L.op) {
+        case B_SMOOTH0 + 0: e = launch_batched<OpSmooth<0>>(P, L, b2, s); break;
+        case B_SMOOTH0 + 1: e = launch_batched<OpSmooth<1>>(P, L, b2, s); break;
+        case B_SMOOTH0 + 2: e = launch_batched<OpSmooth<2>>(P, L, b2, s); break;
+        case B_SMOOTH0 + 3: e = launch_batched<OpSmooth<3>>(P, L, b2, s); break;
+        case B_SMOOTH0 + 4: e = launch_batched<OpSmooth<4>>(P, L, b2, s); break;
+        case B_SMOOTH0 + 5: e = launch_batched<OpSmooth<5>>(P, L, b2, s); break;
+        case B_SMOOTH0 + 6: e = launch_batched<OpSmooth<6>>(P, L, b2, s); break;
+        case B_SMOOTH0 + 7: e = launch_batched<OpSmooth<7>>(P, L, b2, s); break;
+        case B_RESTRICT: e = launch_batched<OpRestrict>(P, L, b2, s); break;
+        case B_COARSE_RHS: e = launch_batched<OpCoarseRhs>(P, L, b2, s); break;
+        case B_PROLONG: e = launch_batched<OpProlong>(P, L, b2, s); break;
+        case B_TAIL: e = launch_batched<OpTail>(P, L, dim3(OpTail::NT), s); break;
+        case B_COARSEST: e = launch_batched<OpCoarsest>(P, L, dim3(OpCoarsest::NT), s); break;
+        case B_UPDATE: e = launch_batched<OpUpdate>(P, L, dim3(OpUpdate::NT), s); break;
+        case B_SPLIT: e = launch_batched<OpSplit>(P, L, b2, s); break;
+        case B_BASE: e = launch_batched<OpBase>(P, L, b2, s); break;
+        case B_RES64: e = launch_batched<OpRes64>(P, L, dim3(resid::RX, resid::RY), s); break;
+        case B_NORM: e = launch_batched<OpNorm>(P, L, dim3(OpNorm::NT), s); break;
+        case B_PSMOOTH16_0: e = launch_batched<OpPlaneSmooth<0, 16, 128>>(P, L, dim3(128), s); break;
+        case B_PSMOOTH16_1: e = launch_batched<OpPlaneSmooth<1, 16, 128>>(P, L, dim3(128), s); break;
+        case B_PSMOOTH32_0: e = launch_batched<OpPlaneSmooth<0, 32, 128>>(P, L, dim3(128), s); break;
+        case B_PSMOOTH32_1: e = launch_batched<OpPlaneSmooth<1, 32, 128>>(P, L, dim3(128), s); break;
+        case B_PRESID16: e = launch_batched<OpPlaneResid<16, 128>>(P, L, dim3(128), s); break;
+        case B_PRESID32: e = launch_batched<OpPlaneResid<32, 128>>(P, L, dim3(128), s); break;
+        case B_PRESID64: e = launch_batched<OpPlaneResid<64, 256>>(P, L, dim3(256), s); break;
+        default: e = cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+unsigned long long batch_plan_launches(const BatchPlan* P) { return P ? P->seq.size() : 0; }
+
+void batch_plan_destroy(BatchPlan* P) { delete P; }
+
+cudaError_t prepare_batched_kernels()
+{
+    const int tail_ns[4] = {17, 9, 5, 3};
+    cudaError_t e = cudaFuncSetAttribute(k_batched<OpTail>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tail_smem_bytes(tail_ns, 4));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_batched<OpPlaneResid<64, 256>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Tile<64>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_batched<OpCoarsest>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)coarsest_corr_smem(17));
 }
 
 }  // namespace ma

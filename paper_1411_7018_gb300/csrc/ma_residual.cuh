@@ -31,13 +31,16 @@ struct NaturalF64Out {
     __device__ __forceinline__ void zero(long long p) const { r[p] = 0.0; }
 };
 
+// Block body with the block index and the grid's dimensions as arguments (a
+// batched launch over several grids runs the same code).
 template <typename Out>
-__global__ void __launch_bounds__(RX * RY) k_residual_col(const double* __restrict__ u, const double* __restrict__ rhs,
-                                                          Out out, int n, double inv_h6, double* partials, int kchunk)
+__device__ __forceinline__ void residual_col_block(const double* __restrict__ u, const double* __restrict__ rhs,
+                                                   const Out& out, int n, double inv_h6, double* partials, int kchunk,
+                                                   uint3 bid, uint3 gdim)
 {
-    const int i = blockIdx.x * RX + threadIdx.x;
-    const int j = blockIdx.y * RY + threadIdx.y;
-    const int k0 = blockIdx.z * kchunk;
+    const int i = bid.x * RX + threadIdx.x;
+    const int j = bid.y * RY + threadIdx.y;
+    const int k0 = bid.z * kchunk;
     const int k1 = min(n, k0 + kchunk);
     const long long sy = n, sz = (long long)n * n;
     float mx = 0.0f, ss = 0.0f;
@@ -106,10 +109,47 @@ __global__ void __launch_bounds__(RX * RY) k_residual_col(const double* __restri
         if (t == 0) {
             double m = f2d(smx[0]), q = f2d(sss[0]);
             for (int w = 1; w < RX * RY / 32; ++w) { m = fmax(m, f2d(smx[w])); q += f2d(sss[w]); }
-            const int slot = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            const int slot = (bid.z * gdim.y + bid.y) * gdim.x + bid.x;
             partials[2 * slot] = m;
             partials[2 * slot + 1] = q;
         }
+    }
+}
+
+template <typename Out>
+__global__ void __launch_bounds__(RX * RY) k_residual_col(const double* __restrict__ u, const double* __restrict__ rhs,
+                                                          Out out, int n, double inv_h6, double* partials, int kchunk)
+{
+    residual_col_block<Out>(u, rhs, out, n, inv_h6, partials, kchunk, blockIdx, gridDim);
+}
+
+// One block of NF = 256 threads folds the (max, sum of squares) partials in
+// a fixed order: out2 = (max, sqrt(h^3 sum)), the max and discrete L2 norms
+// of the stopping rule (Section 4).
+constexpr int NF = 256;
+
+__device__ __forceinline__ void norm_final_block(const double* __restrict__ partials, int count, double h3,
+                                                 double* out2)
+{
+    __shared__ double smx[NF], sss[NF];
+    double mx = 0.0, ss = 0.0;
+    for (int q = threadIdx.x; q < count; q += NF) {
+        mx = fmax(mx, partials[2 * q]);
+        ss += partials[2 * q + 1];
+    }
+    smx[threadIdx.x] = mx;
+    sss[threadIdx.x] = ss;
+    __syncthreads();
+    for (int w = NF / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            smx[threadIdx.x] = fmax(smx[threadIdx.x], smx[threadIdx.x + w]);
+            sss[threadIdx.x] += sss[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out2[0] = smx[0];
+        out2[1] = sqrt(h3 * sss[0]);
     }
 }
 

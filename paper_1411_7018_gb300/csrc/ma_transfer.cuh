@@ -51,14 +51,16 @@ __device__ __forceinline__ T weighted_restrict(const T* __restrict__ v, long lon
 // Coarse-grid outputs, any may be null: rc = I r (0 on the shell);
 // wc = approximation restriction of uf (approx 0: injection everywhere;
 // 1: the kind weighting inside, injection on the shell); uc = copy of wc.
+// The block body takes its block index as an argument, so that a batched
+// launch over the grids of several hierarchies runs the same code.
 template <typename T>
-__global__ void __launch_bounds__(BX * BY) k_restrict(const T* __restrict__ uf, const T* __restrict__ rf, int nf,
-                                                      T* __restrict__ wc, T* __restrict__ uc, T* __restrict__ rc,
-                                                      int nc, int kind, int approx)
+__device__ __forceinline__ void restrict_block(const T* __restrict__ uf, const T* __restrict__ rf, int nf,
+                                               T* __restrict__ wc, T* __restrict__ uc, T* __restrict__ rc, int nc,
+                                               int kind, int approx, uint3 bid)
 {
-    const int I = blockIdx.x * BX + threadIdx.x;
-    const int J = blockIdx.y * BY + threadIdx.y;
-    const int K = blockIdx.z;
+    const int I = bid.x * BX + threadIdx.x;
+    const int J = bid.y * BY + threadIdx.y;
+    const int K = bid.z;
     if (I >= nc || J >= nc) return;
     const long long pc = lin(I, J, K, nc);
     const long long pf = lin(2 * I, 2 * J, 2 * K, nf);
@@ -72,6 +74,14 @@ __global__ void __launch_bounds__(BX * BY) k_restrict(const T* __restrict__ uf, 
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(BX * BY) k_restrict(const T* __restrict__ uf, const T* __restrict__ rf, int nf,
+                                                      T* __restrict__ wc, T* __restrict__ uc, T* __restrict__ rc,
+                                                      int nc, int kind, int approx)
+{
+    restrict_block<T>(uf, rf, nf, wc, uc, rc, nc, kind, approx, blockIdx);
+}
+
 // Trilinear interpolation at fine interior points: along each axis an even
 // index sits on a coarse point, an odd one halfway between two.  Thread
 // (I, j, k) writes fine points i = 2I + 1 and 2I + 2 of row (j, k): with
@@ -82,12 +92,12 @@ __global__ void __launch_bounds__(BX * BY) k_restrict(const T* __restrict__ uf, 
 // add != 0: uf += I(uc - wc) (coarse-grid correction); add == 0: uf = I(uc).
 // Grid: prolong_grid(nf), blocks of BX x BY.
 template <typename T>
-__global__ void __launch_bounds__(BX * BY) k_prolong(const T* __restrict__ uc, const T* __restrict__ wc, int nc,
-                                                     T* __restrict__ uf, int nf, int add)
+__device__ __forceinline__ void prolong_block(const T* __restrict__ uc, const T* __restrict__ wc, int nc,
+                                              T* __restrict__ uf, int nf, int add, uint3 bid)
 {
-    const int I = blockIdx.x * BX + threadIdx.x;
-    const int j = 1 + blockIdx.y * BY + threadIdx.y;
-    const int k = 1 + blockIdx.z;
+    const int I = bid.x * BX + threadIdx.x;
+    const int j = 1 + bid.y * BY + threadIdx.y;
+    const int k = 1 + bid.z;
     const bool row = j <= nf - 2;   // uniform over the warp (BX = 32)
     const int J0 = j >> 1, K0 = k >> 1, oj = j & 1, ok = k & 1;
     const T w = T(1) / T(1 << (oj + ok));
@@ -109,6 +119,13 @@ __global__ void __launch_bounds__(BX * BY) k_prolong(const T* __restrict__ uc, c
     const T mid = (a + b) * T(0.5);
     uf[p] = add ? uf[p] + mid : mid;
     if (2 * I + 2 <= nf - 2) uf[p + 1] = add ? uf[p + 1] + b : b;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX * BY) k_prolong(const T* __restrict__ uc, const T* __restrict__ wc, int nc,
+                                                     T* __restrict__ uf, int nf, int add)
+{
+    prolong_block<T>(uc, wc, nc, uf, nf, add, blockIdx);
 }
 
 inline dim3 prolong_grid(int nf)

@@ -64,6 +64,11 @@ _SIGS = {
     "ma_solve_advance": [_vp, C.POINTER(C.c_int)],
     "ma_solve_get_result": [_vp, C.POINTER(ma_solve_result)],
     "ma_batch_solve": [C.POINTER(_vp), C.c_int, C.POINTER(ma_solve_opts), C.POINTER(ma_solve_result)],
+    "ma_batch_footprint": [C.POINTER(_vp), C.c_int, C.POINTER(C.c_size_t)],
+    "ma_create_batch": [C.POINTER(_vp), C.c_int, _vp, C.c_size_t, _vp, C.POINTER(_vp)],
+    "ma_batch_run": [_vp, C.POINTER(ma_solve_opts), C.POINTER(ma_solve_result)],
+    "ma_destroy_batch": [_vp],
+    "ma_set_batch_groups": [C.c_int],
     "ma_residual_norm": [_vp, C.c_int, C.POINTER(C.c_double)],
     "ma_get_solution": [_vp, _vp],
     "ma_set_solution": [_vp, _vp],
@@ -210,6 +215,38 @@ def ma_batch_solve(hiers, opts: ma_solve_opts, raise_on_error: bool = True):
     if raise_on_error:
         _check(st)
     return list(res)
+
+
+def ma_batch_footprint(hiers) -> int:
+    n = len(hiers)
+    arr = (_vp * n)(*hiers)
+    b = C.c_size_t(0)
+    _check(load().ma_batch_footprint(arr, n, C.byref(b)))
+    return b.value
+
+
+def ma_create_batch(hiers, workspace, nbytes: int, stream=None) -> int:
+    n = len(hiers)
+    arr = (_vp * n)(*hiers)
+    out = _vp()
+    _check(load().ma_create_batch(arr, n, _ptr(workspace), nbytes, _stream(stream), C.byref(out)))
+    return out.value
+
+
+def ma_batch_run(batch: int, count: int, opts: ma_solve_opts, raise_on_error: bool = True):
+    res = (ma_solve_result * count)()
+    st = load().ma_batch_run(batch, C.byref(opts), res)
+    if raise_on_error:
+        _check(st)
+    return list(res)
+
+
+def ma_destroy_batch(batch: int) -> None:
+    _check(load().ma_destroy_batch(batch))
+
+
+def ma_set_batch_groups(groups: int) -> None:
+    _check(load().ma_set_batch_groups(int(groups)))
 
 
 def ma_residual_norm(hier: int, norm: int = MA_NORM_MAX) -> float:
@@ -491,6 +528,39 @@ class Hierarchy:
     def close(self):
         if self.handle:
             ma_destroy_hierarchy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Shared per-level batch over Hierarchy objects (ma_create_batch): owns
+    its torch workspace; the hierarchies must stay open while it lives."""
+
+    def __init__(self, hierarchies, stream=None, device=None):
+        import torch
+        self.hierarchies = list(hierarchies)
+        handles = [h.handle for h in self.hierarchies]
+        self.nbytes = ma_batch_footprint(handles)
+        self.workspace = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device or torch.device("cuda"))
+        aligned = (self.workspace.data_ptr() + 255) // 256 * 256
+        self.handle = ma_create_batch(handles, aligned, self.nbytes, stream)
+
+    def solve(self, tol: float = 1e-10, norm: int = MA_NORM_MAX, relative=True, max_cycles: int = 50,
+              init: int = MA_INIT_FMG, raise_on_error: bool = True):
+        rel = int(relative) if not isinstance(relative, bool) else (MA_REL_RHS if relative else MA_REL_NONE)
+        o = ma_solve_opts(tol, norm, rel, max_cycles, init)
+        rs = ma_batch_run(self.handle, len(self.hierarchies), o, raise_on_error)
+        return [SolveResult(r.cycles, r.res0, r.res, r.status, bool(r.floor_reached), r.nonconvex_root_events)
+                for r in rs]
+
+    def close(self):
+        if self.handle:
+            ma_destroy_batch(self.handle)
             self.handle = 0
 
     def __del__(self):
