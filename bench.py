@@ -349,7 +349,7 @@ def bench_batching(args, M, problems, dev):
         M.ma_solve(H.handle, opts, raise_on_error=False)
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
-    B = M.Batch(hs, device=dev)
+    B = M.Batch(hs, device=dev)   # default grouping: 2 concurrently replayed groups
     B.solve(tol=args.tol, max_cycles=60, raise_on_error=False)   # warm-up: graph capture
     torch.cuda.synchronize()
     l0 = M.ma_kernel_launch_count()
