@@ -601,6 +601,16 @@ ma_status ma_set_solution(ma_hierarchy* H, const double* u_dev)
     return MA_OK;
 }
 
+static void solve_state_reset(ma_hierarchy* H, const ma_solve_opts* opts)
+{
+    H->sv.o = *opts;
+    H->sv.phase = 0;
+    H->sv.stagnant = 0;
+    H->sv.scale = 1.0;
+    H->sv.rel = 0.0;
+    std::memset(&H->sv.r, 0, sizeof H->sv.r);
+}
+
 static ma_status check_opts(const ma_solve_opts* o)
 {
     if (!(o->tol >= 0.0) || o->max_cycles < 0 || (o->norm != MA_NORM_MAX && o->norm != MA_NORM_L2) ||
@@ -623,12 +633,7 @@ ma_status ma_solve_begin(ma_hierarchy* H, const ma_solve_opts* opts)
     ma_status st = check_opts(opts);
     if (st != MA_OK) return st;
     DeviceGuard g(H->device);
-    H->sv.o = *opts;
-    H->sv.phase = 0;
-    H->sv.stagnant = 0;
-    H->sv.scale = 1.0;
-    H->sv.rel = 0.0;
-    std::memset(&H->sv.r, 0, sizeof H->sv.r);
+    solve_state_reset(H, opts);
     MA_CK(cudaMemsetAsync(H->events, 0, sizeof(unsigned long long), H->s));
     const bool mixed = H->d.precision == MA_MIXED;
     // rhs norms, the initial iterate and its residual norm as one graph.  In
@@ -852,6 +857,7 @@ struct ma_batch_group {
     ma::BatchPlan* plan = nullptr;
     cudaStream_t s = nullptr;         // group 0: the batch's stream; others: created here
     cudaStream_t cap = nullptr;       // private capture stream
+    ma::GraphSlot gs;                 // the start: FMG and the first outer iteration
     ma::GraphSlot g;                  // one outer iteration of the group
     cudaEvent_t done = nullptr;
 };
@@ -889,7 +895,8 @@ ma_status batch_describe(ma_hierarchy* const* hs, int count, std::vector<ma::Bat
         if (d.n > 1025) return fail(MA_ERR_INVALID_ARG, "batch: n = %d exceeds 1025", d.n);
         if (d.nu1 != d0.nu1 || d.nu2 != d0.nu2 || d.restrict_kind != d0.restrict_kind ||
             d.approx_restrict != d0.approx_restrict || d.coarse_sweeps != d0.coarse_sweeps ||
-            d.inner_cycles != d0.inner_cycles || H->device != hs[0]->device)
+            d.inner_cycles != d0.inner_cycles || d.coarsest_n != d0.coarsest_n || d.fmg_interp != d0.fmg_interp ||
+            H->device != hs[0]->device)
             return fail(MA_ERR_INVALID_ARG, "batch: hierarchy %d differs from hierarchy 0 in its cycle settings "
                                             "or device", b);
         ma::BatchInstance& I = (*in)[b];
@@ -902,6 +909,8 @@ ma_status batch_describe(ma_hierarchy* const* hs, int count, std::vector<ma::Bat
             V.h = A.h;
             V.u = A.u;
             V.rhs = A.rhs;
+            V.r = A.r;
+            V.w = A.w;
             V.e = A.e;
             V.e2 = A.e2;
             V.res32 = A.res32;
@@ -914,6 +923,7 @@ ma_status batch_describe(ma_hierarchy* const* hs, int count, std::vector<ma::Bat
         I.partials = H->partials;
         I.npartials = H->npartials;
         I.out2 = H->out2;
+        I.ref_out2 = H->rb + 2;
         I.events = H->events;
     }
     const ma_hier_desc& d0 = hs[0]->d;
@@ -924,6 +934,8 @@ ma_status batch_describe(ma_hierarchy* const* hs, int count, std::vector<ma::Bat
     p->coarse_sweeps = d0.coarse_sweeps;
     p->inner = d0.inner_cycles > 0 ? d0.inner_cycles : 3;
     p->tail_max = ma::corr_tail_max_n();
+    p->vtail_max = ma::vcycle_tail_max_n();
+    p->fmg_interp = d0.fmg_interp;
     return MA_OK;
 }
 
@@ -964,13 +976,16 @@ size_t batch_layout(const std::vector<ma::BatchInstance>& in, const ma::BatchPar
     return off;
 }
 
-cudaError_t group_replay(ma_batch_group& G)
+// Replays the group's start (start = true) or outer-iteration graph on its
+// stream, capturing it on first use.
+cudaError_t group_replay(ma_batch_group& G, bool start)
 {
-    if (!G.g.exec) {
+    ma::GraphSlot& gs = start ? G.gs : G.g;
+    if (!gs.exec) {
         const unsigned long long before = ma::launch_count();
         cudaError_t e = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return e;
-        const cudaError_t eb = ma::batch_plan_iteration(G.plan, G.cap);
+        const cudaError_t eb = start ? ma::batch_plan_start(G.plan, G.cap) : ma::batch_plan_iteration(G.plan, G.cap);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(G.cap, &g);
         const unsigned long long captured = ma::launch_count() - before;
@@ -979,17 +994,43 @@ cudaError_t group_replay(ma_batch_group& G)
             if (g) cudaGraphDestroy(g);
             return eb != cudaSuccess ? eb : e;
         }
-        e = cudaGraphInstantiate(&G.g.exec, g, 0);
+        e = cudaGraphInstantiate(&gs.exec, g, 0);
         if (e != cudaSuccess) {
             cudaGraphDestroy(g);
-            G.g.exec = nullptr;
+            gs.exec = nullptr;
             return e;
         }
-        G.g.graph = g;
-        G.g.launches = captured;
+        gs.graph = g;
+        gs.launches = captured;
     }
-    ma::count_launches(G.g.launches);
-    return cudaGraphLaunch(G.g.exec, G.s);
+    ma::count_launches(gs.launches);
+    return cudaGraphLaunch(gs.exec, G.s);
+}
+
+// Uploads the active flags and replays every group with an active
+// hierarchy (start or outer-iteration graphs), the groups concurrently; then
+// reads the packed norms back.  Blocks.
+ma_status batch_round(ma_batch* B, const std::vector<char>& done, bool start)
+{
+    const int count = (int)B->hs.size();
+    for (int b = 0; b < count; ++b) B->active_host[b] = done[b] ? 0 : 1;
+    MA_CK(cudaMemcpyAsync(B->active_dev, B->active_host, sizeof(int) * (size_t)count, cudaMemcpyHostToDevice, B->s));
+    MA_CK(cudaEventRecord(B->flags_ev, B->s));
+    for (ma_batch_group& G : B->grp) {
+        bool any = false;
+        for (int b : G.ids) any = any || !done[b];
+        if (!any) continue;
+        if (G.s != B->s) MA_CK(cudaStreamWaitEvent(G.s, B->flags_ev, 0));
+        MA_CK(group_replay(G, start));
+        if (G.s != B->s) {
+            MA_CK(cudaEventRecord(G.done, G.s));
+            MA_CK(cudaStreamWaitEvent(B->s, G.done, 0));
+        }
+    }
+    MA_CK(cudaMemcpyAsync(B->packed_host, B->packed_dev, 5 * sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost,
+                          B->s));
+    MA_CK(cudaStreamSynchronize(B->s));
+    return MA_OK;
 }
 
 }  // namespace
@@ -1075,46 +1116,47 @@ ma_status ma_batch_run(ma_batch* B, const ma_solve_opts* opts, ma_solve_result* 
     if (st != MA_OK) return st;
     const int count = (int)B->hs.size();
     DeviceGuard g(B->device);
-    // every hierarchy's start (FMG and the first outer iteration, with the
-    // residual norms) on its own stream, concurrently
-    for (int b = 0; b < count; ++b) {
-        std::memset(&results[b], 0, sizeof results[b]);
-        if ((st = ma_solve_begin(B->hs[b], opts)) != MA_OK) return st;
-    }
     std::vector<char> done(count, 0);
-    for (int b = 0; b < count; ++b) {
-        ma_hierarchy* H = B->hs[b];
-        MA_CK(cudaStreamWaitEvent(B->s, H->sv.ev, 0));
-        MA_CK(cudaEventSynchronize(H->sv.ev));
-        done[b] = absorb_norms(H) ? 1 : 0;
-        if (!done[b]) H->sv.phase = 2;
+    if (opts->init == MA_INIT_FMG && opts->relative != MA_REL_INITIAL) {
+        // the start of every hierarchy (the norms of f, FMG, the first outer
+        // iteration) as batched launches too
+        for (int b = 0; b < count; ++b) {
+            ma_hierarchy* H = B->hs[b];
+            std::memset(&results[b], 0, sizeof results[b]);
+            solve_state_reset(H, opts);
+            MA_CK(cudaEventRecord(H->sv.ev, H->s));   // after the caller's work on the hierarchy
+            MA_CK(cudaStreamWaitEvent(B->s, H->sv.ev, 0));
+            MA_CK(cudaMemsetAsync(H->events, 0, sizeof(unsigned long long), B->s));
+        }
+        if ((st = batch_round(B, done, true)) != MA_OK) return st;
+        for (int b = 0; b < count; ++b) {
+            ma_hierarchy* H = B->hs[b];
+            for (int q = 0; q < 5; ++q) H->host[q] = B->packed_host[5 * b + q];
+            H->sv.phase = 1;
+            done[b] = absorb_norms(H) ? 1 : 0;
+            if (!done[b]) H->sv.phase = 2;
+        }
+    } else {
+        // other starts: every hierarchy's own start graph on its own stream
+        for (int b = 0; b < count; ++b) {
+            std::memset(&results[b], 0, sizeof results[b]);
+            if ((st = ma_solve_begin(B->hs[b], opts)) != MA_OK) return st;
+        }
+        for (int b = 0; b < count; ++b) {
+            ma_hierarchy* H = B->hs[b];
+            MA_CK(cudaStreamWaitEvent(B->s, H->sv.ev, 0));
+            MA_CK(cudaEventSynchronize(H->sv.ev));
+            done[b] = absorb_norms(H) ? 1 : 0;
+            if (!done[b]) H->sv.phase = 2;
+        }
     }
     // then each outer iteration of all hierarchies still iterating: one
     // graph per group, the groups' graphs running concurrently
     for (;;) {
         int active = 0;
-        for (int b = 0; b < count; ++b) {
-            B->active_host[b] = done[b] ? 0 : 1;
-            active += B->active_host[b];
-        }
+        for (int b = 0; b < count; ++b) active += done[b] ? 0 : 1;
         if (!active) break;
-        MA_CK(cudaMemcpyAsync(B->active_dev, B->active_host, sizeof(int) * (size_t)count, cudaMemcpyHostToDevice,
-                              B->s));
-        MA_CK(cudaEventRecord(B->flags_ev, B->s));
-        for (ma_batch_group& G : B->grp) {
-            bool any = false;
-            for (int b : G.ids) any = any || !done[b];
-            if (!any) continue;
-            if (G.s != B->s) MA_CK(cudaStreamWaitEvent(G.s, B->flags_ev, 0));
-            MA_CK(group_replay(G));
-            if (G.s != B->s) {
-                MA_CK(cudaEventRecord(G.done, G.s));
-                MA_CK(cudaStreamWaitEvent(B->s, G.done, 0));
-            }
-        }
-        MA_CK(cudaMemcpyAsync(B->packed_host, B->packed_dev, 5 * sizeof(double) * (size_t)count,
-                              cudaMemcpyDeviceToHost, B->s));
-        MA_CK(cudaStreamSynchronize(B->s));
+        if ((st = batch_round(B, done, false)) != MA_OK) return st;
         for (int b = 0; b < count; ++b) {
             if (done[b]) continue;
             ma_hierarchy* H = B->hs[b];
@@ -1147,6 +1189,8 @@ ma_status ma_destroy_batch(ma_batch* B)
         }
         if (G.g.exec) cudaGraphExecDestroy(G.g.exec);
         if (G.g.graph) cudaGraphDestroy(G.g.graph);
+        if (G.gs.exec) cudaGraphExecDestroy(G.gs.exec);
+        if (G.gs.graph) cudaGraphDestroy(G.gs.graph);
         if (G.cap) cudaStreamDestroy(G.cap);
         if (G.s && G.s != B->s) cudaStreamDestroy(G.s);
         if (G.done) cudaEventDestroy(G.done);

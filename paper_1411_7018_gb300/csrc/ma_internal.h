@@ -127,8 +127,7 @@ constexpr int kBatchMaxLevels = 16;
 struct BatchLevel {
     int n;
     double h;
-    double* u;             // FP64 iterate (level 0)
-    const double* rhs;     // FP64 right-hand side (level 0)
+    double *u, *rhs, *r, *w;   // FP64 fields of the level (iterate, right-hand side, residual, restriction)
     float *e, *e2, *res32, *w32, *hi, *lo, *rhs32;   // e2: second buffer of the plane sweeps (null on the coarsest level)
     void* bstore;
 };
@@ -139,12 +138,27 @@ struct BatchInstance {
     double* partials;      // norm partials of the fine residual
     int npartials;
     double* out2;          // the hierarchy's (max, L2) residual norms
+    double* ref_out2;      // the (max, L2) norms of f, the stopping rule's reference
     unsigned long long* events;
 };
 struct BatchParams {
-    int nu1, nu2, kind, approx, coarse_sweeps, inner, tail_max;
+    int nu1, nu2, kind, approx, coarse_sweeps, inner;
+    int tail_max;          // largest level of the fused correction tail
+    int vtail_max;         // largest level of the fused FP64 tail (the FMG V-cycles)
+    int fmg_interp;        // MA_FMG_TRILINEAR | MA_FMG_CUBIC
 };
 struct BatchPlan;
+namespace batched {
+struct BLaunch;
+struct TableBuilder;
+}  // namespace batched
+// The FP64 part of the batched start (ma_kernels_f64.cu): the partials of
+// the norms of f, and the FMG pass of Algorithm 2 with its FP64 V-cycles
+// below the finest level, all hierarchies sharing the coarsest grid size so
+// that every FMG step runs on one level size; and the launcher of its ops.
+void emit_rhs_partials_f64(batched::TableBuilder& T, const BatchInstance* in, int count);
+void emit_fmg_f64(batched::TableBuilder& T, const BatchInstance* in, int count, const BatchParams& p);
+cudaError_t batch_launch_f64(const char* tables, const batched::BLaunch& L, const int* active, cudaStream_t s);
 // Bytes of the device job tables of a batch.
 size_t batch_tables_bytes(const BatchInstance* in, int count, const BatchParams& p);
 // Builds the job tables into tables_dev (batch_tables_bytes, 256-byte
@@ -153,6 +167,9 @@ size_t batch_tables_bytes(const BatchInstance* in, int count, const BatchParams&
 // where each iteration leaves (max, L2, -, -, events).
 BatchPlan* batch_plan_create(const BatchInstance* in, int count, const BatchParams& p, void* tables_dev,
                              const int* active_dev, double* packed_dev, cudaStream_t s, cudaError_t* err);
+// The start (FMG, the first outer iteration and the norms) of every hierarchy;
+// one outer iteration of every active hierarchy.
+cudaError_t batch_plan_start(const BatchPlan* plan, cudaStream_t s);
 cudaError_t batch_plan_iteration(const BatchPlan* plan, cudaStream_t s);
 unsigned long long batch_plan_launches(const BatchPlan* plan);
 void batch_plan_destroy(BatchPlan* plan);

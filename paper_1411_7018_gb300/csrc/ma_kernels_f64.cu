@@ -12,9 +12,14 @@
 // FP64 throughput is the bound of these kernels on GB300 (FP64 issues at
 // about 1/70 of the FP32 rate), so the point solve keeps its FP64 work to the
 // stencil, one determinant and one Newton correction (ma_point.cuh).
+#include <algorithm>
 #include <atomic>
+#include <cstring>
+#include <vector>
 
+#include "ma.h"
 #include "ma_internal.h"
+#include "ma_batched.cuh"
 #include "ma_point.cuh"
 #include "ma_transfer.cuh"
 #include "ma_residual.cuh"
@@ -38,12 +43,12 @@ __device__ __forceinline__ long long lin(int i, int j, int k, int n)
 // update them all in parallel.
 // ---------------------------------------------------------------------------
 template <int PI, int PJ, int PK>
-__global__ void __launch_bounds__(BX * BY) k_smooth_colour(double* u, const double* __restrict__ rhs, int n,
-                                                            double h6, unsigned long long* events)
+__device__ __forceinline__ void smooth_colour_block(double* u, const double* __restrict__ rhs, int n, double h6,
+                                                    unsigned long long* events, uint3 bid)
 {
-    const int i = (PI ? 1 : 2) + 2 * (int)(blockIdx.x * BX + threadIdx.x);
-    const int j = (PJ ? 1 : 2) + 2 * (int)(blockIdx.y * BY + threadIdx.y);
-    const int k = (PK ? 1 : 2) + 2 * (int)blockIdx.z;
+    const int i = (PI ? 1 : 2) + 2 * (int)(bid.x * BX + threadIdx.x);
+    const int j = (PJ ? 1 : 2) + 2 * (int)(bid.y * BY + threadIdx.y);
+    const int k = (PK ? 1 : 2) + 2 * (int)bid.z;
     if (i > n - 2 || j > n - 2 || k > n - 2) return;
     const long long sy = n, sz = (long long)n * n;
     const long long p = lin(i, j, k, n);
@@ -53,6 +58,13 @@ __global__ void __launch_bounds__(BX * BY) k_smooth_colour(double* u, const doub
     const double z = smallest_root(H, __dmul_rn(h6, rhs[p]), &nonconvex);   // h6 = 64 h^6: the 4 Hs scaling
     u[p] = fma(0.125, z, v0);
     if (nonconvex && events) atomicAdd(events, 1ull);
+}
+
+template <int PI, int PJ, int PK>
+__global__ void __launch_bounds__(BX * BY) k_smooth_colour(double* u, const double* __restrict__ rhs, int n,
+                                                            double h6, unsigned long long* events)
+{
+    smooth_colour_block<PI, PJ, PK>(u, rhs, n, h6, events, blockIdx);
 }
 
 // Interior indices of one parity along an axis of n points (n odd).
@@ -96,19 +108,26 @@ constexpr int KZ = 16;   // z-blocks of the reduction grids; each loops over k
 dim3 reduce_grid(int n) { return dim3((n + BX - 1) / BX, (n + BY - 1) / BY, n < KZ ? n : KZ); }
 
 template <typename T>
-__global__ void __launch_bounds__(BX * BY) k_norm_partials(const T* __restrict__ v, int n, double* partials)
+__device__ __forceinline__ void norm_partials_block(const T* __restrict__ v, int n, double* partials, uint3 bid,
+                                                    uint3 gdim)
 {
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
+    const int i = bid.x * BX + threadIdx.x;
+    const int j = bid.y * BY + threadIdx.y;
     double mx = 0.0, ss = 0.0;
-    for (int k = blockIdx.z; k < n; k += gridDim.z) {
+    for (int k = bid.z; k < n; k += gdim.z) {
         if (i > 0 && j > 0 && k > 0 && i < n - 1 && j < n - 1 && k < n - 1) {
             const double x = (double)v[lin(i, j, k, n)];
             mx = fmax(mx, fabs(x));
             ss = fma(x, x, ss);
         }
     }
-    block_reduce_store(mx, ss, partials, (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+    block_reduce_store(mx, ss, partials, (bid.z * gdim.y + bid.y) * gdim.x + bid.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX * BY) k_norm_partials(const T* __restrict__ v, int n, double* partials)
+{
+    norm_partials_block<T>(v, n, partials, blockIdx, gridDim);
 }
 
 // One block folds the partials in a fixed order: out2 = (max, sqrt(h^3 sum)).
@@ -119,12 +138,12 @@ __global__ void __launch_bounds__(resid::NF) k_norm_final(const double* __restri
 }
 
 // b_H = det(D^2_H w_H) + r_H on the interior, 0 on the shell.
-__global__ void __launch_bounds__(BX * BY) k_coarse_rhs(const double* __restrict__ wc, const double* __restrict__ rc,
-                                                        double* __restrict__ bc, int nc, double inv_H6)
+__device__ __forceinline__ void coarse_rhs_block(const double* __restrict__ wc, const double* __restrict__ rc,
+                                                 double* __restrict__ bc, int nc, double inv_H6, uint3 bid)
 {
-    const int I = blockIdx.x * BX + threadIdx.x;
-    const int J = blockIdx.y * BY + threadIdx.y;
-    const int K = blockIdx.z;
+    const int I = bid.x * BX + threadIdx.x;
+    const int J = bid.y * BY + threadIdx.y;
+    const int K = bid.z;
     if (I >= nc || J >= nc) return;
     const long long p = lin(I, J, K, nc);
     double b = 0.0;
@@ -133,6 +152,12 @@ __global__ void __launch_bounds__(BX * BY) k_coarse_rhs(const double* __restrict
         b = fma(det0(H), inv_H6, rc[p]);
     }
     bc[p] = b;
+}
+
+__global__ void __launch_bounds__(BX * BY) k_coarse_rhs(const double* __restrict__ wc, const double* __restrict__ rc,
+                                                        double* __restrict__ bc, int nc, double inv_H6)
+{
+    coarse_rhs_block(wc, rc, bc, nc, inv_H6, blockIdx);
 }
 
 // rhs := f, u := g (whole grids); counts interior points with f not finite
@@ -178,8 +203,8 @@ __device__ __forceinline__ HessS gather_hess_plain(const double* u, int p, int s
     return H;
 }
 
-__global__ void __launch_bounds__(COARSE_THREADS) k_coarsest(double* u, const double* __restrict__ rhs, int n,
-                                                             double h6, int sweeps, unsigned long long* events)
+__device__ __forceinline__ void coarsest64_body(double* u, const double* __restrict__ rhs, int n, double h6, int sweeps,
+                                                unsigned long long* events)
 {
     extern __shared__ double sm[];
     const int m = n * n * n;
@@ -232,6 +257,12 @@ __global__ void __launch_bounds__(COARSE_THREADS) k_coarsest(double* u, const do
     }
     for (int q = threadIdx.x; q < m; q += COARSE_THREADS) u[q] = su[q];
     if (events && ev) atomicAdd(events, ev);
+}
+
+__global__ void __launch_bounds__(COARSE_THREADS) k_coarsest(double* u, const double* __restrict__ rhs, int n,
+                                                             double h6, int sweeps, unsigned long long* events)
+{
+    coarsest64_body(u, rhs, n, h6, sweeps, events);
 }
 
 // ---------------------------------------------------------------------------
@@ -332,7 +363,7 @@ __device__ __forceinline__ double tail64_line(const double* uc, const double* wc
     return s * w;
 }
 
-__global__ void __launch_bounds__(T64, 1) k_vcycle_tail(Tail64Args A)
+__device__ __forceinline__ void vcycle_tail_body(const Tail64Args& A)
 {
     extern __shared__ double t64sm[];
     Tail64Smem S[4];
@@ -465,6 +496,8 @@ __global__ void __launch_bounds__(T64, 1) k_vcycle_tail(Tail64Args A)
     if (A.events && ev) atomicAdd(A.events, ev);
 }
 
+__global__ void __launch_bounds__(T64, 1) k_vcycle_tail(Tail64Args A) { vcycle_tail_body(A); }
+
 int tail64_smem_bytes(const int* ns, int nlev)
 {
     int d = 0;
@@ -473,6 +506,454 @@ int tail64_smem_bytes(const int* ns, int nlev)
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Batched FP64 launches (the start of a shared per-level batch): the norms
+// of f and the FMG pass of Algorithm 2 over several hierarchies at once.
+// With one coarsest grid size for all of them, FMG step j works on the level
+// of size 2^j (coarsest_n - 1) + 1 in every hierarchy that has it, so the
+// V-cycles of a step have the same level sizes everywhere.
+// ---------------------------------------------------------------------------
+namespace {
+
+using batched::split_block;
+using batched::TableBuilder;
+
+enum F64OpId {
+    F_SMOOTH0 = batched::kF64Ops,   // .. + 7
+    F_RESID = batched::kF64Ops + 8, F_RESTRICT, F_COARSE_RHS, F_PROLONG, F_CUBIC0, F_CUBIC1, F_CUBIC2, F_INJECT,
+    F_ZERO, F_COARSEST, F_TAIL, F_NORMPART
+};
+
+struct Smooth64Job {
+    int inst, n, gx, gy;
+    double h6;
+    double* u;
+    const double* rhs;
+    unsigned long long* events;
+};
+
+template <int C>
+struct OpSmooth64 {
+    static constexpr int NT = BX * BY, MINB = 1;
+    using Job = Smooth64Job;
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        smooth_colour_block<C & 1, (C >> 1) & 1, (C >> 2) & 1>(J.u, J.rhs, J.n, J.h6, J.events,
+                                                               split_block(q, J.gx, J.gy));
+    }
+};
+
+struct OpResid64 {
+    static constexpr int NT = resid::RX * resid::RY, MINB = 1;
+    struct Job {
+        int inst, n, kchunk, gx, gy, gz;
+        double inv_h6;
+        const double* u;
+        const double* rhs;
+        double* r;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        resid::residual_col_block<resid::NaturalF64Out>(J.u, J.rhs, resid::NaturalF64Out{J.r}, J.n, J.inv_h6, nullptr,
+                                                        J.kchunk, split_block(q, J.gx, J.gy),
+                                                        make_uint3((unsigned)J.gx, (unsigned)J.gy, (unsigned)J.gz));
+    }
+};
+
+struct OpRestrict64 {
+    static constexpr int NT = BX * BY, MINB = 1;
+    struct Job {
+        int inst, nf, nc, kind, approx, gx, gy;
+        const double* uf;
+        const double* rf;
+        double* wc;
+        double* uc;
+        double* rc;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        xfer::restrict_block<double>(J.uf, J.rf, J.nf, J.wc, J.uc, J.rc, J.nc, J.kind, J.approx,
+                                     split_block(q, J.gx, J.gy));
+    }
+};
+
+struct OpCoarseRhs64 {
+    static constexpr int NT = BX * BY, MINB = 1;
+    struct Job {
+        int inst, nc, gx, gy;
+        double inv_H6;
+        const double* wc;
+        const double* rc;
+        double* bc;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        coarse_rhs_block(J.wc, J.rc, J.bc, J.nc, J.inv_H6, split_block(q, J.gx, J.gy));
+    }
+};
+
+// add != 0: uf += I(uc - wc); add == 0: uf = I(uc) (trilinear)
+struct OpProlong64 {
+    static constexpr int NT = BX * BY, MINB = 1;
+    struct Job {
+        int inst, nc, nf, add, gx, gy;
+        const double* uc;
+        const double* wc;
+        double* uf;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        xfer::prolong_block<double>(J.uc, J.wc, J.nc, J.uf, J.nf, J.add, split_block(q, J.gx, J.gy));
+    }
+};
+
+struct CubicJob {
+    int inst, nc, ox, oy, oz, interior_only, gx, gy;
+    const double* in;
+    double* out;
+};
+
+template <int AX>
+struct OpCubic {
+    static constexpr int NT = BX * BY, MINB = 1;
+    using Job = CubicJob;
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        xfer::cubic_pass_block<AX>(J.in, J.out, J.nc, J.ox, J.oy, J.oz, J.interior_only, split_block(q, J.gx, J.gy));
+    }
+};
+
+struct OpInject64 {
+    static constexpr int NT = BX * BY, MINB = 1;
+    struct Job {
+        int inst, nf, nc, gx, gy;
+        const double* vf;
+        double* vc;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        xfer::inject_block<double>(J.vf, J.nf, J.vc, J.nc, split_block(q, J.gx, J.gy));
+    }
+};
+
+struct OpZero64 {
+    static constexpr int NT = BX * BY, MINB = 1;
+    struct Job {
+        int inst, n, gx, gy;
+        double* u;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        xfer::zero_interior_block<double>(J.u, J.n, split_block(q, J.gx, J.gy));
+    }
+};
+
+struct OpCoarsest64 {
+    static constexpr int NT = COARSE_THREADS, MINB = 1;
+    struct Job {
+        int inst, n, sweeps;
+        double h6;
+        double* u;
+        const double* rhs;
+        unsigned long long* events;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int)
+    {
+        coarsest64_body(J.u, J.rhs, J.n, J.h6, J.sweeps, J.events);
+    }
+};
+
+struct OpTail64 {
+    static constexpr int NT = T64, MINB = 1;
+    struct Job {
+        int inst;
+        Tail64Args A;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int) { vcycle_tail_body(J.A); }
+};
+
+struct OpNormPart64 {
+    static constexpr int NT = BX * BY, MINB = 1;
+    struct Job {
+        int inst, n, gx, gy, gz;
+        const double* v;
+        double* partials;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        norm_partials_block<double>(J.v, J.n, J.partials, split_block(q, J.gx, J.gy),
+                                    make_uint3((unsigned)J.gx, (unsigned)J.gy, (unsigned)J.gz));
+    }
+};
+
+inline double pow6h(double h)
+{
+    const double h2 = h * h;
+    return 64.0 * h2 * h2 * h2;
+}
+
+dim3 grid2(int n) { return dim3((n + BX - 1) / BX, (n + BY - 1) / BY, n); }
+
+// An entry of a batched FP64 V-cycle: instance (index into the array) and the
+// level its cycle starts from.
+struct VEntry {
+    int b, l0;
+};
+
+void emit_smooth64(TableBuilder& T, const BatchInstance* in, const std::vector<VEntry>& E, const std::vector<int>& lev,
+                   int nsweeps)
+{
+    for (int sw = 0; sw < nsweeps; ++sw)
+        for (int c = 0; c < 8; ++c) {
+            std::vector<Smooth64Job> jobs;
+            std::vector<int> blocks;
+            for (size_t q = 0; q < E.size(); ++q) {
+                if (lev[q] < 0) continue;
+                const BatchInstance& I = in[E[q].b];
+                const BatchLevel& F = I.lev[lev[q]];
+                const int ni = colour_count(F.n, c & 1), nj = colour_count(F.n, (c >> 1) & 1),
+                          nk = colour_count(F.n, (c >> 2) & 1);
+                if (ni <= 0 || nj <= 0 || nk <= 0) continue;
+                Smooth64Job J{I.id, F.n, (ni + BX - 1) / BX, (nj + BY - 1) / BY, pow6h(F.h), F.u, F.rhs, I.events};
+                jobs.push_back(J);
+                blocks.push_back(J.gx * J.gy * nk);
+            }
+            T.emit(F_SMOOTH0 + c, jobs, blocks, 0);
+        }
+}
+
+// Algorithm 1 from level l0 of each entry down to the coarsest grid and
+// back, with the fused FP64 tail: the launches of vcycle_from, depth by
+// depth relative to l0.
+void emit_vcycle64(TableBuilder& T, const BatchInstance* in, const std::vector<VEntry>& E, const BatchParams& p)
+{
+    if (E.empty()) return;
+    std::vector<int> lt(E.size()), fused(E.size());
+    int R = 0;
+    for (size_t q = 0; q < E.size(); ++q) {
+        const BatchInstance& I = in[E[q].b];
+        int t = I.L - 1;
+        while (t > E[q].l0 && I.lev[t - 1].n <= p.vtail_max) --t;
+        fused[q] = I.lev[t].n <= p.vtail_max;
+        lt[q] = fused[q] ? t : I.L - 1;
+        R = std::max(R, lt[q] - E[q].l0);
+    }
+    auto level_at = [&](int r) {
+        std::vector<int> lev(E.size(), -1);
+        for (size_t q = 0; q < E.size(); ++q)
+            if (r < lt[q] - E[q].l0) lev[q] = E[q].l0 + r;
+        return lev;
+    };
+    for (int r = 0; r < R; ++r) {
+        const std::vector<int> lev = level_at(r);
+        emit_smooth64(T, in, E, lev, p.nu1);
+        std::vector<OpResid64::Job> rj;
+        std::vector<OpRestrict64::Job> sj;
+        std::vector<OpCoarseRhs64::Job> cj;
+        std::vector<int> rb, sb, cb;
+        for (size_t q = 0; q < E.size(); ++q) {
+            if (lev[q] < 0) continue;
+            const BatchInstance& I = in[E[q].b];
+            const BatchLevel& F = I.lev[lev[q]];
+            const BatchLevel& C = I.lev[lev[q] + 1];
+            const dim3 g = reduce_grid(F.n);
+            const int kchunk = (F.n + (int)g.z - 1) / (int)g.z;
+            rj.push_back(OpResid64::Job{I.id, F.n, kchunk, (int)g.x, (int)g.y, (int)g.z, 1.0 / pow6h(F.h), F.u, F.rhs,
+                                        F.r});
+            rb.push_back((int)(g.x * g.y * g.z));
+            const dim3 gc = grid2(C.n);
+            sj.push_back(OpRestrict64::Job{I.id, F.n, C.n, p.kind, p.approx, (int)gc.x, (int)gc.y, F.u, F.r, C.w, C.u,
+                                           C.r});
+            sb.push_back((int)(gc.x * gc.y * gc.z));
+            cj.push_back(OpCoarseRhs64::Job{I.id, C.n, (int)gc.x, (int)gc.y, 1.0 / pow6h(C.h), C.w, C.r, C.rhs});
+            cb.push_back((int)(gc.x * gc.y * gc.z));
+        }
+        T.emit(F_RESID, rj, rb, 0);
+        T.emit(F_RESTRICT, sj, sb, 0);
+        T.emit(F_COARSE_RHS, cj, cb, 0);
+    }
+    {
+        std::vector<OpTail64::Job> tj;
+        std::vector<OpCoarsest64::Job> kj;
+        std::vector<int> tb, kb;
+        int tsmem = 0, ksmem = 0;
+        for (size_t q = 0; q < E.size(); ++q) {
+            const BatchInstance& I = in[E[q].b];
+            if (fused[q]) {
+                OpTail64::Job J;
+                std::memset(&J, 0, sizeof J);
+                J.inst = I.id;
+                Tail64Args& A = J.A;
+                A.nlev = I.L - lt[q];
+                int ns[4] = {0, 0, 0, 0};
+                for (int v = 0; v < A.nlev; ++v) {
+                    const BatchLevel& V = I.lev[lt[q] + v];
+                    ns[v] = V.n;
+                    A.lev[v].n = V.n;
+                    A.lev[v].h6 = pow6h(V.h);
+                    A.lev[v].inv_h6 = 1.0 / pow6h(V.h);
+                    A.lev[v].u = V.u;
+                    A.lev[v].rhs = V.rhs;
+                }
+                A.nu1 = p.nu1;
+                A.nu2 = p.nu2;
+                A.kind = p.kind;
+                A.approx = p.approx;
+                A.coarse_sweeps = p.coarse_sweeps;
+                A.events = I.events;
+                tsmem = std::max(tsmem, tail64_smem_bytes(ns, A.nlev));
+                tj.push_back(J);
+                tb.push_back(1);
+            } else {
+                const BatchLevel& V = I.lev[I.L - 1];
+                kj.push_back(OpCoarsest64::Job{I.id, V.n, p.coarse_sweeps, pow6h(V.h), V.u, V.rhs, I.events});
+                kb.push_back(1);
+                ksmem = std::max(ksmem, (int)(2 * sizeof(double) * (size_t)V.n * V.n * V.n));
+            }
+        }
+        T.emit(F_TAIL, tj, tb, tsmem);
+        T.emit(F_COARSEST, kj, kb, ksmem);
+    }
+    for (int r = R - 1; r >= 0; --r) {
+        const std::vector<int> lev = level_at(r);
+        std::vector<OpProlong64::Job> pj;
+        std::vector<int> pb;
+        for (size_t q = 0; q < E.size(); ++q) {
+            if (lev[q] < 0) continue;
+            const BatchInstance& I = in[E[q].b];
+            const BatchLevel& F = I.lev[lev[q]];
+            const BatchLevel& C = I.lev[lev[q] + 1];
+            const dim3 g = xfer::prolong_grid(F.n);
+            pj.push_back(OpProlong64::Job{I.id, C.n, F.n, 1, (int)g.x, (int)g.y, C.u, C.w, F.u});
+            pb.push_back((int)(g.x * g.y * g.z));
+        }
+        T.emit(F_PROLONG, pj, pb, 0);
+        emit_smooth64(T, in, E, lev, p.nu2);
+    }
+}
+
+}  // namespace
+
+void emit_rhs_partials_f64(TableBuilder& T, const BatchInstance* in, int count)
+{
+    std::vector<OpNormPart64::Job> jobs;
+    std::vector<int> blocks;
+    for (int b = 0; b < count; ++b) {
+        const BatchLevel& F = in[b].lev[0];
+        const dim3 g = reduce_grid(F.n);
+        jobs.push_back(OpNormPart64::Job{in[b].id, F.n, (int)g.x, (int)g.y, (int)g.z, F.rhs, in[b].partials});
+        blocks.push_back((int)(g.x * g.y * g.z));
+    }
+    T.emit(F_NORMPART, jobs, blocks, 0);
+}
+
+// Algorithm 2 as fmg(H, false) runs it: inject f and the data down, solve the
+// coarsest grid from a zero interior, then up the levels: interpolate and one
+// V-cycle from that level, the finest level receiving the interpolation only.
+void emit_fmg_f64(TableBuilder& T, const BatchInstance* in, int count, const BatchParams& p)
+{
+    int Lmax = 0;
+    for (int b = 0; b < count; ++b) Lmax = std::max(Lmax, in[b].L);
+    for (int d = 0; d + 1 < Lmax; ++d)
+        for (int field = 0; field < 2; ++field) {   // f, then the iterate (its shell carries g)
+            std::vector<OpInject64::Job> jobs;
+            std::vector<int> blocks;
+            for (int b = 0; b < count; ++b) {
+                if (d + 1 >= in[b].L) continue;
+                const BatchLevel& F = in[b].lev[d];
+                const BatchLevel& C = in[b].lev[d + 1];
+                const dim3 g = grid2(C.n);
+                jobs.push_back(OpInject64::Job{in[b].id, F.n, C.n, (int)g.x, (int)g.y, field ? F.u : F.rhs,
+                                               field ? C.u : C.rhs});
+                blocks.push_back((int)(g.x * g.y * g.z));
+            }
+            T.emit(F_INJECT, jobs, blocks, 0);
+        }
+    {
+        std::vector<OpZero64::Job> zj;
+        std::vector<OpCoarsest64::Job> kj;
+        std::vector<int> zb, kb;
+        int ksmem = 0;
+        for (int b = 0; b < count; ++b) {
+            const BatchLevel& V = in[b].lev[in[b].L - 1];
+            const dim3 g = grid2(V.n);
+            zj.push_back(OpZero64::Job{in[b].id, V.n, (int)g.x, (int)g.y, V.u});
+            zb.push_back((int)(g.x * g.y * g.z));
+            kj.push_back(OpCoarsest64::Job{in[b].id, V.n, p.coarse_sweeps, pow6h(V.h), V.u, V.rhs, in[b].events});
+            kb.push_back(1);
+            ksmem = std::max(ksmem, (int)(2 * sizeof(double) * (size_t)V.n * V.n * V.n));
+        }
+        T.emit(F_ZERO, zj, zb, 0);
+        T.emit(F_COARSEST, kj, kb, ksmem);
+    }
+    for (int j = 1; j < Lmax; ++j) {
+        // interpolation into level l = L - 1 - j of every hierarchy that has it
+        std::vector<OpProlong64::Job> lj;
+        std::vector<CubicJob> c0, c1, c2;
+        std::vector<int> lb, b0, b1, b2;
+        std::vector<VEntry> E;
+        for (int b = 0; b < count; ++b) {
+            const int l = in[b].L - 1 - j;
+            if (l < 0) continue;
+            const BatchLevel& F = in[b].lev[l];
+            const BatchLevel& C = in[b].lev[l + 1];
+            const int nc = C.n, nf = F.n;
+            if (p.fmg_interp == MA_FMG_CUBIC) {
+                double* t1 = F.r;                              // the fine level's r is free here
+                double* t2 = F.r + (size_t)nf * nc * nc;
+                auto cj = [&](const double* src, double* dst, int ox, int oy, int oz, int io) {
+                    return CubicJob{in[b].id, nc, ox, oy, oz, io, (ox + BX - 1) / BX, (oy + BY - 1) / BY, src, dst};
+                };
+                c0.push_back(cj(C.u, t1, nf, nc, nc, 0));
+                b0.push_back(c0.back().gx * c0.back().gy * nc);
+                c1.push_back(cj(t1, t2, nf, nf, nc, 0));
+                b1.push_back(c1.back().gx * c1.back().gy * nc);
+                c2.push_back(cj(t2, F.u, nf, nf, nf, 1));
+                b2.push_back(c2.back().gx * c2.back().gy * nf);
+            } else {
+                const dim3 g = xfer::prolong_grid(nf);
+                lj.push_back(OpProlong64::Job{in[b].id, nc, nf, 0, (int)g.x, (int)g.y, C.u, nullptr, F.u});
+                lb.push_back((int)(g.x * g.y * g.z));
+            }
+            if (l >= 1) E.push_back(VEntry{b, l});
+        }
+        T.emit(F_PROLONG, lj, lb, 0);
+        T.emit(F_CUBIC0, c0, b0, 0);
+        T.emit(F_CUBIC1, c1, b1, 0);
+        T.emit(F_CUBIC2, c2, b2, 0);
+        emit_vcycle64(T, in, E, p);
+    }
+}
+
+cudaError_t batch_launch_f64(const char* tables, const batched::BLaunch& L, const int* active, cudaStream_t s)
+{
+    using batched::launch;
+    const dim3 b2(BX, BY);
+    switch (L.op) {
+    case F_SMOOTH0 + 0: return launch<OpSmooth64<0>>(tables, L, b2, active, s);
+    case F_SMOOTH0 + 1: return launch<OpSmooth64<1>>(tables, L, b2, active, s);
+    case F_SMOOTH0 + 2: return launch<OpSmooth64<2>>(tables, L, b2, active, s);
+    case F_SMOOTH0 + 3: return launch<OpSmooth64<3>>(tables, L, b2, active, s);
+    case F_SMOOTH0 + 4: return launch<OpSmooth64<4>>(tables, L, b2, active, s);
+    case F_SMOOTH0 + 5: return launch<OpSmooth64<5>>(tables, L, b2, active, s);
+    case F_SMOOTH0 + 6: return launch<OpSmooth64<6>>(tables, L, b2, active, s);
+    case F_SMOOTH0 + 7: return launch<OpSmooth64<7>>(tables, L, b2, active, s);
+    case F_RESID: return launch<OpResid64>(tables, L, dim3(resid::RX, resid::RY), active, s);
+    case F_RESTRICT: return launch<OpRestrict64>(tables, L, b2, active, s);
+    case F_COARSE_RHS: return launch<OpCoarseRhs64>(tables, L, b2, active, s);
+    case F_PROLONG: return launch<OpProlong64>(tables, L, b2, active, s);
+    case F_CUBIC0: return launch<OpCubic<0>>(tables, L, b2, active, s);
+    case F_CUBIC1: return launch<OpCubic<1>>(tables, L, b2, active, s);
+    case F_CUBIC2: return launch<OpCubic<2>>(tables, L, b2, active, s);
+    case F_INJECT: return launch<OpInject64>(tables, L, b2, active, s);
+    case F_ZERO: return launch<OpZero64>(tables, L, b2, active, s);
+    case F_COARSEST: return launch<OpCoarsest64>(tables, L, dim3(COARSE_THREADS), active, s);
+    case F_TAIL: return launch<OpTail64>(tables, L, dim3(T64), active, s);
+    case F_NORMPART: return launch<OpNormPart64>(tables, L, b2, active, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -695,8 +1176,14 @@ cudaError_t prepare_coarsest_f64()
                                          (int)(2 * sizeof(double) * 17 * 17 * 17));
     if (e != cudaSuccess) return e;
     const int tail_ns[4] = {17, 9, 5, 3};
-    return cudaFuncSetAttribute(k_vcycle_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tail64_smem_bytes(tail_ns, 4));
+    if ((e = cudaFuncSetAttribute(k_vcycle_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tail64_smem_bytes(tail_ns, 4))) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(batched::k_batched<OpTail64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tail64_smem_bytes(tail_ns, 4))) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(batched::k_batched<OpCoarsest64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * sizeof(double) * 17 * 17 * 17));
 }
 
 }  // namespace ma

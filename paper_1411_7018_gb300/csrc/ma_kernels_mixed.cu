@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "ma_internal.h"
+#include "ma_batched.cuh"
 #include "ma_point.cuh"
 #include "ma_transfer.cuh"
 #include "ma_residual.cuh"
@@ -1499,30 +1500,9 @@ cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r_
 // ---------------------------------------------------------------------------
 namespace {
 
-__device__ __forceinline__ uint3 split_block(int q, int gx, int gy)
-{
-    const int gxy = gx * gy;
-    const int bz = q / gxy, r = q - bz * gxy;
-    const int by = r / gx, bx = r - by * gx;
-    return make_uint3((unsigned)bx, (unsigned)by, (unsigned)bz);
-}
-
-template <typename Op>
-__global__ void __launch_bounds__(Op::NT, Op::MINB)
-    k_batched(const typename Op::Job* __restrict__ jobs, const int* __restrict__ start, int njobs,
-              const int* __restrict__ active)
-{
-    const int b = (int)blockIdx.x;
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (start[mid] <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    const typename Op::Job& J = jobs[lo];
-    if (!active[J.inst]) return;   // uniform over the block
-    Op::run(J, b - start[lo]);
-}
+using batched::split_block;
+using batched::BLaunch;
+using batched::TableBuilder;
 
 struct SmoothJob {
     int inst, n, gx, gy;
@@ -1660,12 +1640,15 @@ struct OpCoarsest {
 struct OpUpdate {
     static constexpr int NT = UT, MINB = 1;
     struct Job {
-        int inst;
+        int inst, apply;
         long long m;
         double* u;
         float* e;
     };
-    static __device__ __forceinline__ void run(const Job& J, int q) { update_block(J.u, J.e, J.m, 1, (unsigned)q); }
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        update_block(J.u, J.e, J.m, J.apply, (unsigned)q);
+    }
 };
 
 struct OpSplit {
@@ -1715,6 +1698,8 @@ struct OpRes64 {
     }
 };
 
+// The norms (max, L2) into out2 and a copy into pk (2 doubles); with ev_src,
+// the root-event counter's bits into ev_dst.
 struct OpNorm {
     static constexpr int NT = resid::NF, MINB = 1;
     struct Job {
@@ -1722,19 +1707,24 @@ struct OpNorm {
         double h3;
         const double* partials;
         double* out2;
-        double* packed;   // 5 doubles of this instance
-        const unsigned long long* events;
+        double* pk;
+        const unsigned long long* ev_src;
+        double* ev_dst;
     };
     static __device__ __forceinline__ void run(const Job& J, int)
     {
         resid::norm_final_block(J.partials, J.count, J.h3, J.out2);
         if (threadIdx.x == 0) {
-            J.packed[0] = J.out2[0];
-            J.packed[1] = J.out2[1];
-            unsigned long long ev = J.events ? *J.events : 0ull;
-            double d;
-            memcpy(&d, &ev, sizeof d);
-            J.packed[4] = d;
+            if (J.pk) {
+                J.pk[0] = J.out2[0];
+                J.pk[1] = J.out2[1];
+            }
+            if (J.ev_src && J.ev_dst) {
+                const unsigned long long ev = *J.ev_src;
+                double d;
+                memcpy(&d, &ev, sizeof d);
+                *J.ev_dst = d;
+            }
         }
     }
 };
@@ -1746,57 +1736,18 @@ enum BatchOpId {
     B_PRESID16, B_PRESID32, B_PRESID64                            // residual in plane tiles
 };
 
-struct BLaunch {
-    int op, njobs, blocks, smem;
-    size_t jobs_off, starts_off;
-};
-
 dim3 batch_grid2(int n) { return dim3((n + BX - 1) / BX, (n + BY - 1) / BY, n); }
 
 }  // namespace
 
 struct BatchPlan {
-    std::vector<BLaunch> seq;
+    std::vector<BLaunch> start;   // FMG and the first outer iteration
+    std::vector<BLaunch> seq;     // one outer iteration
     char* dev = nullptr;
     const int* active = nullptr;
 };
 
 namespace {
-
-// Accumulates the job tables of a plan in host memory, each table (jobs,
-// then njobs + 1 block starts) 256-byte aligned.
-struct TableBuilder {
-    std::vector<char> buf;
-    std::vector<BLaunch> seq;
-    size_t align(size_t x) { return (x + 255) / 256 * 256; }
-    template <typename Job>
-    void emit(int op, const std::vector<Job>& jobs, const std::vector<int>& blocks, int smem)
-    {
-        if (jobs.empty()) return;
-        BLaunch L;
-        L.op = op;
-        L.njobs = (int)jobs.size();
-        L.smem = smem;
-        L.jobs_off = align(buf.size());
-        L.starts_off = align(L.jobs_off + sizeof(Job) * jobs.size());
-        buf.resize(align(L.starts_off + sizeof(int) * (jobs.size() + 1)), 0);
-        std::memcpy(buf.data() + L.jobs_off, jobs.data(), sizeof(Job) * jobs.size());
-        int* st = (int*)(buf.data() + L.starts_off);
-        int acc = 0;
-        for (size_t q = 0; q < jobs.size(); ++q) {
-            st[q] = acc;
-            acc += blocks[q];
-        }
-        st[jobs.size()] = acc;
-        L.blocks = acc;
-        if (acc > 0) seq.push_back(L);
-    }
-};
-
-struct LevelRefs {
-    const BatchLevel* lv;
-    float inv_h2, h2half;
-};
 
 int tail_start(const BatchInstance& I, int tmax)
 {
@@ -1805,7 +1756,8 @@ int tail_start(const BatchInstance& I, int tmax)
     return I.lev[lt].n <= tmax ? lt : -1;   // -1: no fused tail (coarsest solve alone)
 }
 
-void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const BatchParams& p, double* packed)
+void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const BatchParams& p, double* packed,
+                    bool start)
 {
     const auto inv_h2 = [](double h) { return (float)(1.0 / (h * h)); };
     const auto h2half = [](double h) { return (float)(0.5 * h * h); };
@@ -1899,6 +1851,7 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
                 T.emit(B_SMOOTH0 + c, jobs, blocks, 0);
             }
     };
+    auto cycles = [&]() {
     for (int cyc = 0; cyc < p.inner; ++cyc) {
         for (int d = 0; d < D; ++d) {
             smooth(d, p.nu1);
@@ -1995,14 +1948,16 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
             smooth(d, p.nu2);
         }
     }
-    // u += e, e = 0; the coarse base Hessians of the new iterate
+    };
+    // u += e (apply) and e = 0; the coarse base Hessians of the iterate
+    auto refresh = [&](int apply) {
     {
         std::vector<OpUpdate::Job> uj;
         std::vector<int> ub;
         for (int b = 0; b < count; ++b) {
             const BatchLevel& F = in[b].lev[0];
             const long long m = (long long)F.n * F.n * F.n;
-            uj.push_back(OpUpdate::Job{in[b].id, m, F.u, F.e});
+            uj.push_back(OpUpdate::Job{in[b].id, apply, m, F.u, F.e});
             ub.push_back((int)((m + UT - 1) / UT));
         }
         T.emit(B_UPDATE, uj, ub, 0);
@@ -2026,8 +1981,9 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
         T.emit(B_SPLIT, sj, sb, 0);
         T.emit(B_BASE, bj, bb, 0);
     }
+    };
     // FP64 fine residual (the next correction rhs and the fine B) and its norms
-    {
+    auto residual_norm = [&]() {
         std::vector<OpRes64::Job> rj;
         std::vector<OpNorm::Job> nj;
         std::vector<int> rb, nb;
@@ -2053,22 +2009,43 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
             J.out = CmF32Out{F.rhs32, (float*)F.bstore, (float)(0.25 / h2)};
             rj.push_back(J);
             rb.push_back((int)(g.x * g.y * g.z));
-            OpNorm::Job N{in[b].id, I.npartials, F.h * F.h * F.h, I.partials, I.out2, packed + 5 * in[b].id, I.events};
+            OpNorm::Job N{in[b].id, I.npartials, F.h * F.h * F.h, I.partials, I.out2,
+                          packed ? packed + 5 * in[b].id : nullptr, I.events,
+                          packed ? packed + 5 * in[b].id + 4 : nullptr};
             nj.push_back(N);
             nb.push_back(1);
         }
         T.emit(B_RES64, rj, rb, 0);
         T.emit(B_NORM, nj, nb, 0);
+    };
+    if (start) {
+        // Algorithm 2 as ma_solve_begin runs it in mixed precision: the
+        // reference norms of f, FMG with FP64 V-cycles below the finest
+        // level, then the finest level's first outer iteration
+        emit_rhs_partials_f64(T, in, count);
+        std::vector<OpNorm::Job> nj;
+        std::vector<int> nb;
+        for (int b = 0; b < count; ++b) {
+            const BatchInstance& I = in[b];
+            const double h = I.lev[0].h;
+            nj.push_back(OpNorm::Job{I.id, I.npartials, h * h * h, I.partials, I.ref_out2,
+                                     packed ? packed + 5 * I.id + 2 : nullptr, nullptr, nullptr});
+            nb.push_back(1);
+        }
+        T.emit(B_NORM, nj, nb, 0);
+        emit_fmg_f64(T, in, count, p);
+        refresh(0);
+        residual_norm();
     }
+    cycles();
+    refresh(1);
+    residual_norm();
 }
 
 template <typename Op>
 cudaError_t launch_batched(const BatchPlan* P, const BLaunch& L, dim3 block, cudaStream_t s)
 {
-    count_launches(1);
-    k_batched<Op><<<L.blocks, block, L.smem, s>>>((const typename Op::Job*)(P->dev + L.jobs_off),
-                                                  (const int*)(P->dev + L.starts_off), L.njobs, P->active);
-    return cudaGetLastError();
+    return batched::launch<Op>(P->dev, L, block, P->active, s);
 }
 
 }  // namespace
@@ -2076,7 +2053,8 @@ cudaError_t launch_batched(const BatchPlan* P, const BLaunch& L, dim3 block, cud
 size_t batch_tables_bytes(const BatchInstance* in, int count, const BatchParams& p)
 {
     TableBuilder T;
-    build_sequence(T, in, count, p, nullptr);
+    build_sequence(T, in, count, p, nullptr, true);
+    build_sequence(T, in, count, p, nullptr, false);
     return T.buf.size();
 }
 
@@ -2084,7 +2062,9 @@ BatchPlan* batch_plan_create(const BatchInstance* in, int count, const BatchPara
                              const int* active_dev, double* packed_dev, cudaStream_t s, cudaError_t* err)
 {
     TableBuilder T;
-    build_sequence(T, in, count, p, packed_dev);
+    build_sequence(T, in, count, p, packed_dev, true);
+    const size_t nstart = T.seq.size();
+    build_sequence(T, in, count, p, packed_dev, false);
     *err = cudaSuccess;
     if (!T.buf.empty()) {
         *err = cudaMemcpyAsync(tables_dev, T.buf.data(), T.buf.size(), cudaMemcpyHostToDevice, s);
@@ -2096,17 +2076,22 @@ BatchPlan* batch_plan_create(const BatchInstance* in, int count, const BatchPara
         *err = cudaErrorMemoryAllocation;
         return nullptr;
     }
-    P->seq = std::move(T.seq);
+    P->start.assign(T.seq.begin(), T.seq.begin() + nstart);
+    P->seq.assign(T.seq.begin() + nstart, T.seq.end());
     P->dev = (char*)tables_dev;
     P->active = active_dev;
     return P;
 }
 
-cudaError_t batch_plan_iteration(const BatchPlan* P, cudaStream_t s)
+static cudaError_t run_sequence(const BatchPlan* P, const std::vector<BLaunch>& seq, cudaStream_t s)
 {
     const dim3 b2(BX, BY);
-    for (const BLaunch& L : P->seq) {
+    for (const BLaunch& L : seq) {
         cudaError_t e;
+        if (L.op >= batched::kF64Ops) {
+            if ((e = batch_launch_f64(P->dev, L, P->active, s)) != cudaSuccess) return e;
+            continue;
+        }
         switch (L.op) {
         case B_SMOOTH0 + 0: e = launch_batched<OpSmooth<0>>(P, L, b2, s); break;
         case B_SMOOTH0 + 1: e = launch_batched<OpSmooth<1>>(P, L, b2, s); break;
@@ -2140,6 +2125,10 @@ cudaError_t batch_plan_iteration(const BatchPlan* P, cudaStream_t s)
     return cudaSuccess;
 }
 
+cudaError_t batch_plan_start(const BatchPlan* P, cudaStream_t s) { return run_sequence(P, P->start, s); }
+
+cudaError_t batch_plan_iteration(const BatchPlan* P, cudaStream_t s) { return run_sequence(P, P->seq, s); }
+
 unsigned long long batch_plan_launches(const BatchPlan* P) { return P ? P->seq.size() : 0; }
 
 void batch_plan_destroy(BatchPlan* P) { delete P; }
@@ -2147,13 +2136,13 @@ void batch_plan_destroy(BatchPlan* P) { delete P; }
 cudaError_t prepare_batched_kernels()
 {
     const int tail_ns[4] = {17, 9, 5, 3};
-    cudaError_t e = cudaFuncSetAttribute(k_batched<OpTail>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(batched::k_batched<OpTail>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          tail_smem_bytes(tail_ns, 4));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_batched<OpPlaneResid<64, 256>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(batched::k_batched<OpPlaneResid<64, 256>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              Tile<64>::SMEM);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_batched<OpCoarsest>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(batched::k_batched<OpCoarsest>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)coarsest_corr_smem(17));
 }
 

@@ -180,12 +180,12 @@ __device__ __forceinline__ int cubic_axis(int i, int nc, double w[4], int* cnt)
 // with every index in 1 .. dim-2 (the last pass, which keeps the Dirichlet
 // shell of the target).
 template <int AX>
-__global__ void __launch_bounds__(BX * BY) k_cubic_pass(const double* __restrict__ in, double* __restrict__ out,
-                                                        int nc, int ox, int oy, int oz, int interior_only)
+__device__ __forceinline__ void cubic_pass_block(const double* __restrict__ in, double* __restrict__ out, int nc,
+                                                 int ox, int oy, int oz, int interior_only, uint3 bid)
 {
-    const int x = blockIdx.x * BX + threadIdx.x;
-    const int y = blockIdx.y * BY + threadIdx.y;
-    const int z = blockIdx.z;
+    const int x = bid.x * BX + threadIdx.x;
+    const int y = bid.y * BY + threadIdx.y;
+    const int z = bid.z;
     if (x >= ox || y >= oy) return;
     if (interior_only && (x < 1 || x > ox - 2 || y < 1 || y > oy - 2 || z < 1 || z > oz - 2)) return;
     const int ix = AX == 0 ? nc : ox, iy = AX == 1 ? nc : oy;
@@ -201,24 +201,43 @@ __global__ void __launch_bounds__(BX * BY) k_cubic_pass(const double* __restrict
     out[((long long)z * oy + y) * ox + x] = s;
 }
 
-template <typename T>
-__global__ void k_inject(const T* __restrict__ vf, int nf, T* __restrict__ vc, int nc)
+template <int AX>
+__global__ void __launch_bounds__(BX * BY) k_cubic_pass(const double* __restrict__ in, double* __restrict__ out,
+                                                        int nc, int ox, int oy, int oz, int interior_only)
 {
-    const int I = blockIdx.x * BX + threadIdx.x;
-    const int J = blockIdx.y * BY + threadIdx.y;
-    const int K = blockIdx.z;
+    cubic_pass_block<AX>(in, out, nc, ox, oy, oz, interior_only, blockIdx);
+}
+
+template <typename T>
+__device__ __forceinline__ void inject_block(const T* __restrict__ vf, int nf, T* __restrict__ vc, int nc, uint3 bid)
+{
+    const int I = bid.x * BX + threadIdx.x;
+    const int J = bid.y * BY + threadIdx.y;
+    const int K = bid.z;
     if (I >= nc || J >= nc) return;
     vc[lin(I, J, K, nc)] = vf[lin(2 * I, 2 * J, 2 * K, nf)];
 }
 
 template <typename T>
-__global__ void k_zero_interior(T* u, int n)
+__global__ void k_inject(const T* __restrict__ vf, int nf, T* __restrict__ vc, int nc)
 {
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z;
+    inject_block<T>(vf, nf, vc, nc, blockIdx);
+}
+
+template <typename T>
+__device__ __forceinline__ void zero_interior_block(T* u, int n, uint3 bid)
+{
+    const int i = bid.x * BX + threadIdx.x;
+    const int j = bid.y * BY + threadIdx.y;
+    const int k = bid.z;
     if (i < 1 || j < 1 || k < 1 || i > n - 2 || j > n - 2 || k > n - 2) return;
     u[lin(i, j, k, n)] = T(0);
+}
+
+template <typename T>
+__global__ void k_zero_interior(T* u, int n)
+{
+    zero_interior_block<T>(u, n, blockIdx);
 }
 
 inline dim3 grid_of(int n) { return dim3((n + BX - 1) / BX, (n + BY - 1) / BY, n); }

@@ -35,10 +35,10 @@ def _problems(spec):
     return out
 
 
-def _solo(pr, desc_kw, tol):
+def _solo(pr, desc_kw, tol, solve_kw):
     H = M.Hierarchy(M.make_desc(pr.n, length=pr.length, precision=M.MA_MIXED, **desc_kw))
     H.set_rhs_bc(torch.from_numpy(pr.f).cuda(), torch.from_numpy(pr.initial()).cuda())
-    r = H.solve(tol=tol, max_cycles=40, raise_on_error=False)
+    r = H.solve(tol=tol, max_cycles=40, raise_on_error=False, **solve_kw)
     u = torch.empty(pr.f.shape, dtype=torch.float64, device="cuda")
     H.get_solution(u)
     torch.cuda.synchronize()
@@ -46,7 +46,7 @@ def _solo(pr, desc_kw, tol):
     return u.cpu().numpy(), r
 
 
-def _batched(prs, desc_kw, tol):
+def _batched(prs, desc_kw, tol, solve_kw):
     hs, keep = [], []
     for pr in prs:
         H = M.Hierarchy(M.make_desc(pr.n, length=pr.length, precision=M.MA_MIXED, **desc_kw),
@@ -58,7 +58,7 @@ def _batched(prs, desc_kw, tol):
         keep += [f, g]
     B = M.Batch(hs)
     c0 = M.ma_kernel_launch_count()
-    res = B.solve(tol=tol, max_cycles=40, raise_on_error=False)
+    res = B.solve(tol=tol, max_cycles=40, raise_on_error=False, **solve_kw)
     launches = M.ma_kernel_launch_count() - c0
     sols = []
     for pr, H in zip(prs, hs):
@@ -72,11 +72,12 @@ def _batched(prs, desc_kw, tol):
     return sols, res, launches
 
 
-def _check_same(prs, desc_kw, tol):
-    sols, res, launches = _batched(prs, desc_kw, tol)
+def _check_same(prs, desc_kw, tol, solve_kw=None):
+    solve_kw = solve_kw or {}
+    sols, res, launches = _batched(prs, desc_kw, tol, solve_kw)
     cycles = set()
     for pr, u, r in zip(prs, sols, res):
-        ref, rr = _solo(pr, desc_kw, tol)
+        ref, rr = _solo(pr, desc_kw, tol, solve_kw)
         assert (r.cycles, r.status, r.floor_reached) == (rr.cycles, rr.status, rr.floor_reached)
         assert r.res == rr.res and r.res0 == rr.res0
         assert r.nonconvex_root_events == rr.nonconvex_root_events
@@ -124,14 +125,25 @@ def test_batch_bitwise_with_other_cycle_settings():
     _check_same(_problems(spec), kw, 1e-9)
 
 
+@pytest.mark.parametrize("relative", [M.MA_REL_RHS, M.MA_REL_INITIAL])
+def test_batch_bitwise_in_the_paper_configuration(relative):
+    """Tricubic FMG, 3^3 coarsest grid with one sweep, the L2 stopping rule:
+    against ||f|| the start runs batched (FMG steps aligned by level size),
+    against the initial residual each hierarchy starts on its own."""
+    kw = dict(coarsest_n=3, coarse_sweeps=1, fmg_interp=M.MA_FMG_CUBIC)
+    spec = [("exp", 33), ("ex6", 65), ("sine", 17), ("cosine", 33)]
+    _check_same(_problems(spec), kw, 1e-8, dict(norm=M.MA_NORM_L2, relative=relative))
+
+
 def test_batch_rejects_mismatched_hierarchies():
     a = M.Hierarchy(M.make_desc(33, precision=M.MA_MIXED))
     b = M.Hierarchy(M.make_desc(33, precision=M.MA_MIXED, nu1=1))
     c = M.Hierarchy(M.make_desc(33, precision=M.MA_FP64))
+    d = M.Hierarchy(M.make_desc(33, precision=M.MA_MIXED, coarsest_n=5))
     try:
-        for hs in ([a.handle, b.handle], [a.handle, c.handle], [a.handle, a.handle], []):
+        for hs in ([a.handle, b.handle], [a.handle, c.handle], [a.handle, a.handle], [a.handle, d.handle], []):
             with pytest.raises(M.MAError):
                 M.ma_batch_footprint(hs)
     finally:
-        for H in (a, b, c):
+        for H in (a, b, c, d):
             H.close()
