@@ -102,7 +102,6 @@ cudaError_t launch_coarse_rhs_corr(const float* w, const void* bstore, const flo
 cudaError_t launch_restrict_level_f32(const float* ef, const float* rf, int nf, float* wc, float* ec, float* rc,
                                       int kind, int approx, cudaStream_t s);
 cudaError_t launch_prolong_add_f32(const float* ec, const float* wc, int nc, float* ef, cudaStream_t s);
-cudaError_t launch_inject_f32(const float* vf, int nf, float* vc, cudaStream_t s);
 cudaError_t launch_coarsest_corr(float* e, const void* bstore, const float* rhs_cm, int n, double h, int sweeps,
                                  unsigned long long* events, cudaStream_t s);
 cudaError_t launch_update(double* u, float* e, int n, int apply, cudaStream_t s);
@@ -171,7 +170,6 @@ BatchPlan* batch_plan_create(const BatchInstance* in, int count, const BatchPara
 // one outer iteration of every active hierarchy.
 cudaError_t batch_plan_start(const BatchPlan* plan, cudaStream_t s);
 cudaError_t batch_plan_iteration(const BatchPlan* plan, cudaStream_t s);
-unsigned long long batch_plan_launches(const BatchPlan* plan);
 void batch_plan_destroy(BatchPlan* plan);
 
 }  // namespace ma

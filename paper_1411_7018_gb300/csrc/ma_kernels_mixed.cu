@@ -1329,14 +1329,6 @@ cudaError_t launch_prolong_add_f32(const float* ec, const float* wc, int nc, flo
     return cudaGetLastError();
 }
 
-cudaError_t launch_inject_f32(const float* vf, int nf, float* vc, cudaStream_t s)
-{
-    const int nc = (nf + 1) / 2;
-    count_launches(1);
-    xfer::k_inject<float><<<grid_of(nc), dim3(BX, BY), 0, s>>>(vf, nf, vc, nc);
-    return cudaGetLastError();
-}
-
 static size_t coarsest_corr_smem(int n)
 {
     return sizeof(float) * ((size_t)n * n * n + 7 * cm_points(n));
@@ -2128,8 +2120,6 @@ static cudaError_t run_sequence(const BatchPlan* P, const std::vector<BLaunch>& 
 cudaError_t batch_plan_start(const BatchPlan* P, cudaStream_t s) { return run_sequence(P, P->start, s); }
 
 cudaError_t batch_plan_iteration(const BatchPlan* P, cudaStream_t s) { return run_sequence(P, P->seq, s); }
-
-unsigned long long batch_plan_launches(const BatchPlan* P) { return P ? P->seq.size() : 0; }
 
 void batch_plan_destroy(BatchPlan* P) { delete P; }
 
