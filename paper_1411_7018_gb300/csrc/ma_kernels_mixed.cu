@@ -333,8 +333,8 @@ __global__ void __launch_bounds__(BX * BY) k_to_cm(const float* __restrict__ nat
 // Correction smoother, one colour per launch: bc / rc point at this colour's
 // B and rhs boxes; e is in the natural layout (19-point stencil).  Idx is int
 // for grids up to 1289^3 (32-bit index arithmetic), long long above.  The
-// point solve is latency-bound, so the launch bounds ask for 10 resident
-// blocks per SM (48 registers).
+// point solve is latency-bound, so the launch bounds ask for 12 resident
+// blocks per SM (40 registers, no spills; 14 would spill).
 template <int PI, int PJ, int PK, typename Idx>
 __device__ __forceinline__ void smooth_corr_block(float* e, const float* __restrict__ bc, const float* __restrict__ rc,
                                                   int n, float inv_h2, float h2half, unsigned long long* events,
@@ -369,7 +369,7 @@ __device__ __forceinline__ void smooth_corr_block(float* e, const float* __restr
 }
 
 template <int PI, int PJ, int PK, typename Idx>
-__global__ void __launch_bounds__(BX * BY, 10) k_smooth_corr(float* e, const float* __restrict__ bc,
+__global__ void __launch_bounds__(BX * BY, 12) k_smooth_corr(float* e, const float* __restrict__ bc,
                                                               const float* __restrict__ rc, int n, float inv_h2,
                                                               float h2half, unsigned long long* events)
 {
@@ -1507,7 +1507,7 @@ struct SmoothJob {
 
 template <int C>
 struct OpSmooth {
-    static constexpr int NT = BX * BY, MINB = 10;
+    static constexpr int NT = BX * BY, MINB = 12;
     using Job = SmoothJob;
     static __device__ __forceinline__ void run(const Job& J, int q)
     {
