@@ -46,8 +46,8 @@ CORR_SMOOTH_BYTES_PER_POINT = 36
 HBM_PEAK_GBS = 6663.9    # MEASURED_PEAKS.json hbm_gbs (copy bandwidth)
 # DRAM bytes (read + write) per launch of the by-colour correction smoother at
 # 257^3, from one ncu capture of the current kernel with a warm L2
-# (--cache-control none): 103.0 MB read + 34.7 MB written.
-CORR_SMOOTH_TRAFFIC_257 = 137.7e6
+# (--cache-control none): 103.4 MB read + 34.7-35.0 MB written.
+CORR_SMOOTH_TRAFFIC_257 = 138.2e6
 
 
 def parse():

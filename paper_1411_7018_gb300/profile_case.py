@@ -7,7 +7,9 @@ Cases: ``smooth`` (FP64 smoother sweeps, 8 colour launches each), ``residual``
 sweeps of the mixed path, two k-parity launches per sweep, on a small
 correction), ``vcycle`` (whole V-cycles of
 a resident hierarchy), ``solve`` (one FMG + V-cycle solve to 1e-10), ``solve2d`` (the 2D paper-configuration solve of
-Example 1 on an n x n grid), ``smooth2d`` (2D red-black sweeps on that grid);
+Example 1 on an n x n grid), ``smooth2d`` (2D red-black sweeps on that grid),
+``batch`` (the batching workload: 64 mixed-precision instances of sizes drawn
+by seed from {33, 65, 129}^3, solved once as a shared per-level batch);
 ``--precision mixed`` runs the hierarchy cases in mixed precision.  The grid holds
 Example 4 (u = exp(|x|^2/2)) with a small seeded perturbation; fields of a
 257^3 grid are 136 MB each, larger than L2.  Prints nothing but a one-line
@@ -26,8 +28,8 @@ from . import problems
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["smooth", "residual", "smooth_corr", "vcycle", "solve", "solve2d", "smooth2d"],
-                    default="smooth")
+    ap.add_argument("--case", choices=["smooth", "residual", "smooth_corr", "vcycle", "solve", "solve2d", "smooth2d",
+                                       "batch"], default="smooth")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--reps", type=int, default=2)
@@ -42,6 +44,26 @@ def main():
             M.ma2d_smooth(u2, f2, a.n, 1.0 / (a.n - 1), 1, M.MA2D_REDBLACK, t2)
         torch.cuda.synchronize()
         print(f"profile_case {a.case} n={a.n} reps={a.reps} done")
+        return
+    if a.case == "batch":
+        rng = np.random.default_rng(2024)
+        sizes = rng.choice([33, 65, 129], size=64)
+        hs, keep = [], []
+        for b, n in enumerate(sizes):
+            f, g, _ = problems.make_on_device("cosine", int(n), seed=1000 + b, eps=(0.005, 0.02))
+            H = M.Hierarchy(M.make_desc(int(n), precision=M.MA_MIXED), stream=torch.cuda.Stream())
+            torch.cuda.synchronize()
+            H.set_rhs_bc(f, g)
+            hs.append(H)
+            keep.append((f, g))
+        B = M.Batch(hs)
+        for _ in range(a.reps):
+            B.solve(tol=1e-10, max_cycles=60, raise_on_error=False)
+        B.close()
+        for H in hs:
+            H.close()
+        torch.cuda.synchronize()
+        print(f"profile_case {a.case} reps={a.reps} done")
         return
     if a.case == "solve2d":
         from . import problems2d
