@@ -168,3 +168,40 @@ def test_orders_of_accuracy(name, order):
     e = {N: _paper2d(name, N, O2.REDBLACK)[1] for N in (256, 512, 1024)}
     for N in (512, 1024):
         assert abs(np.log2(e[N // 2] / e[N]) - order) <= 0.1
+
+
+def test_norm_inject_and_solution_restriction_closed_forms():
+    """Section 4 norms of a constant (max c, discrete L2 c (N-1) h); injection
+    takes the fine value at every other point; both restrictions of the
+    approximation reproduce linear functions (their weights sum to 1 and
+    are symmetric)."""
+    n = 17
+    h = 1.0 / (n - 1)
+    v = np.zeros((n, n))
+    v[1:-1, 1:-1] = 3.0
+    assert O2.norm(v, h, O2.NORM_MAX) == 3.0
+    assert abs(O2.norm(v, h, O2.NORM_L2) - 3.0 * (n - 2) * h) <= 1e-14
+    rng = np.random.default_rng(7)
+    r = rng.standard_normal((n, n))
+    assert np.array_equal(O2.inject(r), r[::2, ::2])
+    x = np.linspace(0.0, 1.0, n)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    lin = 0.3 + 1.7 * X - 2.1 * Y
+    for kind in (O2.FULL_WEIGHTING, O2.HALF_WEIGHTING):
+        uc = O2.restrict_solution(lin, approx=O2.APPROX_WEIGHTED, kind=kind)
+        assert np.max(np.abs(uc - lin[::2, ::2])) <= 1e-14
+
+
+def test_coarse_rhs_of_a_quadratic():
+    """Algorithm 1 step 5 in 2D: b_H = det(D^2_H w_H) + r_H.  For
+    w = a x^2 + b y^2 + c x y the centred scheme is exact, det = 4ab - c^2."""
+    n = 9
+    H = 1.0 / (n - 1)
+    x = np.linspace(0.0, 1.0, n)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    a, b, c = 0.8, 1.3, 0.4
+    w = a * X ** 2 + b * Y ** 2 + c * X * Y
+    r = np.zeros((n, n))
+    r[1:-1, 1:-1] = 0.25
+    bc = O2.coarse_rhs(w, r, H)
+    assert np.max(np.abs(bc[1:-1, 1:-1] - (4 * a * b - c * c + 0.25))) <= 1e-12

@@ -535,3 +535,43 @@ def test_half_weighting_option_converges_on_small_grid():
     info = O.solve(u, pr.f, pr.h, tol=1e-10, max_cycles=40,
                    params=O.Params(restrict_kind=O.HALF_WEIGHTING, approx_restrict=O.APPROX_INJECTION))
     assert info.res_hist[-1] <= 1e-10
+
+
+# --------------------------------------------------------------------------
+# V-cycle and FMG as wholes (Algorithms 1 and 2)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,n,coarsest,kind", [("exp", 9, 3, O.FULL_WEIGHTING), ("cosine", 9, 5, O.FULL_WEIGHTING),
+                                                  ("exp", 9, 3, O.HALF_WEIGHTING), ("exp", 17, 3, O.FULL_WEIGHTING)])
+def test_vcycle_leaves_the_discrete_solution_unchanged(name, n, coarsest, kind):
+    """FAS property of Algorithm 1: at the exact discrete solution (found by
+    an independent dense Newton solve) the fine residual is 0, the coarse
+    right-hand side is S_H(w_H), whose solution is w_H itself, and the
+    correction u_H - w_H vanishes; so a V-cycle changes nothing beyond
+    round-off.  Catches a wrong sign of the tau correction, u_H and w_H
+    taken with different operators, or a prolongation of u_H instead of
+    u_H - w_H."""
+    pr = P.make(name, n, seed=3)
+    if n <= 9:
+        u_ref = _newton_brute_force(pr)
+    else:   # the multigrid solution, itself pinned to brute force on smaller grids
+        u_ref = pr.initial()
+        info = O.solve(u_ref, pr.f, pr.h, tol=1e-13, max_cycles=80,
+                       params=O.Params(coarsest_n=coarsest, restrict_kind=kind))
+        assert info.res_hist[info.cycles] <= 1e-13
+    u = u_ref.copy()
+    O.vcycle(u, pr.f, pr.h, 1, params=O.Params(coarsest_n=coarsest, restrict_kind=kind))
+    assert np.max(np.abs(u - u_ref)) <= 1e-12 * np.max(np.abs(u_ref))
+
+
+@pytest.mark.parametrize("n", [9, 17, 33])
+def test_tricubic_fmg_reproduces_the_quadratic_exactly(n):
+    """u = |x|^2/2 with f = 1 is the discrete solution on every level
+    (the scheme is exact on quadratics); tricubic interpolation (Algorithm 2
+    step 4) reproduces it exactly, so one FMG pass returns it to round-off
+    from a zero interior.  Catches wrong cubic weights, a wrong injection of
+    f or g, or FMG steps in the wrong order."""
+    pr = P.make("quadratic", n)
+    u = pr.initial()
+    O.fmg(u, pr.f, pr.h, params=O.Params(fmg_interp=O.FMG_CUBIC))
+    assert np.max(np.abs(u - pr.u)) <= 1e-13 * np.max(np.abs(pr.u))
