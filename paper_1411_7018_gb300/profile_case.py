@@ -5,7 +5,8 @@
 Cases: ``smooth`` (FP64 smoother sweeps, 8 colour launches each), ``residual``
 (the FP64 residual kernel), ``smooth_corr`` (pairs of FP32 correction-smoother
 sweeps of the mixed path, two k-parity launches per sweep, on a small
-correction), ``vcycle`` (whole V-cycles of
+correction), ``residual_corr`` (the correction residual rhs - N(e) of the mixed
+path, in the residual tiles the tuning table picks for n, on that correction), ``vcycle`` (whole V-cycles of
 a resident hierarchy), ``solve`` (one FMG + V-cycle solve to 1e-10), ``solve2d`` (the 2D paper-configuration solve of
 Example 1 on an n x n grid), ``smooth2d`` (2D red-black sweeps on that grid),
 ``batch`` (the batching workload: 64 mixed-precision instances of sizes drawn
@@ -28,8 +29,8 @@ from . import problems
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["smooth", "residual", "smooth_corr", "vcycle", "solve", "solve2d", "smooth2d",
-                                       "batch"], default="smooth")
+    ap.add_argument("--case", choices=["smooth", "residual", "smooth_corr", "residual_corr", "vcycle", "solve",
+                                       "solve2d", "smooth2d", "batch"], default="smooth")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--reps", type=int, default=2)
@@ -89,6 +90,16 @@ def main():
         r = torch.empty_like(u)
         for _ in range(a.reps):
             M.ma_residual(u, f, r, a.n, pr.h)
+    elif a.case == "residual_corr":
+        hi = u.float()
+        lo = (u - hi.double()).float()
+        e = (1e-7 * (u - torch.from_numpy(pr.u).cuda())).float()
+        res = torch.zeros_like(hi)
+        _keep, scr, nb = M.correction_scratch(a.n)
+        rhs = (1e-6 * f).float()
+        rhs[0], rhs[-1] = 0, 0
+        for _ in range(a.reps):
+            M.ma_residual_correction(e, hi, lo, rhs, res, a.n, pr.h, scr, nb)
     elif a.case == "smooth_corr":
         hi = u.float()
         lo = (u - hi.double()).float()
