@@ -336,16 +336,19 @@ ma_status ma_residual_correction(const float *e_dev, const float *u_hi_dev, cons
  * (MA_CORR_PLANE16/32/64: colours 0-3 of all even planes, then colours 4-7 of
  * all odd planes, 2 launches, in tiles of 16, 32 or 64 points per plane edge
  * with a recomputed halo and a second e buffer); both give the same bits.  The
- * correction residual runs in plane tiles of 16, 32 or 64.  The choice is
- * kept per grid size n (odd, 3 .. 4097) for the whole process; hierarchy
- * calls take it when they first record their CUDA graphs, so set or tune
- * before the first solve. */
-enum { MA_CORR_BY_COLOUR = 0, MA_CORR_PLANE16 = 1, MA_CORR_PLANE32 = 2, MA_CORR_PLANE64 = 3 };
+ * correction residual runs in plane tiles of 16, 32 or 64, or by columns
+ * (MA_CORR_COLUMN: a warp walks 30 columns along k with the neighbour values
+ * in registers and shuffles; residual only); all give the same bits.  The
+ * choice is kept per grid size n (odd, 3 .. 4097) for the whole process;
+ * hierarchy calls take it when they first record their CUDA graphs, so set or
+ * tune before the first solve. */
+enum { MA_CORR_BY_COLOUR = 0, MA_CORR_PLANE16 = 1, MA_CORR_PLANE32 = 2, MA_CORR_PLANE64 = 3, MA_CORR_COLUMN = 4 };
 
 /* Sets the choice for grid size n (-1 restores the built-in default: plane
  * tiles of 16 up to n = 33, 32 at n = 65, by colour above; residual tiles
  * 16 / 32 / 64).  MA_ERR_INVALID_ARG if n is not odd in [3, 4097] or a choice
- * is out of range (the residual has no MA_CORR_BY_COLOUR). */
+ * is out of range (the residual has no MA_CORR_BY_COLOUR, the smoother no
+ * MA_CORR_COLUMN). */
 ma_status ma_set_corr_tuning(int n, int smooth_choice, int residual_choice);
 
 /* The choices in force for grid size n. */
@@ -371,11 +374,12 @@ ma_status ma_set_corr_tail(int max_n);
 ma_status ma_set_vcycle_tail(int max_n);
 
 /* Autotuner: times every smoother variant (reps pairs of sweeps each) and
- * every residual tile on the caller's data of one grid (the arguments of
+ * every residual variant on the caller's data of one grid (the arguments of
  * ma_smooth_correction; e is overwritten by the sweeps), records the fastest
  * of each for grid size n, and writes the mean times in microseconds per
- * sweep (us_smooth[4], indexed by MA_CORR_*) and per residual (us_residual[4],
- * entry 0 unused) when those are not null.  Blocks on the stream. */
+ * sweep (us_smooth[4], indexed by MA_CORR_*) and per residual (us_residual[5],
+ * indexed by MA_CORR_*, entry 0 unused) when those are not null.  Blocks on
+ * the stream. */
 ma_status ma_tune_corr(float *e_dev, const float *u_hi_dev, const float *u_lo_dev, const float *rhs_dev, int n,
                        double h, int reps, void *scratch_dev, size_t scratch_bytes, double *us_smooth,
                        double *us_residual, ma_stream_t stream);

@@ -1364,7 +1364,7 @@ ma_status ma_set_vcycle_tail(int max_n)
 ma_status ma_set_corr_tuning(int n, int smooth_choice, int residual_choice)
 {
     if (smooth_choice < -1 || smooth_choice > MA_CORR_PLANE64 || residual_choice < -1 ||
-        residual_choice == MA_CORR_BY_COLOUR || residual_choice > MA_CORR_PLANE64)
+        residual_choice == MA_CORR_BY_COLOUR || residual_choice > MA_CORR_COLUMN)
         return fail(MA_ERR_INVALID_ARG, "ma_set_corr_tuning: bad choice (%d, %d)", smooth_choice, residual_choice);
     if (!ma::set_corr_tuning(n, smooth_choice, residual_choice))
         return fail(MA_ERR_INVALID_ARG, "ma_set_corr_tuning: n = %d is not an odd size in [3, 4097]", n);
@@ -1395,7 +1395,7 @@ ma_status ma_tune_corr(float* e, const float* hi, const float* lo, const float* 
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     MA_CK(cudaEventCreate(&t0));
     cudaError_t ce = cudaEventCreate(&t1);
-    double ts[4] = {0, 0, 0, 0}, tr[4] = {0, 0, 0, 0};
+    double ts[4] = {0, 0, 0, 0}, tr[5] = {0, 0, 0, 0, 0};
     for (int c = MA_CORR_BY_COLOUR; c <= MA_CORR_PLANE64 && ce == cudaSuccess; ++c) {
         ce = ma::launch_smooth_corr_choice(c, e, e2, scratch, rhs_cm, n, h, 2, nullptr, s);   // warm-up
         if (ce == cudaSuccess) ce = cudaEventRecord(t0, s);
@@ -1408,7 +1408,7 @@ ma_status ma_tune_corr(float* e, const float* hi, const float* lo, const float* 
         ts[c] = 1e3 * ms / (2.0 * reps);
     }
     // the residual writes into the second buffer's interior (its shell stays 0)
-    for (int c = MA_CORR_PLANE16; c <= MA_CORR_PLANE64 && ce == cudaSuccess; ++c) {
+    for (int c = MA_CORR_PLANE16; c <= MA_CORR_COLUMN && ce == cudaSuccess; ++c) {
         ce = ma::launch_residual_corr_choice(c, e, scratch, rhs_cm, e2, n, h, s);
         if (ce == cudaSuccess) ce = cudaEventRecord(t0, s);
         for (int r = 0; r < reps && ce == cudaSuccess; ++r)
@@ -1423,13 +1423,13 @@ ma_status ma_tune_corr(float* e, const float* hi, const float* lo, const float* 
     if (t1) cudaEventDestroy(t1);
     if (ce != cudaSuccess) return fail(MA_ERR_CUDA, "ma_tune_corr: %s", cudaGetErrorString(ce));
     int bs = MA_CORR_BY_COLOUR, br = MA_CORR_PLANE16;
-    for (int c = 1; c <= MA_CORR_PLANE64; ++c) {
+    for (int c = 1; c <= MA_CORR_PLANE64; ++c)
         if (ts[c] < ts[bs]) bs = c;
+    for (int c = MA_CORR_PLANE32; c <= MA_CORR_COLUMN; ++c)
         if (tr[c] < tr[br]) br = c;
-    }
     ma::set_corr_tuning(n, bs, br);
-    for (int c = 0; c < 4; ++c) {
-        if (us_smooth) us_smooth[c] = ts[c];
+    for (int c = 0; c < 5; ++c) {
+        if (us_smooth && c < 4) us_smooth[c] = ts[c];
         if (us_residual) us_residual[c] = tr[c];
     }
     return MA_OK;

@@ -74,6 +74,7 @@ cudaError_t launch_zero_shell_f32(float* v, int n, cudaStream_t s);
 // Correction-smoother and residual variants (values of MA_CORR_* in ma.h) and
 // the per-size choice table the launchers above consult.
 constexpr int CORR_BY_COLOUR = 0, CORR_PLANE16 = 1, CORR_PLANE32 = 2, CORR_PLANE64 = 3;
+constexpr int CORR_COLUMN = 4;   // residual only
 int corr_smooth_choice(int n);
 int corr_resid_choice(int n);
 bool set_corr_tuning(int n, int smooth, int resid);   // -1: built-in default; false unless n is odd in [3, 4097]

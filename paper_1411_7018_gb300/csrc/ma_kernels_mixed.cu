@@ -660,6 +660,94 @@ __global__ void __launch_bounds__(NT, plane_min_blocks(PT, NT))
     residual_corr_plane_block<PT, NT>(e, bstore, rhs_cm, res, n, inv_h2, blockIdx);
 }
 
+// res = rhs - N(e) by columns.  A warp covers CW = 30 interior points of a
+// row (i = i0 .. i0 + 29) with a halo lane on either side and walks a run of
+// planes in k, holding the centre, north (j + 1) and south (j - 1) values of
+// planes k - 1, k, k + 1 in registers; the x-neighbours come from the
+// adjacent lanes by shuffles.  Per point that is three loads and six
+// shuffles instead of staging a halo tile, and the colour-major B and rhs of
+// a column alternate between two colour boxes, addressed incrementally.
+// Every difference to the centre is formed from the same two floats as in
+// the tile kernels, so the values are the same bits.  Grid: col_grid(n, kc),
+// blocks of 32 x 4 (four rows).
+constexpr int CW = 30;
+
+__device__ __forceinline__ void residual_corr_col_block(const float* __restrict__ e, const float* __restrict__ bstore,
+                                                        const float* __restrict__ rhs_cm, float* __restrict__ res,
+                                                        int n, float inv_h2, int kc, uint3 bid)
+{
+    const int lane = threadIdx.x;
+    const int i = (int)bid.x * CW + lane;   // i0 - 1 + lane, i0 = 1 + CW bid.x
+    const int j = 1 + (int)bid.y * 4 + (int)threadIdx.y;
+    if (j > n - 2) return;                  // the whole warp (one row per warp)
+    const int k0 = 1 + (int)bid.z * kc;
+    const int k1 = min(n - 2, k0 + kc - 1);
+    const bool inrow = i <= n - 1;
+    const bool act = lane >= 1 && lane <= CW && i <= n - 2;
+    const long long sy = n, sz = (long long)n * n;
+    const float* q = e + ((long long)j * n + (inrow ? i : 0));
+    auto ld = [&](int k, long long dj) -> float { return inrow ? __ldg(q + k * sz + dj) : 0.0f; };
+    constexpr unsigned FULL = 0xffffffffu;
+    // colour-major addressing of this column: the two colour boxes (k even, odd)
+    const int pi = i & 1, pj = j & 1;
+    const int ni = colour_count(n, pi), nj = colour_count(n, pj);
+    const int ii = (i - (pi ? 1 : 2)) >> 1, jj = (j - (pj ? 1 : 2)) >> 1;
+    const long long off0 = cm_offset(n, pi | (pj << 1)), off1 = cm_offset(n, pi | (pj << 1) | 4);
+    const long long cnt0 = (long long)ni * nj * colour_count(n, 0), cnt1 = (long long)ni * nj * colour_count(n, 1);
+    const long long plane = (long long)ni * nj, rowoff = (long long)jj * ni + ii;
+    float Cm = ld(k0 - 1, 0), Nm = ld(k0 - 1, sy), Sm = ld(k0 - 1, -sy);
+    float Cc = ld(k0, 0), Nc = ld(k0, sy), Sc = ld(k0, -sy);
+    float Cm_e = __shfl_down_sync(FULL, Cm, 1), Cm_w = __shfl_up_sync(FULL, Cm, 1);
+    float Cc_e = __shfl_down_sync(FULL, Cc, 1), Cc_w = __shfl_up_sync(FULL, Cc, 1);
+    for (int k = k0; k <= k1; ++k) {
+        const float Cp = ld(k + 1, 0), Np = ld(k + 1, sy), Sp = ld(k + 1, -sy);
+        const float Cp_e = __shfl_down_sync(FULL, Cp, 1), Cp_w = __shfl_up_sync(FULL, Cp, 1);
+        const float Nc_e = __shfl_down_sync(FULL, Nc, 1), Nc_w = __shfl_up_sync(FULL, Nc, 1);
+        const float Sc_e = __shfl_down_sync(FULL, Sc, 1), Sc_w = __shfl_up_sync(FULL, Sc, 1);
+        if (act) {
+            const float e0 = Cc;
+            const S3f K = hess_from_diff(
+                [&](int di, int dj, int dk) -> float {
+                    float v;
+                    if (dk == 0) {
+                        if (dj == 0) v = di > 0 ? Cc_e : Cc_w;
+                        else if (dj > 0) v = di > 0 ? Nc_e : (di < 0 ? Nc_w : Nc);
+                        else v = di > 0 ? Sc_e : (di < 0 ? Sc_w : Sc);
+                    } else if (dk > 0) {
+                        if (dj == 0) v = di > 0 ? Cp_e : (di < 0 ? Cp_w : Cp);
+                        else v = dj > 0 ? Np : Sp;
+                    } else {
+                        if (dj == 0) v = di > 0 ? Cm_e : (di < 0 ? Cm_w : Cm);
+                        else v = dj > 0 ? Nm : Sm;
+                    }
+                    return v - e0;
+                },
+                inv_h2);
+            const int pk = k & 1;
+            const long long w = (long long)((k - (pk ? 1 : 2)) >> 1) * plane + rowoff;
+            const long long off = pk ? off1 : off0;
+            const S3f B = load_b(bstore + 6 * off + w, pk ? cnt1 : cnt0);
+            const float rr = __ldcs(rhs_cm + off + w);
+            res[((long long)k * n + j) * n + i] = rr - delta_det(B, K);
+        }
+        Cm = Cc; Nm = Nc; Sm = Sc; Cm_e = Cc_e; Cm_w = Cc_w;
+        Cc = Cp; Nc = Np; Sc = Sp; Cc_e = Cp_e; Cc_w = Cp_w;
+    }
+}
+
+__global__ void __launch_bounds__(BX * BY, 8) k_residual_corr_col(const float* __restrict__ e,
+                                                                  const float* __restrict__ bstore,
+                                                                  const float* __restrict__ rhs_cm,
+                                                                  float* __restrict__ res, int n, float inv_h2,
+                                                                  int kc)
+{
+    residual_corr_col_block(e, bstore, rhs_cm, res, n, inv_h2, kc, blockIdx);
+}
+
+// Planes per column run, and the grid of the column residual.
+__host__ __device__ inline int col_chunk(int n) { return n >= 129 ? 16 : 8; }
+inline dim3 col_grid(int n, int kc) { return dim3((n - 2 + CW - 1) / CW, (n - 2 + 3) / 4, (n - 2 + kc - 1) / kc); }
+
 // The shell of res (faces of the cube) is 0.
 __global__ void k_zero_shell(float* v, int n)
 {
@@ -1286,6 +1374,12 @@ cudaError_t launch_residual_corr_choice(int choice, const float* e, const void* 
     switch (choice) {
     case CORR_PLANE16: return residual_t<16, 128>(e, b, rhs_cm, res, n, inv_h2, s);
     case CORR_PLANE32: return residual_t<32, 128>(e, b, rhs_cm, res, n, inv_h2, s);
+    case CORR_COLUMN: {
+        const int kc = col_chunk(n);
+        count_launches(1);
+        k_residual_corr_col<<<col_grid(n, kc), dim3(BX, BY), 0, s>>>(e, b, rhs_cm, res, n, inv_h2, kc);
+        return cudaGetLastError();
+    }
     default: return residual_t<64, 256>(e, b, rhs_cm, res, n, inv_h2, s);
     }
 }
@@ -1557,6 +1651,22 @@ struct OpPlaneResid {
     }
 };
 
+struct OpColResid {
+    static constexpr int NT = BX * BY, MINB = 8;
+    struct Job {
+        int inst, n, kc, gx, gy;
+        float inv_h2;
+        const float* e;
+        const float* b;
+        const float* rhs;
+        float* res;
+    };
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        residual_corr_col_block(J.e, J.b, J.rhs, J.res, J.n, J.inv_h2, J.kc, split_block(q, J.gx, J.gy));
+    }
+};
+
 struct OpRestrict {
     static constexpr int NT = BX * BY, MINB = 1;
     struct Job {
@@ -1725,7 +1835,8 @@ enum BatchOpId {
     B_SMOOTH0 = 0,   // .. B_SMOOTH0 + 7
     B_RESTRICT = 8, B_COARSE_RHS, B_PROLONG, B_TAIL, B_COARSEST, B_UPDATE, B_SPLIT, B_BASE, B_RES64, B_NORM,
     B_PSMOOTH16_0, B_PSMOOTH16_1, B_PSMOOTH32_0, B_PSMOOTH32_1,   // k-parity sweeps, tiles of 16 / 32, parity 0 / 1
-    B_PRESID16, B_PRESID32, B_PRESID64                            // residual in plane tiles
+    B_PRESID16, B_PRESID32, B_PRESID64,                           // residual in plane tiles
+    B_CRESID                                                      // residual by columns
 };
 
 dim3 batch_grid2(int n) { return dim3((n + BX - 1) / BX, (n + BY - 1) / BY, n); }
@@ -2110,6 +2221,7 @@ static cudaError_t run_sequence(const BatchPlan* P, const std::vector<BLaunch>& 
         case B_PRESID16: e = launch_batched<OpPlaneResid<16, 128>>(P, L, dim3(128), s); break;
         case B_PRESID32: e = launch_batched<OpPlaneResid<32, 128>>(P, L, dim3(128), s); break;
         case B_PRESID64: e = launch_batched<OpPlaneResid<64, 256>>(P, L, dim3(256), s); break;
+        case B_CRESID: e = launch_batched<OpColResid>(P, L, b2, s); break;
         default: e = cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;

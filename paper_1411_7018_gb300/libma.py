@@ -22,9 +22,9 @@ MA_NORM_MAX, MA_NORM_L2 = 0, 1
 MA_INIT_FMG, MA_INIT_ZERO, MA_INIT_KEEP = 0, 1, 2
 MA_FMG_TRILINEAR, MA_FMG_CUBIC = 0, 1
 MA_REL_NONE, MA_REL_RHS, MA_REL_INITIAL = 0, 1, 2
-MA_CORR_BY_COLOUR, MA_CORR_PLANE16, MA_CORR_PLANE32, MA_CORR_PLANE64 = 0, 1, 2, 3
+MA_CORR_BY_COLOUR, MA_CORR_PLANE16, MA_CORR_PLANE32, MA_CORR_PLANE64, MA_CORR_COLUMN = 0, 1, 2, 3, 4
 CORR_NAMES = {MA_CORR_BY_COLOUR: "by_colour", MA_CORR_PLANE16: "plane16", MA_CORR_PLANE32: "plane32",
-              MA_CORR_PLANE64: "plane64"}
+              MA_CORR_PLANE64: "plane64", MA_CORR_COLUMN: "column"}
 
 STATUS_NAMES = {0: "MA_OK", 1: "MA_ERR_INVALID_ARG", 2: "MA_ERR_OOM", 3: "MA_ERR_CUDA",
                 4: "MA_ERR_NOT_CONVERGED", 5: "MA_ERR_NONFINITE"}
@@ -375,9 +375,9 @@ def ma_get_corr_tuning(n: int):
 
 
 def ma_tune_corr(e, u_hi, u_lo, rhs, n: int, h: float, reps: int, scratch, scratch_bytes: int, stream=None):
-    """Runs the autotuner on one grid; returns (us_smooth[4], us_residual[4]) and records the fastest."""
+    """Runs the autotuner on one grid; returns (us_smooth[4], us_residual[5]) and records the fastest."""
     us = (C.c_double * 4)()
-    ur = (C.c_double * 4)()
+    ur = (C.c_double * 5)()
     _check(load().ma_tune_corr(_ptr(e), _ptr(u_hi), _ptr(u_lo), _ptr(rhs), n, h, reps, _ptr(scratch), scratch_bytes,
                                us, ur, _stream(stream)))
     return list(us), list(ur)
@@ -412,7 +412,7 @@ def autotune(sizes, reps: int = 5, device=None) -> dict:
         sm, rs = ma_get_corr_tuning(n)
         out[n] = {"smoother": CORR_NAMES[sm], "residual": CORR_NAMES[rs],
                   "us_per_sweep": {CORR_NAMES[c]: round(us[c], 2) for c in range(4)},
-                  "us_residual": {CORR_NAMES[c]: round(ur[c], 2) for c in range(1, 4)}}
+                  "us_residual": {CORR_NAMES[c]: round(ur[c], 2) for c in range(1, 5)}}
         del keep, u, hi, lo, e, rhs
     return out
 

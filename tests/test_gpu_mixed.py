@@ -141,11 +141,12 @@ def test_plane_sweeps_equal_colour_sweeps_bitwise(name, n):
         M.ma_set_corr_tuning(n, -1, -1)
 
 
-@pytest.mark.parametrize("n", [129, 71])
-@pytest.mark.parametrize("choice", [1, 2, 3])
+@pytest.mark.parametrize("n", [129, 71, 33, 257, 9])
+@pytest.mark.parametrize("choice", [1, 2, 3, 4])
 def test_residual_tiles_agree(choice, n):
-    """The three residual tile sizes compute the same values (the same
-    arithmetic per point), with a zero shell."""
+    """The three residual tile sizes and the column kernel compute the same
+    values (the same arithmetic per point), with a zero shell; sizes whose
+    interior is not a multiple of the 30-point column span or the tiles."""
     pr = P.make("cosine", n, seed=7)
     e = smooth_correction_field(n, 1e-5, 11)
     rng = np.random.default_rng(4)
