@@ -345,8 +345,8 @@ ma_status ma_residual_correction(const float *e_dev, const float *u_hi_dev, cons
 enum { MA_CORR_BY_COLOUR = 0, MA_CORR_PLANE16 = 1, MA_CORR_PLANE32 = 2, MA_CORR_PLANE64 = 3, MA_CORR_COLUMN = 4 };
 
 /* Sets the choice for grid size n (-1 restores the built-in default: plane
- * tiles of 16 up to n = 33, 32 at n = 65, by colour above; residual tiles
- * 16 / 32 / 64).  MA_ERR_INVALID_ARG if n is not odd in [3, 4097] or a choice
+ * tiles of 16 up to n = 33, 32 at n = 65, by colour above; the residual by
+ * columns).  MA_ERR_INVALID_ARG if n is not odd in [3, 4097] or a choice
  * is out of range (the residual has no MA_CORR_BY_COLOUR, the smoother no
  * MA_CORR_COLUMN). */
 ma_status ma_set_corr_tuning(int n, int smooth_choice, int residual_choice);

@@ -695,12 +695,33 @@ __device__ __forceinline__ void residual_corr_col_block(const float* __restrict_
     const long long off0 = cm_offset(n, pi | (pj << 1)), off1 = cm_offset(n, pi | (pj << 1) | 4);
     const long long cnt0 = (long long)ni * nj * colour_count(n, 0), cnt1 = (long long)ni * nj * colour_count(n, 1);
     const long long plane = (long long)ni * nj, rowoff = (long long)jj * ni + ii;
+    // B and rhs of point k (act lanes only): the loads are issued one point ahead
+    auto load_bk = [&](int k, S3f* B, float* rr) {
+        const int pk = k & 1;
+        const long long w = (long long)((k - (pk ? 1 : 2)) >> 1) * plane + rowoff;
+        const long long off = pk ? off1 : off0;
+        *B = load_b(bstore + 6 * off + w, pk ? cnt1 : cnt0);
+        *rr = __ldcs(rhs_cm + off + w);
+    };
     float Cm = ld(k0 - 1, 0), Nm = ld(k0 - 1, sy), Sm = ld(k0 - 1, -sy);
     float Cc = ld(k0, 0), Nc = ld(k0, sy), Sc = ld(k0, -sy);
+    float Cp = ld(k0 + 1, 0), Np = ld(k0 + 1, sy), Sp = ld(k0 + 1, -sy);
     float Cm_e = __shfl_down_sync(FULL, Cm, 1), Cm_w = __shfl_up_sync(FULL, Cm, 1);
     float Cc_e = __shfl_down_sync(FULL, Cc, 1), Cc_w = __shfl_up_sync(FULL, Cc, 1);
+    S3f Bk = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    float rk = 0.0f;
+    if (act) load_bk(k0, &Bk, &rk);
     for (int k = k0; k <= k1; ++k) {
-        const float Cp = ld(k + 1, 0), Np = ld(k + 1, sy), Sp = ld(k + 1, -sy);
+        // plane k + 2 and the B, rhs of point k + 1, in flight while point k is computed
+        float Cq = 0.0f, Nq = 0.0f, Sq = 0.0f;
+        S3f Bq = Bk;
+        float rq = rk;
+        if (k < k1) {
+            Cq = ld(k + 2, 0);
+            Nq = ld(k + 2, sy);
+            Sq = ld(k + 2, -sy);
+            if (act) load_bk(k + 1, &Bq, &rq);
+        }
         const float Cp_e = __shfl_down_sync(FULL, Cp, 1), Cp_w = __shfl_up_sync(FULL, Cp, 1);
         const float Nc_e = __shfl_down_sync(FULL, Nc, 1), Nc_w = __shfl_up_sync(FULL, Nc, 1);
         const float Sc_e = __shfl_down_sync(FULL, Sc, 1), Sc_w = __shfl_up_sync(FULL, Sc, 1);
@@ -723,19 +744,17 @@ __device__ __forceinline__ void residual_corr_col_block(const float* __restrict_
                     return v - e0;
                 },
                 inv_h2);
-            const int pk = k & 1;
-            const long long w = (long long)((k - (pk ? 1 : 2)) >> 1) * plane + rowoff;
-            const long long off = pk ? off1 : off0;
-            const S3f B = load_b(bstore + 6 * off + w, pk ? cnt1 : cnt0);
-            const float rr = __ldcs(rhs_cm + off + w);
-            res[((long long)k * n + j) * n + i] = rr - delta_det(B, K);
+            res[((long long)k * n + j) * n + i] = rk - delta_det(Bk, K);
         }
         Cm = Cc; Nm = Nc; Sm = Sc; Cm_e = Cc_e; Cm_w = Cc_w;
         Cc = Cp; Nc = Np; Sc = Sp; Cc_e = Cp_e; Cc_w = Cp_w;
+        Cp = Cq; Np = Nq; Sp = Sq;
+        Bk = Bq;
+        rk = rq;
     }
 }
 
-__global__ void __launch_bounds__(BX * BY, 8) k_residual_corr_col(const float* __restrict__ e,
+__global__ void __launch_bounds__(BX * BY, 6) k_residual_corr_col(const float* __restrict__ e,
                                                                   const float* __restrict__ bstore,
                                                                   const float* __restrict__ rhs_cm,
                                                                   float* __restrict__ res, int n, float inv_h2,
@@ -1265,7 +1284,7 @@ void tune_init()
 // Defaults before tuning: small grids are launch-latency bound, so the
 // plane-phase sweep (2 launches per sweep instead of 8) with small tiles.
 int default_smooth_choice(int n) { return n <= 33 ? CORR_PLANE16 : (n <= 65 ? CORR_PLANE32 : CORR_BY_COLOUR); }
-int default_resid_choice(int n) { return n <= 33 ? CORR_PLANE16 : (n <= 65 ? CORR_PLANE32 : CORR_PLANE64); }
+int default_resid_choice(int) { return CORR_COLUMN; }   // the fastest residual at 33^3 .. 513^3 on GB300
 
 template <int PT>
 dim3 tile_grid(int n, int planes)
@@ -1621,15 +1640,6 @@ struct PlaneSmoothJob {
     unsigned long long* events;
 };
 
-struct PlaneResidJob {
-    int inst, n, gx, gy;
-    float inv_h2;
-    const float* e;
-    const float* b;
-    const float* rhs;
-    float* res;
-};
-
 template <int PK, int PT, int NTH>
 struct OpPlaneSmooth {
     static constexpr int NT = NTH, MINB = plane_min_blocks(PT, NTH);
@@ -1641,18 +1651,8 @@ struct OpPlaneSmooth {
     }
 };
 
-template <int PT, int NTH>
-struct OpPlaneResid {
-    static constexpr int NT = NTH, MINB = plane_min_blocks(PT, NTH);
-    using Job = PlaneResidJob;
-    static __device__ __forceinline__ void run(const Job& J, int q)
-    {
-        residual_corr_plane_block<PT, NTH>(J.e, J.b, J.rhs, J.res, J.n, J.inv_h2, split_block(q, J.gx, J.gy));
-    }
-};
-
 struct OpColResid {
-    static constexpr int NT = BX * BY, MINB = 8;
+    static constexpr int NT = BX * BY, MINB = 6;
     struct Job {
         int inst, n, kc, gx, gy;
         float inv_h2;
@@ -1835,7 +1835,6 @@ enum BatchOpId {
     B_SMOOTH0 = 0,   // .. B_SMOOTH0 + 7
     B_RESTRICT = 8, B_COARSE_RHS, B_PROLONG, B_TAIL, B_COARSEST, B_UPDATE, B_SPLIT, B_BASE, B_RES64, B_NORM,
     B_PSMOOTH16_0, B_PSMOOTH16_1, B_PSMOOTH32_0, B_PSMOOTH32_1,   // k-parity sweeps, tiles of 16 / 32, parity 0 / 1
-    B_PRESID16, B_PRESID32, B_PRESID64,                           // residual in plane tiles
     B_CRESID                                                      // residual by columns
 };
 
@@ -1958,22 +1957,20 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
     for (int cyc = 0; cyc < p.inner; ++cyc) {
         for (int d = 0; d < D; ++d) {
             smooth(d, p.nu1);
-            std::vector<PlaneResidJob> rj;
+            std::vector<OpColResid::Job> rj;
             std::vector<OpRestrict::Job> sj;
             std::vector<OpCoarseRhs::Job> cj;
             std::vector<int> rb, sb, cb;
-            const int mx = max_n_at(d);
-            const int RT = mx >= 129 ? 64 : (mx >= 65 ? 32 : 16);   // residual tile
             for (int b = 0; b < count; ++b) {
                 if (d >= lt[b]) continue;
                 const BatchLevel& F = in[b].lev[d];
                 const BatchLevel& C = in[b].lev[d + 1];
                 const dim3 gc = batch_grid2(C.n);
-                const int t = (F.n - 2 + RT - 1) / RT;
-                PlaneResidJob r{in[b].id, F.n, t, t, inv_h2(F.h), F.e, (const float*)F.bstore, F.rhs32,
-                                                      F.res32};
-                rj.push_back(r);
-                rb.push_back(t * t * (F.n - 2));
+                const int kc = col_chunk(F.n);
+                const dim3 gr = col_grid(F.n, kc);
+                rj.push_back(OpColResid::Job{in[b].id, F.n, kc, (int)gr.x, (int)gr.y, inv_h2(F.h), F.e,
+                                             (const float*)F.bstore, F.rhs32, F.res32});
+                rb.push_back((int)(gr.x * gr.y * gr.z));
                 OpRestrict::Job s{in[b].id, F.n, C.n, p.kind, p.approx, (int)gc.x, (int)gc.y, F.e, F.res32, C.w32, C.e,
                                   C.res32};
                 sj.push_back(s);
@@ -1983,8 +1980,7 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
                 cj.push_back(q);
                 cb.push_back((int)(gc.x * gc.y * gc.z));
             }
-            T.emit(RT == 64 ? B_PRESID64 : (RT == 32 ? B_PRESID32 : B_PRESID16), rj, rb,
-                   RT == 64 ? Tile<64>::SMEM : (RT == 32 ? Tile<32>::SMEM : Tile<16>::SMEM));
+            T.emit(B_CRESID, rj, rb, 0);   // the residual by columns: the fastest form at every size
             T.emit(B_RESTRICT, sj, sb, 0);
             T.emit(B_COARSE_RHS, cj, cb, 0);
         }
@@ -2218,9 +2214,6 @@ static cudaError_t run_sequence(const BatchPlan* P, const std::vector<BLaunch>& 
         case B_PSMOOTH16_1: e = launch_batched<OpPlaneSmooth<1, 16, 128>>(P, L, dim3(128), s); break;
         case B_PSMOOTH32_0: e = launch_batched<OpPlaneSmooth<0, 32, 128>>(P, L, dim3(128), s); break;
         case B_PSMOOTH32_1: e = launch_batched<OpPlaneSmooth<1, 32, 128>>(P, L, dim3(128), s); break;
-        case B_PRESID16: e = launch_batched<OpPlaneResid<16, 128>>(P, L, dim3(128), s); break;
-        case B_PRESID32: e = launch_batched<OpPlaneResid<32, 128>>(P, L, dim3(128), s); break;
-        case B_PRESID64: e = launch_batched<OpPlaneResid<64, 256>>(P, L, dim3(256), s); break;
         case B_CRESID: e = launch_batched<OpColResid>(P, L, b2, s); break;
         default: e = cudaErrorInvalidValue;
         }
@@ -2240,9 +2233,6 @@ cudaError_t prepare_batched_kernels()
     const int tail_ns[4] = {17, 9, 5, 3};
     cudaError_t e = cudaFuncSetAttribute(batched::k_batched<OpTail>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          tail_smem_bytes(tail_ns, 4));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(batched::k_batched<OpPlaneResid<64, 256>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Tile<64>::SMEM);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(batched::k_batched<OpCoarsest>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)coarsest_corr_smem(17));
