@@ -878,6 +878,7 @@ struct ma_batch {
 namespace {
 
 std::atomic<int> g_batch_groups{2};
+std::atomic<int> g_batch_start{0};   // 1: the start as batched launches; 0: each hierarchy's own start graph
 
 ma_status batch_describe(ma_hierarchy* const* hs, int count, std::vector<ma::BatchInstance>* in,
                          ma::BatchParams* p)
@@ -1044,6 +1045,13 @@ ma_status ma_set_batch_groups(int groups)
     return MA_OK;
 }
 
+ma_status ma_set_batch_start(int batched)
+{
+    if (batched != 0 && batched != 1) return fail(MA_ERR_INVALID_ARG, "ma_set_batch_start: %d is not 0 or 1", batched);
+    g_batch_start.store(batched, std::memory_order_relaxed);
+    return MA_OK;
+}
+
 ma_status ma_batch_footprint(ma_hierarchy* const* hs, int count, size_t* bytes)
 {
     if (!bytes) return fail(MA_ERR_INVALID_ARG, "null bytes");
@@ -1117,7 +1125,8 @@ ma_status ma_batch_run(ma_batch* B, const ma_solve_opts* opts, ma_solve_result* 
     const int count = (int)B->hs.size();
     DeviceGuard g(B->device);
     std::vector<char> done(count, 0);
-    if (opts->init == MA_INIT_FMG && opts->relative != MA_REL_INITIAL) {
+    if (g_batch_start.load(std::memory_order_relaxed) && opts->init == MA_INIT_FMG &&
+        opts->relative != MA_REL_INITIAL) {
         // the start of every hierarchy (the norms of f, FMG, the first outer
         // iteration) as batched launches too
         for (int b = 0; b < count; ++b) {

@@ -69,6 +69,7 @@ _SIGS = {
     "ma_batch_run": [_vp, C.POINTER(ma_solve_opts), C.POINTER(ma_solve_result)],
     "ma_destroy_batch": [_vp],
     "ma_set_batch_groups": [C.c_int],
+    "ma_set_batch_start": [C.c_int],
     "ma_residual_norm": [_vp, C.c_int, C.POINTER(C.c_double)],
     "ma_get_solution": [_vp, _vp],
     "ma_set_solution": [_vp, _vp],
@@ -247,6 +248,10 @@ def ma_destroy_batch(batch: int) -> None:
 
 def ma_set_batch_groups(groups: int) -> None:
     _check(load().ma_set_batch_groups(int(groups)))
+
+
+def ma_set_batch_start(batched: bool) -> None:
+    _check(load().ma_set_batch_start(1 if batched else 0))
 
 
 def ma_residual_norm(hier: int, norm: int = MA_NORM_MAX) -> float:

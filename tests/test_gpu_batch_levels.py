@@ -94,6 +94,17 @@ def test_uneven_batch_is_bitwise_the_solo_solves():
     assert len(cycles) > 1
 
 
+def test_batch_bitwise_with_the_batched_start():
+    """The start (norms of f, FMG, first outer iteration) as batched launches
+    too: FMG step j on one level size across the hierarchies."""
+    spec = [("cosine", 33), ("exp", 65), ("quadratic", 17), ("exp", 129)]
+    try:
+        M.ma_set_batch_start(True)
+        _check_same(_problems(spec), {}, 1e-10)
+    finally:
+        M.ma_set_batch_start(False)
+
+
 @pytest.mark.parametrize("groups", [1, 3])
 def test_batch_bitwise_for_any_grouping(groups):
     spec = [("cosine", 33), ("exp", 65), ("cosine", 17), ("quadratic", 33), ("exp", 33)]
@@ -127,12 +138,17 @@ def test_batch_bitwise_with_other_cycle_settings():
 
 @pytest.mark.parametrize("relative", [M.MA_REL_RHS, M.MA_REL_INITIAL])
 def test_batch_bitwise_in_the_paper_configuration(relative):
-    """Tricubic FMG, 3^3 coarsest grid with one sweep, the L2 stopping rule:
-    against ||f|| the start runs batched (FMG steps aligned by level size),
-    against the initial residual each hierarchy starts on its own."""
+    """Tricubic FMG, 3^3 coarsest grid with one sweep, the L2 stopping rule,
+    with the batched start: against ||f|| the start runs batched (FMG steps
+    aligned by level size), against the initial residual each hierarchy
+    starts on its own."""
     kw = dict(coarsest_n=3, coarse_sweeps=1, fmg_interp=M.MA_FMG_CUBIC)
     spec = [("exp", 33), ("ex6", 65), ("sine", 17), ("cosine", 33)]
-    _check_same(_problems(spec), kw, 1e-8, dict(norm=M.MA_NORM_L2, relative=relative))
+    try:
+        M.ma_set_batch_start(True)
+        _check_same(_problems(spec), kw, 1e-8, dict(norm=M.MA_NORM_L2, relative=relative))
+    finally:
+        M.ma_set_batch_start(False)
 
 
 def test_batch_rejects_mismatched_hierarchies():
