@@ -64,3 +64,39 @@ def test_step_calls_reject_bad_arguments_before_any_launch():
     assert lib.ma_residual(C.c_void_p(256), C.c_void_p(256), C.c_void_p(256), 32, 0.1, None) == M.MA_ERR_INVALID_ARG
     assert lib.ma_coarsest_solve(C.c_void_p(256), C.c_void_p(256), 33, 0.1, 0, None, None) == M.MA_ERR_INVALID_ARG
     assert M.ma_norm_scratch_bytes(33) > 0
+
+
+def test_host_only_settings_validate_their_arguments():
+    """The process-wide switches of the fused tails, the batches and the
+    correction tuning table check their values without touching a GPU."""
+    for fn, bad in ((M.ma_set_corr_tail, (2, 4, 7, 33, -1)), (M.ma_set_vcycle_tail, (2, 6, 65, -3)),
+                    (M.ma_set_batch_groups, (0, 17, -1))):
+        for v in bad:
+            with pytest.raises(M.MAError) as ei:
+                fn(v)
+            assert ei.value.status == M.MA_ERR_INVALID_ARG
+    # the C entry point of the start switch takes 0 or 1 only (the binding maps a bool)
+    assert M.load().ma_set_batch_start(2) == M.MA_ERR_INVALID_ARG
+    M.ma_set_batch_start(False)
+    for v in (0, 3, 5, 9, 17, True):
+        M.ma_set_corr_tail(v)
+        M.ma_set_vcycle_tail(v)
+    M.ma_set_corr_tail(True)
+    M.ma_set_vcycle_tail(True)
+    for g in (1, 16, 2):
+        M.ma_set_batch_groups(g)
+    with pytest.raises(M.MAError):
+        M.ma_set_corr_tuning(34, 1, 1)          # n must be odd
+    with pytest.raises(M.MAError):
+        M.ma_set_corr_tuning(33, 5, 1)          # no smoother variant 5
+    with pytest.raises(M.MAError):
+        M.ma_set_corr_tuning(33, 1, M.MA_CORR_BY_COLOUR)   # the residual has no by-colour form
+    M.ma_set_corr_tuning(33, M.MA_CORR_PLANE32, M.MA_CORR_COLUMN)
+    assert M.ma_get_corr_tuning(33) == (M.MA_CORR_PLANE32, M.MA_CORR_COLUMN)
+    M.ma_set_corr_tuning(33, -1, -1)
+
+
+def test_batch_footprint_rejects_an_empty_batch():
+    with pytest.raises(M.MAError) as ei:
+        M.ma_batch_footprint([])
+    assert ei.value.status == M.MA_ERR_INVALID_ARG
