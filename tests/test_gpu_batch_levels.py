@@ -163,3 +163,15 @@ def test_batch_rejects_mismatched_hierarchies():
     finally:
         for H in (a, b, c, d):
             H.close()
+
+
+def test_batch_with_single_level_and_deep_hierarchies():
+    """A 3^3 hierarchy (one unknown: its whole cycle is the coarsest solve in
+    the fused tail) and a 5^3 one batched with deeper ones."""
+    spec = [("exp", 3), ("cosine", 5), ("exp", 9), ("cosine", 33)]
+    for start in (False, True):
+        try:
+            M.ma_set_batch_start(start)
+            _check_same(_problems(spec), {}, 1e-10)
+        finally:
+            M.ma_set_batch_start(False)

@@ -344,3 +344,24 @@ def test_not_converged_status():
     r = H.solve(tol=1e-14, max_cycles=2, raise_on_error=False)
     assert r.status == M.MA_ERR_NOT_CONVERGED and r.cycles == 2
     H.close()
+
+
+@pytest.mark.parametrize("precision", [M.MA_FP64, M.MA_MIXED, M.MA_FP32])
+@pytest.mark.parametrize("n", [3, 5])
+def test_single_level_hierarchy_solves(n, precision):
+    """n = coarsest_n: the hierarchy is its coarsest grid, FMG is the coarsest
+    solve and every cycle is one.  FP64 and mixed reach the oracle's discrete
+    solution; FP32 reaches it to FP32 round-off."""
+    pr = P.make("exp", n)
+    H = M.Hierarchy(M.make_desc(n, coarsest_n=n, precision=precision))
+    H.set_rhs_bc(dev(pr.f), dev(pr.initial()))
+    r = H.solve(tol=1e-11 if precision != M.MA_FP32 else 1e-5, max_cycles=40, raise_on_error=False)
+    u = torch.empty_like(dev(pr.f))
+    H.get_solution(u)
+    got = host(u)
+    H.close()
+    assert r.status == M.MA_OK or (r.status == M.MA_ERR_NOT_CONVERGED and r.floor_reached)
+    ref = pr.initial()
+    O.solve(ref, pr.f, pr.h, tol=1e-13, max_cycles=60, params=O.Params(coarsest_n=n))
+    bound = 1e-10 if precision != M.MA_FP32 else 1e-6
+    assert np.max(np.abs(got - ref)) <= bound * np.max(np.abs(ref))
