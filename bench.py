@@ -437,7 +437,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
-    # autotune the correction smoother and residual tiles for every grid size
+    # autotune the correction smoother and residual variants for every grid size
     # the workloads use (before any hierarchy records its graphs)
     tune_sizes = set(M.level_sizes(args.n)) | set(M.level_sizes(129)) | set(M.level_sizes(257)) | {513}
     tuning = M.autotune(sorted(tune_sizes), reps=5, device=dev)

@@ -898,7 +898,7 @@ __global__ void __launch_bounds__(CT) k_coarsest_corr(float* e, const float* __r
 // there down to the coarsest grid and back,
 // with e, w, the residual, B and rhs of those levels in shared memory.  Each
 // step does the per-point arithmetic of its separate kernel -- the sweeps of
-// k_smooth_corr, the residual of k_residual_corr_plane, the restriction of
+// k_smooth_corr, the residual of the plane and column kernels, the restriction of
 // xfer::k_restrict, the right-hand side of k_coarse_rhs_corr, the coarsest
 // solve of k_coarsest_corr, the prolongation of xfer::k_prolong -- so the
 // result is the same bits; it replaces the ~25-40 launches of these latency-
@@ -1262,7 +1262,8 @@ namespace {
 
 // ---- choice of smoother and residual kernels per level size ----------------
 // Tuning table: per grid size n (odd, 3 .. 4097), the correction-smoother
-// variant (CORR_BY_COLOUR or a plane tile) and the residual tile, set by the
+// variant (CORR_BY_COLOUR or a plane tile) and the residual variant (a plane
+// tile or CORR_COLUMN), set by the
 // autotuner (ma_tune_corr) or by hand; -1 = the built-in default.
 constexpr int kTuneMaxN = 4097;
 std::atomic<int> g_smooth_choice[kTuneMaxN + 1];

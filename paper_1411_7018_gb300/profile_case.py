@@ -6,7 +6,7 @@ Cases: ``smooth`` (FP64 smoother sweeps, 8 colour launches each), ``residual``
 (the FP64 residual kernel), ``smooth_corr`` (pairs of FP32 correction-smoother
 sweeps of the mixed path, two k-parity launches per sweep, on a small
 correction), ``residual_corr`` (the correction residual rhs - N(e) of the mixed
-path, in the residual tiles the tuning table picks for n, on that correction), ``vcycle`` (whole V-cycles of
+path, in the residual variant the tuning table picks for n, on that correction), ``vcycle`` (whole V-cycles of
 a resident hierarchy), ``solve`` (one FMG + V-cycle solve to 1e-10), ``solve2d`` (the 2D paper-configuration solve of
 Example 1 on an n x n grid), ``smooth2d`` (2D red-black sweeps on that grid),
 ``batch`` (the batching workload: 64 mixed-precision instances of sizes drawn
