@@ -43,7 +43,7 @@
 
 #define AT(u, n, i, j, k) ((u)[(((size_t)(k)) * (size_t)(n) + (size_t)(j)) * (size_t)(n) + (size_t)(i)])
 
-enum { ORC_COLOUR8 = 0, ORC_LEXICOGRAPHIC = 1, ORC_COLOUR8_REVERSED = 2 };
+enum { ORC_COLOUR8 = 0, ORC_LEXICOGRAPHIC = 1, ORC_COLOUR8_REVERSED = 2, ORC_COLOUR8_PAIRS = 3 };
 enum { ORC_HALF_WEIGHTING = 0, ORC_FULL_WEIGHTING = 1 };
 enum { ORC_NORM_MAX = 0, ORC_NORM_L2 = 1 };
 enum { ORC_APPROX_INJECTION = 0, ORC_APPROX_WEIGHTED = 1 };
@@ -230,6 +230,8 @@ static int first_interior(int parity) { return parity ? 1 : 2; }
  * least one index parity), so the points of one colour are independent and
  * may be updated in any order.  ORC_COLOUR8_REVERSED visits each colour's
  * points in the opposite order (same result by that independence).
+ * ORC_COLOUR8_PAIRS visits the colours in the order 0, 7, 1, 6, 2, 5, 3, 4
+ * (each colour followed by the one that differs in all three parities).
  * ORC_LEXICOGRAPHIC is the paper's own ordering.  rhs is f on the finest
  * level and b_H on coarse levels.  Returns the number of point updates whose
  * right-hand side was <= 0. */
@@ -246,7 +248,9 @@ long orc_gs_sweep(double *u, const double *rhs, int n, double h, int ordering)
                 }
         return events;
     }
-    for (int c = 0; c < 8; ++c) {
+    static const int pair_order[8] = {0, 7, 1, 6, 2, 5, 3, 4};
+    for (int q = 0; q < 8; ++q) {
+        const int c = (ordering == ORC_COLOUR8_PAIRS) ? pair_order[q] : q;
         const int pi = c & 1, pj = (c >> 1) & 1, pk = (c >> 2) & 1;
         const int i0 = first_interior(pi), j0 = first_interior(pj), k0 = first_interior(pk);
         const int nk = (n - 2 >= k0) ? (n - 2 - k0) / 2 + 1 : 0;

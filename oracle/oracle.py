@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-COLOUR8, LEXICOGRAPHIC, COLOUR8_REVERSED = 0, 1, 2
+COLOUR8, LEXICOGRAPHIC, COLOUR8_REVERSED, COLOUR8_PAIRS = 0, 1, 2, 3
 HALF_WEIGHTING, FULL_WEIGHTING = 0, 1
 NORM_MAX, NORM_L2 = 0, 1
 APPROX_INJECTION, APPROX_WEIGHTED = 0, 1

@@ -315,6 +315,52 @@ def test_colour_points_are_independent():
     assert np.max(np.abs(c - a)) > 0
 
 
+def _python_colour_sweep(u, f, h, order):
+    """One sweep visiting the colours c = (i&1)|(j&1)<<1|(k&1)<<2 in `order`,
+    written with plain loops: the neighbour sums a, b, c, r, s, t of
+    Eq. (MA3Dcubic) taken from the grid here, the point update the pinned
+    smallest-root routine."""
+    n = u.shape[0]
+    for c in order:
+        for k in range(1, n - 1):
+            for j in range(1, n - 1):
+                for i in range(1, n - 1):
+                    if (i & 1) | (j & 1) << 1 | (k & 1) << 2 != c:
+                        continue
+                    q = [u[k, j, i + 1] + u[k, j, i - 1],
+                         u[k, j + 1, i] + u[k, j - 1, i],
+                         u[k + 1, j, i] + u[k - 1, j, i],
+                         0.25 * (u[k, j + 1, i + 1] + u[k, j - 1, i - 1] - u[k, j + 1, i - 1] - u[k, j - 1, i + 1]),
+                         0.25 * (u[k + 1, j, i + 1] + u[k - 1, j, i - 1] - u[k + 1, j, i - 1] - u[k - 1, j, i + 1]),
+                         0.25 * (u[k + 1, j + 1, i] + u[k - 1, j - 1, i] - u[k - 1, j + 1, i] - u[k + 1, j - 1, i])]
+                    u[k, j, i] = O.point_update(q, u[k, j, i], h, f[k, j, i])
+
+
+def test_colour_pair_ordering_is_the_stated_colour_sequence():
+    """COLOUR8_PAIRS visits the colours 0, 7, 1, 6, 2, 5, 3, 4: a plain-loop
+    sweep in that order gives the same grid (a wrong order table or a
+    skipped colour fails), the order matters (it differs from ascending), and
+    each pair (c, c^7) may be swept either way round, since no stencil
+    neighbour of a colour-c point has colour c^7."""
+    pr = P.make("exp", 9)
+    rng = np.random.default_rng(5)
+    u0 = np.ascontiguousarray(pr.u + 2e-2 * rng.normal(size=pr.u.shape) * (pr.initial() == 0))
+    a = u0.copy()
+    O.gs_sweep(a, pr.f, pr.h, O.COLOUR8_PAIRS)
+    b = u0.copy()
+    _python_colour_sweep(b, pr.f, pr.h, [0, 7, 1, 6, 2, 5, 3, 4])
+    assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
+    c = u0.copy()
+    _python_colour_sweep(c, pr.f, pr.h, [7, 0, 6, 1, 5, 2, 4, 3])
+    assert np.max(np.abs(c - b)) <= 1e-13 * np.max(np.abs(b))
+    d = u0.copy()
+    O.gs_sweep(d, pr.f, pr.h, O.COLOUR8)
+    e = u0.copy()
+    _python_colour_sweep(e, pr.f, pr.h, range(8))
+    assert np.max(np.abs(d - e)) <= 1e-13 * np.max(np.abs(e))
+    assert np.max(np.abs(a - d)) > 1e-8 * np.max(np.abs(d))
+
+
 # --------------------------------------------------------------------------
 # The discrete solution: brute force, theorems, printed errors
 # --------------------------------------------------------------------------
