@@ -44,10 +44,12 @@ FP64_PEAK_GOPS = 629.0   # 2 FP64 ops/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 
 # once per sweep for the stencils, counted at its own update).
 CORR_SMOOTH_BYTES_PER_POINT = 36
 HBM_PEAK_GBS = 6663.9    # MEASURED_PEAKS.json hbm_gbs (copy bandwidth)
-# DRAM bytes (read + write) per launch of the by-colour correction smoother at
-# 257^3, from one ncu capture of the current kernel with a warm L2
-# (--cache-control none): 103.4 MB read + 34.7-35.0 MB written.
-CORR_SMOOTH_TRAFFIC_257 = 138.2e6
+# DRAM bytes (read + write) per launch of the correction smoother at 257^3,
+# from one ncu capture of the current kernels with a warm L2 (--cache-control
+# none), keyed by the variant (MA_CORR_BY_COLOUR = 0: one colour, 103.4 MB read
+# + 34.7-35.0 MB written; MA_CORR_PAIRS = 5: two colours, 167.3-169.4 MB read +
+# 42.4-43.1 MB written).
+CORR_SMOOTH_TRAFFIC_257 = {0: 138.2e6, 5: 211.1e6}
 
 
 def parse():
@@ -111,7 +113,8 @@ class ClockSampler:
 
 
 def oracle_sample(pr, tol, problem_cycles=None):
-    """Time the CPU oracle on the benchmark grid: FMG + one V-cycle + residual,
+    """Time the CPU oracle on the benchmark grid: FMG (tricubic, as the GPU
+    solve) + one V-cycle + residual,
     extrapolated to a full solve with the oracle's own cycle count (measured on
     the same problem at 65^3; V-cycle counts are mesh-independent)."""
     import numpy as np
@@ -120,10 +123,10 @@ def oracle_sample(pr, tol, problem_cycles=None):
         from paper_1411_7018_gb300 import problems
         small = problems.make(pr.name, 65)
         u = small.initial()
-        problem_cycles = O.solve(u, small.f, small.h, tol=tol).cycles
+        problem_cycles = O.solve(u, small.f, small.h, tol=tol, params=O.Params(fmg_interp=O.FMG_CUBIC)).cycles
     u = pr.initial()
     t0 = time.perf_counter()
-    O.fmg(u, pr.f, pr.h)
+    O.fmg(u, pr.f, pr.h, params=O.Params(fmg_interp=O.FMG_CUBIC))
     t1 = time.perf_counter()
     O.vcycle(u, pr.f, pr.h, 1)
     r = O.residual(u, pr.f, pr.h)
@@ -138,11 +141,11 @@ def oracle_sample(pr, tol, problem_cycles=None):
 
 def workload_config(args, world: int = 1) -> dict:
     """The benchmark's workload description, shared by both arms."""
-    return {"workload": f"Example 4 exp(|x|^2/2) {args.n}^3, FMG + FAS V(2,2), 8-colour nonlinear GS, "
+    return {"workload": f"Example 4 exp(|x|^2/2) {args.n}^3, FMG (tricubic) + FAS V(2,2), 8-colour nonlinear GS, "
                         f"tol {args.tol:g} relative max-norm residual (FP64)",
             "n": args.n, "tol": args.tol,
             "precision": "mixed: FP32 correction V-cycles x3 per FP64 fine residual and update",
-            "restrict": "full weighting", "parallelism": f"replicas x{world}",
+            "restrict": "full weighting", "fmg_interpolation": "tricubic", "parallelism": f"replicas x{world}",
             "l2": "working set larger than L2 (no flush needed)"}
 
 
@@ -513,12 +516,14 @@ def main():
     b1.record(stream)
     torch.cuda.synchronize()
     # the variant in force at this size: by colour (8 launches per sweep, an
-    # eighth of the points each) or by k parity (2 launches, half the points)
+    # eighth of the points each), colour pairs (4 launches, a quarter each) or
+    # by k parity (2 launches, half the points)
     corr_choice = M.ma_get_corr_tuning(n)[0]
-    corr_launches = 8 if corr_choice == M.MA_CORR_BY_COLOUR else 2
-    corr_kernel = ("k_smooth_corr (FP32 correction smoother, one colour phase)" if corr_launches == 8 else
-                   f"k_smooth_corr_plane (FP32 correction smoother, {M.CORR_NAMES[corr_choice]}, one k-parity "
-                   f"phase: four colours)")
+    corr_launches = {M.MA_CORR_BY_COLOUR: 8, M.MA_CORR_PAIRS: 4}.get(corr_choice, 2)
+    corr_kernel = {8: "k_smooth_corr (FP32 correction smoother, one colour phase)",
+                   4: "k_smooth_corr_pair (FP32 correction smoother, colours c and c^7 in one launch)"}.get(
+        corr_launches, f"k_smooth_corr_plane (FP32 correction smoother, {M.CORR_NAMES[corr_choice]}, one k-parity "
+                       f"phase: four colours)")
     corr_launch_ms = (e0.elapsed_time(e1) - b0.elapsed_time(b1)) / (corr_launches * sweeps)
     corr_gbs = CORR_SMOOTH_BYTES_PER_POINT * ((n - 2) ** 3 / corr_launches) / (corr_launch_ms / 1e3) / 1e9
     pts_launch = (n - 2) ** 3 / 8.0
@@ -598,8 +603,9 @@ def main():
             "roofline": {"bound": "hbm", "kernel": corr_kernel,
                          "achieved": corr_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                          "frac": corr_gbs / HBM_PEAK_GBS,
-                         "traffic": CORR_SMOOTH_TRAFFIC_257 if (n == 257 and corr_launches == 8) else None,
-                         "traffic_note": "ncu dram bytes per launch, warm L2; algorithmic 36 B x (n-2)^3/8 = 74 MB",
+                         "traffic": CORR_SMOOTH_TRAFFIC_257.get(corr_choice) if n == 257 else None,
+                         "traffic_note": (f"ncu dram bytes per launch, warm L2; algorithmic 36 B x (n-2)^3/"
+                                          f"{corr_launches} = {36 * (n - 2) ** 3 / corr_launches / 1e6:.0f} MB"),
                          "launch_ms": corr_launch_ms, "bytes_per_point": CORR_SMOOTH_BYTES_PER_POINT,
                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
             "roofline_fp64_smoother": {"bound": "alu", "kernel": "k_smooth_colour (FP64 smoother, one colour phase)",

@@ -335,6 +335,14 @@ ma_status ma_smooth_correction(float *e_dev, const float *u_hi_dev, const float 
                                double h, int nsweeps, void *scratch_dev, size_t scratch_bytes,
                                unsigned long long *events_dev, ma_stream_t stream);
 
+/* One colour phase of that sweep: the points of colour
+ * c = (i&1) | (j&1)<<1 | (k&1)<<2 (0 <= c < 8) only, in place; the eight
+ * phases in ascending c are one sweep.  Same arguments otherwise;
+ * MA_ERR_INVALID_ARG for a colour outside 0..7. */
+ma_status ma_smooth_correction_colour(float *e_dev, const float *u_hi_dev, const float *u_lo_dev,
+                                      const float *rhs_dev, int n, double h, int colour, void *scratch_dev,
+                                      size_t scratch_bytes, unsigned long long *events_dev, ma_stream_t stream);
+
 /* res = rhs - N(e) on the interior, 0 on the shell (same B store; same
  * scratch rules as ma_smooth_correction). */
 ma_status ma_residual_correction(const float *e_dev, const float *u_hi_dev, const float *u_lo_dev,
@@ -342,24 +350,36 @@ ma_status ma_residual_correction(const float *e_dev, const float *u_hi_dev, cons
                                  size_t scratch_bytes, ma_stream_t stream);
 
 /* ---- kernel choice for the correction cycle (tile shapes, colour blocking) --
- * No counterpart in the paper.  A correction sweep runs either colour by
- * colour (MA_CORR_BY_COLOUR: 8 launches in place) or by k parity
- * (MA_CORR_PLANE16/32/64: colours 0-3 of all even planes, then colours 4-7 of
- * all odd planes, 2 launches, in tiles of 16, 32 or 64 points per plane edge
- * with a recomputed halo and a second e buffer); both give the same bits.  The
+ * No counterpart in the paper.  A correction sweep visits the colours in
+ * ascending order, either colour by colour (MA_CORR_BY_COLOUR: 8 launches in
+ * place) or by k parity (MA_CORR_PLANE16/32/64: colours 0-3 of all even
+ * planes, then colours 4-7 of all odd planes, 2 launches, in tiles of 16, 32
+ * or 64 points per plane edge with a recomputed halo and a second e buffer),
+ * which give the same bits; or in colour pairs (MA_CORR_PAIRS: colours c and
+ * c^7, which share no stencil, in one launch, 4 launches in place), which is
+ * the sequential sweep in the colour order 0, 7, 1, 6, 2, 5, 3, 4: another
+ * 8-colour Gauss-Seidel sweep, other bits.  The
  * correction residual runs in plane tiles of 16, 32 or 64, or by columns
  * (MA_CORR_COLUMN: a warp walks 30 columns along k with the neighbour values
  * in registers and shuffles; residual only); all give the same bits.  The
  * choice is kept per grid size n (odd, 3 .. 4097) for the whole process;
  * hierarchy calls take it when they first record their CUDA graphs, so set or
  * tune before the first solve. */
-enum { MA_CORR_BY_COLOUR = 0, MA_CORR_PLANE16 = 1, MA_CORR_PLANE32 = 2, MA_CORR_PLANE64 = 3, MA_CORR_COLUMN = 4 };
+enum {
+    MA_CORR_BY_COLOUR = 0,
+    MA_CORR_PLANE16 = 1,
+    MA_CORR_PLANE32 = 2,
+    MA_CORR_PLANE64 = 3,
+    MA_CORR_COLUMN = 4,
+    MA_CORR_PAIRS = 5
+};
 
 /* Sets the choice for grid size n (-1 restores the built-in default: plane
- * tiles of 16 up to n = 33, 32 at n = 65, by colour above; the residual by
- * columns).  MA_ERR_INVALID_ARG if n is not odd in [3, 4097] or a choice
- * is out of range (the residual has no MA_CORR_BY_COLOUR, the smoother no
- * MA_CORR_COLUMN). */
+ * tiles of 16 up to n = 33, colour pairs above; the residual by columns).
+ * The shared per-level batch (ma_create_batch) sweeps each grid with the
+ * colour order of its size's choice, as a solo solve does.  MA_ERR_INVALID_ARG if n is not odd in [3, 4097] or a choice
+ * is out of range (the residual has no MA_CORR_BY_COLOUR or MA_CORR_PAIRS,
+ * the smoother no MA_CORR_COLUMN). */
 ma_status ma_set_corr_tuning(int n, int smooth_choice, int residual_choice);
 
 /* The choices in force for grid size n. */
@@ -388,8 +408,9 @@ ma_status ma_set_vcycle_tail(int max_n);
  * every residual variant on the caller's data of one grid (the arguments of
  * ma_smooth_correction; e is overwritten by the sweeps), records the fastest
  * of each for grid size n, and writes the mean times in microseconds per
- * sweep (us_smooth[4], indexed by MA_CORR_*) and per residual (us_residual[5],
- * indexed by MA_CORR_*, entry 0 unused) when those are not null.  Blocks on
+ * sweep (us_smooth[6], indexed by MA_CORR_*, entry 4 unused) and per residual
+ * (us_residual[5], indexed by MA_CORR_*, entry 0 unused) when those are not
+ * null.  Blocks on
  * the stream. */
 ma_status ma_tune_corr(float *e_dev, const float *u_hi_dev, const float *u_lo_dev, const float *rhs_dev, int n,
                        double h, int reps, void *scratch_dev, size_t scratch_bytes, double *us_smooth,

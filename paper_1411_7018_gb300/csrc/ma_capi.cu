@@ -1344,6 +1344,20 @@ ma_status ma_smooth_correction(float* e, const float* hi, const float* lo, const
     return MA_OK;
 }
 
+ma_status ma_smooth_correction_colour(float* e, const float* hi, const float* lo, const float* rhs, int n, double h,
+                                      int colour, void* scratch, size_t scratch_bytes, unsigned long long* events,
+                                      ma_stream_t stream)
+{
+    if (!e || !scratch || !hi || !lo || !rhs || !valid_step_grid(n) || !(h > 0.0) || colour < 0 || colour > 7)
+        return fail(MA_ERR_INVALID_ARG, "ma_smooth_correction_colour: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    float* rhs_cm = nullptr;
+    ma_status st = corr_setup(hi, lo, rhs, n, h, scratch, scratch_bytes, s, &rhs_cm);
+    if (st != MA_OK) return st;
+    MA_CK(ma::launch_smooth_corr_colour(colour, e, scratch, rhs_cm, n, h, events, s));
+    return MA_OK;
+}
+
 ma_status ma_residual_correction(const float* e, const float* hi, const float* lo, const float* rhs, float* res,
                                  int n, double h, void* scratch, size_t scratch_bytes, ma_stream_t stream)
 {
@@ -1372,8 +1386,8 @@ ma_status ma_set_vcycle_tail(int max_n)
 
 ma_status ma_set_corr_tuning(int n, int smooth_choice, int residual_choice)
 {
-    if (smooth_choice < -1 || smooth_choice > MA_CORR_PLANE64 || residual_choice < -1 ||
-        residual_choice == MA_CORR_BY_COLOUR || residual_choice > MA_CORR_COLUMN)
+    if (smooth_choice < -1 || smooth_choice == MA_CORR_COLUMN || smooth_choice > MA_CORR_PAIRS ||
+        residual_choice < -1 || residual_choice == MA_CORR_BY_COLOUR || residual_choice > MA_CORR_COLUMN)
         return fail(MA_ERR_INVALID_ARG, "ma_set_corr_tuning: bad choice (%d, %d)", smooth_choice, residual_choice);
     if (!ma::set_corr_tuning(n, smooth_choice, residual_choice))
         return fail(MA_ERR_INVALID_ARG, "ma_set_corr_tuning: n = %d is not an odd size in [3, 4097]", n);
@@ -1404,8 +1418,9 @@ ma_status ma_tune_corr(float* e, const float* hi, const float* lo, const float* 
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     MA_CK(cudaEventCreate(&t0));
     cudaError_t ce = cudaEventCreate(&t1);
-    double ts[4] = {0, 0, 0, 0}, tr[5] = {0, 0, 0, 0, 0};
-    for (int c = MA_CORR_BY_COLOUR; c <= MA_CORR_PLANE64 && ce == cudaSuccess; ++c) {
+    double ts[6] = {0, 0, 0, 0, 0, 0}, tr[5] = {0, 0, 0, 0, 0};
+    for (int c = MA_CORR_BY_COLOUR; c <= MA_CORR_PAIRS && ce == cudaSuccess; ++c) {
+        if (c == MA_CORR_COLUMN) continue;
         ce = ma::launch_smooth_corr_choice(c, e, e2, scratch, rhs_cm, n, h, 2, nullptr, s);   // warm-up
         if (ce == cudaSuccess) ce = cudaEventRecord(t0, s);
         for (int r = 0; r < reps && ce == cudaSuccess; ++r)
@@ -1432,14 +1447,14 @@ ma_status ma_tune_corr(float* e, const float* hi, const float* lo, const float* 
     if (t1) cudaEventDestroy(t1);
     if (ce != cudaSuccess) return fail(MA_ERR_CUDA, "ma_tune_corr: %s", cudaGetErrorString(ce));
     int bs = MA_CORR_BY_COLOUR, br = MA_CORR_PLANE16;
-    for (int c = 1; c <= MA_CORR_PLANE64; ++c)
-        if (ts[c] < ts[bs]) bs = c;
+    for (int c = 1; c <= MA_CORR_PAIRS; ++c)
+        if (c != MA_CORR_COLUMN && ts[c] < ts[bs]) bs = c;
     for (int c = MA_CORR_PLANE32; c <= MA_CORR_COLUMN; ++c)
         if (tr[c] < tr[br]) br = c;
     ma::set_corr_tuning(n, bs, br);
-    for (int c = 0; c < 5; ++c) {
-        if (us_smooth && c < 4) us_smooth[c] = ts[c];
-        if (us_residual) us_residual[c] = tr[c];
+    for (int c = 0; c < 6; ++c) {
+        if (us_smooth) us_smooth[c] = ts[c];
+        if (us_residual && c < 5) us_residual[c] = tr[c];
     }
     return MA_OK;
 }

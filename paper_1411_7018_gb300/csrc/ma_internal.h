@@ -75,9 +75,13 @@ cudaError_t launch_zero_shell_f32(float* v, int n, cudaStream_t s);
 // the per-size choice table the launchers above consult.
 constexpr int CORR_BY_COLOUR = 0, CORR_PLANE16 = 1, CORR_PLANE32 = 2, CORR_PLANE64 = 3;
 constexpr int CORR_COLUMN = 4;   // residual only
+constexpr int CORR_PAIRS = 5;    // smoother only: colours c and c^7 per launch
 int corr_smooth_choice(int n);
 int corr_resid_choice(int n);
 bool set_corr_tuning(int n, int smooth, int resid);   // -1: built-in default; false unless n is odd in [3, 4097]
+// One colour phase (colour 0..7) of the by-colour correction sweep, in place.
+cudaError_t launch_smooth_corr_colour(int colour, float* e, const void* bstore, const float* rhs_cm, int n, double h,
+                                      unsigned long long* events, cudaStream_t s);
 cudaError_t launch_smooth_corr_choice(int choice, float* e, float* e2, const void* bstore, const float* rhs_cm, int n,
                                       double h, int nsweeps, unsigned long long* events, cudaStream_t s);
 // One correction V-cycle over the levels with n <= corr_tail_max_n() (the

@@ -395,6 +395,52 @@ cudaError_t launch_colour_corr(float* e, const float* bstore, const float* rhs_c
     return cudaGetLastError();
 }
 
+// Colours C and C^7 in one launch.  The 19-point stencil of a colour-C
+// point holds every colour but C^7 (the corners are not in it), so the
+// updates of the two colours are independent, and one launch performs the
+// sequential sweep of colour C followed by colour C^7.  Blocks with z below
+// nk0 sweep colour C, the rest colour C^7; x and y cover the larger of the
+// two colour boxes.
+template <int C, typename Idx>
+__global__ void __launch_bounds__(BX * BY, 12) k_smooth_corr_pair(float* e, const float* __restrict__ b0,
+                                                                   const float* __restrict__ r0,
+                                                                   const float* __restrict__ b1,
+                                                                   const float* __restrict__ r1, int n, float inv_h2,
+                                                                   float h2half, unsigned long long* events, int nk0)
+{
+    constexpr int D = C ^ 7;
+    uint3 bid = blockIdx;
+    if ((int)bid.z < nk0) {
+        smooth_corr_block<C & 1, (C >> 1) & 1, (C >> 2) & 1, Idx>(e, b0, r0, n, inv_h2, h2half, events, bid);
+    } else {
+        bid.z -= nk0;
+        smooth_corr_block<D & 1, (D >> 1) & 1, (D >> 2) & 1, Idx>(e, b1, r1, n, inv_h2, h2half, events, bid);
+    }
+}
+
+template <int C>
+cudaError_t launch_colour_corr_pair(float* e, const float* bstore, const float* rhs_cm, int n, float inv_h2,
+                                    float h2half, unsigned long long* ev, cudaStream_t s)
+{
+    constexpr int D = C ^ 7;
+    const int nk0 = colour_count(n, (C >> 2) & 1), nk1 = colour_count(n, (D >> 2) & 1);
+    const int ni = colour_count(n, 1), nj = colour_count(n, 1);   // the larger box edge
+    if (ni <= 0 || nk0 + nk1 <= 0) return cudaSuccess;
+    if (colour_count(n, 0) <= 0)   // n = 3: colour 7 alone
+        return C == 0 ? launch_colour_corr<7>(e, bstore, rhs_cm, n, inv_h2, h2half, ev, s) : cudaSuccess;
+    dim3 grid((ni + BX - 1) / BX, (nj + BY - 1) / BY, nk0 + nk1);
+    const long long o0 = cm_offset(n, C), o1 = cm_offset(n, D);
+    count_launches(1);
+    if (n <= 1289)
+        k_smooth_corr_pair<C, int><<<grid, dim3(BX, BY), 0, s>>>(e, bstore + 6 * o0, rhs_cm + o0, bstore + 6 * o1,
+                                                                  rhs_cm + o1, n, inv_h2, h2half, ev, nk0);
+    else
+        k_smooth_corr_pair<C, long long><<<grid, dim3(BX, BY), 0, s>>>(e, bstore + 6 * o0, rhs_cm + o0,
+                                                                        bstore + 6 * o1, rhs_cm + o1, n, inv_h2,
+                                                                        h2half, ev, nk0);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Plane-phase correction sweep.  Colours 0-3 lie on even planes k and colours
 // 4-7 on odd planes, and every neighbour of a point in planes k +- 1 has the
@@ -1243,6 +1289,18 @@ cudaError_t launch_to_cm(const float* nat, float* cm, int n, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// One sweep in colour pairs (4 launches): the colour order 0, 7, 1, 6, 2, 5,
+// 3, 4.
+static cudaError_t colour_sweep_corr_pair(float* e, const float* b, const float* rhs_cm, int n, float inv_h2,
+                                          float h2half, unsigned long long* events, cudaStream_t s)
+{
+    cudaError_t e_;
+    if ((e_ = launch_colour_corr_pair<0>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+    if ((e_ = launch_colour_corr_pair<1>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+    if ((e_ = launch_colour_corr_pair<2>(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+    return launch_colour_corr_pair<3>(e, b, rhs_cm, n, inv_h2, h2half, events, s);
+}
+
 // One sweep of in-place per-colour launches (8 launches).
 static cudaError_t colour_sweep_corr(float* e, const float* b, const float* rhs_cm, int n, float inv_h2, float h2half,
                                      unsigned long long* events, cudaStream_t s)
@@ -1284,7 +1342,7 @@ void tune_init()
 
 // Defaults before tuning: small grids are launch-latency bound, so the
 // plane-phase sweep (2 launches per sweep instead of 8) with small tiles.
-int default_smooth_choice(int n) { return n <= 33 ? CORR_PLANE16 : (n <= 65 ? CORR_PLANE32 : CORR_BY_COLOUR); }
+int default_smooth_choice(int n) { return n <= 33 ? CORR_PLANE16 : CORR_PAIRS; }
 int default_resid_choice(int) { return CORR_COLUMN; }   // the fastest residual at 33^3 .. 513^3 on GB300
 
 template <int PT>
@@ -1369,6 +1427,11 @@ cudaError_t launch_smooth_corr_choice(int choice, float* e, float* e2, const voi
     int sw = 0;
     cudaError_t e_;
     // pairs of sweeps e -> e2 -> e by k parity; the rest in place by colour
+    if (choice == CORR_PAIRS) {
+        for (; sw < nsweeps; ++sw)
+            if ((e_ = colour_sweep_corr_pair(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
+        return cudaSuccess;
+    }
     if (choice != CORR_BY_COLOUR && e2 && n >= 5)
         for (; sw + 2 <= nsweeps; sw += 2) {
             if ((e_ = plane_sweep(choice, e, e2, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
@@ -1377,6 +1440,25 @@ cudaError_t launch_smooth_corr_choice(int choice, float* e, float* e2, const voi
     for (; sw < nsweeps; ++sw)
         if ((e_ = colour_sweep_corr(e, b, rhs_cm, n, inv_h2, h2half, events, s)) != cudaSuccess) return e_;
     return cudaSuccess;
+}
+
+cudaError_t launch_smooth_corr_colour(int colour, float* e, const void* bstore, const float* rhs_cm, int n, double h,
+                                      unsigned long long* events, cudaStream_t s)
+{
+    const float inv_h2 = (float)(1.0 / (h * h));
+    const float h2half = (float)(0.5 * h * h);
+    const float* b = (const float*)bstore;
+    switch (colour) {
+    case 0: return launch_colour_corr<0>(e, b, rhs_cm, n, inv_h2, h2half, events, s);
+    case 1: return launch_colour_corr<1>(e, b, rhs_cm, n, inv_h2, h2half, events, s);
+    case 2: return launch_colour_corr<2>(e, b, rhs_cm, n, inv_h2, h2half, events, s);
+    case 3: return launch_colour_corr<3>(e, b, rhs_cm, n, inv_h2, h2half, events, s);
+    case 4: return launch_colour_corr<4>(e, b, rhs_cm, n, inv_h2, h2half, events, s);
+    case 5: return launch_colour_corr<5>(e, b, rhs_cm, n, inv_h2, h2half, events, s);
+    case 6: return launch_colour_corr<6>(e, b, rhs_cm, n, inv_h2, h2half, events, s);
+    case 7: return launch_colour_corr<7>(e, b, rhs_cm, n, inv_h2, h2half, events, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_smooth_corr(float* e, float* e2, const void* bstore, const float* rhs_cm, int n, double h,
@@ -1630,6 +1712,38 @@ struct OpSmooth {
     }
 };
 
+// Colours C and C^7 of one grid (the colour-pair sweep): blocks with z below
+// nk0 sweep colour C from the boxes b0 / r0, the rest colour C^7 from b1 / r1.
+struct PairSmoothJob {
+    int inst, n, gx, gy, nk0;
+    float inv_h2, h2half;
+    float* e;
+    const float* b0;
+    const float* r0;
+    const float* b1;
+    const float* r1;
+    unsigned long long* events;
+};
+
+template <int C>
+struct OpSmoothPair {
+    static constexpr int NT = BX * BY, MINB = 12;
+    using Job = PairSmoothJob;
+    static __device__ __forceinline__ void run(const Job& J, int q)
+    {
+        constexpr int D = C ^ 7;
+        uint3 bid = split_block(q, J.gx, J.gy);
+        if ((int)bid.z < J.nk0) {
+            smooth_corr_block<C & 1, (C >> 1) & 1, (C >> 2) & 1, int>(J.e, J.b0, J.r0, J.n, J.inv_h2, J.h2half,
+                                                                      J.events, bid);
+        } else {
+            bid.z -= J.nk0;
+            smooth_corr_block<D & 1, (D >> 1) & 1, (D >> 2) & 1, int>(J.e, J.b1, J.r1, J.n, J.inv_h2, J.h2half,
+                                                                      J.events, bid);
+        }
+    }
+};
+
 struct PlaneSmoothJob {
     int inst, n, gx, gy;
     float inv_h2, h2half;
@@ -1836,7 +1950,8 @@ enum BatchOpId {
     B_SMOOTH0 = 0,   // .. B_SMOOTH0 + 7
     B_RESTRICT = 8, B_COARSE_RHS, B_PROLONG, B_TAIL, B_COARSEST, B_UPDATE, B_SPLIT, B_BASE, B_RES64, B_NORM,
     B_PSMOOTH16_0, B_PSMOOTH16_1, B_PSMOOTH32_0, B_PSMOOTH32_1,   // k-parity sweeps, tiles of 16 / 32, parity 0 / 1
-    B_CRESID                                                      // residual by columns
+    B_CRESID,                                                     // residual by columns
+    B_PAIR0                                                       // .. B_PAIR0 + 3: colours c and c^7
 };
 
 dim3 batch_grid2(int n) { return dim3((n + BX - 1) / BX, (n + BY - 1) / BY, n); }
@@ -1874,15 +1989,53 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
         lt[b] = t >= 0 ? t : in[b].L - 1;
         D = lt[b] > D ? lt[b] : D;
     }
-    // Sweeps at depth d: by k parity through e2 (pairs of sweeps, 4 launches
-    // a pair) when every grid at this depth has n <= 65, where launches cost
-    // more than the sweeps' work; by colour otherwise.  Both are the same
-    // sequential 8-colour sweep, bit for bit.
-    auto max_n_at = [&](int d) {
+    // Sweeps at depth d.  A grid whose size takes the colour-pair sweep
+    // (corr_smooth_choice) runs it: 4 launches a sweep, colours c and c^7
+    // together, the sequential sweep in the colour order 0, 7, 1, 6, 2, 5,
+    // 3, 4.  The other grids sweep colours in ascending order: by k parity
+    // through e2 (pairs of sweeps, 4 launches a pair) when all of them have
+    // n <= 65, where launches cost more than the sweeps' work, by colour
+    // otherwise, which are the same sweep bit for bit.  Every grid thus
+    // takes the bits of its solo sweep.
+    auto pairs_at = [&](int b, int d) { return corr_smooth_choice(in[b].lev[d].n) == CORR_PAIRS; };
+    auto max_n_at = [&](int d) {   // over the grids that sweep in ascending order
         int m = 0;
         for (int b = 0; b < count; ++b)
-            if (d < lt[b]) m = in[b].lev[d].n > m ? in[b].lev[d].n : m;
+            if (d < lt[b] && !pairs_at(b, d)) m = in[b].lev[d].n > m ? in[b].lev[d].n : m;
         return m;
+    };
+    auto pair_sweep = [&](int d) {
+        for (int c = 0; c < 4; ++c) {
+            std::vector<PairSmoothJob> jobs;
+            std::vector<int> blocks;
+            for (int b = 0; b < count; ++b) {
+                if (d >= lt[b] || !pairs_at(b, d)) continue;
+                const BatchLevel& F = in[b].lev[d];
+                const int n = F.n;
+                const int c7 = c ^ 7;
+                const int nk0 = colour_count(n, (c >> 2) & 1), nk1 = colour_count(n, (c7 >> 2) & 1);
+                const int edge = colour_count(n, 1);   // the larger box edge
+                if (edge <= 0 || nk0 + nk1 <= 0) continue;
+                const long long o0 = cm_offset(n, c), o1 = cm_offset(n, c7);
+                PairSmoothJob J;
+                J.inst = in[b].id;
+                J.n = n;
+                J.gx = (edge + BX - 1) / BX;
+                J.gy = (edge + BY - 1) / BY;
+                J.nk0 = nk0;
+                J.inv_h2 = inv_h2(F.h);
+                J.h2half = h2half(F.h);
+                J.e = F.e;
+                J.b0 = (const float*)F.bstore + 6 * o0;
+                J.r0 = F.rhs32 + o0;
+                J.b1 = (const float*)F.bstore + 6 * o1;
+                J.r1 = F.rhs32 + o1;
+                J.events = in[b].events;
+                jobs.push_back(J);
+                blocks.push_back(J.gx * J.gy * (nk0 + nk1));
+            }
+            T.emit(B_PAIR0 + c, jobs, blocks, 0);
+        }
     };
     auto plane_pair = [&](int d) {
         const int mx = max_n_at(d);
@@ -1892,7 +2045,7 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
                 std::vector<PlaneSmoothJob> jobs;
                 std::vector<int> blocks;
                 for (int b = 0; b < count; ++b) {
-                    if (d >= lt[b]) continue;
+                    if (d >= lt[b] || pairs_at(b, d)) continue;
                     const BatchLevel& F = in[b].lev[d];
                     const int n = F.n;
                     const int planes = colour_count(n, pk);
@@ -1919,10 +2072,16 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
             }
     };
     auto smooth = [&](int d, int nsweeps) {
+        bool any_pairs = false, any_ascending = false;
+        for (int b = 0; b < count; ++b)
+            if (d < lt[b]) (pairs_at(b, d) ? any_pairs : any_ascending) = true;
+        if (any_pairs)
+            for (int q = 0; q < nsweeps; ++q) pair_sweep(d);
+        if (!any_ascending) return;
         int sw = 0;
         bool plane = max_n_at(d) <= 65;
         for (int b = 0; b < count && plane; ++b)
-            if (d < lt[b] && (!in[b].lev[d].e2 || in[b].lev[d].n < 5)) plane = false;
+            if (d < lt[b] && !pairs_at(b, d) && (!in[b].lev[d].e2 || in[b].lev[d].n < 5)) plane = false;
         if (plane)
             for (; sw + 2 <= nsweeps; sw += 2) plane_pair(d);
         for (; sw < nsweeps; ++sw)
@@ -1930,7 +2089,7 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
                 std::vector<SmoothJob> jobs;
                 std::vector<int> blocks;
                 for (int b = 0; b < count; ++b) {
-                    if (d >= lt[b]) continue;
+                    if (d >= lt[b] || pairs_at(b, d)) continue;
                     const BatchLevel& F = in[b].lev[d];
                     const int n = F.n;
                     const int ni = colour_count(n, c & 1), nj = colour_count(n, (c >> 1) & 1),
@@ -2216,6 +2375,10 @@ static cudaError_t run_sequence(const BatchPlan* P, const std::vector<BLaunch>& 
         case B_PSMOOTH32_0: e = launch_batched<OpPlaneSmooth<0, 32, 128>>(P, L, dim3(128), s); break;
         case B_PSMOOTH32_1: e = launch_batched<OpPlaneSmooth<1, 32, 128>>(P, L, dim3(128), s); break;
         case B_CRESID: e = launch_batched<OpColResid>(P, L, b2, s); break;
+        case B_PAIR0 + 0: e = launch_batched<OpSmoothPair<0>>(P, L, b2, s); break;
+        case B_PAIR0 + 1: e = launch_batched<OpSmoothPair<1>>(P, L, b2, s); break;
+        case B_PAIR0 + 2: e = launch_batched<OpSmoothPair<2>>(P, L, b2, s); break;
+        case B_PAIR0 + 3: e = launch_batched<OpSmoothPair<3>>(P, L, b2, s); break;
         default: e = cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;

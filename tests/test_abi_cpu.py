@@ -88,11 +88,20 @@ def test_host_only_settings_validate_their_arguments():
     with pytest.raises(M.MAError):
         M.ma_set_corr_tuning(34, 1, 1)          # n must be odd
     with pytest.raises(M.MAError):
-        M.ma_set_corr_tuning(33, 5, 1)          # no smoother variant 5
+        M.ma_set_corr_tuning(33, 6, 1)          # no smoother variant 6
+    with pytest.raises(M.MAError):
+        M.ma_set_corr_tuning(33, M.MA_CORR_COLUMN, 1)      # the column form is a residual only
+    with pytest.raises(M.MAError):
+        M.ma_set_corr_tuning(33, 1, M.MA_CORR_PAIRS)      # the paired form is a smoother only
     with pytest.raises(M.MAError):
         M.ma_set_corr_tuning(33, 1, M.MA_CORR_BY_COLOUR)   # the residual has no by-colour form
     M.ma_set_corr_tuning(33, M.MA_CORR_PLANE32, M.MA_CORR_COLUMN)
     assert M.ma_get_corr_tuning(33) == (M.MA_CORR_PLANE32, M.MA_CORR_COLUMN)
+    M.ma_set_corr_tuning(33, M.MA_CORR_PAIRS, M.MA_CORR_PLANE16)
+    assert M.ma_get_corr_tuning(33) == (M.MA_CORR_PAIRS, M.MA_CORR_PLANE16)
+    for colour in (-1, 8):   # rejected on the host, before any device work
+        with pytest.raises(M.MAError):
+            M.ma_smooth_correction_colour(256, 256, 256, 256, 33, 0.1, colour, 256, 1 << 24, stream=0)
     M.ma_set_corr_tuning(33, -1, -1)
 
 

@@ -76,14 +76,17 @@ def test_correction_residual_matches_oracle_definition(name, n, amp):
     assert np.max(np.abs(got - ref)) <= 2e-4 * scale
 
 
+@pytest.mark.parametrize("pairs", [False, True])
 @pytest.mark.parametrize("name,n,amp", [("exp", 33, 1e-4), ("cosine", 65, 1e-5), ("exp", 129, 1e-6),
                                         ("exp", 45, 1e-5)])
-def test_correction_sweep_matches_oracle_sweep(name, n, amp):
+def test_correction_sweep_matches_oracle_sweep(name, n, amp, pairs):
     """One correction sweep against the oracle's Gauss-Seidel sweep on
     w = u + e with right-hand side det(D^2_h u) + rhs, in the regime the
     inner cycles run in (|rhs| ~ 1e-5 |f|, corrections of that order).  The
     kernel's base Hessian comes from the FP32 hi/lo split (~1e-5 relative),
-    and e is FP32."""
+    and e is FP32.  pairs: the colour-pair sweep (colours c and c^7 in one
+    launch) against the oracle's sweep in the colour order 0, 7, 1, 6, 2, 5,
+    3, 4; otherwise the by-colour sweep against ascending colours."""
     pr = P.make(name, n, seed=4)
     u = pr.u
     e = smooth_correction_field(n, amp, n + 1)
@@ -92,13 +95,17 @@ def test_correction_sweep_matches_oracle_sweep(name, n, amp):
     rhs[0], rhs[-1] = 0, 0
     w = np.ascontiguousarray(u + e.astype(np.float64))
     ftot = O.discrete_ma(u, pr.h) + rhs.astype(np.float64)
-    O.gs_sweep(w, ftot, pr.h)
+    O.gs_sweep(w, ftot, pr.h, O.COLOUR8_PAIRS if pairs else O.COLOUR8)
     e_ref = w - u
     hi, lo = split(u)
     ed = dev(e)
     _keep, scr, nb = M.correction_scratch(n)
-    M.ma_smooth_correction(ed, dev(hi), dev(lo), dev(rhs), n, pr.h, 1, scr, nb)
-    got = host(ed).astype(np.float64)
+    try:
+        M.ma_set_corr_tuning(n, M.MA_CORR_PAIRS if pairs else M.MA_CORR_BY_COLOUR, -1)
+        M.ma_smooth_correction(ed, dev(hi), dev(lo), dev(rhs), n, pr.h, 1, scr, nb)
+        got = host(ed).astype(np.float64)
+    finally:
+        M.ma_set_corr_tuning(n, -1, -1)
     change = np.max(np.abs(e_ref - e.astype(np.float64)))
     assert change > 0
     assert np.max(np.abs(got - e_ref)) <= 1e-3 * change + 1e-6 * np.max(np.abs(e_ref))
@@ -139,6 +146,44 @@ def test_plane_sweeps_equal_colour_sweeps_bitwise(name, n):
                 assert torch.equal(a, refs[sweeps]), f"{M.CORR_NAMES[choice]}, {sweeps} sweeps: max diff {d}"
     finally:
         M.ma_set_corr_tuning(n, -1, -1)
+
+
+@pytest.mark.parametrize("n", [71, 129, 65])
+def test_colour_pair_sweep_equals_its_colour_sequence_on_slow_points(n):
+    """The colour-pair sweep (colours c and c^7 in one launch) is the
+    sequential sweep in the order 0, 7, 1, 6, 2, 5, 3, 4: the same bits as
+    the by-colour launches run in that order, here where the FP32 fast path
+    fails.  A rough correction (K of the size of B) leaves G = B + K
+    indefinite at many points, and a right-hand side of -2 f at scattered
+    points makes det(B) + r <= 0 (the nonconvex branch); e and the count of
+    nonconvex points agree bit for bit."""
+    pr = P.make("exp", n, seed=2)
+    rng = np.random.default_rng(n)
+    e = np.zeros(pr.u.shape, dtype=np.float32)
+    e[1:-1, 1:-1, 1:-1] = (0.5 * pr.h ** 2 * rng.standard_normal((n - 2,) * 3)).astype(np.float32)
+    rhs = (1e-3 * rng.standard_normal(pr.u.shape) * pr.f).astype(np.float32)
+    pick = rng.random(pr.u.shape) < 0.02
+    rhs[pick] = (-2.0 * pr.f[pick]).astype(np.float32)
+    rhs[0], rhs[-1], rhs[:, 0], rhs[:, -1], rhs[:, :, 0], rhs[:, :, -1] = 0, 0, 0, 0, 0, 0
+    hi, lo = (dev(a) for a in split(pr.u))
+    rhs_d = dev(rhs)
+    _keep, scr, nb = M.correction_scratch(n)
+    try:
+        M.ma_set_corr_tuning(n, M.MA_CORR_PAIRS, -1)
+        ed = dev(e)
+        ev = torch.zeros(1, dtype=torch.int64, device="cuda")
+        M.ma_smooth_correction(ed, hi, lo, rhs_d, n, pr.h, 2, scr, nb, events=ev)
+        got = (host(ed), int(ev.item()))
+    finally:
+        M.ma_set_corr_tuning(n, -1, -1)
+    ref = dev(e)
+    ev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        for c in (0, 7, 1, 6, 2, 5, 3, 4):
+            M.ma_smooth_correction_colour(ref, hi, lo, rhs_d, n, pr.h, c, scr, nb, events=ev)
+    assert got[1] > 0 and got[1] == int(ev.item())
+    assert np.array_equal(got[0], host(ref), equal_nan=True)
+    assert not np.array_equal(got[0], e)
 
 
 @pytest.mark.parametrize("n", [129, 71, 33, 257, 9])

@@ -210,8 +210,9 @@ def test_norms_match_oracle(n):
 # ---------------------------------------------------------------------------
 
 def _params(kind=M.MA_FULL_WEIGHTING, approx=M.MA_APPROX_WEIGHTED, coarsest=3, csweeps=0):
+    # the settings of M.make_desc's defaults (tricubic FMG start)
     return O.Params(nu1=2, nu2=2, coarsest_n=coarsest, restrict_kind=kind, coarse_sweeps=csweeps,
-                    approx_restrict=approx)
+                    approx_restrict=approx, fmg_interp=O.FMG_CUBIC)
 
 
 @pytest.mark.parametrize("name,n,kind,approx", [
