@@ -44,6 +44,13 @@ FP64_PEAK_GOPS = 629.0   # 2 FP64 ops/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 
 # once per sweep for the stencils, counted at its own update).
 CORR_SMOOTH_BYTES_PER_POINT = 36
 HBM_PEAK_GBS = 6663.9    # MEASURED_PEAKS.json hbm_gbs (copy bandwidth)
+# FP32 correction V-cycles per outer iteration of the single mixed solves
+# (129^3 and up): with 2 the FP64 residual checks the stopping rule every two
+# cycles, which ends a solve nearer the cycle that reaches the tolerance and
+# spends fewer cycles detecting a round-off floor; the library default, 3,
+# suits small grids and batches, where an outer iteration's fixed cost weighs
+# more.
+MIXED_INNER = 2
 # DRAM bytes (read + write) per launch of the correction smoother at 257^3,
 # from one ncu capture of the current kernels with a warm L2 (--cache-control
 # none), keyed by the variant (MA_CORR_BY_COLOUR = 0: one colour, 103.4 MB read
@@ -144,7 +151,7 @@ def workload_config(args, world: int = 1) -> dict:
     return {"workload": f"Example 4 exp(|x|^2/2) {args.n}^3, FMG (tricubic) + FAS V(2,2), 8-colour nonlinear GS, "
                         f"tol {args.tol:g} relative max-norm residual (FP64)",
             "n": args.n, "tol": args.tol,
-            "precision": "mixed: FP32 correction V-cycles x3 per FP64 fine residual and update",
+            "precision": f"mixed: FP32 correction V-cycles x{MIXED_INNER} per FP64 fine residual and update",
             "restrict": "full weighting", "fmg_interpolation": "tricubic", "parallelism": f"replicas x{world}",
             "l2": "working set larger than L2 (no flush needed)"}
 
@@ -300,7 +307,8 @@ def bench_precision(args, M, problems, dev):
             unknowns = (n - 2) ** 3
             row, sols = {}, {}
             for prec, key in ((M.MA_MIXED, "mixed"), (M.MA_FP64, "fp64")):
-                H = M.Hierarchy(M.make_desc(n, length=length, precision=prec), device=dev)
+                H = M.Hierarchy(M.make_desc(n, length=length, precision=prec, inner_cycles=MIXED_INNER),
+                                device=dev)
                 for _ in range(2):
                     H.set_rhs_bc(f, g)
                     ms, r = _timed_solve(H, torch, stream, tol=args.tol, max_cycles=60, raise_on_error=False)
@@ -448,7 +456,8 @@ def main():
     pr = problems.make(args.problem, args.n)
     f_dev = torch.from_numpy(pr.f).to(dev)
     g_dev = torch.from_numpy(pr.initial()).to(dev)
-    hier = {"mixed": M.Hierarchy(M.make_desc(pr.n, length=pr.length, precision=M.MA_MIXED), device=dev),
+    hier = {"mixed": M.Hierarchy(M.make_desc(pr.n, length=pr.length, precision=M.MA_MIXED,
+                                             inner_cycles=MIXED_INNER), device=dev),
             "fp64": M.Hierarchy(M.make_desc(pr.n, length=pr.length, precision=M.MA_FP64), device=dev)}
 
     def step(H):
@@ -551,7 +560,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         per = e0.elapsed_time(e1) / 3.0
-        inner = 3 if key == "mixed" else 1
+        inner = MIXED_INNER if key == "mixed" else 1
         vc[key] = {"ms_per_cycle": per / inner, "vcycles_per_s": 1e3 * inner / per}
 
     # end to end through the C ABI with host buffers (pinned), mixed precision

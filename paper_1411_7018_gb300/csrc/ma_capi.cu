@@ -862,14 +862,18 @@ struct ma_batch_group {
     cudaEvent_t done = nullptr;
 };
 
+// The active flags and packed norms are held once per group (group q's
+// slice starts at q * count flags and 5 q * count norms, indexed by the
+// hierarchy's place in the batch), so that each group uploads its flags and
+// reads its norms on its own stream while the other groups run.
 struct ma_batch {
     std::vector<ma_hierarchy*> hs;
     int device = 0;
     cudaStream_t s = nullptr;        // the caller's stream
-    int* active_dev = nullptr;       // per hierarchy: 1 while it iterates
-    double* packed_dev = nullptr;    // per hierarchy: (max, L2, -, -, events) after an iteration
-    int* active_host = nullptr;      // pinned
-    double* packed_host = nullptr;   // pinned
+    int* active_dev = nullptr;       // per group and hierarchy: 1 while it iterates
+    double* packed_dev = nullptr;    // per group and hierarchy: (max, L2, -, -, events) after an iteration
+    int* active_host = nullptr;      // pinned, the same shape
+    double* packed_host = nullptr;   // pinned, the same shape
     std::vector<ma_batch_group> grp;
     cudaEvent_t flags_ev = nullptr;
     cudaEvent_t done_ev = nullptr;
@@ -961,13 +965,14 @@ std::vector<ma::BatchInstance> subset(const std::vector<ma::BatchInstance>& in, 
     return out;
 }
 
-// Workspace: active flags, packed norms, then the job tables of each group.
+// Workspace: active flags and packed norms (one slice per group), then the
+// job tables of each group.
 size_t batch_layout(const std::vector<ma::BatchInstance>& in, const ma::BatchParams& p,
                     const std::vector<std::vector<int>>& grp, size_t* off_packed, std::vector<size_t>* off_tables)
 {
-    const size_t count = in.size();
-    *off_packed = align_up(sizeof(int) * count);
-    size_t off = *off_packed + align_up(5 * sizeof(double) * count);
+    const size_t count = in.size(), ng = grp.size();
+    *off_packed = align_up(sizeof(int) * count * ng);
+    size_t off = *off_packed + align_up(5 * sizeof(double) * count * ng);
     off_tables->clear();
     for (const std::vector<int>& ids : grp) {
         off_tables->push_back(off);
@@ -1008,30 +1013,23 @@ cudaError_t group_replay(ma_batch_group& G, bool start)
     return cudaGraphLaunch(gs.exec, G.s);
 }
 
-// Uploads the active flags and replays every group with an active
-// hierarchy (start or outer-iteration graphs), the groups concurrently; then
-// reads the packed norms back.  Blocks.
-ma_status batch_round(ma_batch* B, const std::vector<char>& done, bool start)
+// Uploads group q's active flags, replays its start (start = true) or
+// outer-iteration graph and reads its packed norms back, all on the group's
+// stream, and records G.done after them.  Touches only the group's slices.
+cudaError_t group_launch(ma_batch* B, int q, const std::vector<char>& done, bool start)
 {
-    const int count = (int)B->hs.size();
-    for (int b = 0; b < count; ++b) B->active_host[b] = done[b] ? 0 : 1;
-    MA_CK(cudaMemcpyAsync(B->active_dev, B->active_host, sizeof(int) * (size_t)count, cudaMemcpyHostToDevice, B->s));
-    MA_CK(cudaEventRecord(B->flags_ev, B->s));
-    for (ma_batch_group& G : B->grp) {
-        bool any = false;
-        for (int b : G.ids) any = any || !done[b];
-        if (!any) continue;
-        if (G.s != B->s) MA_CK(cudaStreamWaitEvent(G.s, B->flags_ev, 0));
-        MA_CK(group_replay(G, start));
-        if (G.s != B->s) {
-            MA_CK(cudaEventRecord(G.done, G.s));
-            MA_CK(cudaStreamWaitEvent(B->s, G.done, 0));
-        }
-    }
-    MA_CK(cudaMemcpyAsync(B->packed_host, B->packed_dev, 5 * sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost,
-                          B->s));
-    MA_CK(cudaStreamSynchronize(B->s));
-    return MA_OK;
+    ma_batch_group& G = B->grp[q];
+    const size_t count = B->hs.size();
+    int* ah = B->active_host + (size_t)q * count;
+    for (int b : G.ids) ah[b] = done[b] ? 0 : 1;
+    cudaError_t e =
+        cudaMemcpyAsync(B->active_dev + (size_t)q * count, ah, sizeof(int) * count, cudaMemcpyHostToDevice, G.s);
+    if (e == cudaSuccess) e = group_replay(G, start);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(B->packed_host + 5 * (size_t)q * count, B->packed_dev + 5 * (size_t)q * count,
+                            5 * sizeof(double) * count, cudaMemcpyDeviceToHost, G.s);
+    if (e == cudaSuccess) e = cudaEventRecord(G.done, G.s);
+    return e;
 }
 
 }  // namespace
@@ -1088,11 +1086,16 @@ ma_status ma_create_batch(ma_hierarchy* const* hs, int count, void* dev_workspac
     B->device = hs[0]->device;
     B->s = (cudaStream_t)stream;
     char* ws = (char*)dev_workspace;
+    const size_t ng = grouping.size();
     B->active_dev = (int*)ws;
     B->packed_dev = (double*)(ws + op);
-    B->grp.resize(grouping.size());
-    cudaError_t e = cudaMallocHost((void**)&B->active_host, sizeof(int) * (size_t)count);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&B->packed_host, 5 * sizeof(double) * (size_t)count);
+    B->grp.resize(ng);
+    cudaError_t e = cudaMallocHost((void**)&B->active_host, sizeof(int) * (size_t)count * ng);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&B->packed_host, 5 * sizeof(double) * (size_t)count * ng);
+    if (e == cudaSuccess) {
+        std::memset(B->active_host, 0, sizeof(int) * (size_t)count * ng);
+        std::memset(B->packed_host, 0, 5 * sizeof(double) * (size_t)count * ng);
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->flags_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->done_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, ot.empty() ? 0 : ot[0], B->s);
@@ -1105,8 +1108,8 @@ ma_status ma_create_batch(ma_hierarchy* const* hs, int count, void* dev_workspac
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming);
         if (e != cudaSuccess) break;
         const std::vector<ma::BatchInstance> sub = subset(in, G.ids);
-        G.plan = ma::batch_plan_create(sub.data(), (int)sub.size(), p, ws + ot[q], B->active_dev, B->packed_dev, B->s,
-                                       &e);
+        G.plan = ma::batch_plan_create(sub.data(), (int)sub.size(), p, ws + ot[q], B->active_dev + q * (size_t)count,
+                                       B->packed_dev + 5 * q * (size_t)count, B->s, &e);
         if (!G.plan && e == cudaSuccess) e = cudaErrorMemoryAllocation;
     }
     if (e != cudaSuccess) {
@@ -1123,8 +1126,14 @@ ma_status ma_batch_run(ma_batch* B, const ma_solve_opts* opts, ma_solve_result* 
     ma_status st = check_opts(opts);
     if (st != MA_OK) return st;
     const int count = (int)B->hs.size();
+    const int ng = (int)B->grp.size();
     DeviceGuard g(B->device);
-    std::vector<char> done(count, 0);
+    std::vector<char> done(count, 0), started(count, 0);
+    // per group: WAIT for its hierarchies' own start graphs, READY to launch,
+    // START or ITER in flight (its batched start or an outer iteration), OVER
+    enum { WAIT, READY, START, ITER, OVER };
+    std::vector<int> state(ng, WAIT);
+    auto packed = [&](int q, int b) { return B->packed_host + 5 * ((size_t)q * count + b); };
     if (g_batch_start.load(std::memory_order_relaxed) && opts->init == MA_INIT_FMG &&
         opts->relative != MA_REL_INITIAL) {
         // the start of every hierarchy (the norms of f, FMG, the first outer
@@ -1136,14 +1145,14 @@ ma_status ma_batch_run(ma_batch* B, const ma_solve_opts* opts, ma_solve_result* 
             MA_CK(cudaEventRecord(H->sv.ev, H->s));   // after the caller's work on the hierarchy
             MA_CK(cudaStreamWaitEvent(B->s, H->sv.ev, 0));
             MA_CK(cudaMemsetAsync(H->events, 0, sizeof(unsigned long long), B->s));
+            started[b] = 1;
         }
-        if ((st = batch_round(B, done, true)) != MA_OK) return st;
-        for (int b = 0; b < count; ++b) {
-            ma_hierarchy* H = B->hs[b];
-            for (int q = 0; q < 5; ++q) H->host[q] = B->packed_host[5 * b + q];
-            H->sv.phase = 1;
-            done[b] = absorb_norms(H) ? 1 : 0;
-            if (!done[b]) H->sv.phase = 2;
+        MA_CK(cudaEventRecord(B->flags_ev, B->s));
+        for (int q = 0; q < ng; ++q) {
+            ma_batch_group& G = B->grp[q];
+            if (G.s != B->s) MA_CK(cudaStreamWaitEvent(G.s, B->flags_ev, 0));
+            MA_CK(group_launch(B, q, done, true));
+            state[q] = START;
         }
     } else {
         // other starts: every hierarchy's own start graph on its own stream
@@ -1151,31 +1160,81 @@ ma_status ma_batch_run(ma_batch* B, const ma_solve_opts* opts, ma_solve_result* 
             std::memset(&results[b], 0, sizeof results[b]);
             if ((st = ma_solve_begin(B->hs[b], opts)) != MA_OK) return st;
         }
-        for (int b = 0; b < count; ++b) {
-            ma_hierarchy* H = B->hs[b];
-            MA_CK(cudaStreamWaitEvent(B->s, H->sv.ev, 0));
-            MA_CK(cudaEventSynchronize(H->sv.ev));
-            done[b] = absorb_norms(H) ? 1 : 0;
-            if (!done[b]) H->sv.phase = 2;
-        }
     }
-    // then each outer iteration of all hierarchies still iterating: one
-    // graph per group, the groups' graphs running concurrently
+    // Each group advances on its own: its first outer iteration once its
+    // hierarchies' starts are in, each next one once its own norms are back.
     for (;;) {
-        int active = 0;
-        for (int b = 0; b < count; ++b) active += done[b] ? 0 : 1;
-        if (!active) break;
-        if ((st = batch_round(B, done, false)) != MA_OK) return st;
-        for (int b = 0; b < count; ++b) {
-            if (done[b]) continue;
-            ma_hierarchy* H = B->hs[b];
-            H->host[0] = B->packed_host[5 * b];
-            H->host[1] = B->packed_host[5 * b + 1];
-            H->host[4] = B->packed_host[5 * b + 4];
-            done[b] = absorb_norms(H) ? 1 : 0;
+        bool all_over = true, moved = false;
+        cudaEvent_t pending = nullptr;
+        for (int q = 0; q < ng; ++q) {
+            ma_batch_group& G = B->grp[q];
+            if (state[q] == OVER) continue;
+            all_over = false;
+            if (state[q] == WAIT) {
+                bool ready = true;
+                for (int b : G.ids) {
+                    if (started[b]) continue;
+                    ma_hierarchy* H = B->hs[b];
+                    const cudaError_t qe = cudaEventQuery(H->sv.ev);
+                    if (qe == cudaErrorNotReady) {
+                        ready = false;
+                        if (!pending) pending = H->sv.ev;
+                        continue;
+                    }
+                    MA_CK(qe);
+                    started[b] = 1;
+                    done[b] = absorb_norms(H) ? 1 : 0;
+                    if (!done[b]) H->sv.phase = 2;
+                }
+                if (!ready) continue;
+                for (int b : G.ids) MA_CK(cudaStreamWaitEvent(G.s, B->hs[b]->sv.ev, 0));
+                state[q] = READY;
+                moved = true;
+            } else if (state[q] == START || state[q] == ITER) {
+                const cudaError_t qe = cudaEventQuery(G.done);
+                if (qe == cudaErrorNotReady) {
+                    if (!pending) pending = G.done;
+                    continue;
+                }
+                MA_CK(qe);
+                for (int b : G.ids) {
+                    if (done[b]) continue;
+                    ma_hierarchy* H = B->hs[b];
+                    const double* pk = packed(q, b);
+                    if (state[q] == START) {
+                        for (int k = 0; k < 5; ++k) H->host[k] = pk[k];
+                        H->sv.phase = 1;
+                    } else {
+                        H->host[0] = pk[0];
+                        H->host[1] = pk[1];
+                        H->host[4] = pk[4];
+                    }
+                    done[b] = absorb_norms(H) ? 1 : 0;
+                    if (!done[b]) H->sv.phase = 2;
+                }
+                state[q] = READY;
+                moved = true;
+            }
+            if (state[q] == READY) {
+                bool any = false;
+                for (int b : G.ids) any = any || !done[b];
+                if (!any) {
+                    state[q] = OVER;
+                } else {
+                    MA_CK(group_launch(B, q, done, false));
+                    state[q] = ITER;
+                }
+                moved = true;
+            }
         }
+        if (all_over) break;
+        if (!moved && pending) MA_CK(cudaEventSynchronize(pending));   // wait instead of spinning
     }
-    // later work on a hierarchy's own stream follows the batch's
+    // later work on the caller's stream and on each hierarchy's own stream
+    // follows the batch's
+    for (int q = 0; q < ng; ++q)
+        if (B->grp[q].s != B->s) MA_CK(cudaStreamWaitEvent(B->s, B->grp[q].done, 0));
+    for (int b = 0; b < count; ++b) MA_CK(cudaStreamWaitEvent(B->s, B->hs[b]->sv.ev, 0));
     MA_CK(cudaEventRecord(B->done_ev, B->s));
     ma_status worst = MA_OK;
     for (int b = 0; b < count; ++b) {
