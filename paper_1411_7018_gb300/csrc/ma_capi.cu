@@ -313,7 +313,10 @@ cudaError_t fp32_prepare(ma_hierarchy* H)
 }
 
 // Algorithm 2 in FP32: zero coarsest interior, coarsest solve, then up the
-// levels: interpolate and one cycle from that level.
+// levels: interpolate and one cycle from that level.  The tricubic
+// interpolation (MA_FMG_CUBIC) runs on the levels' FP64 arrays: coarse e to
+// FP64, the fine interior interpolated, the fine grid back to FP32 (its shell
+// holds the boundary data, which e carries as well).
 cudaError_t fp32_fmg(ma_hierarchy* H)
 {
     cudaStream_t s = H->s;
@@ -326,7 +329,13 @@ cudaError_t fp32_fmg(ma_hierarchy* H)
     for (int l = H->L - 2; l >= 0; --l) {
         ma::Level& F = H->lev[l];
         ma::Level& C = H->lev[l + 1];
-        if ((e = ma::launch_interpolate_f32(C.e, C.n, F.e, s)) != cudaSuccess) return e;
+        if (H->d.fmg_interp == MA_FMG_CUBIC) {
+            if ((e = ma::launch_f32_to_f64(C.e, C.u, C.n, s)) != cudaSuccess) return e;
+            if ((e = ma::launch_interpolate_cubic(C.u, C.n, F.u, F.r, s)) != cudaSuccess) return e;
+            if ((e = ma::launch_f64_to_f32(F.u, F.e, F.n, s)) != cudaSuccess) return e;
+        } else if ((e = ma::launch_interpolate_f32(C.e, C.n, F.e, s)) != cudaSuccess) {
+            return e;
+        }
         if ((e = corr_vcycle_from(H, l)) != cudaSuccess) return e;
     }
     return cudaSuccess;
