@@ -180,6 +180,26 @@ cudaError_t vcycle_from(ma_hierarchy* H, int l0)
 // problem from a zero interior, then interpolate up with one V-cycle per level.
 // With finest_vcycle false the finest level only receives the interpolated
 // iterate (the mixed-precision solve continues from there).
+cudaError_t refresh_base(ma_hierarchy* H, int apply, int l0 = 0);
+cudaError_t corr_vcycle_from(ma_hierarchy* H, int l0);
+
+// An FMG level of the mixed solve below the finest: one outer iteration with
+// kFmgCorrCycles FP32 correction V-cycles from level l, in place of
+// Algorithm 2's FP64 V-cycle there (cheaper, and at least as strong).  e_l = 0
+// and the base Hessians below l from the FP32 split of u_l; the FP64 residual
+// at l (the correction rhs and the B of level l); the cycles; u_l += e_l.
+cudaError_t mixed_fmg_step(ma_hierarchy* H, int l)
+{
+    cudaError_t e;
+    if ((e = refresh_base(H, 0, l)) != cudaSuccess) return e;
+    ma::Level& F = H->lev[l];
+    if ((e = ma::launch_residual64_to32(F.u, F.rhs, F.rhs32, F.bstore, F.n, F.h, H->partials, H->s)) != cudaSuccess)
+        return e;
+    for (int c = 0; c < ma::kFmgCorrCycles; ++c)
+        if ((e = corr_vcycle_from(H, l)) != cudaSuccess) return e;
+    return ma::launch_update(F.u, F.e, F.n, 1, H->s);
+}
+
 cudaError_t fmg(ma_hierarchy* H, bool finest_vcycle = true)
 {
     cudaStream_t s = H->s;
@@ -201,7 +221,8 @@ cudaError_t fmg(ma_hierarchy* H, bool finest_vcycle = true)
                                             : ma::launch_interpolate(C.u, C.n, F.u, s);
         if (e != cudaSuccess) return e;
         if (l == 0 && !finest_vcycle) break;
-        if ((e = vcycle_from(H, l)) != cudaSuccess) return e;
+        e = H->d.precision == MA_MIXED ? mixed_fmg_step(H, l) : vcycle_from(H, l);
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -212,15 +233,15 @@ cudaError_t fmg(ma_hierarchy* H, bool finest_vcycle = true)
 // the coarse correction levels from the FP32 split of the injected iterate.
 // The finest B is written by the FP64 residual (mixed_residual), which
 // always follows.
-cudaError_t refresh_base(ma_hierarchy* H, int apply)
+cudaError_t refresh_base(ma_hierarchy* H, int apply, int l0)
 {
     cudaStream_t s = H->s;
     cudaError_t e;
-    ma::Level& F = H->lev[0];
+    ma::Level& F = H->lev[l0];
     if ((e = ma::launch_update(F.u, F.e, F.n, apply, s)) != cudaSuccess) return e;
-    for (int l = 1; l < H->L; ++l) {
+    for (int l = l0 + 1; l < H->L; ++l) {
         ma::Level& A = H->lev[l];
-        if ((e = ma::launch_split_inject(F.u, F.n, 1 << l, A.hi, A.lo, A.n, s)) != cudaSuccess) return e;
+        if ((e = ma::launch_split_inject(F.u, F.n, 1 << (l - l0), A.hi, A.lo, A.n, s)) != cudaSuccess) return e;
         if ((e = ma::launch_base_colour(A.hi, A.lo, A.bstore, A.n, A.h, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -4,6 +4,10 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <functional>
+#include <utility>
+#include <vector>
+
 namespace ma {
 
 // Kernel launches issued by this library in this process (all devices).
@@ -76,6 +80,9 @@ cudaError_t launch_zero_shell_f32(float* v, int n, cudaStream_t s);
 constexpr int CORR_BY_COLOUR = 0, CORR_PLANE16 = 1, CORR_PLANE32 = 2, CORR_PLANE64 = 3;
 constexpr int CORR_COLUMN = 4;   // residual only
 constexpr int CORR_PAIRS = 5;    // smoother only: colours c and c^7 per launch
+// FP32 correction V-cycles of each FMG level below the finest in a mixed solve
+// (the FP64 V-cycle of Algorithm 2 step 5 there); solo and batched starts alike.
+constexpr int kFmgCorrCycles = 2;
 int corr_smooth_choice(int n);
 int corr_resid_choice(int n);
 bool set_corr_tuning(int n, int smooth, int resid);   // -1: built-in default; false unless n is odd in [3, 4097]
@@ -161,7 +168,11 @@ struct TableBuilder;
 // below the finest level, all hierarchies sharing the coarsest grid size so
 // that every FMG step runs on one level size; and the launcher of its ops.
 void emit_rhs_partials_f64(batched::TableBuilder& T, const BatchInstance* in, int count);
-void emit_fmg_f64(batched::TableBuilder& T, const BatchInstance* in, int count, const BatchParams& p);
+// level_step, when given, replaces the FP64 V-cycle of each FMG level below
+// the finest: it receives (instance index, level) for the instances that
+// have that level.
+void emit_fmg_f64(batched::TableBuilder& T, const BatchInstance* in, int count, const BatchParams& p,
+                  const std::function<void(const std::vector<std::pair<int, int>>&)>& level_step = nullptr);
 cudaError_t batch_launch_f64(const char* tables, const batched::BLaunch& L, const int* active, cudaStream_t s);
 // Bytes of the device job tables of a batch.
 size_t batch_tables_bytes(const BatchInstance* in, int count, const BatchParams& p);

@@ -851,7 +851,8 @@ void emit_rhs_partials_f64(TableBuilder& T, const BatchInstance* in, int count)
 // Algorithm 2 as fmg(H, false) runs it: inject f and the data down, solve the
 // coarsest grid from a zero interior, then up the levels: interpolate and one
 // V-cycle from that level, the finest level receiving the interpolation only.
-void emit_fmg_f64(TableBuilder& T, const BatchInstance* in, int count, const BatchParams& p)
+void emit_fmg_f64(TableBuilder& T, const BatchInstance* in, int count, const BatchParams& p,
+                  const std::function<void(const std::vector<std::pair<int, int>>&)>& level_step)
 {
     int Lmax = 0;
     for (int b = 0; b < count; ++b) Lmax = std::max(Lmax, in[b].L);
@@ -922,7 +923,13 @@ void emit_fmg_f64(TableBuilder& T, const BatchInstance* in, int count, const Bat
         T.emit(F_CUBIC0, c0, b0, 0);
         T.emit(F_CUBIC1, c1, b1, 0);
         T.emit(F_CUBIC2, c2, b2, 0);
-        emit_vcycle64(T, in, E, p);
+        if (level_step) {
+            std::vector<std::pair<int, int>> steps;
+            for (const VEntry& v : E) steps.emplace_back(v.b, v.l0);
+            if (!steps.empty()) level_step(steps);
+        } else {
+            emit_vcycle64(T, in, E, p);
+        }
     }
 }
 

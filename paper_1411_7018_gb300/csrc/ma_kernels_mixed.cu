@@ -1974,8 +1974,13 @@ int tail_start(const BatchInstance& I, int tmax)
     return I.lev[lt].n <= tmax ? lt : -1;   // -1: no fused tail (coarsest solve alone)
 }
 
+// The launches of one batched outer iteration (start: the whole start, FMG
+// included, before it; fmg_step: instead, an FMG level of the mixed solve,
+// which ma_capi.cu's mixed_fmg_step runs for one hierarchy: e = 0 and the
+// base Hessians below the top, the FP64 residual at the top without norms,
+// the correction cycles, u += e at the top).
 void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const BatchParams& p, double* packed,
-                    bool start)
+                    bool start, bool fmg_step = false)
 {
     const auto inv_h2 = [](double h) { return (float)(1.0 / (h * h)); };
     const auto h2half = [](double h) { return (float)(0.5 * h * h); };
@@ -2209,8 +2214,7 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
     }
     };
     // u += e (apply) and e = 0; the coarse base Hessians of the iterate
-    auto refresh = [&](int apply) {
-    {
+    auto update = [&](int apply) {
         std::vector<OpUpdate::Job> uj;
         std::vector<int> ub;
         for (int b = 0; b < count; ++b) {
@@ -2220,29 +2224,32 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
             ub.push_back((int)((m + UT - 1) / UT));
         }
         T.emit(B_UPDATE, uj, ub, 0);
-    }
-    int Lmax = 0;
-    for (int b = 0; b < count; ++b) Lmax = in[b].L > Lmax ? in[b].L : Lmax;
-    for (int l = 1; l < Lmax; ++l) {
-        std::vector<OpSplit::Job> sj;
-        std::vector<OpBase::Job> bj;
-        std::vector<int> sb, bb;
-        for (int b = 0; b < count; ++b) {
-            if (l >= in[b].L) continue;
-            const BatchLevel& F = in[b].lev[0];
-            const BatchLevel& A = in[b].lev[l];
-            const dim3 g = batch_grid2(A.n);
-            sj.push_back(OpSplit::Job{in[b].id, F.n, 1 << l, A.n, (int)g.x, (int)g.y, F.u, A.hi, A.lo});
-            sb.push_back((int)(g.x * g.y * g.z));
-            bj.push_back(OpBase::Job{in[b].id, A.n, (int)g.x, (int)g.y, inv_h2(A.h), A.hi, A.lo, (float*)A.bstore});
-            bb.push_back((int)(g.x * g.y * g.z));
+    };
+    auto refresh = [&](int apply) {
+        update(apply);
+        int Lmax = 0;
+        for (int b = 0; b < count; ++b) Lmax = in[b].L > Lmax ? in[b].L : Lmax;
+        for (int l = 1; l < Lmax; ++l) {
+            std::vector<OpSplit::Job> sj;
+            std::vector<OpBase::Job> bj;
+            std::vector<int> sb, bb;
+            for (int b = 0; b < count; ++b) {
+                if (l >= in[b].L) continue;
+                const BatchLevel& F = in[b].lev[0];
+                const BatchLevel& A = in[b].lev[l];
+                const dim3 g = batch_grid2(A.n);
+                sj.push_back(OpSplit::Job{in[b].id, F.n, 1 << l, A.n, (int)g.x, (int)g.y, F.u, A.hi, A.lo});
+                sb.push_back((int)(g.x * g.y * g.z));
+                bj.push_back(
+                    OpBase::Job{in[b].id, A.n, (int)g.x, (int)g.y, inv_h2(A.h), A.hi, A.lo, (float*)A.bstore});
+                bb.push_back((int)(g.x * g.y * g.z));
+            }
+            T.emit(B_SPLIT, sj, sb, 0);
+            T.emit(B_BASE, bj, bb, 0);
         }
-        T.emit(B_SPLIT, sj, sb, 0);
-        T.emit(B_BASE, bj, bb, 0);
-    }
     };
     // FP64 fine residual (the next correction rhs and the fine B) and its norms
-    auto residual_norm = [&]() {
+    auto residual_norm = [&](bool norms) {
         std::vector<OpRes64::Job> rj;
         std::vector<OpNorm::Job> nj;
         std::vector<int> rb, nb;
@@ -2275,8 +2282,15 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
             nb.push_back(1);
         }
         T.emit(B_RES64, rj, rb, 0);
-        T.emit(B_NORM, nj, nb, 0);
+        if (norms) T.emit(B_NORM, nj, nb, 0);
     };
+    if (fmg_step) {
+        refresh(0);
+        residual_norm(false);
+        cycles();
+        update(1);
+        return;
+    }
     if (start) {
         // Algorithm 2 as ma_solve_begin runs it in mixed precision: the
         // reference norms of f, FMG with FP64 V-cycles below the finest
@@ -2292,13 +2306,27 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
             nb.push_back(1);
         }
         T.emit(B_NORM, nj, nb, 0);
-        emit_fmg_f64(T, in, count, p);
+        // the FMG levels below the finest as mixed steps on the hierarchies
+        // seen from that level down (in an FMG step they all have the same
+        // level sizes, so the depth-aligned launches apply)
+        emit_fmg_f64(T, in, count, p, [&](const std::vector<std::pair<int, int>>& E) {
+            std::vector<BatchInstance> sub;
+            for (const std::pair<int, int>& v : E) {
+                BatchInstance I = in[v.first];
+                I.L = in[v.first].L - v.second;
+                for (int k = 0; k < I.L; ++k) I.lev[k] = in[v.first].lev[v.second + k];
+                sub.push_back(I);
+            }
+            BatchParams q = p;
+            q.inner = kFmgCorrCycles;
+            build_sequence(T, sub.data(), (int)sub.size(), q, packed, false, true);
+        });
         refresh(0);
-        residual_norm();
+        residual_norm(true);
     }
     cycles();
     refresh(1);
-    residual_norm();
+    residual_norm(true);
 }
 
 template <typename Op>
