@@ -667,9 +667,10 @@ ma_status ma_solve_begin(ma_hierarchy* H, const ma_solve_opts* opts)
     MA_CK(cudaMemsetAsync(H->events, 0, sizeof(unsigned long long), H->s));
     const bool mixed = H->d.precision == MA_MIXED;
     // rhs norms, the initial iterate and its residual norm as one graph.  In
-    // mixed precision the FMG pass runs its FP64 V-cycles below the finest
-    // level and completes with one outer iteration (FP32 correction cycles
-    // and the FP64 update) in place of the finest FP64 V-cycle.
+    // mixed precision every FMG level runs an outer iteration (FP64
+    // residual, FP32 correction cycles, FP64 update) in place of the FP64
+    // V-cycle of Algorithm 2; the finest level's is the first outer
+    // iteration of the solve.
     const int init = opts->init;
     const bool ref_initial = opts->relative == MA_REL_INITIAL;
     MA_CK(run_graph(H, H->g_init[init + (ref_initial ? 3 : 0)], [&]() -> cudaError_t {

@@ -2293,8 +2293,8 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
     }
     if (start) {
         // Algorithm 2 as ma_solve_begin runs it in mixed precision: the
-        // reference norms of f, FMG with FP64 V-cycles below the finest
-        // level, then the finest level's first outer iteration
+        // reference norms of f, FMG with a mixed step on each level below
+        // the finest, then the finest level's first outer iteration
         emit_rhs_partials_f64(T, in, count);
         std::vector<OpNorm::Job> nj;
         std::vector<int> nb;

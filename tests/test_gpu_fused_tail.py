@@ -102,8 +102,9 @@ def test_fp64_fused_tail_bitwise_in_the_paper_configuration(name, n):
 
 @pytest.mark.parametrize("precision", [M.MA_MIXED, M.MA_FP32])
 def test_fused_fp64_tail_bitwise_under_the_other_precisions(precision):
-    """The mixed solve runs FP64 FMG below the finest level; the FP32 mode
-    runs no FP64 cycle (the switch must not change anything there)."""
+    """Neither the mixed solve (its FMG levels run FP32 correction cycles)
+    nor the FP32 mode runs an FP64 V-cycle: the switch must not change
+    anything there."""
     outs = _runs(lambda pr: M.make_desc(65, length=pr.length, precision=precision), "exp", 65,
                  dict(tol=1e-10 if precision == M.MA_MIXED else 1e-5, max_cycles=40))
     _same_bits(outs)
