@@ -361,6 +361,28 @@ def test_colour_pair_ordering_is_the_stated_colour_sequence():
     assert np.max(np.abs(a - d)) > 1e-8 * np.max(np.abs(d))
 
 
+def test_colour_pair_ordering_reaches_the_same_discrete_solution():
+    """The colour order changes the path of the iteration, not its fixed
+    point: whole solves with the pair order and with ascending colours end
+    on the same discrete solution (to the solve tolerance), at about the
+    same V-cycle count, and both are fixed points of a sweep in either
+    order."""
+    pr = P.make("exp", 33)
+    sols = {}
+    for ordering in (O.COLOUR8, O.COLOUR8_PAIRS):
+        u = pr.initial()
+        info = O.solve(u, pr.f, pr.h, tol=1e-12, params=O.Params(ordering=ordering, fmg_interp=O.FMG_CUBIC))
+        sols[ordering] = (u, info.cycles)
+    (a, ca), (b, cb) = sols[O.COLOUR8], sols[O.COLOUR8_PAIRS]
+    scale = np.max(np.abs(a))
+    assert np.max(np.abs(a - b)) <= 1e-11 * scale
+    assert abs(ca - cb) <= 1
+    for ordering in (O.COLOUR8, O.COLOUR8_PAIRS):
+        v = b.copy()
+        O.gs_sweep(v, pr.f, pr.h, ordering)
+        assert np.max(np.abs(v - b)) <= 1e-11 * scale
+
+
 # --------------------------------------------------------------------------
 # The discrete solution: brute force, theorems, printed errors
 # --------------------------------------------------------------------------
