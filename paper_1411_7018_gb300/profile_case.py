@@ -3,10 +3,11 @@
     python -m paper_1411_7018_gb300.profile_case --case smooth --n 257 --reps 2
 
 Cases: ``smooth`` (FP64 smoother sweeps, 8 colour launches each), ``residual``
-(the FP64 residual kernel), ``smooth_corr`` (pairs of FP32 correction-smoother
-sweeps of the mixed path, two k-parity launches per sweep, on a small
-correction), ``residual_corr`` (the correction residual rhs - N(e) of the mixed
-path, in the residual variant the tuning table picks for n, on that correction), ``vcycle`` (whole V-cycles of
+(the FP64 residual kernel), ``smooth_corr`` (FP32 correction-smoother sweeps of
+the mixed path on a small correction, in the variant the tuning table picks for
+n or the one --smoother names), ``residual_corr`` (the correction residual
+rhs - N(e) of the mixed path on that correction, in the variant the tuning
+table picks for n or the one --residual names), ``vcycle`` (whole V-cycles of
 a resident hierarchy), ``solve`` (one FMG + V-cycle solve to 1e-10), ``solve2d`` (the 2D paper-configuration solve of
 Example 1 on an n x n grid), ``smooth2d`` (2D red-black sweeps on that grid),
 ``batch`` (the batching workload: 64 mixed-precision instances of sizes drawn
@@ -35,7 +36,15 @@ def main():
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--problem", default="exp")
+    variants = {name: c for c, name in M.CORR_NAMES.items()}
+    ap.add_argument("--smoother", choices=["by_colour", "colour_pairs", "plane16", "plane32", "plane64"], default=None,
+                    help="correction-smoother variant for grid size n (default: the tuning table's)")
+    ap.add_argument("--residual", choices=["column", "plane16", "plane32", "plane64"], default=None,
+                    help="correction-residual variant for grid size n (default: the tuning table's)")
     a = ap.parse_args()
+    if a.smoother or a.residual:
+        M.ma_set_corr_tuning(a.n, variants[a.smoother] if a.smoother else -1,
+                             variants[a.residual] if a.residual else -1)
     if a.case == "smooth2d":
         from . import problems2d
         u_ex, f2, g2 = problems2d.make2d_on_device("ex1", a.n)
