@@ -179,14 +179,17 @@ ma_status ma_batch_solve(ma_hierarchy *const *hs, int count, const ma_solve_opts
 
 /* Shared per-level batch.  Binds `count` MA_MIXED hierarchies of any sizes
  * (n <= 1025; equal nu1, nu2, restrict_kind, approx_restrict, coarse_sweeps,
- * inner_cycles; one device; each at most once) so that their solves share
+ * inner_cycles, coarsest_n, fmg_interp; one device; each at most once) so
+ * that their solves share
  * kernel launches.  ma_batch_run starts every hierarchy as ma_solve_begin
  * does (FMG and the first outer iteration, each on its own stream; or as
  * batched launches, ma_set_batch_start), then runs the outer iterations
  * (Algorithm 1 V-cycles on the correction, the FP64 update and residual) of
  * all hierarchies still iterating as CUDA graphs, one per group of
- * hierarchies (ma_set_batch_groups), the first on `stream`: each of their
- * kernels covers one level depth of every
+ * hierarchies (ma_set_batch_groups), the first on `stream`.  Each group
+ * advances on its own: its first outer iteration once its hierarchies'
+ * starts are done, each next one once its own norms are back.  Each graph
+ * kernel covers one level depth of every
  * hierarchy (its blocks find their hierarchy in a job table kept in the
  * workspace), the levels <= the fused-tail bound of every hierarchy take one
  * launch, and a hierarchy that has met the stopping rule is skipped.  Each
@@ -220,10 +223,10 @@ ma_status ma_set_batch_groups(int groups);
 /* How ma_batch_run starts its hierarchies: 0 (the default) runs each
  * hierarchy's own start graph on its own stream, concurrently; 1 runs the
  * start (the norms of f, FMG, the first outer iteration) as batched launches
- * too (with MA_INIT_FMG and a reference other than MA_REL_INITIAL).  The
- * batched start keeps every hierarchy on the FP64 pipe at once and measured
- * ~4 % slower on 64 mixed hierarchies of {33, 65, 129}^3.  The results do not
- * depend on it. */
+ * too (with MA_INIT_FMG and a reference other than MA_REL_INITIAL).  With
+ * FP64 V-cycles on the FMG levels the batched start measured ~4 % slower on
+ * 64 mixed hierarchies of {33, 65, 129}^3.  The results do not depend on
+ * it. */
 ma_status ma_set_batch_start(int batched);
 
 /* Norm of the fine-level FP64 residual f - det(D^2_h u) of the current
