@@ -28,16 +28,18 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+@pytest.mark.parametrize("interp", [M.MA_FMG_CUBIC, M.MA_FMG_TRILINEAR])
 @pytest.mark.parametrize("name,n", [("exp", 17), ("exp", 33), ("exp", 65), ("cosine", 65)])
-def test_fp32_mode_floor_and_parity(name, n):
+def test_fp32_mode_floor_and_parity(name, n, interp):
     """The FP32 residual stalls at its round-off floor, stated as
     4 eps_32 max|u| N^2 relative to max|f| (second differences carry
     ~eps_32 |u| N^2 each; measured 0.04-0.5 of the bound), and the
     solution then agrees with the FP64 discrete solution to 1e-6 relative
     (measured <= 1.3e-7 up to 129^3) with the same error against the exact
-    solution to 10 %."""
+    solution to 10 %; from the tricubic FMG start (through the FP64 level
+    arrays) and from the trilinear one (FP32 throughout)."""
     pr = P.make(name, n)
-    H = M.Hierarchy(M.make_desc(n, precision=M.MA_FP32))
+    H = M.Hierarchy(M.make_desc(n, precision=M.MA_FP32, fmg_interp=interp))
     H.set_rhs_bc(dev(pr.f), dev(pr.initial()))
     r = H.solve(tol=1e-12, max_cycles=40, raise_on_error=False)
     u = torch.empty_like(dev(pr.f))
