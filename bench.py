@@ -152,7 +152,9 @@ def workload_config(args, world: int = 1) -> dict:
                         f"tol {args.tol:g} relative max-norm residual (FP64)",
             "n": args.n, "tol": args.tol,
             "precision": f"mixed: FP32 correction V-cycles x{MIXED_INNER} per FP64 fine residual and update",
-            "restrict": "full weighting", "fmg_interpolation": "tricubic", "parallelism": f"replicas x{world}",
+            "restrict": "full weighting", "fmg_interpolation": "tricubic",
+            "fmg_levels": "mixed outer iterations (FP64 residual, 2 FP32 correction cycles, FP64 update)",
+            "parallelism": f"replicas x{world}",
             "l2": "working set larger than L2 (no flush needed)"}
 
 
