@@ -458,7 +458,11 @@ ma_status ma_norm(const double *v_dev, int n, double h, void *scratch_dev, size_
  *    contents (each call overwrites every entry it reads, so nothing needs
  *    clearing).  Calls whose kernels overlap on the GPU -- on different
  *    streams, or from different host threads -- race on it and may return
- *    wrong norms; serialise them. */
+ *    wrong norms; serialise them.
+ *  - Each call waits for its stream (cudaStreamSynchronize) before it
+ *    returns the norms on the host.
+ *  - On failure the message for ma_last_error_string() is kept per host
+ *    thread, like every other entry point's. */
 ma_status ma_norm_static(const double *v_dev, int n, double h, double *out_host, ma_stream_t stream);
 
 #ifdef __cplusplus

@@ -8,7 +8,8 @@ ma_solve_begin / ma_solve_advance calls: each pass over the active set
 advances every solve whose last cycle has finished, so the cycles of all
 admitted requests overlap on the GPU (each hierarchy has its own stream).  A
 request's latency is its completion time minus its arrival time, queueing
-included.
+included.  A request whose hierarchy alone exceeds the HBM budget can never be
+admitted; it is finished at once with status REJECTED_FOOTPRINT.
 
 The scheduling logic only talks to a small backend interface (footprint,
 create, begin, advance, result, solution), so it can be exercised on the CPU
@@ -20,6 +21,10 @@ import collections
 import dataclasses
 import time
 from typing import Any, Callable, Sequence
+
+# Request.status of a request whose hierarchy is larger than the server's
+# whole HBM budget (never admitted); the other values are ma_status codes.
+REJECTED_FOOTPRINT = -2
 
 
 @dataclasses.dataclass
@@ -107,9 +112,12 @@ class Server:
         self.on_complete = on_complete
         self.clock = clock
         self.idle_sleep = idle_sleep
-        self.free = collections.defaultdict(list)     # n -> [hierarchy]
+        # Resident hierarchies are pooled by (n, domain edge length): a
+        # hierarchy's mesh width h = length / (n - 1) is fixed when it is
+        # created, so one of another length must not serve the request.
+        self.free = collections.defaultdict(list)     # (n, length) -> [hierarchy]
         self.held = 0                                  # bytes of all resident hierarchies
-        self.live = collections.Counter()              # n -> resident hierarchies (busy or free)
+        self.live = collections.Counter()              # (n, length) -> resident hierarchies (busy or free)
         self.created = 0
         self.footprints: dict[int, int] = {}
 
@@ -119,17 +127,19 @@ class Server:
         return self.footprints[n]
 
     def _acquire(self, n: int, length: float):
-        """A resident hierarchy of size n: a free one, else a new one within the
-        budget.  When the budget is full and a hierarchy of this size exists
-        (busy), wait for it rather than evict; otherwise evict idle
-        hierarchies of other sizes, largest first, to make room."""
-        if self.free[n]:
-            return self.free[n].pop()
+        """A resident hierarchy of size n and domain length `length`: a free
+        one, else a new one within the budget.  When the budget is full and a
+        hierarchy of this kind exists (busy), wait for it rather than evict;
+        otherwise evict idle hierarchies of other kinds, largest first, to
+        make room."""
+        kind = (n, length)
+        if self.free[kind]:
+            return self.free[kind].pop()
         need = self._footprint(n)
         if self.held + need > self.budget:
-            if self.live[n] > 0:
+            if self.live[kind] > 0:
                 return None
-            for m in sorted(self.free, key=lambda m: -self._footprint(m)):
+            for m in sorted(self.free, key=lambda m: -self._footprint(m[0])):
                 while self.free[m] and self.held + need > self.budget:
                     H = self.free[m].pop()
                     self._release_memory(H, m)
@@ -137,16 +147,16 @@ class Server:
                 return None
         H = self.b.create(n, length)
         self.held += need
-        self.live[n] += 1
+        self.live[kind] += 1
         self.created += 1
         return H
 
-    def _release_memory(self, H, n: int):
+    def _release_memory(self, H, kind):
         close = getattr(H, "close", None)
         if close:
             close()
-        self.held -= self._footprint(n)
-        self.live[n] -= 1
+        self.held -= self._footprint(kind[0])
+        self.live[kind] -= 1
 
     def run(self, requests: Sequence[Request]) -> list[Request]:
         """Serve requests (sorted by arrival time) to completion; returns them
@@ -159,7 +169,14 @@ class Server:
         while pending or waiting or active:
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
-                waiting.append(pending.popleft())
+                req = pending.popleft()
+                if self._footprint(req.n) > self.budget:
+                    # can never fit, even with every other hierarchy evicted
+                    req.admitted = req.finished = now
+                    req.status = REJECTED_FOOTPRINT
+                    done.append(req)
+                    continue
+                waiting.append(req)
             # admission: first come, first served, but a request that does not
             # fit yet does not block smaller ones behind it
             if waiting and len(active) < self.max_active:
@@ -172,33 +189,33 @@ class Server:
                         continue
                     req.admitted = self.clock() - t0
                     self.b.begin(H, req)
-                    active.append((req, H))
+                    active.append((req, H, (req.n, self.b.length_of(req.key))))
                 waiting = still
             progressed = False
             still_active = []
-            for req, H in active:
+            for req, H, kind in active:
                 if self.b.advance(H):
                     req.finished = self.clock() - t0
                     req.cycles, req.status, req.residual = self.b.result(H)
                     if self.on_complete:
                         self.on_complete(req, H)
-                    self.free[req.n].append(H)
+                    self.free[kind].append(H)
                     done.append(req)
                     progressed = True
                 else:
-                    still_active.append((req, H))
+                    still_active.append((req, H, kind))
             active = still_active
             if not progressed:
-                if active:
+                if active or waiting:
                     time.sleep(self.idle_sleep)
                 elif pending and not waiting:
                     time.sleep(max(0.0, min(pending[0].arrival - (self.clock() - t0), 0.01)))
         return done
 
     def close(self):
-        for n, hs in self.free.items():
+        for kind, hs in self.free.items():
             for H in hs:
-                self._release_memory(H, n)
+                self._release_memory(H, kind)
         self.free.clear()
 
 
@@ -224,4 +241,5 @@ def summarize(done: Sequence[Request], wall: float | None = None) -> dict:
     return {"requests": len(done), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "throughput_req_s": len(done) / span,
             "unknowns_per_s": unknowns / span, "wall_s": span,
-            "converged": int(sum(1 for r in done if r.status == 0))}
+            "converged": int(sum(1 for r in done if r.status == 0)),
+            "rejected": int(sum(1 for r in done if r.status == REJECTED_FOOTPRINT))}

@@ -109,3 +109,12 @@ def test_batch_footprint_rejects_an_empty_batch():
     with pytest.raises(M.MAError) as ei:
         M.ma_batch_footprint([])
     assert ei.value.status == M.MA_ERR_INVALID_ARG
+
+
+def test_static_norm_limit_in_the_binding_matches_the_header():
+    """The Python binding's copy of MA_NORM_STATIC_MAX_N is the value the C
+    header defines, so the no-allocation norm's tests probe the real limit."""
+    txt = open(os.path.join(ROOT, "include", "ma.h")).read()
+    m = re.search(r"^#define\s+MA_NORM_STATIC_MAX_N\s+(\d+)\s*$", txt, re.M)
+    assert m is not None
+    assert int(m.group(1)) == M.MA_NORM_STATIC_MAX_N

@@ -5,7 +5,7 @@ from __future__ import annotations
 
 import pytest
 
-from paper_1411_7018_gb300.serve import Request, Server, poisson_stream, summarize
+from paper_1411_7018_gb300.serve import REJECTED_FOOTPRINT, Request, Server, poisson_stream, summarize
 
 
 class FakeClock:
@@ -19,8 +19,9 @@ class FakeClock:
 
 
 class FakeHierarchy:
-    def __init__(self, n, backend):
+    def __init__(self, n, backend, length=1.0):
         self.n = n
+        self.length = length
         self.left = 0
         self.closed = False
         self.solves = 0
@@ -43,7 +44,7 @@ class FakeBackend:
         return n ** 3
 
     def create(self, n, length):
-        H = FakeHierarchy(n, self)
+        H = FakeHierarchy(n, self, length)
         self.created.append(H)
         self.live_bytes += n ** 3
         self.max_live = max(self.max_live, self.live_bytes)
@@ -51,6 +52,7 @@ class FakeBackend:
 
     def begin(self, H, req):
         assert not H.closed
+        assert H.length == self.length_of(req.key), "hierarchy of another domain length"
         H.left = H.n // 16
         H.solves += 1
 
@@ -62,6 +64,9 @@ class FakeBackend:
         return H.n // 16, 0, 1e-9
 
     def length_of(self, key):
+        # keys ("L", length) name a domain edge length; every other key the unit cube
+        if isinstance(key, tuple) and len(key) == 2 and key[0] == "L":
+            return key[1]
         return 1.0
 
 
@@ -127,3 +132,34 @@ def test_close_releases_resident_hierarchies():
     srv.close()
     assert all(H.closed for H in be.created)
     assert srv.held == 0
+
+
+def test_a_request_larger_than_the_whole_budget_is_rejected_and_the_server_returns():
+    """A hierarchy that alone exceeds the HBM budget can never be admitted:
+    the request finishes at once with REJECTED_FOOTPRINT, the others are
+    served, and run() returns instead of waiting for it forever."""
+    be = FakeBackend()
+    srv = Server(be, hbm_budget=65 ** 3, max_active=4, clock=FakeClock(), idle_sleep=0)
+    reqs = [Request(rid=0, n=33, arrival=0.0, key=None), Request(rid=1, n=129, arrival=0.0, key=None),
+            Request(rid=2, n=65, arrival=0.002, key=None)]
+    done = srv.run(reqs)
+    by = {r.rid: r for r in done}
+    assert sorted(by) == [0, 1, 2]
+    assert by[1].status == REJECTED_FOOTPRINT and by[1].cycles == -1
+    assert by[0].status == 0 and by[2].status == 0
+    assert all(H.n != 129 for H in be.created)
+    assert summarize(done)["rejected"] == 1
+
+
+def test_pool_keeps_hierarchies_of_different_domain_lengths_apart():
+    """Two requests of the same grid size on domains of different edge length
+    need different mesh widths, so they are never served by one pooled
+    hierarchy (the fake backend asserts the length at every begin)."""
+    be = FakeBackend()
+    srv = Server(be, hbm_budget=10 ** 9, max_active=1, clock=FakeClock(), idle_sleep=0)
+    import math
+    reqs = [Request(rid=i, n=33, arrival=0.001 * i, key=("L", 1.0 if i % 2 == 0 else math.pi)) for i in range(6)]
+    done = srv.run(reqs)
+    assert len(done) == 6 and all(r.status == 0 for r in done)
+    lengths = sorted(H.length for H in be.created)
+    assert lengths == [1.0, math.pi]
