@@ -43,7 +43,21 @@ FP64_PEAK_GOPS = 629.0   # 2 FP64 ops/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 
 # Hessian 6 x 4 B, rhs 4 B, e read 4 B and written 4 B (each e value read
 # once per sweep for the stencils, counted at its own update).
 CORR_SMOOTH_BYTES_PER_POINT = 36
-HBM_PEAK_GBS = 6663.9    # MEASURED_PEAKS.json hbm_gbs (copy bandwidth)
+# HBM roofline denominator: the copy bandwidth measured on this GPU model
+# (hbm_gbs of MEASURED_PEAKS.json at the repository root, written by the
+# measurement of the pool's peaks); 6800 GB/s, an earlier GB300 measurement,
+# when that file is absent.
+HBM_PEAK_FALLBACK_GBS = 6800.0
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"
+    except (OSError, KeyError, ValueError, TypeError):
+        return HBM_PEAK_FALLBACK_GBS, "fallback (6.8 TB/s, an earlier GB300 copy measurement)"
+
+
 # FP32 correction V-cycles per outer iteration of the single mixed solves
 # (129^3 and up): with 2 the FP64 residual checks the stopping rule every two
 # cycles, which ends a solve nearer the cycle that reaches the tolerance and
@@ -69,9 +83,13 @@ def parse():
     ap.add_argument("--problem", default="exp")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--serve-requests", type=int, default=2000)
-
-
-    return ap.parse_args()
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="host threads of the oracle (cpu_baseline and --impl reference); 0 = all cores")
+    args = ap.parse_args()
+    if args.cpu_threads > 0:
+        # read by the oracle's OpenMP runtime when the library is first loaded
+        os.environ["OMP_NUM_THREADS"] = str(args.cpu_threads)
+    return args
 
 
 class ClockSampler:
@@ -119,31 +137,29 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample(pr, tol, problem_cycles=None):
-    """Time the CPU oracle on the benchmark grid: FMG (tricubic, as the GPU
-    solve) + one V-cycle + residual,
-    extrapolated to a full solve with the oracle's own cycle count (measured on
-    the same problem at 65^3; V-cycle counts are mesh-independent)."""
-    import numpy as np
+def oracle_solve(pr, tol):
+    """One complete oracle solve of the benchmark workload, timed: FMG with
+    tricubic interpolation (Algorithm 2, as the GPU solve), then FAS V(2,2)
+    cycles (Algorithm 1) until the relative max-norm residual is <= tol
+    (full weighting, 3^3 coarsest grid, ascending 8-colour Gauss-Seidel), on
+    the host cores (OpenMP within a colour; OMP_NUM_THREADS sets how many)."""
     from oracle import oracle as O
-    if problem_cycles is None:
-        from paper_1411_7018_gb300 import problems
-        small = problems.make(pr.name, 65)
-        u = small.initial()
-        problem_cycles = O.solve(u, small.f, small.h, tol=tol, params=O.Params(fmg_interp=O.FMG_CUBIC)).cycles
     u = pr.initial()
     t0 = time.perf_counter()
-    O.fmg(u, pr.f, pr.h, params=O.Params(fmg_interp=O.FMG_CUBIC))
-    t1 = time.perf_counter()
-    O.vcycle(u, pr.f, pr.h, 1)
-    r = O.residual(u, pr.f, pr.h)
-    O.norm(r, pr.h)
-    t2 = time.perf_counter()
-    est = (t1 - t0) + problem_cycles * (t2 - t1)
-    return {"value": pr.unknowns / est, "unit": "unknowns/s", "cores": O.max_threads(), "kind": "oracle",
-            "sample": (f"oracle FMG + 1 V-cycle + residual on the {pr.n}^3 grid ({t2 - t0:.1f} s), "
-                       f"extrapolated to {problem_cycles} V-cycles (the oracle's count at 65^3)"),
-            "est_solve_s": est, "cycles": problem_cycles}
+    info = O.solve(u, pr.f, pr.h, tol=tol, max_cycles=30, params=O.Params(fmg_interp=O.FMG_CUBIC))
+    secs = time.perf_counter() - t0
+    return {"s": secs, "cycles": info.cycles, "residual": float(info.res_hist[-1]), "cores": O.max_threads()}
+
+
+def oracle_baseline(pr, tol):
+    """cpu_baseline: one measured oracle solve of the same workload (about
+    20 s on 16 Grace cores at 257^3)."""
+    r = oracle_solve(pr, tol)
+    return {"value": pr.unknowns / r["s"], "unit": "unknowns/s", "cores": r["cores"], "kind": "oracle",
+            "sample": (f"one complete oracle solve of the {pr.n}^3 workload, measured: tricubic FMG + "
+                       f"{r['cycles']} V(2,2) cycles to relative residual {r['residual']:.2e} "
+                       f"(tol {tol:g}) in {r['s']:.1f} s on {r['cores']} host threads"),
+            "solve_s": r["s"], "cycles": r["cycles"], "residual": r["residual"]}
 
 
 def workload_config(args, world: int = 1) -> dict:
@@ -158,34 +174,52 @@ def workload_config(args, world: int = 1) -> dict:
             "l2": "working set larger than L2 (no flush needed)"}
 
 
+# Wall-clock budget of the reference arm's timed solves: each step is one
+# complete oracle solve (about 20 s at 257^3 on 16 cores), so the arm times as
+# many of the requested steps as fit, at least one, and reports that count.
+REFERENCE_BUDGET_S = 150.0
+
+
 def run_reference(args):
+    """The oracle arm: every timed step is one complete, measured oracle solve
+    of the benchmark workload on the host cores.  Warm-up is one solve of the
+    same problem on a 33^3 grid (loads the library, faults in its code).
+    Steps beyond the time budget are not run; `steps` is the number timed and
+    `steps_requested` the number asked for."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_1411_7018_gb300 import problems
     pr = problems.make(args.problem, args.n)
-    samples = []
-    for _ in range(args.warmup):
-        oracle_sample(pr, args.tol, problem_cycles=None if not samples else samples[-1]["cycles"])
-    cyc = None
-    vals = []
+    warm = min(args.warmup, 1)
+    for _ in range(warm):
+        oracle_solve(problems.make(args.problem, 33), args.tol)
+    runs = []
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        s = oracle_sample(pr, args.tol, problem_cycles=cyc)
-        cyc = s["cycles"]
-        vals.append(s["est_solve_s"])
+    while len(runs) < max(1, args.steps):
+        runs.append(oracle_solve(pr, args.tol))
+        if time.perf_counter() - t0 + runs[-1]["s"] > REFERENCE_BUDGET_S:
+            break
     wall = time.perf_counter() - t0
-    ms = 1e3 * statistics.mean(vals)
+    ms = 1e3 * statistics.mean(r["s"] for r in runs)
     value = pr.unknowns / (ms / 1e3)
+    last = runs[-1]
+    sample = (f"{len(runs)} complete oracle solve(s) of the {pr.n}^3 workload, each measured: tricubic FMG + "
+              f"{last['cycles']} V(2,2) cycles to relative residual {last['residual']:.2e} (tol {args.tol:g}), "
+              f"{ms / 1e3:.1f} s per solve on {last['cores']} host threads")
     line = {"impl": "reference", "metric": "unknowns solved to tolerance per second", "value": value,
-            "unit": "unknowns/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "unit": "unknowns/s", "n_gpus": args.gpus, "steps": len(runs), "warmup": warm,
+            "steps_requested": args.steps, "warmup_requested": args.warmup,
+            "steps_note": (f"each step is one complete solve (~{ms / 1e3:.0f} s); the steps that fit a "
+                           f"{REFERENCE_BUDGET_S:.0f} s budget were timed"),
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": workload_config(args),
-            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": s["cores"], "kind": "oracle",
-                             "sample": s["sample"]},
+            "cpu_baseline": {"value": value, "unit": "unknowns/s", "cores": last["cores"], "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "unknowns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": wall}
+            "cycles_per_solve": last["cycles"], "residual": last["residual"],
+            "solve_s": [r["s"] for r in runs], "wall_s": wall}
     print(json.dumps(line), flush=True)
 
 
@@ -405,12 +439,15 @@ def bench_serving(args, M, problems, dev):
                                                      device=dev)
     torch.cuda.synchronize()
     out = {"offered_req_s": 200.0, "sizes": list(sizes), "tol": 1e-8,
-           "note": "200 req/s of this size mix exceeds one GPU's capacity, so latency there is mostly "
-                   "queueing; the *_60 runs offer 60 req/s"}
-    runs = (("mixed_continuous", M.MA_MIXED, args.serve_requests, 32, 200.0),
-            ("fp64_one_at_a_time", M.MA_FP64, max(50, args.serve_requests // 8), 1, 200.0),
-            ("mixed_continuous_60", M.MA_MIXED, max(100, args.serve_requests // 2), 32, 60.0),
-            ("fp64_one_at_a_time_60", M.MA_FP64, max(50, args.serve_requests // 8), 1, 60.0))
+           "note": "the *_60 runs offer 60 req/s to both arms with the same requests (the latency comparison); "
+                   "200 req/s of this size mix exceeds one GPU's capacity, so latency there is mostly queueing"}
+    # the 60 req/s pair is the latency comparison (both arms serve the same
+    # requests); at 200 req/s the FP64 arm is far beyond its capacity, so it
+    # serves a shorter prefix of the stream and its latency is queueing
+    runs = (("mixed_continuous_60", M.MA_MIXED, max(100, args.serve_requests // 2), 32, 60.0),
+            ("fp64_one_at_a_time_60", M.MA_FP64, max(100, args.serve_requests // 2), 1, 60.0),
+            ("mixed_continuous", M.MA_MIXED, args.serve_requests, 32, 200.0),
+            ("fp64_one_at_a_time", M.MA_FP64, max(50, args.serve_requests // 8), 1, 200.0))
     for label, precision, count, max_active, rate in runs:
         be = serve.LibmaBackend(precision, inputs, device=dev)
         srv = serve.Server(be, hbm_budget=48 << 30, max_active=max_active)
@@ -428,6 +465,8 @@ def bench_serving(args, M, problems, dev):
         out[label] = summ
     out["unknowns_per_s_mixed_vs_fp64"] = (out["mixed_continuous"]["unknowns_per_s"]
                                           / out["fp64_one_at_a_time"]["unknowns_per_s"])
+    out["latency_60_req_s"] = {k: {q: out[f"{k}_60"][q] for q in ("requests", "p50_ms", "p99_ms", "unknowns_per_s")}
+                               for k in ("mixed_continuous", "fp64_one_at_a_time")}
     return out
 
 
@@ -574,14 +613,10 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        fd = f_host.to(dev, non_blocking=True)
-        gd = g_host.to(dev, non_blocking=True)
-        H.set_rhs_bc(fd, gd)
+        # the C ABI's host-buffer calls: f, g in and u out over PCIe/C2C
+        H.set_rhs_bc_host(f_host, g_host)
         H.solve(tol=args.tol, max_cycles=60)
-        ud = torch.empty_like(fd)
-        H.get_solution(ud)
-        u_host.copy_(ud, non_blocking=True)
-        torch.cuda.synchronize()
+        H.get_solution_host(u_host)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
     for H in hier.values():
@@ -597,7 +632,8 @@ def main():
             except Exception as exc:   # reported, not fatal: the headline line still prints
                 extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
             torch.cuda.empty_cache()
-    cpu = oracle_sample(pr, args.tol) if (rank == 0 and world == 1) else None
+    cpu = oracle_baseline(pr, args.tol) if (rank == 0 and world == 1) else None
+    peak_gbs, peak_src = hbm_peak()
     if rank == 0:
         line = {
             "metric": "unknowns solved to tolerance per second",
@@ -612,13 +648,13 @@ def main():
             "accuracy": {"max_err_vs_exact_mixed": err["mixed"], "max_err_vs_exact_fp64": err["fp64"],
                          "max_rel_diff_mixed_vs_fp64": diff},
             "roofline": {"bound": "hbm", "kernel": corr_kernel,
-                         "achieved": corr_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                         "frac": corr_gbs / HBM_PEAK_GBS,
+                         "achieved": corr_gbs, "peak": peak_gbs, "unit": "GB/s",
+                         "frac": corr_gbs / peak_gbs,
                          "traffic": CORR_SMOOTH_TRAFFIC_257.get(corr_choice) if n == 257 else None,
                          "traffic_note": (f"ncu dram bytes per launch, warm L2; algorithmic 36 B x (n-2)^3/"
                                           f"{corr_launches} = {36 * (n - 2) ** 3 / corr_launches / 1e6:.0f} MB"),
                          "launch_ms": corr_launch_ms, "bytes_per_point": CORR_SMOOTH_BYTES_PER_POINT,
-                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"},
+                         "peak_source": peak_src},
             "roofline_fp64_smoother": {"bound": "alu", "kernel": "k_smooth_colour (FP64 smoother, one colour phase)",
                                        "achieved": f64_gops, "peak": FP64_PEAK_GOPS, "unit": "GFP64op/s",
                                        "frac": f64_gops / FP64_PEAK_GOPS, "launch_ms": f64_launch_ms,

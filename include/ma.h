@@ -145,6 +145,14 @@ ma_status ma_create_hierarchy(const ma_hier_desc *desc, void *dev_workspace, siz
  * reaches this point.  Checks f > 0 on the device and blocks for that check. */
 ma_status ma_set_rhs_bc(ma_hierarchy *h, const double *f_dev, const double *g_dev);
 
+/* ma_set_rhs_bc with f and g in HOST memory (n^3 doubles each, [k][j][i]),
+ * for callers whose data live on the host: both are copied to the device on
+ * the hierarchy's stream (into the fine level's scratch fields), then checked
+ * and moved into place as above.  Blocks for the check, so the host buffers
+ * may be reused on return.  Page-locked (pinned) buffers make the copies
+ * asynchronous DMA; pageable ones work but are staged by the driver. */
+ma_status ma_set_rhs_bc_host(ma_hierarchy *h, const double *f_host, const double *g_host);
+
 /* ncycles FAS V-cycles (Algorithm 1) on the finest level.  Asynchronous. */
 ma_status ma_vcycle(ma_hierarchy *h, int ncycles);
 
@@ -236,6 +244,11 @@ ma_status ma_residual_norm(ma_hierarchy *h, int norm, double *out);
 /* Copy the current fine-level iterate (n^3 doubles, shell included) to u_dev.
  * Asynchronous. */
 ma_status ma_get_solution(ma_hierarchy *h, double *u_dev);
+
+/* Copy the current fine-level iterate (n^3 doubles, shell included) to HOST
+ * memory u_host.  Blocks until the copy has landed (pinned memory makes it a
+ * direct DMA). */
+ma_status ma_get_solution_host(ma_hierarchy *h, double *u_host);
 
 /* Replace the current fine-level iterate (shell included) from u_dev
  * (checkpoint/restart).  Asynchronous. */

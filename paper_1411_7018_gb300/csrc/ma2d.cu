@@ -703,7 +703,9 @@ ma_status ma2d_solve(ma2d_hierarchy* H, const ma_solve_opts* o, ma_solve_result*
     double rel = (o->norm == MA_NORM_MAX ? mx : l2) / scale;
     res->res0 = rel;
     int stagnant = 0;
-    while (std::isfinite(rel) && rel > o->tol && res->cycles < o->max_cycles && stagnant < 3) {
+    // the max norm folds with fmax, which skips NaN entries; the L2 norm's
+    // sum of squares does not, so both are checked
+    while (std::isfinite(rel) && std::isfinite(l2) && rel > o->tol && res->cycles < o->max_cycles && stagnant < 3) {
         CK2(vcycle2_from(H, 0));
         res->cycles += 1;
         if ((st = fine_norms2(H, 0, &mx, &l2)) != MA_OK) return st;
@@ -712,7 +714,7 @@ ma_status ma2d_solve(ma2d_hierarchy* H, const ma_solve_opts* o, ma_solve_result*
         rel = nrel;
     }
     res->res = rel;
-    if (!std::isfinite(rel)) res->status = MA_ERR_NONFINITE;
+    if (!std::isfinite(rel) || !std::isfinite(l2)) res->status = MA_ERR_NONFINITE;
     else if (rel <= o->tol) res->status = MA_OK;
     else {
         res->status = MA_ERR_NOT_CONVERGED;

@@ -585,6 +585,30 @@ ma_status ma_set_rhs_bc(ma_hierarchy* H, const double* f_dev, const double* g_de
     return MA_OK;
 }
 
+// Host-buffer variants: the inputs land in the fine level's residual and
+// coarse-approximation fields (n^3 doubles each, scratch until the next cycle
+// overwrites them), and the same validating copy kernel moves them into place.
+ma_status ma_set_rhs_bc_host(ma_hierarchy* H, const double* f_host, const double* g_host)
+{
+    if (!H || !f_host || !g_host) return fail(MA_ERR_INVALID_ARG, "null argument");
+    DeviceGuard g(H->device);
+    ma::Level& F = H->lev[0];
+    const size_t bytes = (size_t)F.n * F.n * F.n * sizeof(double);
+    MA_CK(cudaMemcpyAsync(F.r, f_host, bytes, cudaMemcpyHostToDevice, H->s));
+    MA_CK(cudaMemcpyAsync(F.w, g_host, bytes, cudaMemcpyHostToDevice, H->s));
+    return ma_set_rhs_bc(H, F.r, F.w);
+}
+
+ma_status ma_get_solution_host(ma_hierarchy* H, double* u_host)
+{
+    if (!H || !u_host) return fail(MA_ERR_INVALID_ARG, "null argument");
+    DeviceGuard g(H->device);
+    const size_t pts = (size_t)H->d.n * H->d.n * H->d.n;
+    MA_CK(cudaMemcpyAsync(u_host, H->lev[0].u, pts * sizeof(double), cudaMemcpyDeviceToHost, H->s));
+    MA_CK(cudaStreamSynchronize(H->s));
+    return MA_OK;
+}
+
 ma_status ma_vcycle(ma_hierarchy* H, int ncycles)
 {
     if (!H || ncycles < 0) return fail(MA_ERR_INVALID_ARG, "bad arguments");
@@ -765,8 +789,11 @@ static bool absorb_norms(ma_hierarchy* H)
         H->sv.rel = nrel;
     }
     const double rel = H->sv.rel;
+    // The max norm folds with fmax, which skips NaN entries; the sum of
+    // squares behind the L2 norm does not, so both are checked.
+    const bool finite = std::isfinite(rel) && std::isfinite(H->host[0]) && std::isfinite(H->host[1]);
     int out = -1;
-    if (!std::isfinite(rel)) out = MA_ERR_NONFINITE;
+    if (!finite) out = MA_ERR_NONFINITE;
     else if (rel <= o.tol) out = MA_OK;
     else if (r.cycles >= o.max_cycles) out = MA_ERR_NOT_CONVERGED;
     else if (H->sv.stagnant >= 3) {

@@ -58,6 +58,7 @@ _SIGS = {
     "ma_hierarchy_footprint": [C.POINTER(ma_hier_desc), C.POINTER(C.c_size_t)],
     "ma_create_hierarchy": [C.POINTER(ma_hier_desc), _vp, C.c_size_t, _vp, C.POINTER(_vp)],
     "ma_set_rhs_bc": [_vp, _vp, _vp],
+    "ma_set_rhs_bc_host": [_vp, _vp, _vp],
     "ma_vcycle": [_vp, C.c_int],
     "ma_solve": [_vp, C.POINTER(ma_solve_opts), C.POINTER(ma_solve_result)],
     "ma_solve_begin": [_vp, C.POINTER(ma_solve_opts)],
@@ -72,6 +73,7 @@ _SIGS = {
     "ma_set_batch_start": [C.c_int],
     "ma_residual_norm": [_vp, C.c_int, C.POINTER(C.c_double)],
     "ma_get_solution": [_vp, _vp],
+    "ma_get_solution_host": [_vp, _vp],
     "ma_set_solution": [_vp, _vp],
     "ma_hierarchy_info": [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)],
     "ma_destroy_hierarchy": [_vp],
@@ -152,6 +154,18 @@ def _ptr(x) -> int | None:
     return x.data_ptr()
 
 
+def _host_ptr(x) -> int:
+    """Host address of a contiguous CPU float64 array (numpy array or torch
+    tensor, pinned or pageable)."""
+    if hasattr(x, "is_cuda"):
+        if x.is_cuda or not x.is_contiguous() or x.element_size() != 8:
+            raise ValueError("expected a contiguous CPU float64 tensor")
+        return x.data_ptr()
+    if not (x.flags["C_CONTIGUOUS"] and x.dtype.itemsize == 8):
+        raise ValueError("expected a C-contiguous float64 array")
+    return x.ctypes.data
+
+
 def _stream(s) -> int | None:
     if s is None:
         import torch
@@ -177,6 +191,11 @@ def ma_create_hierarchy(desc: ma_hier_desc, workspace, nbytes: int, stream=None)
 
 def ma_set_rhs_bc(hier: int, f, g) -> None:
     _check(load().ma_set_rhs_bc(hier, _ptr(f), _ptr(g)))
+
+
+def ma_set_rhs_bc_host(hier: int, f, g) -> None:
+    """f and g in host memory (numpy arrays or CPU tensors, n^3 float64)."""
+    _check(load().ma_set_rhs_bc_host(hier, _host_ptr(f), _host_ptr(g)))
 
 
 def ma_vcycle(hier: int, ncycles: int = 1) -> None:
@@ -263,6 +282,11 @@ def ma_residual_norm(hier: int, norm: int = MA_NORM_MAX) -> float:
 
 def ma_get_solution(hier: int, u) -> None:
     _check(load().ma_get_solution(hier, _ptr(u)))
+
+
+def ma_get_solution_host(hier: int, u) -> None:
+    """u in host memory (numpy array or CPU tensor, n^3 float64); blocks."""
+    _check(load().ma_get_solution_host(hier, _host_ptr(u)))
 
 
 def ma_set_solution(hier: int, u) -> None:
@@ -526,6 +550,9 @@ class Hierarchy:
     def set_rhs_bc(self, f, g):
         ma_set_rhs_bc(self.handle, f, g)
 
+    def set_rhs_bc_host(self, f, g):
+        ma_set_rhs_bc_host(self.handle, f, g)
+
     def vcycle(self, ncycles: int = 1):
         ma_vcycle(self.handle, ncycles)
 
@@ -542,6 +569,9 @@ class Hierarchy:
 
     def get_solution(self, u):
         ma_get_solution(self.handle, u)
+
+    def get_solution_host(self, u):
+        ma_get_solution_host(self.handle, u)
 
     def set_solution(self, u):
         ma_set_solution(self.handle, u)

@@ -111,6 +111,160 @@ def test_correction_sweep_matches_oracle_sweep(name, n, amp, pairs):
     assert np.max(np.abs(got - e_ref)) <= 1e-3 * change + 1e-6 * np.max(np.abs(e_ref))
 
 
+# ---- large corrections: a bound derived from the FP32 rounding model ----------
+#
+# The kernel and the oracle solve the same point equation
+#     det(B + K - z I) - det(B) = r,   e_new = e_old + h^2 z / 2,
+# with B = D^2_h u, K = D^2_h e; the oracle in FP64 on w = u + e, the kernel
+# in FP32 with B from the FP32 hi/lo split of u.  The inputs e are the same
+# FP32 values on both sides.  To first order the kernel's root differs from
+# the oracle's by
+#   dz = [ tr((cof G_z - cof B) dB) + tr(cof(G_z) dK) + dF ] / M(G_z),
+# G_z = B + K - z I at the root, M = tr cof G_z = -dF/dz, where
+#   dB, dK: FP32 rounding of the second differences, at most
+#           4 u (sum of |first differences| / h^2 + |entry|) per entry
+#           (u = 2^-24; the split's hi differences, the lo part, two sums and
+#           the 1/h^2 scaling each round once);
+#   dF:     FP32 evaluation of F = c - M z + T z^2 - z^3 with
+#           c = tr(cof(B)K) + tr(B cof K) + det K - r: at most 16 u times the
+#           sum of the magnitudes of its terms, plus 1e-7 |z| for the
+#           Newton stop (a step <= 1e-4 |z| leaves ~(1e-4)^2 |z|).
+# e_new adds one FP32 rounding, u |e_new|.  Within a sweep a point reads the
+# new values of the colours before it, so their errors enter its K: with
+# weights |cof_qq| / (2|M|) per face neighbour and |cof_pq| / (4|M|) per edge
+# neighbour (the linearised update).  The bound D is propagated colour by
+# colour in the sweep's order, with G_z taken at the moment of the update
+# (the oracle's new values on the colours already swept, the old ones
+# elsewhere), and the test allows 2 D for the first-order approximation.
+
+_U32 = 2.0 ** -24
+_SYM = np.array([1.0, 1.0, 1.0, 2.0, 2.0, 2.0])   # off-diagonal entries count twice
+_FACES = [((0, 0, 1), 0), ((0, 0, -1), 0), ((0, 1, 0), 1), ((0, -1, 0), 1), ((1, 0, 0), 2), ((-1, 0, 0), 2)]
+_EDGES = ([((0, s, t), 3) for s in (1, -1) for t in (1, -1)] + [((s, 0, t), 4) for s in (1, -1) for t in (1, -1)]
+          + [((s, t, 0), 5) for s in (1, -1) for t in (1, -1)])
+
+
+def _cof6(A):
+    xx, yy, zz, xy, xz, yz = A
+    return np.stack([yy * zz - yz * yz, xx * zz - xz * xz, xx * yy - xy * xy,
+                     xz * yz - xy * zz, xy * yz - xz * yy, xy * xz - xx * yz])
+
+
+def _shift(a, off):
+    """a at interior point + off (zero on the shell)."""
+    dk, dj, di = off
+    n = a.shape[0]
+    out = np.zeros_like(a)
+    out[1:-1, 1:-1, 1:-1] = a[1 + dk:n - 1 + dk, 1 + dj:n - 1 + dj, 1 + di:n - 1 + di]
+    return out
+
+
+def _diff_sums(v, h):
+    """Per Hessian entry, the sum of |v(neighbour) - v(centre)| that enters it,
+    scaled as the entry (1/h^2 faces, 1/(4 h^2) edges)."""
+    out = np.zeros((6,) + v.shape)
+    for off, q in _FACES:
+        out[q] += np.abs(_shift(v, off) - v) / h ** 2
+    for off, q in _EDGES:
+        out[q] += np.abs(_shift(v, off) - v) / (4 * h ** 2)
+    out[:, 0], out[:, -1], out[:, :, 0], out[:, :, -1], out[:, :, :, 0], out[:, :, :, -1] = 0, 0, 0, 0, 0, 0
+    return out
+
+
+def correction_sweep_bound(u, e, e_ref, rhs, h, order):
+    """Per-point bound D on |kernel - oracle| after one correction sweep in
+    the colour order `order` (see the derivation above)."""
+    n = u.shape[0]
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    colour = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2)
+    interior = np.zeros((n,) * 3, bool)
+    interior[1:-1, 1:-1, 1:-1] = True
+    e64 = e.astype(np.float64)
+    B = O.discrete_hessian(np.ascontiguousarray(u), h)
+    cB = _cof6(B)
+    dB = 4 * _U32 * (_diff_sums(u, h) + np.abs(B))
+    z = 2 * (e_ref - e64) / h ** 2
+    D = np.zeros((n,) * 3)
+    done = np.zeros((n,) * 3, bool)
+    for c in order:
+        m = (colour == c) & interior
+        before = np.where(done, e_ref, e64)
+        at = np.where(done | m, e_ref, e64)
+        Y = O.discrete_hessian(np.ascontiguousarray(at), h)
+        K0 = O.discrete_hessian(np.ascontiguousarray(before), h)
+        cG = _cof6(B + Y)
+        aM = np.where(m, np.abs(cG[0] + cG[1] + cG[2]), 1.0)
+        dK = 4 * _U32 * (_diff_sums(at, h) + np.abs(Y))
+        zB = (_SYM[:, None, None, None] * np.abs(cG - cB) * dB).sum(0) / aM
+        zK = (_SYM[:, None, None, None] * np.abs(cG) * dK).sum(0) / aM
+        bm, km, gm = np.abs(B).max(0), np.abs(K0).max(0), np.abs(B + K0).max(0)
+        terms = (18 * (bm * bm * km + bm * km * km + km ** 3) + np.abs(rhs)
+                 + 3 * gm * gm * np.abs(z) + 3 * gm * z * z + np.abs(z) ** 3)
+        zF = 16 * _U32 * terms / aM + 1e-7 * np.abs(z)
+        own = h * h / 2 * (zB + zK + zF) + _U32 * np.abs(e_ref)
+        prop = np.zeros((n,) * 3)
+        for off, q in _FACES:
+            prop += np.abs(cG[q]) / (2 * aM) * _shift(D, off)
+        for off, q in _EDGES:
+            prop += np.abs(cG[q]) / (4 * aM) * _shift(D, off)
+        D = np.where(m, own + prop, D)
+        done |= m
+    return D
+
+
+@pytest.mark.parametrize("pairs", [False, True])
+@pytest.mark.parametrize("name,n,kamp,nonconvex", [("exp", 33, 1.5, False), ("exp", 45, 1.5, False),
+                                                   ("cosine", 65, 0.5, False), ("exp", 71, 1.0, False),
+                                                   ("exp", 33, 0.5, True), ("cosine", 65, 0.5, True)])
+def test_correction_sweep_large_corrections_match_oracle_within_derived_bound(name, n, kamp, nonconvex, pairs):
+    """One correction sweep far from convergence, against the oracle's
+    Gauss-Seidel sweep on w = u + e (right-hand side det(D^2_h u) + rhs),
+    element by element within the bound derived above: a rough e whose
+    K = D^2_h e is as large as B (G = B + K indefinite at many points, so the
+    FP64 fallback runs), rhs = 1e-2 f, and with `nonconvex` 2 % of scattered
+    points at rhs = -2 f, where det(B) + rhs <= 0 takes the smallest-real-
+    root branch; the count of those updates equals the oracle's.  Sizes with
+    several blocks per colour box and ragged last blocks (45, 71)."""
+    pr = P.make(name, n, seed=4)
+    u, h = pr.u, pr.h
+    rng = np.random.default_rng(n)
+    Bd = O.discrete_hessian(u, h)
+    scale = np.median(np.abs(Bd[:3, 1:-1, 1:-1, 1:-1]))
+    e = np.zeros(u.shape, dtype=np.float32)
+    e[1:-1, 1:-1, 1:-1] = (kamp * h * h * scale / 4 * rng.standard_normal((n - 2,) * 3)).astype(np.float32)
+    rhs = (1e-2 * rng.standard_normal(u.shape) * pr.f).astype(np.float32)
+    if nonconvex:
+        pick = rng.random(u.shape) < 0.02
+        rhs[pick] = (-2.0 * pr.f[pick]).astype(np.float32)
+    rhs[0], rhs[-1], rhs[:, 0], rhs[:, -1], rhs[:, :, 0], rhs[:, :, -1] = 0, 0, 0, 0, 0, 0
+    K = O.discrete_hessian(e.astype(np.float64), h)
+    assert np.abs(K).max() >= 0.3 * np.abs(Bd).max()
+    order = (0, 7, 1, 6, 2, 5, 3, 4) if pairs else tuple(range(8))
+    w = np.ascontiguousarray(u + e.astype(np.float64))
+    ftot = O.discrete_ma(u, h) + rhs.astype(np.float64)
+    ev_ref = O.gs_sweep(w, ftot, h, O.COLOUR8_PAIRS if pairs else O.COLOUR8)
+    e_ref = w - u
+    hi, lo = split(u)
+    ed = dev(e)
+    ev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    _keep, scr, nb = M.correction_scratch(n)
+    try:
+        M.ma_set_corr_tuning(n, M.MA_CORR_PAIRS if pairs else M.MA_CORR_BY_COLOUR, -1)
+        M.ma_smooth_correction(ed, dev(hi), dev(lo), dev(rhs), n, h, 1, scr, nb, events=ev)
+        got = host(ed).astype(np.float64)
+    finally:
+        M.ma_set_corr_tuning(n, -1, -1)
+    assert int(ev.item()) == ev_ref and (ev_ref > 0) == nonconvex
+    D = correction_sweep_bound(u, e, e_ref, rhs, h, order)
+    err = np.abs(got - e_ref)
+    change = np.max(np.abs(e_ref - e.astype(np.float64)))
+    worst = np.unravel_index(np.argmax(err - 2 * D), err.shape)
+    assert np.all(err <= 2 * D), (f"max err {err.max():.3e} (change {change:.3e}); at {worst}: "
+                                  f"err {err[worst]:.3e} > 2 D = {2 * D[worst]:.3e}")
+    # the bound is tight enough to mean something: far below the sweep's change
+    assert 2 * D.max() <= 2e-3 * change
+
+
 @pytest.mark.parametrize("name,n", [("exp", 33), ("cosine", 129), ("exp", 257), ("exp", 37), ("cosine", 71),
                                     ("exp", 135)])   # ragged last tiles for every tile size
 def test_plane_sweeps_equal_colour_sweeps_bitwise(name, n):
