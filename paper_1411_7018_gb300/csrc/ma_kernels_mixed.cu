@@ -118,10 +118,15 @@ __device__ __forceinline__ float delta_det(const S3f& B, const S3f& K)
 // Smallest-root update of the correction problem at one point, z with
 // e_new = e0 + h^2 z / 2.  Fast path: FP32 Newton on
 // F(z) = det(G - zI) - det(B) - r from z = 0 (its first step is z = F(0) / M)
-// when G = B + K is positive definite and not near-degenerate; it stops once
-// a step is at most 1e-4 |z|: Newton converges quadratically there, so the
-// step just taken leaves an error of order (1e-4)^2 |z|, below FP32
-// resolution.  Returns false (z unset) when the point needs the FP64 path.
+// when G = B + K is positive definite and not near-degenerate, and the
+// target det(B) + r = det(G) - F(0) is clearly positive (Theorem 2.2: then F
+// is decreasing and convex left of the smallest eigenvalue of G, which lies
+// right of z = 0, and has its one root there; with a target <= 0 Eq.
+// (realroots) asks for the smallest real root elsewhere, which only the FP64
+// path finds and counts).  It stops once a step is at most 1e-4 |z|: Newton
+// converges quadratically there, so the step just taken leaves an error of
+// order (1e-4)^2 |z|, below FP32 resolution.  Returns false (z unset) when
+// the point needs the FP64 path.
 __device__ __forceinline__ bool corr_root_fast(const S3f& B, const S3f& K, float r, float* zout)
 {
     S3f G;
@@ -131,10 +136,14 @@ __device__ __forceinline__ bool corr_root_fast(const S3f& B, const S3f& K, float
     const float T = G.xx + G.yy + G.zz;
     const float m2 = mdiff(G.xx, G.yy, G.xy, G.xy);
     const float M = m2 + mdiff(G.xx, G.zz, G.xz, G.xz) + mdiff(G.yy, G.zz, G.yz, G.yz);
-    const bool pd = G.xx > 0.0f && m2 > 0.0f && det3(G) > 0.0f;
+    const float dG = det3(G);
+    const bool pd = G.xx > 0.0f && m2 > 0.0f && dG > 0.0f;
     // with a positive diagonal, |G| summed entrywise is T + |off-diagonals|
     const float scale = T + fabsf(G.xy) + fabsf(G.xz) + fabsf(G.yz);
     if (!(pd && M > 0.05f * (scale * scale))) return false;
+    // the target det(B) + r, far enough above 0 that FP32 rounding of the
+    // two determinants cannot flip its sign (margin 1e-5 scale^3)
+    if (!(dG - c > 1e-5f * (scale * scale * scale))) return false;
     // F(z) = c - z M + z^2 T - z^3 = c - z (M - z (T - z));  M(z) = -F'(z)
     float z = __fdividef(c, M);
     const float T2 = 2.0f * T;
@@ -334,12 +343,17 @@ __global__ void __launch_bounds__(BX * BY) k_to_cm(const float* __restrict__ nat
 // B and rhs boxes; e is in the natural layout (19-point stencil).  Idx is int
 // for grids up to 1289^3 (32-bit index arithmetic), long long above.  The
 // point solve is latency-bound, so the launch bounds ask for 12 resident
-// blocks per SM (40 registers, no spills; 14 would spill).
-template <int PI, int PJ, int PK, typename Idx>
+// blocks per SM (40 registers, no spills; 14 would spill).  NN > 0 fixes the
+// grid size at compile time (n = NN): the 18 neighbour offsets and the box
+// strides become constants, so each load is one instruction with an
+// immediate offset instead of an address computed per load; the arithmetic
+// of a point is the same, and so are the bits.
+template <int PI, int PJ, int PK, typename Idx, int NN = 0>
 __device__ __forceinline__ void smooth_corr_block(float* e, const float* __restrict__ bc, const float* __restrict__ rc,
-                                                  int n, float inv_h2, float h2half, unsigned long long* events,
+                                                  int n_rt, float inv_h2, float h2half, unsigned long long* events,
                                                   uint3 bid)
 {
+    const int n = NN > 0 ? NN : n_rt;
     const int ii = bid.x * BX + threadIdx.x;
     const int jj = bid.y * BY + threadIdx.y;
     const int kk = bid.z;
@@ -401,7 +415,7 @@ cudaError_t launch_colour_corr(float* e, const float* bstore, const float* rhs_c
 // sequential sweep of colour C followed by colour C^7.  Blocks with z below
 // nk0 sweep colour C, the rest colour C^7; x and y cover the larger of the
 // two colour boxes.
-template <int C, typename Idx>
+template <int C, typename Idx, int NN = 0>
 __global__ void __launch_bounds__(BX * BY, 12) k_smooth_corr_pair(float* e, const float* __restrict__ b0,
                                                                    const float* __restrict__ r0,
                                                                    const float* __restrict__ b1,
@@ -411,11 +425,20 @@ __global__ void __launch_bounds__(BX * BY, 12) k_smooth_corr_pair(float* e, cons
     constexpr int D = C ^ 7;
     uint3 bid = blockIdx;
     if ((int)bid.z < nk0) {
-        smooth_corr_block<C & 1, (C >> 1) & 1, (C >> 2) & 1, Idx>(e, b0, r0, n, inv_h2, h2half, events, bid);
+        smooth_corr_block<C & 1, (C >> 1) & 1, (C >> 2) & 1, Idx, NN>(e, b0, r0, n, inv_h2, h2half, events, bid);
     } else {
         bid.z -= nk0;
-        smooth_corr_block<D & 1, (D >> 1) & 1, (D >> 2) & 1, Idx>(e, b1, r1, n, inv_h2, h2half, events, bid);
+        smooth_corr_block<D & 1, (D >> 1) & 1, (D >> 2) & 1, Idx, NN>(e, b1, r1, n, inv_h2, h2half, events, bid);
     }
+}
+
+// The pair launch with the grid size fixed at compile time for the sizes
+// where the sweep streams from HBM (see smooth_corr_block).
+template <int C, int NN>
+void launch_pair_fixed(dim3 grid, cudaStream_t s, float* e, const float* b0, const float* r0, const float* b1,
+                       const float* r1, float inv_h2, float h2half, unsigned long long* ev, int nk0)
+{
+    k_smooth_corr_pair<C, int, NN><<<grid, dim3(BX, BY), 0, s>>>(e, b0, r0, b1, r1, NN, inv_h2, h2half, ev, nk0);
 }
 
 template <int C>
@@ -431,6 +454,14 @@ cudaError_t launch_colour_corr_pair(float* e, const float* bstore, const float* 
     dim3 grid((ni + BX - 1) / BX, (nj + BY - 1) / BY, nk0 + nk1);
     const long long o0 = cm_offset(n, C), o1 = cm_offset(n, D);
     count_launches(1);
+    const float *b0 = bstore + 6 * o0, *r0 = rhs_cm + o0, *b1 = bstore + 6 * o1, *r1 = rhs_cm + o1;
+    switch (n) {
+    case 129: launch_pair_fixed<C, 129>(grid, s, e, b0, r0, b1, r1, inv_h2, h2half, ev, nk0); return cudaGetLastError();
+    case 257: launch_pair_fixed<C, 257>(grid, s, e, b0, r0, b1, r1, inv_h2, h2half, ev, nk0); return cudaGetLastError();
+    case 513: launch_pair_fixed<C, 513>(grid, s, e, b0, r0, b1, r1, inv_h2, h2half, ev, nk0); return cudaGetLastError();
+    case 1025: launch_pair_fixed<C, 1025>(grid, s, e, b0, r0, b1, r1, inv_h2, h2half, ev, nk0); return cudaGetLastError();
+    default: break;
+    }
     if (n <= 1289)
         k_smooth_corr_pair<C, int><<<grid, dim3(BX, BY), 0, s>>>(e, bstore + 6 * o0, rhs_cm + o0, bstore + 6 * o1,
                                                                   rhs_cm + o1, n, inv_h2, h2half, ev, nk0);
