@@ -268,6 +268,14 @@ const char *ma_last_error_string(void);
  * process so far (all devices, all hierarchies).  Host only. */
 ma_status ma_kernel_launch_count(unsigned long long *out);
 
+/* Diagnostics: the FP64 fused-multiply-add rate of the current device,
+ * measured (thread-level DFMA operations per second, one DFMA = one
+ * operation), by independent chains of DFMAs on every SM timed with CUDA
+ * events on the stream.  No counterpart in the paper: the FP64 kernels of
+ * this library are bound by the FP64 pipe, and this is their peak.  Blocks
+ * on the stream (~a millisecond). */
+ma_status ma_probe_fp64_rate(double *ops_per_s, ma_stream_t stream);
+
 /* ---- single steps on raw device grids (each row of the V-cycle) ----------
  * These run exactly the kernels a hierarchy runs, on caller arrays of one
  * level (n^3 doubles, [k][j][i]).  n must be odd and >= 3.  All are
@@ -287,6 +295,16 @@ ma_status ma_smooth(double *u_dev, const double *rhs_dev, int n, double h, int n
  * step 3, the operator of Eq. MA_discrete). */
 ma_status ma_residual(const double *u_dev, const double *rhs_dev, double *r_dev, int n, double h,
                       ma_stream_t stream);
+
+/* The same residual (Algorithm 1 step 3, Eq. MA_discrete) as the fine-grid
+ * residual of MA_MIXED solves computes it, without FP64 arithmetic: where the
+ * 19 stencil values of a point share one sign and one binade, the second
+ * differences are exact integer differences of their bit patterns, and the
+ * determinant and rhs - det are taken in two-float (hi + lo FP32)
+ * arithmetic, about 48 significant bits; elsewhere the FP64 evaluation of
+ * ma_residual.  Same layout and arguments as ma_residual; asynchronous. */
+ma_status ma_residual_f2(const double *u_dev, const double *rhs_dev, double *r_dev, int n, double h,
+                         ma_stream_t stream);
 
 /* Residual restriction r_H = I_h^H r_h (Section 3) from a fine grid of nf
  * points per side to the coarse grid of (nf+1)/2: kind MA_HALF_WEIGHTING or

@@ -15,6 +15,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ma.h"
 #include "ma_hier.h"
 #include "ma_internal.h"
@@ -462,6 +464,15 @@ ma_status fine_residual_norms(ma_hierarchy* H, double* mx, double* l2)
     return read_norms(H, mx, l2);
 }
 
+// NVTX range over a host call (visible to ncu --nvtx and other tracers;
+// a no-op unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev)
@@ -611,6 +622,7 @@ ma_status ma_get_solution_host(ma_hierarchy* H, double* u_host)
 
 ma_status ma_vcycle(ma_hierarchy* H, int ncycles)
 {
+    NvtxRange nv("ma_vcycle");
     if (!H || ncycles < 0) return fail(MA_ERR_INVALID_ARG, "bad arguments");
     DeviceGuard g(H->device);
     if (H->d.precision == MA_FP32) {
@@ -683,6 +695,7 @@ static cudaError_t queue_readback(ma_hierarchy* H)
 
 ma_status ma_solve_begin(ma_hierarchy* H, const ma_solve_opts* opts)
 {
+    NvtxRange nv("ma_solve_begin: init + first cycle");
     if (!H || !opts) return fail(MA_ERR_INVALID_ARG, "null argument");
     ma_status st = check_opts(opts);
     if (st != MA_OK) return st;
@@ -743,6 +756,7 @@ ma_status ma_solve_begin(ma_hierarchy* H, const ma_solve_opts* opts)
 // cycles + FP64 update) and the new residual norm, as one graph.
 static cudaError_t launch_cycle(ma_hierarchy* H)
 {
+    NvtxRange nv("cycle");
     const bool mixed = H->d.precision == MA_MIXED;
     return run_graph(H, H->g_cycle, [&]() -> cudaError_t {
         cudaError_t e;
@@ -850,6 +864,7 @@ ma_status ma_solve_get_result(const ma_hierarchy* H, ma_solve_result* res)
 
 ma_status ma_solve(ma_hierarchy* H, const ma_solve_opts* opts, ma_solve_result* res)
 {
+    NvtxRange nv("ma_solve");
     if (!H || !opts || !res) return fail(MA_ERR_INVALID_ARG, "null argument");
     std::memset(res, 0, sizeof *res);
     ma_status st = ma_solve_begin(H, opts);
@@ -868,6 +883,7 @@ ma_status ma_solve(ma_hierarchy* H, const ma_solve_opts* opts, ma_solve_result* 
 
 ma_status ma_batch_solve(ma_hierarchy* const* hs, int count, const ma_solve_opts* opts, ma_solve_result* results)
 {
+    NvtxRange nv("ma_batch_solve");
     if (!hs || count < 0 || !opts || (count > 0 && !results)) return fail(MA_ERR_INVALID_ARG, "null argument");
     for (int b = 0; b < count; ++b) {
         if (!hs[b]) return fail(MA_ERR_INVALID_ARG, "null hierarchy %d", b);
@@ -1180,6 +1196,7 @@ ma_status ma_create_batch(ma_hierarchy* const* hs, int count, void* dev_workspac
 
 ma_status ma_batch_run(ma_batch* B, const ma_solve_opts* opts, ma_solve_result* results)
 {
+    NvtxRange nv("ma_batch_run");
     if (!B || !opts || !results) return fail(MA_ERR_INVALID_ARG, "null argument");
     ma_status st = check_opts(opts);
     if (st != MA_OK) return st;
@@ -1346,6 +1363,14 @@ ma_status ma_residual(const double* u, const double* rhs, double* r, int n, doub
 {
     if (!u || !rhs || !r || !valid_step_grid(n) || !(h > 0.0)) return fail(MA_ERR_INVALID_ARG, "ma_residual: bad arguments");
     MA_CK(ma::launch_residual(u, rhs, r, n, h, nullptr, (cudaStream_t)stream));
+    return MA_OK;
+}
+
+ma_status ma_residual_f2(const double* u, const double* rhs, double* r, int n, double h, ma_stream_t stream)
+{
+    if (!u || !rhs || !r || !valid_step_grid(n) || !(h > 0.0))
+        return fail(MA_ERR_INVALID_ARG, "ma_residual_f2: bad arguments");
+    MA_CK(ma::launch_residual_f2(u, rhs, r, n, h, (cudaStream_t)stream));
     return MA_OK;
 }
 

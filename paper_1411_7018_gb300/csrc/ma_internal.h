@@ -27,6 +27,9 @@ cudaError_t launch_smooth(double* u, const double* rhs, int n, double h, int nsw
                           unsigned long long* events, cudaStream_t s);
 cudaError_t launch_residual(const double* u, const double* rhs, double* r, int n, double h,
                             double* partials, cudaStream_t s);
+// The same residual with exact integer second differences and a two-float
+// determinant (no FP64 arithmetic where a point's stencil lies in one binade).
+cudaError_t launch_residual_f2(const double* u, const double* rhs, double* r, int n, double h, cudaStream_t s);
 int residual_partial_count(int n);
 cudaError_t launch_norm_partials(const double* v, int n, double* partials, cudaStream_t s);
 int norm_partial_count(int n);

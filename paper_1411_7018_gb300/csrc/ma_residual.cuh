@@ -155,5 +155,268 @@ __device__ __forceinline__ void norm_final_block(const double* __restrict__ part
 
 inline dim3 grid_for(int n, int kz) { return dim3((n + RX - 1) / RX, (n + RY - 1) / RY, kz); }
 
+// ---------------------------------------------------------------------------
+// The residual without FP64 arithmetic (the fine-grid residual of the mixed
+// solve).  GB300 issues FP64 at 1/64 of its FP32 rate, which made the FP64
+// residual the second most expensive kernel of a mixed solve.  Two facts
+// take it off the FP64 pipe:
+//  * Doubles of one sign and one binade (one exponent) differ by exact
+//    integer multiples of their ulp: x - y = (bits(x) - bits(y)) 2^(E-1075)
+//    for the 64-bit patterns, negated for negative values.  When the 19
+//    stencil values of a point share the centre's binade, the six second
+//    differences of 4 h^2 D^2_h u (the sums of Eq. MA_discrete's stencil,
+//    Section 2) are formed exactly in int64 -- more accurately than the FP64
+//    gather, which rounds the sums u(x+h) + u(x-h).
+//  * The determinant and rhs - det / (64 h^6) are then evaluated in
+//    two-float arithmetic (value = hi + lo, two FP32 numbers, about 48
+//    significant bits), with Knuth's two-sum and the FMA form of Dekker's
+//    exact product: |error| of a few 2^-46 relative to the sum of the
+//    magnitudes of the determinant's terms.
+// A stencil that spans up to three binades is handled the same way with each
+// significand shifted to the smallest exponent; one whose values change sign
+// across several binades, or are zero, huge or tiny, takes the FP64
+// evaluation instead.
+// ---------------------------------------------------------------------------
+namespace f2 {
+
+struct F2 {
+    float hi, lo;
+};
+
+// a + b = s + e exactly (Knuth).
+__device__ __forceinline__ F2 two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float v = s - a;
+    return {s, (a - (s - v)) + (b - v)};
+}
+
+// a + b = s + e exactly when |a| >= |b| or a = 0 (Dekker).
+__device__ __forceinline__ F2 fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ F2 mul(F2 x, F2 y)
+{
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);   // a * b = p + e exactly
+    e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ F2 add(F2 x, F2 y)
+{
+    const F2 s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+
+__device__ __forceinline__ F2 neg(F2 x) { return {-x.hi, -x.lo}; }
+
+// Exact FP32 value of an integer y in [0, 2^23) or, for the signed form, in
+// (-2^22, 2^22): placed in the significand of 2^23 (or 1.5 * 2^23) by an
+// integer add, the constant then subtracted exactly.  Integer and FP32
+// instructions only (GB300 runs 64-bit integer conversions at its FP64 rate).
+__device__ __forceinline__ float u23_to_f(unsigned y) { return __int_as_float(0x4B000000 | (int)y) - 8388608.0f; }
+__device__ __forceinline__ float s22_to_f(int y) { return __int_as_float(0x4B400000 + y) - 12582912.0f; }
+
+// x * scale as hi + lo, |x| < 2^68 (exact to ~2^-48 relative), scale a
+// power of two: x = a 2^46 + b 2^23 + c with b, c in [0, 2^23).
+__device__ __forceinline__ F2 from_i64(long long x, float scale)
+{
+    const unsigned c = (unsigned)x & 0x7fffffu;
+    const unsigned b = (unsigned)(x >> 23) & 0x7fffffu;
+    const int a = (int)(x >> 46);
+    const F2 ab = fast_two_sum(s22_to_f(a) * 70368744177664.0f, u23_to_f(b) * 8388608.0f);   // 2^46, 2^23
+    const F2 t = two_sum(ab.hi, u23_to_f(c));
+    const F2 r = fast_two_sum(t.hi, t.lo + ab.lo);
+    return {r.hi * scale, r.lo * scale};
+}
+
+// A normal double as hi + lo (hi: its leading 24 significand bits, lo: the
+// next 23 of the remaining 29), with integer and FP32 operations only.
+__device__ __forceinline__ F2 from_f64(double x)
+{
+    const int hw = __double2hiint(x);
+    const unsigned lw = (unsigned)__double2loint(x);
+    const int ex = (hw >> 20) & 0x7ff;
+    const unsigned low29 = lw & 0x1fffffffu;
+    const float hi = d2f_trunc(x);
+    if (ex < 1075 - 126 + 6 || low29 == 0) return {hi, 0.0f};   // 2^(ex-1069) below FP32's normal range
+    const float unit = __int_as_float(((ex - 1069 + 127) << 23) | (hw & 0x80000000));   // +-2^(ex-1069)
+    return {hi, u23_to_f(low29 >> 6) * unit};   // the lo part to 23 bits: ~2^-47 of x
+}
+
+// det(H) for the symmetric 3x3 H = [[A, R, S], [R, B, T], [S, T, C]]: the
+// cofactor expansion along the first row.
+__device__ __forceinline__ F2 det3(const F2& A, const F2& B, const F2& C, const F2& R, const F2& S, const F2& T)
+{
+    const F2 c1 = add(mul(B, C), neg(mul(T, T)));
+    const F2 c2 = add(mul(R, C), neg(mul(S, T)));
+    const F2 c3 = add(mul(R, T), neg(mul(B, S)));
+    return add(add(mul(A, c1), neg(mul(R, c2))), mul(S, c3));
+}
+
+// The exact paths accept binades E with 2^(E-1075) and the cube of the
+// scaled second differences inside FP32's normal range: 2^-40 <= |u| < 2^20
+// (every grid function here lies far inside).
+constexpr int kMinE = 1023 - 40, kMaxE = 1023 + 20;
+
+}  // namespace f2
+
+// Residual rhs - det(D^2_h u) at interior point p and 4 H (H = h^2 D^2_h u)
+// for outputs that store it: value as two-float, v32 its FP32 rounding.
+struct ResF2 {
+    f2::F2 val;
+    f2::F2 H[6];   // 4 h^2 D^2_h u: xx, yy, zz, xy, xz, yz
+};
+
+__device__ __forceinline__ ResF2 residual_point_f2(const double* __restrict__ u, long long p, long long sy,
+                                                   long long sz, double rhs, f2::F2 inv_h6, double inv_h6_d)
+{
+    const long long* q = reinterpret_cast<const long long*>(u) + p;
+    const long long b0 = __ldg(q);
+    const long long bxp = __ldg(q + 1), bxm = __ldg(q - 1);
+    const long long byp = __ldg(q + sy), bym = __ldg(q - sy);
+    const long long bzp = __ldg(q + sz), bzm = __ldg(q - sz);
+    const long long rpp = __ldg(q + sy + 1), rmm = __ldg(q - sy - 1), rpm = __ldg(q + sy - 1), rmp = __ldg(q - sy + 1);
+    const long long spp = __ldg(q + sz + 1), smm = __ldg(q - sz - 1), spm = __ldg(q + sz - 1), smp = __ldg(q - sz + 1);
+    const long long tpp = __ldg(q + sz + sy), tmm = __ldg(q - sz - sy), tpm = __ldg(q + sz - sy),
+                    tmp = __ldg(q - sz + sy);
+    // one sign and one exponent: the top 12 bits of every pattern equal b0's
+    const unsigned h0 = (unsigned)(b0 >> 32);
+    unsigned diff = 0;
+#define MA_F2_CK(v) diff |= (unsigned)((v) >> 32) ^ h0
+    MA_F2_CK(bxp); MA_F2_CK(bxm); MA_F2_CK(byp); MA_F2_CK(bym); MA_F2_CK(bzp); MA_F2_CK(bzm);
+    MA_F2_CK(rpp); MA_F2_CK(rmm); MA_F2_CK(rpm); MA_F2_CK(rmp);
+    MA_F2_CK(spp); MA_F2_CK(smm); MA_F2_CK(spm); MA_F2_CK(smp);
+    MA_F2_CK(tpp); MA_F2_CK(tmm); MA_F2_CK(tpm); MA_F2_CK(tmp);
+#undef MA_F2_CK
+    const int E = (int)((h0 >> 20) & 0x7ff);
+    ResF2 out;
+    auto finish = [&](long long A, long long B, long long C, long long R, long long S, long long T, float unit) {
+        out.H[0] = f2::from_i64(A, unit);
+        out.H[1] = f2::from_i64(B, unit);
+        out.H[2] = f2::from_i64(C, unit);
+        out.H[3] = f2::from_i64(R, unit);
+        out.H[4] = f2::from_i64(S, unit);
+        out.H[5] = f2::from_i64(T, unit);
+        const f2::F2 d = f2::det3(out.H[0], out.H[1], out.H[2], out.H[3], out.H[4], out.H[5]);
+        out.val = f2::add(f2::from_f64(rhs), f2::neg(f2::mul(d, inv_h6)));
+    };
+    if ((diff >> 20) == 0 && E >= f2::kMinE && E <= f2::kMaxE) {
+        // ulp of the binade, negated for negative values
+        const float unit = __int_as_float(((E - 1075 + 127) << 23) | (int)(h0 & 0x80000000u));
+        finish(4 * ((bxp - b0) + (bxm - b0)), 4 * ((byp - b0) + (bym - b0)), 4 * ((bzp - b0) + (bzm - b0)),
+               (rpp - rmp) - (rpm - rmm), (spp - smp) - (spm - smm), (tpp - tmp) - (tpm - tmm), unit);
+        return out;
+    }
+    // The stencil spans a few binades: each value as its signed significand
+    // shifted to the smallest exponent among them, still exact in int64
+    // (53 bits + a shift of at most 3), in units of that exponent's ulp.
+    {
+        auto ex = [](long long b) { return (int)((b >> 52) & 0x7ff); };
+        int emin = ex(b0), emax = emin;
+#define MA_F2_MM(v) emin = min(emin, ex(v)), emax = max(emax, ex(v))
+        MA_F2_MM(bxp); MA_F2_MM(bxm); MA_F2_MM(byp); MA_F2_MM(bym); MA_F2_MM(bzp); MA_F2_MM(bzm);
+        MA_F2_MM(rpp); MA_F2_MM(rmm); MA_F2_MM(rpm); MA_F2_MM(rmp);
+        MA_F2_MM(spp); MA_F2_MM(smm); MA_F2_MM(spm); MA_F2_MM(smp);
+        MA_F2_MM(tpp); MA_F2_MM(tmm); MA_F2_MM(tpm); MA_F2_MM(tmp);
+#undef MA_F2_MM
+        if (emax - emin <= 3 && emin >= f2::kMinE - 3 && emax <= f2::kMaxE) {
+            auto sg = [emin](long long b) -> long long {
+                const long long m = ((b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll) << (((b >> 52) & 0x7ff) - emin);
+                return b < 0 ? -m : m;
+            };
+            const long long m0 = sg(b0);
+            const float unit = __int_as_float((emin - 1075 + 127) << 23);
+            finish(4 * ((sg(bxp) - m0) + (sg(bxm) - m0)), 4 * ((sg(byp) - m0) + (sg(bym) - m0)),
+                   4 * ((sg(bzp) - m0) + (sg(bzm) - m0)), (sg(rpp) - sg(rmp)) - (sg(rpm) - sg(rmm)),
+                   (sg(spp) - sg(smp)) - (sg(spm) - sg(smm)), (sg(tpp) - sg(tmp)) - (sg(tpm) - sg(tmm)), unit);
+            return out;
+        }
+    }
+    // FP64 evaluation (the stencil crosses a binade)
+    HessS H = gather_hess(u, p, sy, sz, __longlong_as_double(b0));
+    const double v = fma(-det0(H), inv_h6_d, rhs);
+    const double hs[6] = {H.A, H.B, H.C, H.R, H.S, H.T};
+    for (int c = 0; c < 6; ++c) {
+        const float hi = __double2float_rn(hs[c]);
+        out.H[c] = {hi, __double2float_rn(hs[c] - (double)hi)};
+    }
+    const float vh = __double2float_rn(v);
+    out.val = {vh, __double2float_rn(v - (double)vh)};
+    return out;
+}
+
+// Block body: one (i, j) column per thread over a run of k (as
+// residual_col_block), each point evaluated by residual_point_f2; Out::put2
+// receives (p, i, j, k, n, ResF2).  Norm partials from the FP32 rounding of
+// the value.
+template <typename Out>
+__device__ __forceinline__ void residual_f2_block(const double* __restrict__ u, const double* __restrict__ rhs,
+                                                  const Out& out, int n, double inv_h6_d, double* partials,
+                                                  int kchunk, uint3 bid, uint3 gdim)
+{
+    const int i = bid.x * RX + threadIdx.x;
+    const int j = bid.y * RY + threadIdx.y;
+    const int k0 = bid.z * kchunk;
+    const int k1 = min(n, k0 + kchunk);
+    const long long sy = n, sz = (long long)n * n;
+    const float ih = (float)inv_h6_d;   // the two-float 1 / (64 h^6)
+    const f2::F2 inv_h6 = {ih, (float)(inv_h6_d - (double)ih)};
+    float mx = 0.0f, ss = 0.0f;
+    if (i < n && j < n && k0 < k1) {
+        const bool col_interior = i > 0 && j > 0 && i < n - 1 && j < n - 1;
+        for (int k = k0; k < k1; ++k) {
+            const long long p = ((long long)k * n + j) * n + i;
+            if (!col_interior || k == 0 || k == n - 1) {
+                out.zero(p);
+                continue;
+            }
+            const ResF2 r = residual_point_f2(u, p, sy, sz, rhs[p], inv_h6, inv_h6_d);
+            const float v32 = r.val.hi;
+            mx = fmaxf(mx, fabsf(v32));
+            ss = fmaf(v32, v32, ss);
+            out.put2(p, i, j, k, n, r);
+        }
+    }
+    if (partials) {
+        __shared__ float smx[RX * RY / 32], sss[RX * RY / 32];
+        for (int o = 16; o > 0; o >>= 1) {
+            mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            ss += __shfl_down_sync(0xffffffffu, ss, o);
+        }
+        const int t = threadIdx.y * RX + threadIdx.x;
+        if ((t & 31) == 0) { smx[t >> 5] = mx; sss[t >> 5] = ss; }
+        __syncthreads();
+        if (t == 0) {
+            double m = f2d(smx[0]), q = f2d(sss[0]);
+            for (int w = 1; w < RX * RY / 32; ++w) { m = fmax(m, f2d(smx[w])); q += f2d(sss[w]); }
+            const int slot = (bid.z * gdim.y + bid.y) * gdim.x + bid.x;
+            partials[2 * slot] = m;
+            partials[2 * slot + 1] = q;
+        }
+    }
+}
+
+template <typename Out>
+__global__ void __launch_bounds__(RX * RY) k_residual_f2(const double* __restrict__ u, const double* __restrict__ rhs,
+                                                         Out out, int n, double inv_h6, double* partials, int kchunk)
+{
+    residual_f2_block<Out>(u, rhs, out, n, inv_h6, partials, kchunk, blockIdx, gridDim);
+}
+
+// FP64 output of the two-float residual (hi + lo rounded once to double).
+struct NaturalF2Out {
+    double* r;
+    __device__ __forceinline__ void put2(long long p, int, int, int, int, const ResF2& v) const
+    {
+        r[p] = f2d(v.val.hi) + f2d(v.val.lo);
+    }
+    __device__ __forceinline__ void zero(long long p) const { r[p] = 0.0; }
+};
+
 }  // namespace resid
 }  // namespace ma

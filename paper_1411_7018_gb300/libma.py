@@ -79,6 +79,7 @@ _SIGS = {
     "ma_destroy_hierarchy": [_vp],
     "ma_smooth": [_vp, _vp, C.c_int, C.c_double, C.c_int, _vp, _vp],
     "ma_residual": [_vp, _vp, _vp, C.c_int, C.c_double, _vp],
+    "ma_residual_f2": [_vp, _vp, _vp, C.c_int, C.c_double, _vp],
     "ma_restrict_residual": [_vp, C.c_int, _vp, C.c_int, _vp],
     "ma_restrict_solution": [_vp, C.c_int, _vp, C.c_int, C.c_int, _vp],
     "ma_coarse_rhs": [_vp, _vp, _vp, C.c_int, C.c_double, _vp],
@@ -88,6 +89,7 @@ _SIGS = {
     "ma_norm_scratch_bytes": [C.c_int, C.POINTER(C.c_size_t)],
     "ma_norm": [_vp, C.c_int, C.c_double, _vp, C.c_size_t, C.POINTER(C.c_double), _vp],
     "ma_kernel_launch_count": [C.POINTER(C.c_ulonglong)],
+    "ma_probe_fp64_rate": [C.POINTER(C.c_double), _vp],
     "ma_correction_scratch_bytes": [C.c_int, C.POINTER(C.c_size_t)],
     "ma_smooth_correction": [_vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp, C.c_size_t, _vp, _vp],
     "ma_smooth_correction_colour": [_vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp, C.c_size_t, _vp, _vp],
@@ -309,6 +311,13 @@ def ma_kernel_launch_count() -> int:
     return out.value
 
 
+def ma_probe_fp64_rate(stream=None) -> float:
+    """Measured FP64 DFMA operations per second of the current device."""
+    out = C.c_double(0.0)
+    _check(load().ma_probe_fp64_rate(C.byref(out), _stream(stream)))
+    return out.value
+
+
 def ma_last_error_string() -> str:
     return load().ma_last_error_string().decode(errors="replace")
 
@@ -321,6 +330,10 @@ def ma_smooth(u, rhs, n: int, h: float, nsweeps: int = 1, events=None, stream=No
 
 def ma_residual(u, rhs, r, n: int, h: float, stream=None) -> None:
     _check(load().ma_residual(_ptr(u), _ptr(rhs), _ptr(r), n, h, _stream(stream)))
+
+
+def ma_residual_f2(u, rhs, r, n: int, h: float, stream=None) -> None:
+    _check(load().ma_residual_f2(_ptr(u), _ptr(rhs), _ptr(r), n, h, _stream(stream)))
 
 
 def ma_restrict_residual(rf, nf: int, rc, kind: int, stream=None) -> None:

@@ -36,6 +36,8 @@ def main():
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--problem", default="exp")
+    ap.add_argument("--inner", type=int, default=0,
+                    help="FP32 correction cycles per outer iteration of a mixed hierarchy (0: library default)")
     variants = {name: c for c, name in M.CORR_NAMES.items()}
     ap.add_argument("--smoother", choices=["by_colour", "colour_pairs", "plane16", "plane32", "plane64"], default=None,
                     help="correction-smoother variant for grid size n (default: the tuning table's)")
@@ -120,7 +122,8 @@ def main():
             M.ma_smooth_correction(e, hi, lo, rhs, a.n, pr.h, 2, scr, nb)
     else:
         prec = M.MA_MIXED if a.precision == "mixed" else M.MA_FP64
-        H = M.Hierarchy(M.make_desc(a.n, length=pr.length, precision=prec))
+        kw = {"inner_cycles": a.inner} if a.inner > 0 else {}
+        H = M.Hierarchy(M.make_desc(a.n, length=pr.length, precision=prec, **kw))
         H.set_rhs_bc(f, u)
         if a.case == "vcycle":
             H.vcycle(a.reps)

@@ -124,10 +124,71 @@ def test_residual_matches_oracle(name, n):
     assert np.max(np.abs(got - ref)) <= _residual_bound(u0, pr.h, name)
 
 
+@pytest.mark.parametrize("name,n", [("exp", 17), ("exp", 65), ("cosine", 129), ("sine", 33), ("exp", 23),
+                                    ("cosine", 71)])
+def test_residual_f2_matches_oracle(name, n):
+    """The residual of the mixed solve's fine grid (exact integer second
+    differences, two-float determinant, FP64 where a stencil crosses a
+    binade) against the oracle's FP64 residual, with the FP64 kernel's bound
+    (the oracle's own rounding is the larger error), and 0 on the shell."""
+    pr, u0 = perturbed(name, n, 1e-6)
+    ref = O.residual(u0, pr.f, pr.h)
+    r = torch.full_like(dev(u0), 7.0)
+    M.ma_residual_f2(dev(u0), dev(pr.f), r, n, pr.h)
+    got = host(r)
+    shell = np.ones_like(got, bool)
+    shell[1:-1, 1:-1, 1:-1] = False
+    assert np.all(got[shell] == 0.0)
+    assert np.max(np.abs(got - ref)) <= _residual_bound(u0, pr.h, name)
+
+
+def _exact_residual(u, f, h, k, j, i):
+    """f - det(D^2_h u) at one point in exact rational arithmetic on the FP64
+    input values (the discrete operator of Eq. MA_discrete written out)."""
+    from fractions import Fraction as Fr
+    v = lambda dk, dj, di: Fr(float(u[k + dk, j + dj, i + di]))
+    c = v(0, 0, 0)
+    h2 = Fr(float(h)) ** 2
+    xx = (v(0, 0, 1) + v(0, 0, -1) - 2 * c) / h2
+    yy = (v(0, 1, 0) + v(0, -1, 0) - 2 * c) / h2
+    zz = (v(1, 0, 0) + v(-1, 0, 0) - 2 * c) / h2
+    xy = ((v(0, 1, 1) + v(0, -1, -1)) - (v(0, 1, -1) + v(0, -1, 1))) / (4 * h2)
+    xz = ((v(1, 0, 1) + v(-1, 0, -1)) - (v(1, 0, -1) + v(-1, 0, 1))) / (4 * h2)
+    yz = ((v(1, 1, 0) + v(-1, -1, 0)) - (v(1, -1, 0) + v(-1, 1, 0))) / (4 * h2)
+    det = xx * (yy * zz - yz * yz) - xy * (xy * zz - xz * yz) + xz * (xy * yz - yy * xz)
+    return Fr(float(f[k, j, i])) - det
+
+
+@pytest.mark.parametrize("name,n", [("exp", 129), ("cosine", 65)])
+def test_residual_f2_against_exact_rational_arithmetic(name, n):
+    """At 60 sampled points the two-float residual is within 1e-12 max|f| of
+    the residual computed in exact rational arithmetic from the same FP64
+    values (brute force), which the FP64 kernel, whose gather rounds the
+    sums of neighbours, misses by orders of magnitude more at 129^3."""
+    pr, u0 = perturbed(name, n, 1e-6)
+    r2 = torch.empty_like(dev(u0))
+    r64 = torch.empty_like(dev(u0))
+    M.ma_residual_f2(dev(u0), dev(pr.f), r2, n, pr.h)
+    M.ma_residual(dev(u0), dev(pr.f), r64, n, pr.h)
+    g2, g64 = host(r2), host(r64)
+    rng = np.random.default_rng(n)
+    pts = rng.integers(1, n - 1, size=(60, 3))
+    fmax = np.max(np.abs(pr.f[1:-1, 1:-1, 1:-1]))
+    e2 = max(abs(float(_exact_residual(u0, pr.f, pr.h, *p) - __import__("fractions").Fraction(float(g2[tuple(p)]))))
+             for p in pts)
+    e64 = max(abs(float(_exact_residual(u0, pr.f, pr.h, *p) - __import__("fractions").Fraction(float(g64[tuple(p)]))))
+              for p in pts)
+    assert e2 <= 1e-12 * fmax, (e2, e64)
+    if name == "exp":
+        assert e2 < e64
+
+
 def test_residual_of_quadratic_is_exactly_zero():
     pr = P.make("quadratic", 129)
     r = torch.empty_like(dev(pr.u))
     M.ma_residual(dev(pr.u), dev(pr.f), r, 129, pr.h)
+    assert np.all(host(r) == 0.0)
+    M.ma_residual_f2(dev(pr.u), dev(pr.f), r, 129, pr.h)
     assert np.all(host(r) == 0.0)
 
 
