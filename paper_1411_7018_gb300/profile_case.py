@@ -3,7 +3,8 @@
     python -m paper_1411_7018_gb300.profile_case --case smooth --n 257 --reps 2
 
 Cases: ``smooth`` (FP64 smoother sweeps, 8 colour launches each), ``residual``
-(the FP64 residual kernel), ``smooth_corr`` (FP32 correction-smoother sweeps of
+(the FP64 residual kernel), ``residual_f2`` (the mixed solve's fine residual:
+exact integer differences, two-float determinant), ``smooth_corr`` (FP32 correction-smoother sweeps of
 the mixed path on a small correction, in the variant the tuning table picks for
 n or the one --smoother names), ``residual_corr`` (the correction residual
 rhs - N(e) of the mixed path on that correction, in the variant the tuning
@@ -30,8 +31,8 @@ from . import problems
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["smooth", "residual", "smooth_corr", "residual_corr", "vcycle", "solve",
-                                       "solve2d", "smooth2d", "batch"], default="smooth")
+    ap.add_argument("--case", choices=["smooth", "residual", "residual_f2", "smooth_corr", "residual_corr", "vcycle",
+                                       "solve", "solve2d", "smooth2d", "batch"], default="smooth")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--reps", type=int, default=2)
@@ -101,6 +102,10 @@ def main():
         r = torch.empty_like(u)
         for _ in range(a.reps):
             M.ma_residual(u, f, r, a.n, pr.h)
+    elif a.case == "residual_f2":
+        r = torch.empty_like(u)
+        for _ in range(a.reps):
+            M.ma_residual_f2(u, f, r, a.n, pr.h)
     elif a.case == "residual_corr":
         hi = u.float()
         lo = (u - hi.double()).float()
