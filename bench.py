@@ -65,12 +65,11 @@ def hbm_peak():
 # suits small grids and batches, where an outer iteration's fixed cost weighs
 # more.
 MIXED_INNER = 2
-# DRAM bytes (read + write) per launch of the correction smoother at 257^3,
-# from one ncu capture of the current kernels with a warm L2 (--cache-control
-# none), keyed by the variant (MA_CORR_BY_COLOUR = 0: one colour, 103.4 MB read
-# + 34.7-35.0 MB written; MA_CORR_PAIRS = 5: two colours, 167.3-169.4 MB read +
-# 42.4-43.1 MB written).
-CORR_SMOOTH_TRAFFIC_257 = {0: 138.2e6, 5: 211.1e6}
+# DRAM bytes (read + write) per launch of the colour-pair correction smoother
+# (MA_CORR_PAIRS = 5) at 257^3, from one ncu capture of the current kernel
+# with a warm L2 (--cache-control none): 167.0-168.9 MB read + 43.0-43.4 MB
+# written.  Other variants: no current capture (null).
+CORR_SMOOTH_TRAFFIC_257 = {5: 211.2e6}
 
 
 def parse():
