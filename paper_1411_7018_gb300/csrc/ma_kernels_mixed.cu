@@ -1750,8 +1750,8 @@ cudaError_t launch_residual_f2(const double* u, const double* rhs, double* r, in
     count_launches(1);
     const int kz = n < 16 ? n : 16;
     const int kchunk = (n + kz - 1) / kz;
-    resid::k_residual_f2<resid::NaturalF2Out><<<resid::grid_for(n, kz), dim3(resid::RX, resid::RY), 0, s>>>(
-        u, rhs, resid::NaturalF2Out{r}, n, 1.0 / (64.0 * h2 * h2 * h2), nullptr, kchunk);
+    resid::launch_k_residual_f2(resid::grid_for(n, kz), s, u, rhs, resid::NaturalF2Out{r}, n,
+                                1.0 / (64.0 * h2 * h2 * h2), nullptr, kchunk);
     return cudaGetLastError();
 }
 
@@ -1762,9 +1762,8 @@ cudaError_t launch_residual64_to32(const double* u, const double* rhs, float* r_
     count_launches(1);
     const int kz = n < 16 ? n : 16;
     const int kchunk = (n + kz - 1) / kz;
-    resid::k_residual_f2<CmF32Out><<<resid::grid_for(n, kz), dim3(resid::RX, resid::RY), 0, s>>>(
-        u, rhs, CmF32Out{r_cm, (float*)bstore, (float)(0.25 / h2)}, n, 1.0 / (64.0 * h2 * h2 * h2), partials,
-        kchunk);
+    resid::launch_k_residual_f2(resid::grid_for(n, kz), s, u, rhs, CmF32Out{r_cm, (float*)bstore, (float)(0.25 / h2)},
+                                n, 1.0 / (64.0 * h2 * h2 * h2), partials, kchunk);
     return cudaGetLastError();
 }
 

@@ -206,6 +206,15 @@ __device__ __forceinline__ F2 mul(F2 x, F2 y)
     return fast_two_sum(p, e);
 }
 
+// The product left unnormalised (|lo| may exceed half an ulp of hi by the
+// few roundings of the cross terms); for operands of add, which renormalises.
+__device__ __forceinline__ F2 mul_u(F2 x, F2 y)
+{
+    const float p = x.hi * y.hi;
+    const float e = fmaf(x.hi, y.hi, -p);
+    return {p, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e))};
+}
+
 __device__ __forceinline__ F2 add(F2 x, F2 y)
 {
     const F2 s = two_sum(x.hi, y.hi);
@@ -220,6 +229,14 @@ __device__ __forceinline__ F2 neg(F2 x) { return {-x.hi, -x.lo}; }
 // instructions only (GB300 runs 64-bit integer conversions at its FP64 rate).
 __device__ __forceinline__ float u23_to_f(unsigned y) { return __int_as_float(0x4B000000 | (int)y) - 8388608.0f; }
 __device__ __forceinline__ float s22_to_f(int y) { return __int_as_float(0x4B400000 + y) - 12582912.0f; }
+
+// x * scale as hi + lo, exact, for |x| < 2^45: x = a 2^23 + c with c in
+// [0, 2^23) and |a| < 2^22; scale a power of two.
+__device__ __forceinline__ F2 from_i45(long long x, float scale)
+{
+    const F2 r = fast_two_sum(s22_to_f((int)(x >> 23)) * 8388608.0f, u23_to_f((unsigned)x & 0x7fffffu));
+    return {r.hi * scale, r.lo * scale};
+}
 
 // x * scale as hi + lo, |x| < 2^68 (exact to ~2^-48 relative), scale a
 // power of two: x = a 2^46 + b 2^23 + c with b, c in [0, 2^23).
@@ -252,10 +269,10 @@ __device__ __forceinline__ F2 from_f64(double x)
 // cofactor expansion along the first row.
 __device__ __forceinline__ F2 det3(const F2& A, const F2& B, const F2& C, const F2& R, const F2& S, const F2& T)
 {
-    const F2 c1 = add(mul(B, C), neg(mul(T, T)));
-    const F2 c2 = add(mul(R, C), neg(mul(S, T)));
-    const F2 c3 = add(mul(R, T), neg(mul(B, S)));
-    return add(add(mul(A, c1), neg(mul(R, c2))), mul(S, c3));
+    const F2 c1 = add(mul_u(B, C), neg(mul_u(T, T)));
+    const F2 c2 = add(mul_u(R, C), neg(mul_u(S, T)));
+    const F2 c3 = add(mul_u(R, T), neg(mul_u(B, S)));
+    return add(add(mul_u(A, c1), neg(mul_u(R, c2))), mul_u(S, c3));
 }
 
 // The exact paths accept binades E with 2^(E-1075) and the cube of the
@@ -296,12 +313,26 @@ __device__ __forceinline__ ResF2 residual_point_f2(const double* __restrict__ u,
     const int E = (int)((h0 >> 20) & 0x7ff);
     ResF2 out;
     auto finish = [&](long long A, long long B, long long C, long long R, long long S, long long T, float unit) {
-        out.H[0] = f2::from_i64(A, unit);
-        out.H[1] = f2::from_i64(B, unit);
-        out.H[2] = f2::from_i64(C, unit);
-        out.H[3] = f2::from_i64(R, unit);
-        out.H[4] = f2::from_i64(S, unit);
-        out.H[5] = f2::from_i64(T, unit);
+        // |x| < 2^45 for all six (the common case on fine grids): the two-piece
+        // conversion; otherwise the three-piece one
+        const unsigned long long big = 1ull << 45;
+        if ((unsigned long long)(A + big) < 2 * big && (unsigned long long)(B + big) < 2 * big &&
+            (unsigned long long)(C + big) < 2 * big && (unsigned long long)(R + big) < 2 * big &&
+            (unsigned long long)(S + big) < 2 * big && (unsigned long long)(T + big) < 2 * big) {
+            out.H[0] = f2::from_i45(A, unit);
+            out.H[1] = f2::from_i45(B, unit);
+            out.H[2] = f2::from_i45(C, unit);
+            out.H[3] = f2::from_i45(R, unit);
+            out.H[4] = f2::from_i45(S, unit);
+            out.H[5] = f2::from_i45(T, unit);
+        } else {
+            out.H[0] = f2::from_i64(A, unit);
+            out.H[1] = f2::from_i64(B, unit);
+            out.H[2] = f2::from_i64(C, unit);
+            out.H[3] = f2::from_i64(R, unit);
+            out.H[4] = f2::from_i64(S, unit);
+            out.H[5] = f2::from_i64(T, unit);
+        }
         const f2::F2 d = f2::det3(out.H[0], out.H[1], out.H[2], out.H[3], out.H[4], out.H[5]);
         out.val = f2::add(f2::from_f64(rhs), f2::neg(f2::mul(d, inv_h6)));
     };
@@ -354,11 +385,14 @@ __device__ __forceinline__ ResF2 residual_point_f2(const double* __restrict__ u,
 // residual_col_block), each point evaluated by residual_point_f2; Out::put2
 // receives (p, i, j, k, n, ResF2).  Norm partials from the FP32 rounding of
 // the value.
-template <typename Out>
+template <typename Out, int NN = 0>
 __device__ __forceinline__ void residual_f2_block(const double* __restrict__ u, const double* __restrict__ rhs,
-                                                  const Out& out, int n, double inv_h6_d, double* partials,
+                                                  const Out& out, int n_rt, double inv_h6_d, double* partials,
                                                   int kchunk, uint3 bid, uint3 gdim)
 {
+    // NN > 0: the grid size at compile time, so the stencil offsets are
+    // immediates of the loads (the same values and arithmetic either way)
+    const int n = NN > 0 ? NN : n_rt;
     const int i = bid.x * RX + threadIdx.x;
     const int j = bid.y * RY + threadIdx.y;
     const int k0 = bid.z * kchunk;
@@ -401,11 +435,26 @@ __device__ __forceinline__ void residual_f2_block(const double* __restrict__ u, 
     }
 }
 
-template <typename Out>
+template <typename Out, int NN = 0>
 __global__ void __launch_bounds__(RX * RY) k_residual_f2(const double* __restrict__ u, const double* __restrict__ rhs,
                                                          Out out, int n, double inv_h6, double* partials, int kchunk)
 {
-    residual_f2_block<Out>(u, rhs, out, n, inv_h6, partials, kchunk, blockIdx, gridDim);
+    residual_f2_block<Out, NN>(u, rhs, out, n, inv_h6, partials, kchunk, blockIdx, gridDim);
+}
+
+// Launch with the grid size fixed at compile time for the sizes that stream
+// from HBM.
+template <typename Out>
+void launch_k_residual_f2(dim3 grid, cudaStream_t s, const double* u, const double* rhs, Out out, int n,
+                          double inv_h6, double* partials, int kchunk)
+{
+    const dim3 blk(RX, RY);
+    switch (n) {
+    case 129: k_residual_f2<Out, 129><<<grid, blk, 0, s>>>(u, rhs, out, n, inv_h6, partials, kchunk); break;
+    case 257: k_residual_f2<Out, 257><<<grid, blk, 0, s>>>(u, rhs, out, n, inv_h6, partials, kchunk); break;
+    case 513: k_residual_f2<Out, 513><<<grid, blk, 0, s>>>(u, rhs, out, n, inv_h6, partials, kchunk); break;
+    default: k_residual_f2<Out, 0><<<grid, blk, 0, s>>>(u, rhs, out, n, inv_h6, partials, kchunk); break;
+    }
 }
 
 // FP64 output of the two-float residual (hi + lo rounded once to double).

@@ -12,7 +12,9 @@ table picks for n or the one --residual names), ``vcycle`` (whole V-cycles of
 a resident hierarchy), ``solve`` (one FMG + V-cycle solve to 1e-10), ``solve2d`` (the 2D paper-configuration solve of
 Example 1 on an n x n grid), ``smooth2d`` (2D red-black sweeps on that grid),
 ``batch`` (the batching workload: 64 mixed-precision instances of sizes drawn
-by seed from {33, 65, 129}^3, solved once as a shared per-level batch);
+by seed from {33, 65, 129}^3, solved once as a shared per-level batch),
+``batch_graphs`` (the same instances solved with ma_batch_solve: each
+hierarchy's own graphs on its own stream);
 ``--precision mixed`` runs the hierarchy cases in mixed precision.  The grid holds
 Example 4 (u = exp(|x|^2/2)) with a small seeded perturbation; fields of a
 257^3 grid are 136 MB each, larger than L2.  Prints nothing but a one-line
@@ -32,7 +34,7 @@ from . import problems
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", choices=["smooth", "residual", "residual_f2", "smooth_corr", "residual_corr", "vcycle",
-                                       "solve", "solve2d", "smooth2d", "batch"], default="smooth")
+                                       "solve", "solve2d", "smooth2d", "batch", "batch_graphs"], default="smooth")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--n", type=int, default=257)
     ap.add_argument("--reps", type=int, default=2)
@@ -58,7 +60,7 @@ def main():
         torch.cuda.synchronize()
         print(f"profile_case {a.case} n={a.n} reps={a.reps} done")
         return
-    if a.case == "batch":
+    if a.case in ("batch", "batch_graphs"):
         rng = np.random.default_rng(2024)
         sizes = rng.choice([33, 65, 129], size=64)
         hs, keep = [], []
@@ -69,10 +71,15 @@ def main():
             H.set_rhs_bc(f, g)
             hs.append(H)
             keep.append((f, g))
-        B = M.Batch(hs)
-        for _ in range(a.reps):
-            B.solve(tol=1e-10, max_cycles=60, raise_on_error=False)
-        B.close()
+        if a.case == "batch":
+            B = M.Batch(hs)
+            for _ in range(a.reps):
+                B.solve(tol=1e-10, max_cycles=60, raise_on_error=False)
+            B.close()
+        else:   # each hierarchy's own cycle graphs on its own stream, overlapping
+            opts = M.ma_solve_opts(1e-10, M.MA_NORM_MAX, 1, 60, M.MA_INIT_FMG)
+            for _ in range(a.reps):
+                M.ma_batch_solve([H.handle for H in hs], opts, raise_on_error=False)
         for H in hs:
             H.close()
         torch.cuda.synchronize()
