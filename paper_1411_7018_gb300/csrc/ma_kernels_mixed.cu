@@ -787,10 +787,14 @@ __global__ void __launch_bounds__(NT, plane_min_blocks(PT, NT))
 // blocks of 32 x 4 (four rows).
 constexpr int CW = 30;
 
+template <int NN = 0>
 __device__ __forceinline__ void residual_corr_col_block(const float* __restrict__ e, const float* __restrict__ bstore,
                                                         const float* __restrict__ rhs_cm, float* __restrict__ res,
-                                                        int n, float inv_h2, int kc, uint3 bid)
+                                                        int n_rt, float inv_h2, int kc, uint3 bid)
 {
+    // NN > 0: the grid size at compile time (strides and box sizes become
+    // constants; the same arithmetic and bits)
+    const int n = NN > 0 ? NN : n_rt;
     const int lane = threadIdx.x;
     const int i = (int)bid.x * CW + lane;   // i0 - 1 + lane, i0 = 1 + CW bid.x
     const int j = 1 + (int)bid.y * 4 + (int)threadIdx.y;
@@ -869,13 +873,14 @@ __device__ __forceinline__ void residual_corr_col_block(const float* __restrict_
     }
 }
 
+template <int NN = 0>
 __global__ void __launch_bounds__(BX * BY, 6) k_residual_corr_col(const float* __restrict__ e,
                                                                   const float* __restrict__ bstore,
                                                                   const float* __restrict__ rhs_cm,
                                                                   float* __restrict__ res, int n, float inv_h2,
                                                                   int kc)
 {
-    residual_corr_col_block(e, bstore, rhs_cm, res, n, inv_h2, kc, blockIdx);
+    residual_corr_col_block<NN>(e, bstore, rhs_cm, res, n, inv_h2, kc, blockIdx);
 }
 
 // Planes per column run, and the grid of the column residual.
@@ -1561,7 +1566,13 @@ cudaError_t launch_residual_corr_choice(int choice, const float* e, const void* 
     case CORR_COLUMN: {
         const int kc = col_chunk(n);
         count_launches(1);
-        k_residual_corr_col<<<col_grid(n, kc), dim3(BX, BY), 0, s>>>(e, b, rhs_cm, res, n, inv_h2, kc);
+        const dim3 g = col_grid(n, kc), blk(BX, BY);
+        switch (n) {
+        case 129: k_residual_corr_col<129><<<g, blk, 0, s>>>(e, b, rhs_cm, res, n, inv_h2, kc); break;
+        case 257: k_residual_corr_col<257><<<g, blk, 0, s>>>(e, b, rhs_cm, res, n, inv_h2, kc); break;
+        case 513: k_residual_corr_col<513><<<g, blk, 0, s>>>(e, b, rhs_cm, res, n, inv_h2, kc); break;
+        default: k_residual_corr_col<0><<<g, blk, 0, s>>>(e, b, rhs_cm, res, n, inv_h2, kc); break;
+        }
         return cudaGetLastError();
     }
     default: return residual_t<64, 256>(e, b, rhs_cm, res, n, inv_h2, s);
