@@ -408,6 +408,16 @@ def bench_batching(args, M, problems, dev):
     unknowns = int(sum((int(n) - 2) ** 3 for n in sizes))
     for H in hs:
         H.close()
+    # the persistent alternative to the shared batch's launch chains: per
+    # phase, a launch edge in a CUDA graph against a grid barrier in one
+    # cooperative kernel (ma_probe_phase_chain), at a small and a large phase
+    chain = {}
+    for n_el in (1 << 16, 1 << 21):
+        a = torch.zeros(n_el, dtype=torch.float32, device=dev)
+        b = torch.zeros_like(a)
+        sync = torch.zeros(4, dtype=torch.int32, device=dev)
+        chain[str(n_el)] = M.ma_probe_phase_chain(a, b, sync, phases=64, blocks_per_sm=4)
+        del a, b, sync
     return {"instances": 64, "sizes": {str(k): int((sizes == k).sum()) for k in (33, 65, 129)},
             "unknowns": unknowns, "tol": args.tol, "precision": "mixed",
             "ms": t_levels * 1e3, "unknowns_per_s": unknowns / t_levels,
@@ -416,7 +426,8 @@ def bench_batching(args, M, problems, dev):
             "concurrent_graphs_ms": t_batch * 1e3, "concurrent_graphs_unknowns_per_s": unknowns / t_batch,
             "concurrent_graphs_converged": int(sum(1 for r in res if r.status == 0)),
             "sequential_ms": t_seq * 1e3, "sequential_unknowns_per_s": unknowns / t_seq,
-            "speedup_vs_sequential": t_seq / t_levels}
+            "speedup_vs_sequential": t_seq / t_levels,
+            "persistent_phase_chain_us_per_phase": chain}
 
 
 def bench_serving(args, M, problems, dev):

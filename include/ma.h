@@ -276,6 +276,28 @@ ma_status ma_kernel_launch_count(unsigned long long *out);
  * on the stream (~a millisecond). */
 ma_status ma_probe_fp64_rate(double *ops_per_s, ma_stream_t stream);
 
+/* Diagnostics: the cost per phase of a chain of `phases` dependent phases on
+ * the current device, three ways, in microseconds per phase (best of 5 timed
+ * runs after 2 untimed ones, CUDA events).  A phase computes
+ * b[i] = a[i] * 1.0001 + 1 for i < n, and the next phase reads what it wrote
+ * (a and b swap).  No counterpart in the paper: a multigrid cycle is such a
+ * chain (colour sweeps, residual, transfers on every level), run here as
+ * CUDA graphs, and this probe measures the persistent-kernel alternative.
+ *    out_us[0]: a CUDA graph of `phases` launches, one element per thread;
+ *    out_us[1]: the same graph with blocks_per_sm x (SM count) blocks, each
+ *               striding over the elements;
+ *    out_us[2]: one cooperative launch of that grid running all phases, a
+ *               grid-wide barrier between consecutive ones.
+ * out_us[2] - out_us[1] is the cost of a grid barrier over a launch edge.
+ * a_dev, b_dev: n floats each on the device, sync_dev: 3 unsigned ints on the
+ * device, all owned by the caller and overwritten.  n in [1, 2^40], phases in
+ * [2, 4096], blocks_per_sm in [1, the resident limit of 128-thread blocks];
+ * MA_ERR_INVALID_ARG otherwise or where the device has no cooperative launch.
+ * Each barrier's wait is bounded (about a second); if one gives up, the
+ * kernel ends and the call returns MA_ERR_CUDA.  Blocks until done. */
+ma_status ma_probe_phase_chain(float *a_dev, float *b_dev, size_t n, int phases, int blocks_per_sm,
+                               unsigned *sync_dev, double *out_us, ma_stream_t stream);
+
 /* ---- single steps on raw device grids (each row of the V-cycle) ----------
  * These run exactly the kernels a hierarchy runs, on caller arrays of one
  * level (n^3 doubles, [k][j][i]).  n must be odd and >= 3.  All are

@@ -90,6 +90,7 @@ _SIGS = {
     "ma_norm": [_vp, C.c_int, C.c_double, _vp, C.c_size_t, C.POINTER(C.c_double), _vp],
     "ma_kernel_launch_count": [C.POINTER(C.c_ulonglong)],
     "ma_probe_fp64_rate": [C.POINTER(C.c_double), _vp],
+    "ma_probe_phase_chain": [_vp, _vp, C.c_size_t, C.c_int, C.c_int, _vp, C.POINTER(C.c_double), _vp],
     "ma_correction_scratch_bytes": [C.c_int, C.POINTER(C.c_size_t)],
     "ma_smooth_correction": [_vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp, C.c_size_t, _vp, _vp],
     "ma_smooth_correction_colour": [_vp, _vp, _vp, _vp, C.c_int, C.c_double, C.c_int, _vp, C.c_size_t, _vp, _vp],
@@ -316,6 +317,22 @@ def ma_probe_fp64_rate(stream=None) -> float:
     out = C.c_double(0.0)
     _check(load().ma_probe_fp64_rate(C.byref(out), _stream(stream)))
     return out.value
+
+
+def ma_probe_phase_chain(a, b, sync, phases: int, blocks_per_sm: int, stream=None) -> dict:
+    """Per-phase cost (us) of a chain of dependent phases: a CUDA graph of
+    launches (one element per thread, and a grid-stride grid of blocks_per_sm
+    blocks per SM) and one cooperative kernel with grid barriers.  a, b: float32
+    device tensors of n elements; sync: 3 int32 on the device."""
+    if a.element_size() != 4 or b.element_size() != 4 or b.numel() != a.numel():
+        raise ValueError("a, b: float32 device tensors of one size")
+    if sync.element_size() != 4 or sync.numel() < 3:
+        raise ValueError("sync: at least 3 int32 on the device")
+    out = (C.c_double * 3)()
+    _check(load().ma_probe_phase_chain(_ptr(a), _ptr(b), a.numel(), phases, blocks_per_sm, _ptr(sync), out,
+                                       _stream(stream)))
+    return {"graph_one_element_per_thread_us": out[0], "graph_grid_stride_us": out[1],
+            "cooperative_barriers_us": out[2]}
 
 
 def ma_last_error_string() -> str:
