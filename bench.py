@@ -616,25 +616,58 @@ def main():
         inner = MIXED_INNER if key == "mixed" else 1
         vc[key] = {"ms_per_cycle": per / inner, "vcycles_per_s": 1e3 * inner / per}
 
-    # end to end through the C ABI with host buffers (pinned), mixed precision
-    H = hier["mixed"]
+    # end to end through the C ABI with host buffers (pinned), mixed precision.
+    # Two resident hierarchies, each on its own stream, take the steps in
+    # turn.  While the main thread solves step k on one of them (ma_solve
+    # blocks), a second host thread reads step k-1's solution out of the other
+    # and uploads step k+1's f and g into it (ma_get_solution_host, then
+    # ma_set_rhs_bc_host, in that order on that hierarchy's stream), so the
+    # host-link copies run beside the solve.  One solve runs at a time.  Every
+    # step's copies lie inside the timed region: it opens before step 0's
+    # upload and closes after the last step's download.
+    from concurrent.futures import ThreadPoolExecutor
+    e2e_h = [M.Hierarchy(M.make_desc(pr.n, length=pr.length, precision=M.MA_MIXED, inner_cycles=MIXED_INNER),
+                         stream=torch.cuda.Stream(device=dev), device=dev) for _ in range(2)]
     f_host = torch.from_numpy(pr.f).pin_memory()
     g_host = torch.from_numpy(pr.initial()).pin_memory()
-    u_host = torch.empty_like(f_host).pin_memory()
-    e2e_steps = max(1, min(args.steps, 5))
+    u_host = [torch.empty_like(f_host).pin_memory() for _ in range(2)]
+    e2e_steps = max(2, min(args.steps, 10))
+    e2e_res = []
 
-    def e2e_step():
-        # the C ABI's host-buffer calls: f, g in and u out over the host link
-        H.set_rhs_bc_host(f_host, g_host)
-        H.solve(tol=args.tol, max_cycles=60)
-        H.get_solution_host(u_host)
+    def e2e_run(steps):
+        with ThreadPoolExecutor(max_workers=1) as io:
+            e2e_h[0].set_rhs_bc_host(f_host, g_host)
+            pending = None
+            for k in range(steps):
+                H, other = e2e_h[k % 2], e2e_h[(k + 1) % 2]
+                if pending is not None:
+                    pending.result()          # step k's inputs are in H
 
-    e2e_step()   # warm-up: first use of the freshly pinned buffers
+                def io_job(k=k, other=other):
+                    if k >= 1:
+                        other.get_solution_host(u_host[(k - 1) % 2])   # step k-1's result
+                    if k + 1 < steps:
+                        other.set_rhs_bc_host(f_host, g_host)          # step k+1's inputs
+
+                pending = io.submit(io_job)
+                e2e_res.append(H.solve(tol=args.tol, max_cycles=60))
+            pending.result()
+            e2e_h[(steps - 1) % 2].get_solution_host(u_host[(steps - 1) % 2])
+
+    e2e_run(2)   # warm-up: graph capture on both hierarchies, first use of the pinned buffers
     torch.cuda.synchronize()
+    e2e_res.clear()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
+    e2e_run(e2e_steps)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_ok = all(r.status == 0 and r.cycles == e2e_res[0].cycles for r in e2e_res)
+    u_check = torch.empty_like(f_dev)
+    e2e_h[(e2e_steps - 1) % 2].get_solution(u_check)
+    torch.cuda.synchronize()
+    e2e_same = bool(torch.equal(u_check.cpu(), u_host[(e2e_steps - 1) % 2]))
+    for H in e2e_h:
+        H.close()
+    del e2e_h, u_check
 
     for H in hier.values():
         H.close()
@@ -681,7 +714,12 @@ def main():
                                        "nominal_peak": FP64_NOMINAL_GOPS},
             "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")} if cpu else None,
             "e2e": {"value": world * pr.unknowns / e2e_s, "unit": "unknowns/s",
-                    "h2d_bytes_per_step": 2 * 8 * pr.n ** 3, "d2h_bytes_per_step": 8 * pr.n ** 3},
+                    "h2d_bytes_per_step": 2 * 8 * pr.n ** 3, "d2h_bytes_per_step": 8 * pr.n ** 3,
+                    "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s, "converged_all": e2e_ok,
+                    "solution_read_matches_device": e2e_same,
+                    "mode": "ma_set_rhs_bc_host / ma_solve / ma_get_solution_host on pinned buffers; "
+                            "2 resident hierarchies in turn, a host thread moving step k-1's solution out "
+                            "and step k+1's inputs in while step k solves; one solve at a time"},
             "clocks": clocks,
             "gpu_launches": launches,
             "vcycles": {"fp64_fas_vcycle": vc["fp64"],
