@@ -471,7 +471,7 @@ __device__ __forceinline__ void vcycle_tail_body(const Tail64Args& A)
         const Tail64Smem& F = S[l];
         const Tail64Smem& C = S[l + 1];
         const int nf = A.lev[l].n, nc = A.lev[l + 1].n;
-        // (7)-(8) u_h += I(u_H - w_H) on the fine interior (the pair form of xfer::k_prolong)
+        // (7)-(8) u_h += I(u_H - w_H) on the fine interior, each value formed as xfer::k_prolong forms it
         for (int q = threadIdx.x; q < (nf - 2) * (nf - 2) * (nf - 2); q += T64) {
             const int i = 1 + q % (nf - 2), j = 1 + (q / (nf - 2)) % (nf - 2), k = 1 + q / ((nf - 2) * (nf - 2));
             const int J0 = j >> 1, K0 = k >> 1, oj = j & 1, ok = k & 1;

@@ -1237,7 +1237,7 @@ __device__ __forceinline__ void corr_tail_body(const TailArgs& A)
         const TailSmem& F = S[l];
         const TailSmem& C = S[l + 1];
         const int nf = A.lev[l].n, nc = A.lev[l + 1].n;
-        // prolongation e_h += I(e_H - w_H) on the fine interior (the pair form of xfer::k_prolong)
+        // prolongation e_h += I(e_H - w_H) on the fine interior, each value formed as xfer::k_prolong forms it
         for (int q = threadIdx.x; q < (nf - 2) * (nf - 2) * (nf - 2); q += TT) {
             const int i = 1 + q % (nf - 2), j = 1 + (q / (nf - 2)) % (nf - 2), k = 1 + q / ((nf - 2) * (nf - 2));
             const int J0 = j >> 1, K0 = k >> 1, oj = j & 1, ok = k & 1;

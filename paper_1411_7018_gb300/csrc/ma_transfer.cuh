@@ -83,42 +83,133 @@ __global__ void __launch_bounds__(BX * BY) k_restrict(const T* __restrict__ uf, 
 }
 
 // Trilinear interpolation at fine interior points: along each axis an even
-// index sits on a coarse point, an odd one halfway between two.  Thread
-// (I, j, k) writes fine points i = 2I + 1 and 2I + 2 of row (j, k): with
-// L(I) the coarse values d = uc - wc (add != 0) or d = uc (add == 0) summed
-// over the one, two or four coarse rows around (j, k) and scaled by their
-// weight, fine 2I + 2 gets L(I + 1) and fine 2I + 1 gets (L(I) + L(I + 1)) / 2.
-// A lane computes L(I + 1) and takes L(I) from the lane before it.
+// index sits on a coarse point, an odd one halfway between two.  With L(I) the
+// coarse values d = uc - wc (add != 0) or d = uc (add == 0) summed over the
+// one, two or four coarse rows around fine row (j, k) and scaled by their
+// weight, fine point 2I gets L(I) and fine point 2I + 1 gets
+// (L(I) + L(I + 1)) / 2.
 // add != 0: uf += I(uc - wc) (coarse-grid correction); add == 0: uf = I(uc).
+//
+// Thread (I, J, K) owns the coarse cell between coarse points I..I+1,
+// J..J+1, K..K+1: the four fine rows j in {2J, 2J + 1}, k in {2K, 2K + 1}
+// (rows on the shell skipped) and two fine points of each.  It loads the four
+// coarse rows' values at column I + 1 once for all four fine rows and takes
+// those at column I from the lane before it (lane 0 loads them).  nf is odd,
+// so in fine row (j, k) the point pair that starts at an even linear index is
+// (2I, 2I + 1) when j + k is even and (2I + 1, 2I + 2) when it is odd: each
+// lane moves that pair as one aligned 2-element access (scalar accesses
+// where the pair would reach the shell, or where uf is not aligned to two
+// elements).  With add != 0 the fine pairs are loaded first, so their HBM
+// latency overlaps the coarse loads.  Every fine value is the same
+// expression, summed in the same order (dk outer, dj inner), as one thread
+// per fine point would form it.
 // Grid: prolong_grid(nf), blocks of BX x BY.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+
 template <typename T>
 __device__ __forceinline__ void prolong_block(const T* __restrict__ uc, const T* __restrict__ wc, int nc,
                                               T* __restrict__ uf, int nf, int add, uint3 bid)
 {
+    using V = typename Vec2<T>::type;
     const int I = bid.x * BX + threadIdx.x;
-    const int j = 1 + bid.y * BY + threadIdx.y;
-    const int k = 1 + bid.z;
-    const bool row = j <= nf - 2;   // uniform over the warp (BX = 32)
-    const int J0 = j >> 1, K0 = k >> 1, oj = j & 1, ok = k & 1;
-    const T w = T(1) / T(1 << (oj + ok));
-    auto line = [&](int Ic) -> T {
-        T s = T(0);
-        for (int dk = 0; dk <= ok; ++dk)
-            for (int dj = 0; dj <= oj; ++dj) {
-                const long long q = lin(Ic, J0 + dj, K0 + dk, nc);
-                s += add ? (uc[q] - wc[q]) : uc[q];
-            }
-        return s * w;
+    const int J = bid.y * BY + threadIdx.y;
+    const int K = bid.z;
+    const bool act = I <= nc - 2 && J <= nc - 2;   // J uniform over the warp (BX = 32)
+    const bool vec = ((unsigned long long)uf & (2 * sizeof(T) - 1)) == 0;
+    // the fine pair of row (j, k): its first point p0 and whether both points
+    // are interior (else only the second, 2I + 1, for even rows at I = 0, or
+    // only the first, 2I + 1, for odd rows at the far end)
+    auto pair_at = [&](int j, int k, long long* p0, bool* full) {
+        const bool even = ((j + k) & 1) == 0;
+        *p0 = lin(even ? 2 * I : 2 * I + 1, j, k, nf);
+        *full = even ? I >= 1 : 2 * I + 2 <= nf - 2;
+        return even;
     };
-    const bool act = row && I <= nc - 2;
-    const T b = act ? line(I + 1) : T(0);
-    T a = __shfl_up_sync(0xffffffffu, b, 1);
+    T f[2][2][2];
+#pragma unroll
+    for (int ok = 0; ok < 2; ++ok)
+#pragma unroll
+        for (int oj = 0; oj < 2; ++oj) {
+            f[ok][oj][0] = f[ok][oj][1] = T(0);
+            const int j = 2 * J + oj, k = 2 * K + ok;
+            if (!add || !act || j < 1 || k < 1) continue;
+            long long p0;
+            bool full;
+            const bool even = pair_at(j, k, &p0, &full);
+            if (full && vec) {
+                const V v = *reinterpret_cast<const V*>(uf + p0);
+                f[ok][oj][0] = v.x;
+                f[ok][oj][1] = v.y;
+            } else {
+                if (full || !even) f[ok][oj][0] = uf[p0];
+                if (full || even) f[ok][oj][1] = uf[p0 + 1];
+            }
+        }
+    T db[2][2], da[2][2];   // [dk][dj]: coarse d at columns I + 1 and I
+#pragma unroll
+    for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+        for (int dj = 0; dj < 2; ++dj) {
+            T v = T(0);
+            if (act) {
+                const long long q = lin(I + 1, J + dj, K + dk, nc);
+                v = add ? uc[q] - wc[q] : uc[q];
+            }
+            db[dk][dj] = v;
+        }
+#pragma unroll
+    for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+        for (int dj = 0; dj < 2; ++dj) {
+            T v = __shfl_up_sync(0xffffffffu, db[dk][dj], 1);
+            if (threadIdx.x == 0 && act) {
+                const long long q = lin(I, J + dj, K + dk, nc);
+                v = add ? uc[q] - wc[q] : uc[q];
+            }
+            da[dk][dj] = v;
+        }
     if (!act) return;
-    if (threadIdx.x == 0) a = line(I);
-    const long long p = lin(2 * I + 1, j, k, nf);
-    const T mid = (a + b) * T(0.5);
-    uf[p] = add ? uf[p] + mid : mid;
-    if (2 * I + 2 <= nf - 2) uf[p + 1] = add ? uf[p + 1] + b : b;
+#pragma unroll
+    for (int ok = 0; ok < 2; ++ok)
+#pragma unroll
+        for (int oj = 0; oj < 2; ++oj) {
+            const int j = 2 * J + oj, k = 2 * K + ok;
+            if (j < 1 || k < 1) continue;
+            const T w = T(1) / T(1 << (oj + ok));
+            T sa = T(0), sb = T(0);
+#pragma unroll
+            for (int dk = 0; dk <= ok; ++dk)
+#pragma unroll
+                for (int dj = 0; dj <= oj; ++dj) {
+                    sa += da[dk][dj];
+                    sb += db[dk][dj];
+                }
+            const T a = sa * w, b = sb * w;
+            const T mid = (a + b) * T(0.5);
+            long long p0;
+            bool full;
+            const bool even = pair_at(j, k, &p0, &full);
+            const T v0 = even ? a : mid, v1 = even ? mid : b;   // values at p0, p0 + 1
+            const T r0 = add ? f[ok][oj][0] + v0 : v0, r1 = add ? f[ok][oj][1] + v1 : v1;
+            if (full && vec) {
+                V v;
+                v.x = r0;
+                v.y = r1;
+                *reinterpret_cast<V*>(uf + p0) = v;
+            } else {
+                if (full || !even) uf[p0] = r0;
+                if (full || even) uf[p0 + 1] = r1;
+            }
+        }
 }
 
 template <typename T>
@@ -128,10 +219,11 @@ __global__ void __launch_bounds__(BX * BY) k_prolong(const T* __restrict__ uc, c
     prolong_block<T>(uc, wc, nc, uf, nf, add, blockIdx);
 }
 
+// One thread per coarse cell (I, J, K), I, J, K in [0, nc - 2].
 inline dim3 prolong_grid(int nf)
 {
     const int nc = (nf + 1) / 2;
-    return dim3((nc - 1 + BX - 1) / BX, (nf - 2 + BY - 1) / BY, nf - 2);
+    return dim3((nc - 1 + BX - 1) / BX, (nc - 1 + BY - 1) / BY, nc - 1);
 }
 
 // Cubic interpolation (Algorithm 2 step 4) as three 1-D passes, x then y
