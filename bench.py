@@ -575,6 +575,34 @@ def main():
     M.ma_smooth_correction(e, hi, lo, rhs, n, h, 0, scr, nb)
     b1.record(stream)
     torch.cuda.synchronize()
+    stream_sweeps_ms = e0.elapsed_time(e1) - b0.elapsed_time(b1)
+
+    def graph_ms(nsw, reps=5):
+        """Median time of one replay of a CUDA graph holding the call with nsw
+        sweeps: the form in which the solve runs its sweeps."""
+        cap = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(cap):
+            M.ma_smooth_correction(e, hi, lo, rhs, n, h, nsw, scr, nb)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            M.ma_smooth_correction(e, hi, lo, rhs, n, h, nsw, scr, nb)
+        torch.cuda.synchronize()
+        cs = torch.cuda.current_stream()
+        ts = []
+        for r in range(reps + 1):
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(cs)
+            g.replay()
+            g1.record(cs)
+            torch.cuda.synchronize()
+            if r:
+                ts.append(g0.elapsed_time(g1))
+        del g
+        return sorted(ts)[len(ts) // 2]
+
+    graph_sweeps = 8
+    graph_sweeps_ms = graph_ms(graph_sweeps) - graph_ms(0)
     # the variant in force at this size: by colour (8 launches per sweep, an
     # eighth of the points each), colour pairs (4 launches, a quarter each) or
     # by k parity (2 launches, half the points)
@@ -584,7 +612,10 @@ def main():
                    4: "k_smooth_corr_pair (FP32 correction smoother, colours c and c^7 in one launch)"}.get(
         corr_launches, f"k_smooth_corr_plane (FP32 correction smoother, {M.CORR_NAMES[corr_choice]}, one k-parity "
                        f"phase: four colours)")
-    corr_launch_ms = (e0.elapsed_time(e1) - b0.elapsed_time(b1)) / (corr_launches * sweeps)
+    # the roofline kernel's launch time as the solve runs it (graph replays);
+    # the stream-launched figure is reported beside it
+    corr_launch_ms = graph_sweeps_ms / (corr_launches * graph_sweeps)
+    corr_launch_ms_stream = stream_sweeps_ms / (corr_launches * sweeps)
     corr_gbs = CORR_SMOOTH_BYTES_PER_POINT * ((n - 2) ** 3 / corr_launches) / (corr_launch_ms / 1e3) / 1e9
     pts_launch = (n - 2) ** 3 / 8.0
     u_tmp = u64.clone()
@@ -703,7 +734,11 @@ def main():
                          "traffic": CORR_SMOOTH_TRAFFIC_257.get(corr_choice) if n == 257 else None,
                          "traffic_note": (f"ncu dram bytes per launch, warm L2; algorithmic 36 B x (n-2)^3/"
                                           f"{corr_launches} = {36 * (n - 2) ** 3 / corr_launches / 1e6:.0f} MB"),
-                         "launch_ms": corr_launch_ms, "bytes_per_point": CORR_SMOOTH_BYTES_PER_POINT,
+                         "launch_ms": corr_launch_ms,
+                         "launch_timing": f"CUDA events around replays of a CUDA graph of {graph_sweeps} sweeps "
+                                          f"(the form the solve runs), median of 5, minus the same graph with none",
+                         "launch_ms_stream_launched": corr_launch_ms_stream,
+                         "bytes_per_point": CORR_SMOOTH_BYTES_PER_POINT,
                          "peak_source": peak_src},
             "roofline_fp64_smoother": {"bound": "alu", "kernel": "k_smooth_colour (FP64 smoother, one colour phase)",
                                        "achieved": f64_gops, "peak": fp64_peak_gops, "unit": "GFP64op/s",

@@ -435,10 +435,10 @@ enum {
     MA_CORR_PAIRS = 5
 };
 
-/* Sets the choice for grid size n (-1 restores the built-in default: plane
- * tiles of 16 up to n = 33, colour pairs above; the residual by columns).
- * The shared per-level batch (ma_create_batch) sweeps each grid with the
- * colour order of its size's choice, as a solo solve does.  MA_ERR_INVALID_ARG if n is not odd in [3, 4097] or a choice
+/* Sets the choice for grid size n (-1 restores the built-in default: colour
+ * pairs at every size; the residual by columns).  The shared per-level batch
+ * (ma_create_batch) and the fused tails (ma_set_corr_tail) sweep each grid
+ * with the colour order of its size's choice, as a level-by-level cycle does.  MA_ERR_INVALID_ARG if n is not odd in [3, 4097] or a choice
  * is out of range (the residual has no MA_CORR_BY_COLOUR or MA_CORR_PAIRS,
  * the smoother no MA_CORR_COLUMN). */
 ma_status ma_set_corr_tuning(int n, int smooth_choice, int residual_choice);
@@ -466,13 +466,14 @@ ma_status ma_set_corr_tail(int max_n);
 ma_status ma_set_vcycle_tail(int max_n);
 
 /* Autotuner: times every smoother variant (reps pairs of sweeps each) and
- * every residual variant on the caller's data of one grid (the arguments of
- * ma_smooth_correction; e is overwritten by the sweeps), records the fastest
- * of each for grid size n, and writes the mean times in microseconds per
+ * every residual variant (reps each) on the caller's data of one grid (the
+ * arguments of ma_smooth_correction; e is overwritten by the sweeps), the way
+ * hierarchies run them: each variant's launches are captured into a CUDA
+ * graph and replayed, the fastest of 3 replays counting.  It records the
+ * fastest of each for grid size n and writes the times in microseconds per
  * sweep (us_smooth[6], indexed by MA_CORR_*, entry 4 unused) and per residual
  * (us_residual[5], indexed by MA_CORR_*, entry 0 unused) when those are not
- * null.  Blocks on
- * the stream. */
+ * null.  Blocks on the stream. */
 ma_status ma_tune_corr(float *e_dev, const float *u_hi_dev, const float *u_lo_dev, const float *rhs_dev, int n,
                        double h, int reps, void *scratch_dev, size_t scratch_bytes, double *us_smooth,
                        double *us_residual, ma_stream_t stream);

@@ -1029,6 +1029,7 @@ constexpr int TT = 1024;
 
 struct TailLevel {
     int n;
+    int pairs;           // sweep order: colour pairs (c, c^7) in the order 0, 7, 1, 6, 2, 5, 3, 4, else ascending
     float inv_h2, h2half;
     float* e;            // global iterate (read on the top level, written back there)
     const float* b;      // global colour-major B store
@@ -1052,33 +1053,64 @@ struct TailSmem {
     float *e, *w, *r, *b, *rhs;
 };
 
-__device__ __forceinline__ void tail_smooth(const TailSmem& S, int n, float inv_h2, float h2half, int nsw,
+// nsw sweeps of one tail level in shared memory, in the order the level's
+// own sweep uses (its corr_smooth_choice, recorded in TailLevel::pairs), so
+// that the tail and the level-by-level cycle give the same bits under any
+// tuning.  Pairs: colours c and c^7 in one phase (independent: the stencil
+// of a colour-c point holds every colour but c^7), phases (0, 7), (1, 6),
+// (2, 5), (3, 4), the colour-pair kernel's sweep; otherwise one colour a
+// phase in ascending order.  Each point runs the separate kernels'
+// arithmetic; a colour with no points takes no barrier.
+__device__ __forceinline__ void tail_smooth(const TailSmem& S, int n, float inv_h2, float h2half, int nsw, bool pairs,
                                             unsigned long long* ev)
 {
-    for (int sw = 0; sw < nsw; ++sw) {
+    int cnts[8], offs[8];
+    {
         int off = 0;
         for (int c = 0; c < 8; ++c) {
-            const int pi = c & 1, pj = (c >> 1) & 1, pk = (c >> 2) & 1;
-            const int ni = colour_count(n, pi), nj = colour_count(n, pj), nk = colour_count(n, pk);
-            const int cnt = (ni > 0 && nj > 0 && nk > 0) ? ni * nj * nk : 0;
-            for (int t = threadIdx.x; t < cnt; t += TT) {
-                const int i = (pi ? 1 : 2) + 2 * (t % ni);
-                const int j = (pj ? 1 : 2) + 2 * ((t / ni) % nj);
-                const int k = (pk ? 1 : 2) + 2 * (t / (ni * nj));
-                const int p = (k * n + j) * n + i;
-                const float* bp = S.b + 6 * off + t;
-                S3f B;
-                B.xx = bp[0]; B.yy = bp[cnt]; B.zz = bp[2 * cnt]; B.xy = bp[3 * cnt]; B.xz = bp[4 * cnt];
-                B.yz = bp[5 * cnt];
-                const float e0 = S.e[p];
-                const S3f K = corr_hess_sm(S.e, p, n, n * n, e0, inv_h2);
-                bool nonconvex = false;
-                const float z = corr_root(B, K, S.rhs[off + t], &nonconvex);
-                S.e[p] = fmaf(h2half, z, e0);
-                *ev += nonconvex ? 1ull : 0ull;
+            const int ni = colour_count(n, c & 1), nj = colour_count(n, (c >> 1) & 1),
+                      nk = colour_count(n, (c >> 2) & 1);
+            cnts[c] = (ni > 0 && nj > 0 && nk > 0) ? ni * nj * nk : 0;
+            offs[c] = off;
+            off += cnts[c];
+        }
+    }
+    auto point = [&](int c, int t) {
+        const int pi = c & 1, pj = (c >> 1) & 1, pk = (c >> 2) & 1;
+        const int ni = colour_count(n, pi), nj = colour_count(n, pj);
+        const int cnt = cnts[c], off = offs[c];
+        const int i = (pi ? 1 : 2) + 2 * (t % ni);
+        const int j = (pj ? 1 : 2) + 2 * ((t / ni) % nj);
+        const int k = (pk ? 1 : 2) + 2 * (t / (ni * nj));
+        const int p = (k * n + j) * n + i;
+        const float* bp = S.b + 6 * off + t;
+        S3f B;
+        B.xx = bp[0]; B.yy = bp[cnt]; B.zz = bp[2 * cnt]; B.xy = bp[3 * cnt]; B.xz = bp[4 * cnt];
+        B.yz = bp[5 * cnt];
+        const float e0 = S.e[p];
+        const S3f K = corr_hess_sm(S.e, p, n, n * n, e0, inv_h2);
+        bool nonconvex = false;
+        const float z = corr_root(B, K, S.rhs[off + t], &nonconvex);
+        S.e[p] = fmaf(h2half, z, e0);
+        *ev += nonconvex ? 1ull : 0ull;
+    };
+    for (int sw = 0; sw < nsw; ++sw) {
+        if (pairs) {
+            for (int c = 0; c < 4; ++c) {
+                const int d = c ^ 7, nc_ = cnts[c], tot = cnts[c] + cnts[d];
+                if (tot == 0) continue;
+                for (int t = threadIdx.x; t < tot; t += TT) {
+                    if (t < nc_) point(c, t);
+                    else point(d, t - nc_);
+                }
+                __syncthreads();
             }
-            off += cnt;
-            __syncthreads();
+        } else {
+            for (int c = 0; c < 8; ++c) {
+                if (cnts[c] == 0) continue;
+                for (int t = threadIdx.x; t < cnts[c]; t += TT) point(c, t);
+                __syncthreads();
+            }
         }
     }
 }
@@ -1146,7 +1178,7 @@ __device__ __forceinline__ void corr_tail_body(const TailArgs& A)
         const TailSmem& F = S[l];
         const TailSmem& C = S[l + 1];
         const int nf = A.lev[l].n, nc = A.lev[l + 1].n;
-        tail_smooth(F, nf, A.lev[l].inv_h2, A.lev[l].h2half, A.nu1, &ev);
+        tail_smooth(F, nf, A.lev[l].inv_h2, A.lev[l].h2half, A.nu1, A.lev[l].pairs != 0, &ev);
         // residual on the fine interior
         for (int q = threadIdx.x; q < (nf - 2) * (nf - 2) * (nf - 2); q += TT) {
             const int i = 1 + q % (nf - 2), j = 1 + (q / (nf - 2)) % (nf - 2), k = 1 + q / ((nf - 2) * (nf - 2));
@@ -1255,7 +1287,7 @@ __device__ __forceinline__ void corr_tail_body(const TailArgs& A)
             F.e[p] = F.e[p] + v;
         }
         __syncthreads();
-        tail_smooth(F, nf, A.lev[l].inv_h2, A.lev[l].h2half, A.nu2, &ev);
+        tail_smooth(F, nf, A.lev[l].inv_h2, A.lev[l].h2half, A.nu2, A.lev[l].pairs != 0, &ev);
     }
     const int m0 = A.lev[0].n * A.lev[0].n * A.lev[0].n;
     for (int q = threadIdx.x; q < m0; q += TT) A.lev[0].e[q] = S[0].e[q];
@@ -1429,7 +1461,11 @@ void tune_init()
 
 // Defaults before tuning: small grids are launch-latency bound, so the
 // plane-phase sweep (2 launches per sweep instead of 8) with small tiles.
-int default_smooth_choice(int n) { return n <= 33 ? CORR_PLANE16 : CORR_PAIRS; }
+// The colour-pair sweep at every size: timed inside CUDA graphs, the form in
+// which hierarchies run their cycles, it is the fastest variant from 9^3 to
+// 513^3 (a dependent launch costs ~1 us there, so its 4 launches a sweep
+// beat the plane tiles' 2 longer ones even on small grids).
+int default_smooth_choice(int) { return CORR_PAIRS; }
 int default_resid_choice(int) { return CORR_COLUMN; }   // the fastest residual at 33^3 .. 513^3 on GB300
 
 template <int PT>
@@ -1666,6 +1702,7 @@ cudaError_t launch_corr_vcycle_tail(const TailSpec* lv, int nlev, int nu1, int n
     for (int l = 0; l < nlev; ++l) {
         const double h = lv[l].h;
         A.lev[l].n = ns[l] = lv[l].n;
+        A.lev[l].pairs = corr_smooth_choice(lv[l].n) == CORR_PAIRS;
         A.lev[l].inv_h2 = (float)(1.0 / (h * h));
         A.lev[l].h2half = (float)(0.5 * h * h);
         A.lev[l].e = lv[l].e;
@@ -2270,6 +2307,7 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
                         const BatchLevel& V = I.lev[lt[b] + q];
                         ns[q] = V.n;
                         A.lev[q].n = V.n;
+                        A.lev[q].pairs = corr_smooth_choice(V.n) == CORR_PAIRS;
                         A.lev[q].inv_h2 = inv_h2(V.h);
                         A.lev[q].h2half = h2half(V.h);
                         A.lev[q].e = V.e;
