@@ -74,14 +74,6 @@ __device__ __forceinline__ S3f base_hess(const float* __restrict__ hi, const flo
         inv_h2);
 }
 
-// K = D^2_h e at the current centre value e0, e in global memory.
-__device__ __forceinline__ S3f corr_hess(const float* __restrict__ e, long long p, long long sy, long long sz,
-                                         float e0, float inv_h2)
-{
-    return hess_from_diff(
-        [&](int di, int dj, int dk) -> float { return __ldg(e + p + di + dj * sy + dk * sz) - e0; }, inv_h2);
-}
-
 // The FP32 products below are written as explicit fused multiply-adds in a
 // fixed order, so that every kernel that inlines them (by-colour and plane
 // sweeps, residuals, the fused tail) rounds identically: the compiler may
@@ -261,13 +253,18 @@ __host__ __device__ __forceinline__ int colour_count(int n, int parity) { return
 // iteration per solve, more than the sweeps saved.)
 // ---------------------------------------------------------------------------
 
-// Points of colours 0..c-1.
+// Points of colours 0..c-1.  With a, b the interior counts of even and odd
+// indices along an axis and S(p) = p ? b : a, colour q = (pi, pj, pk) holds
+// S(pi) S(pj) S(pk) points, and the colours before c = (pi, pj, pk) are those
+// with a smaller pk, then those with pk and a smaller pj, then (0, pj, pk)
+// when pi = 1:
+//     offset = pk (a + b)^2 a + pj (a + b) a S(pk) + pi a S(pj) S(pk),
+// the same integer as the sum over the boxes, without a loop.
 __host__ __device__ __forceinline__ long long cm_offset(int n, int c)
 {
-    long long off = 0;
-    for (int q = 0; q < c; ++q)
-        off += (long long)colour_count(n, q & 1) * colour_count(n, (q >> 1) & 1) * colour_count(n, (q >> 2) & 1);
-    return off;
+    const long long a = colour_count(n, 0), b = colour_count(n, 1);
+    const long long sj = (c & 2) ? b : a, sk = (c & 4) ? b : a;
+    return ((c & 4) ? (a + b) * (a + b) * a : 0) + ((c & 2) ? (a + b) * a * sk : 0) + ((c & 1) ? a * sj * sk : 0);
 }
 
 struct CmPos {
@@ -787,7 +784,12 @@ __global__ void __launch_bounds__(NT, plane_min_blocks(PT, NT))
 // blocks of 32 x 4 (four rows).
 constexpr int CW = 30;
 
-template <int NN = 0>
+// CRHS = false: the correction residual res = rhs - N(e), rhs colour-major,
+// res natural.  CRHS = true: the tau-corrected coarse right-hand side
+// out = N(w) + r with e = w, rhs_cm = r (natural layout) and res = out
+// (colour-major), the same stencil values and the same delta_det(B, K) + r as
+// one thread per point forms them.
+template <int NN = 0, bool CRHS = false>
 __device__ __forceinline__ void residual_corr_col_block(const float* __restrict__ e, const float* __restrict__ bstore,
                                                         const float* __restrict__ rhs_cm, float* __restrict__ res,
                                                         int n_rt, float inv_h2, int kc, uint3 bid)
@@ -820,7 +822,7 @@ __device__ __forceinline__ void residual_corr_col_block(const float* __restrict_
         const long long w = (long long)((k - (pk ? 1 : 2)) >> 1) * plane + rowoff;
         const long long off = pk ? off1 : off0;
         *B = load_b(bstore + 6 * off + w, pk ? cnt1 : cnt0);
-        *rr = __ldcs(rhs_cm + off + w);
+        *rr = CRHS ? __ldcs(rhs_cm + (((long long)k * n + j) * n + i)) : __ldcs(rhs_cm + off + w);
     };
     float Cm = ld(k0 - 1, 0), Nm = ld(k0 - 1, sy), Sm = ld(k0 - 1, -sy);
     float Cc = ld(k0, 0), Nc = ld(k0, sy), Sc = ld(k0, -sy);
@@ -863,7 +865,13 @@ __device__ __forceinline__ void residual_corr_col_block(const float* __restrict_
                     return v - e0;
                 },
                 inv_h2);
-            res[((long long)k * n + j) * n + i] = rk - delta_det(Bk, K);
+            if constexpr (CRHS) {
+                const int pk = k & 1;
+                const long long w = (long long)((k - (pk ? 1 : 2)) >> 1) * plane + rowoff;
+                res[(pk ? off1 : off0) + w] = delta_det(Bk, K) + rk;
+            } else {
+                res[((long long)k * n + j) * n + i] = rk - delta_det(Bk, K);
+            }
         }
         Cm = Cc; Nm = Nc; Sm = Sc; Cm_e = Cc_e; Cm_w = Cc_w;
         Cc = Cp; Nc = Np; Sc = Sp; Cc_e = Cp_e; Cc_w = Cp_w;
@@ -903,6 +911,25 @@ __global__ void k_zero_shell(float* v, int n)
 }
 
 // rhs_H = N_H(w_H) + res_H on the coarse interior, written colour-major.
+// The tau-corrected coarse right-hand side of the correction problem,
+// rhs_H = N_H(w_H) + I r_h (Algorithm 1 step 4; N(w) = det(B + D^2_h w) -
+// det(B)), colour-major.  From 129^3 up by columns as the correction residual
+// walks them (k_coarse_rhs_corr_col: 3 loads of w a point); below, where the
+// level is latency-bound and a column of 8 points a thread would cut the
+// parallelism 8-fold, one point a thread (k_coarse_rhs_corr).  The same
+// values either way.
+constexpr int kCoarseRhsColMin = 129;
+
+template <int NN = 0>
+__global__ void __launch_bounds__(BX * BY, 6) k_coarse_rhs_corr_col(const float* __restrict__ w,
+                                                                    const float* __restrict__ bstore,
+                                                                    const float* __restrict__ resc,
+                                                                    float* __restrict__ rhs_cm, int n, float inv_h2,
+                                                                    int kc)
+{
+    residual_corr_col_block<NN, true>(w, bstore, resc, rhs_cm, n, inv_h2, kc, blockIdx);
+}
+
 __device__ __forceinline__ void coarse_rhs_corr_block(const float* __restrict__ w, const float* __restrict__ bstore,
                                                       const float* __restrict__ resc, float* __restrict__ rhs_cm,
                                                       int n, float inv_h2, uint3 bid)
@@ -915,7 +942,9 @@ __device__ __forceinline__ void coarse_rhs_corr_block(const float* __restrict__ 
     const long long sy = n, sz = (long long)n * n;
     const CmPos c = cm_pos(i, j, k, n);
     const S3f B = load_b(bstore + 6 * c.off + c.idx, c.cnt);
-    const S3f K = corr_hess(w, p, sy, sz, w[p], inv_h2);
+    const float e0 = w[p];
+    const S3f K = hess_from_diff(
+        [&](int di, int dj, int dk) -> float { return __ldg(w + p + di + dj * sy + dk * sz) - e0; }, inv_h2);
     rhs_cm[c.off + c.idx] = delta_det(B, K) + resc[p];
 }
 
@@ -1317,19 +1346,6 @@ struct CmF32Out {
     float* r;
     float* b;        // colour-major B store of the level
     float inv_4h2;   // 1 / (4 h^2)
-    __device__ __forceinline__ void put(long long, int i, int j, int k, int n, double, float v32,
-                                        const HessS& H4) const
-    {
-        const CmPos c = cm_pos(i, j, k, n);
-        r[c.off + c.idx] = v32;
-        float* q = b + 6 * c.off + c.idx;
-        q[0] = d2f_trunc(H4.A) * inv_4h2;
-        q[c.cnt] = d2f_trunc(H4.B) * inv_4h2;
-        q[2 * c.cnt] = d2f_trunc(H4.C) * inv_4h2;
-        q[3 * c.cnt] = d2f_trunc(H4.R) * inv_4h2;
-        q[4 * c.cnt] = d2f_trunc(H4.S) * inv_4h2;
-        q[5 * c.cnt] = d2f_trunc(H4.T) * inv_4h2;
-    }
     // the residual without FP64 arithmetic (resid::residual_f2_block)
     __device__ __forceinline__ void put2(long long, int i, int j, int k, int n, const resid::ResF2& v) const
     {
@@ -1631,9 +1647,23 @@ cudaError_t launch_zero_shell_f32(float* v, int n, cudaStream_t s)
 cudaError_t launch_coarse_rhs_corr(const float* w, const void* bstore, const float* resc, float* rhs_cm, int nc,
                                    double H, cudaStream_t s)
 {
+    if (nc < 3) return cudaSuccess;
+    const float* b = (const float*)bstore;
+    const float inv_h2 = (float)(1.0 / (H * H));
+    const dim3 blk(BX, BY);
     count_launches(1);
-    k_coarse_rhs_corr<<<grid_of(nc), dim3(BX, BY), 0, s>>>(w, (const float*)bstore, resc, rhs_cm, nc,
-                                                           (float)(1.0 / (H * H)));
+    if (nc < kCoarseRhsColMin) {
+        k_coarse_rhs_corr<<<grid_of(nc), blk, 0, s>>>(w, b, resc, rhs_cm, nc, inv_h2);
+        return cudaGetLastError();
+    }
+    const int kc = col_chunk(nc);
+    const dim3 g = col_grid(nc, kc);
+    switch (nc) {
+    case 129: k_coarse_rhs_corr_col<129><<<g, blk, 0, s>>>(w, b, resc, rhs_cm, nc, inv_h2, kc); break;
+    case 257: k_coarse_rhs_corr_col<257><<<g, blk, 0, s>>>(w, b, resc, rhs_cm, nc, inv_h2, kc); break;
+    case 513: k_coarse_rhs_corr_col<513><<<g, blk, 0, s>>>(w, b, resc, rhs_cm, nc, inv_h2, kc); break;
+    default: k_coarse_rhs_corr_col<0><<<g, blk, 0, s>>>(w, b, resc, rhs_cm, nc, inv_h2, kc); break;
+    }
     return cudaGetLastError();
 }
 
@@ -1939,10 +1969,12 @@ struct OpRestrict {
     }
 };
 
+// kc > 0: by columns (kc planes a thread, col_grid); kc = 0: one point a
+// thread (grid_of), the forms and sizes of launch_coarse_rhs_corr.
 struct OpCoarseRhs {
-    static constexpr int NT = BX * BY, MINB = 1;
+    static constexpr int NT = BX * BY, MINB = 6;
     struct Job {
-        int inst, n, gx, gy;
+        int inst, n, kc, gx, gy;
         float inv_h2;
         const float* w;
         const float* b;
@@ -1951,7 +1983,11 @@ struct OpCoarseRhs {
     };
     static __device__ __forceinline__ void run(const Job& J, int q)
     {
-        coarse_rhs_corr_block(J.w, J.b, J.resc, J.rhs, J.n, J.inv_h2, split_block(q, J.gx, J.gy));
+        if (J.kc > 0)
+            residual_corr_col_block<0, true>(J.w, J.b, J.resc, J.rhs, J.n, J.inv_h2, J.kc,
+                                             split_block(q, J.gx, J.gy));
+        else
+            coarse_rhs_corr_block(J.w, J.b, J.resc, J.rhs, J.n, J.inv_h2, split_block(q, J.gx, J.gy));
     }
 };
 
@@ -2280,10 +2316,12 @@ void build_sequence(TableBuilder& T, const BatchInstance* in, int count, const B
                                   C.res32};
                 sj.push_back(s);
                 sb.push_back((int)(gc.x * gc.y * gc.z));
-                OpCoarseRhs::Job q{in[b].id, C.n, (int)gc.x, (int)gc.y, inv_h2(C.h), C.w32, (const float*)C.bstore,
-                                   C.res32, C.rhs32};
+                const int kcc = C.n >= kCoarseRhsColMin ? col_chunk(C.n) : 0;
+                const dim3 gq = kcc > 0 ? col_grid(C.n, kcc) : batch_grid2(C.n);
+                OpCoarseRhs::Job q{in[b].id, C.n, kcc, (int)gq.x, (int)gq.y, inv_h2(C.h), C.w32,
+                                   (const float*)C.bstore, C.res32, C.rhs32};
                 cj.push_back(q);
-                cb.push_back((int)(gc.x * gc.y * gc.z));
+                cb.push_back((int)(gq.x * gq.y * gq.z));
             }
             T.emit(B_CRESID, rj, rb, 0);   // the residual by columns: the fastest form at every size
             T.emit(B_RESTRICT, sj, sb, 0);
