@@ -882,7 +882,7 @@ __device__ __forceinline__ void residual_corr_col_block(const float* __restrict_
 }
 
 template <int NN = 0>
-__global__ void __launch_bounds__(BX * BY, 6) k_residual_corr_col(const float* __restrict__ e,
+__global__ void __launch_bounds__(BX * BY, 8) k_residual_corr_col(const float* __restrict__ e,
                                                                   const float* __restrict__ bstore,
                                                                   const float* __restrict__ rhs_cm,
                                                                   float* __restrict__ res, int n, float inv_h2,
@@ -892,7 +892,9 @@ __global__ void __launch_bounds__(BX * BY, 6) k_residual_corr_col(const float* _
 }
 
 // Planes per column run, and the grid of the column residual.
-__host__ __device__ inline int col_chunk(int n) { return n >= 129 ? 16 : 8; }
+// (8 planes up to 129^3, 16 from 257^3: measured, 21.1 against 24.6 us at 129^3 and
+// 147.3 against 150.4 us at 257^3 under graph replay)
+__host__ __device__ inline int col_chunk(int n) { return n >= 257 ? 16 : 8; }
 inline dim3 col_grid(int n, int kc) { return dim3((n - 2 + CW - 1) / CW, (n - 2 + 3) / 4, (n - 2 + kc - 1) / kc); }
 
 // The shell of res (faces of the cube) is 0.
@@ -921,7 +923,7 @@ __global__ void k_zero_shell(float* v, int n)
 constexpr int kCoarseRhsColMin = 129;
 
 template <int NN = 0>
-__global__ void __launch_bounds__(BX * BY, 6) k_coarse_rhs_corr_col(const float* __restrict__ w,
+__global__ void __launch_bounds__(BX * BY, 8) k_coarse_rhs_corr_col(const float* __restrict__ w,
                                                                     const float* __restrict__ bstore,
                                                                     const float* __restrict__ resc,
                                                                     float* __restrict__ rhs_cm, int n, float inv_h2,
@@ -1937,7 +1939,7 @@ struct OpPlaneSmooth {
 };
 
 struct OpColResid {
-    static constexpr int NT = BX * BY, MINB = 6;
+    static constexpr int NT = BX * BY, MINB = 6;   // 8 spills with the job lookup
     struct Job {
         int inst, n, kc, gx, gy;
         float inv_h2;
