@@ -340,6 +340,43 @@ def test_colour_pair_sweep_equals_its_colour_sequence_on_slow_points(n):
     assert not np.array_equal(got[0], e)
 
 
+@pytest.mark.parametrize("n", [129, 257])
+def test_colour_pair_sweep_on_an_unaligned_correction_grid_gives_the_same_bits(n):
+    """At 129^3 and up the colour-pair kernel is compiled for the grid size and
+    reads the neighbour pairs its colour aligns as 8-byte loads; an e that is
+    not 8-byte aligned goes to the generic kernel (4-byte loads, the size at
+    run time).  Both run the same arithmetic: e and the count of nonconvex
+    points must agree bit for bit."""
+    pr = P.make("exp", n, seed=3)
+    rng = np.random.default_rng(7 * n)
+    e = np.zeros(pr.u.shape, dtype=np.float32)
+    e[1:-1, 1:-1, 1:-1] = (0.5 * pr.h ** 2 * rng.standard_normal((n - 2,) * 3)).astype(np.float32)
+    rhs = (1e-3 * rng.standard_normal(pr.u.shape) * pr.f).astype(np.float32)
+    pick = rng.random(pr.u.shape) < 0.02
+    rhs[pick] = (-2.0 * pr.f[pick]).astype(np.float32)
+    rhs[0], rhs[-1], rhs[:, 0], rhs[:, -1], rhs[:, :, 0], rhs[:, :, -1] = 0, 0, 0, 0, 0, 0
+    hi, lo = (dev(a) for a in split(pr.u))
+    rhs_d = dev(rhs)
+    _keep, scr, nb = M.correction_scratch(n)
+    m = n ** 3
+    outs = []
+    try:
+        M.ma_set_corr_tuning(n, M.MA_CORR_PAIRS, -1)
+        for offset in (0, 1):
+            store = torch.zeros(m + 2, dtype=torch.float32, device="cuda")
+            ed = store[offset:offset + m].view(n, n, n)
+            ed.copy_(dev(e))
+            assert (ed.data_ptr() % 8 == 0) == (offset == 0)
+            ev = torch.zeros(1, dtype=torch.int64, device="cuda")
+            M.ma_smooth_correction(ed, hi, lo, rhs_d, n, pr.h, 2, scr, nb, events=ev)
+            outs.append((host(ed), int(ev.item())))
+    finally:
+        M.ma_set_corr_tuning(n, -1, -1)
+    assert outs[0][1] == outs[1][1] and outs[0][1] > 0
+    assert np.array_equal(outs[0][0], outs[1][0], equal_nan=True)
+    assert not np.array_equal(outs[0][0], e)
+
+
 @pytest.mark.parametrize("n", [129, 71, 33, 257, 9])
 @pytest.mark.parametrize("choice", [1, 2, 3, 4])
 def test_residual_tiles_agree(choice, n):

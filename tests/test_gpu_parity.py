@@ -235,6 +235,35 @@ def test_prolong_interpolate_coarse_rhs_match_oracle(nc):
     np.testing.assert_allclose(host(b), O.coarse_rhs(w, r, H), rtol=0, atol=_residual_bound(w, H, "cosine"))
 
 
+@pytest.mark.parametrize("nc", [5, 13, 65])
+def test_prolongation_on_a_buffer_not_aligned_to_pairs_gives_the_same_bits(nc):
+    """The prolongation moves each fine row's two points as one aligned
+    2-element access where the fine array allows it and as scalars otherwise:
+    a fine array that starts one element (8 bytes) past a 16-byte boundary
+    takes the scalar path and must give the same bits, in both modes."""
+    nf = 2 * nc - 1
+    rng = np.random.default_rng(100 + nc)
+    uc = dev(rng.standard_normal((nc, nc, nc)))
+    wc = dev(rng.standard_normal((nc, nc, nc)))
+    uf0 = rng.standard_normal((nf, nf, nf))
+    m = nf ** 3
+    for mode in ("add", "interpolate"):
+        aligned = dev(uf0).reshape(-1).clone()
+        store = torch.zeros(m + 2, dtype=torch.float64, device="cuda")
+        shifted = store[1:1 + m]
+        shifted.copy_(aligned)
+        assert shifted.data_ptr() % 16 == 8 and aligned.data_ptr() % 16 == 0
+        if mode == "add":
+            M.ma_prolong_add(uc, wc, nc, aligned)
+            M.ma_prolong_add(uc, wc, nc, shifted)
+        else:
+            M.ma_interpolate(uc, nc, aligned)
+            M.ma_interpolate(uc, nc, shifted)
+        torch.cuda.synchronize()
+        assert torch.equal(aligned, shifted), mode
+        assert store[0].item() == 0.0 and store[-1].item() == 0.0   # nothing written outside
+
+
 @pytest.mark.parametrize("n,sweeps", [(5, 0), (9, 0), (5, 1), (3, 1), (17, 3)])
 def test_coarsest_solve_matches_oracle(n, sweeps):
     pr = P.make("exp", n)
