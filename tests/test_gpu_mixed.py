@@ -452,6 +452,43 @@ def test_mixed_and_fp64_agree_at_257():
     assert np.max(np.abs(r)) <= 1.5e-10 * np.max(np.abs(pr.f[1:-1, 1:-1, 1:-1]))
 
 
+@pytest.mark.parametrize("choice", [M.MA_CORR_BY_COLOUR, M.MA_CORR_PLANE16])
+def test_fused_tail_follows_each_levels_tuned_sweep_order(choice):
+    """The fused correction tail sweeps each of its levels in the order that
+    level's own sweep uses (colour pairs by default, ascending for the
+    by-colour and plane variants).  With the tail levels tuned to an
+    ascending variant, the tail must still give the bits, cycle count and
+    residual of the level-by-level cycle, and those must differ from the
+    colour-pair default (the order matters)."""
+    n = 33
+    pr = P.make("exp", n)
+    runs = {}
+    try:
+        for tuned in (False, True):
+            for sz in (5, 9, 17):
+                M.ma_set_corr_tuning(sz, choice if tuned else -1, -1)
+            outs = []
+            for max_n in (17, 9, 0):
+                M.ma_set_corr_tail(max_n)
+                H = M.Hierarchy(M.make_desc(n, length=pr.length, precision=M.MA_MIXED))
+                H.set_rhs_bc(dev(pr.f), dev(pr.initial()))
+                r = H.solve(tol=1e-10, max_cycles=40, raise_on_error=False)
+                u = torch.empty_like(dev(pr.f))
+                H.get_solution(u)
+                outs.append((host(u), r.cycles, r.res))
+                H.close()
+            runs[tuned] = outs
+    finally:
+        M.ma_set_corr_tail(True)
+        for sz in (5, 9, 17):
+            M.ma_set_corr_tuning(sz, -1, -1)
+    for outs in runs.values():
+        for u, cycles, res in outs[:-1]:
+            assert cycles == outs[-1][1] and res == outs[-1][2]
+            assert np.array_equal(u, outs[-1][0])
+    assert not np.array_equal(runs[True][-1][0], runs[False][-1][0])
+
+
 @pytest.mark.parametrize("precision", [M.MA_MIXED, M.MA_FP32])
 @pytest.mark.parametrize("name,n,coarsest", [("exp", 65, 3), ("cosine", 17, 3), ("exp", 33, 5), ("sine", 129, 3)])
 def test_fused_tail_cycle_is_bitwise_the_level_by_level_cycle(name, n, coarsest, precision):
