@@ -272,7 +272,7 @@ def bench_fp32_mode(args, M, problems, dev):
     against the FP64 discrete solution (the round-off floor per N)."""
     import torch
     stream = torch.cuda.current_stream(dev)
-    out = {"mode": "FP32 FAS cycles on the solution, stop at the FP32 residual floor (3 stagnant cycles)"}
+    out = {"mode": "FP32 FAS cycles on the solution, stop at the FP32 residual floor (2 stagnant cycles)"}
     for n in (129, 257):
         f, g, length = problems.make_on_device("exp", n, device=dev)
         u_ex = torch.from_numpy(problems.make("exp", n).u).to(dev)

@@ -158,7 +158,7 @@ ma_status ma_vcycle(ma_hierarchy *h, int ncycles);
 
 /* Solve to tolerance: the chosen initial iterate, then V-cycles until the
  * stopping rule holds (MA_OK), max_cycles is reached, or the residual
- * stagnates above tol (three cycles in a row each reducing it by less than
+ * stagnates above tol (two cycles in a row each reducing it by less than
  * 20 %: the round-off floor; result->floor_reached = 1).  Both of the latter
  * return MA_ERR_NOT_CONVERGED; a NaN/Inf residual returns MA_ERR_NONFINITE.
  * Blocks on the stream (one small read-back per cycle); result is filled in

@@ -705,7 +705,8 @@ ma_status ma2d_solve(ma2d_hierarchy* H, const ma_solve_opts* o, ma_solve_result*
     int stagnant = 0;
     // the max norm folds with fmax, which skips NaN entries; the L2 norm's
     // sum of squares does not, so both are checked
-    while (std::isfinite(rel) && std::isfinite(l2) && rel > o->tol && res->cycles < o->max_cycles && stagnant < 3) {
+    while (std::isfinite(rel) && std::isfinite(l2) && rel > o->tol && res->cycles < o->max_cycles &&
+           stagnant < ma::kFloorStagnantCycles) {
         CK2(vcycle2_from(H, 0));
         res->cycles += 1;
         if ((st = fine_norms2(H, 0, &mx, &l2)) != MA_OK) return st;
@@ -718,7 +719,7 @@ ma_status ma2d_solve(ma2d_hierarchy* H, const ma_solve_opts* o, ma_solve_result*
     else if (rel <= o->tol) res->status = MA_OK;
     else {
         res->status = MA_ERR_NOT_CONVERGED;
-        res->floor_reached = stagnant >= 3;
+        res->floor_reached = stagnant >= ma::kFloorStagnantCycles;
     }
     if (res->status == MA_ERR_NONFINITE) return fail2(MA_ERR_NONFINITE, "residual became non-finite");
     if (res->status == MA_ERR_NOT_CONVERGED)

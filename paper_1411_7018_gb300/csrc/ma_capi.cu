@@ -798,7 +798,7 @@ static bool absorb_norms(ma_hierarchy* H)
     } else {
         const double nrel = resn / H->sv.scale;
         r.cycles += 1;
-        // three cycles in a row that barely reduce the residual: round-off floor
+        // cycles in a row that barely reduce the residual: round-off floor
         H->sv.stagnant = (nrel > 0.8 * H->sv.rel) ? H->sv.stagnant + 1 : 0;
         H->sv.rel = nrel;
     }
@@ -810,7 +810,7 @@ static bool absorb_norms(ma_hierarchy* H)
     if (!finite) out = MA_ERR_NONFINITE;
     else if (rel <= o.tol) out = MA_OK;
     else if (r.cycles >= o.max_cycles) out = MA_ERR_NOT_CONVERGED;
-    else if (H->sv.stagnant >= 3) {
+    else if (H->sv.stagnant >= ma::kFloorStagnantCycles) {
         r.floor_reached = 1;
         out = MA_ERR_NOT_CONVERGED;
     }

@@ -86,6 +86,12 @@ constexpr int CORR_PAIRS = 5;    // smoother only: colours c and c^7 per launch
 // FP32 correction V-cycles of each FMG level below the finest in a mixed solve
 // (the FP64 V-cycle of Algorithm 2 step 5 there); solo and batched starts alike.
 constexpr int kFmgCorrCycles = 2;
+// Round-off floor of the stopping rule: this many cycles in a row that each
+// cut the residual by less than 20 % end a solve as "floor reached".  Two:
+// on every floor-limited solve measured (513^3 mixed and FP64, 257^3 FP64,
+// the FP32 mode) a third such cycle left the error against the exact
+// solution unchanged to seven digits.
+constexpr int kFloorStagnantCycles = 2;
 int corr_smooth_choice(int n);
 int corr_resid_choice(int n);
 bool set_corr_tuning(int n, int smooth, int resid);   // -1: built-in default; false unless n is odd in [3, 4097]
